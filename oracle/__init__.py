@@ -1,0 +1,219 @@
+"""Plain FP64 CPU oracle for the DEM hot path (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+``cpu_baseline`` / ``--impl reference`` legs may import this package.  The
+product path (``paper_1705_03850_gb300``) never imports it, and it imports
+nothing from the product path.
+
+The arithmetic lives in ``dem_oracle.c`` (plain C, double precision), compiled
+here with gcc into ``oracle/_build/liboracle.so`` and called through ctypes.
+What it follows, by section and equation of Queteschiner et al. (2017):
+
+* Sec. 2.1, Eqs. 1-2: Newton's equations for translation and rotation,
+  advanced by velocity Verlet (the paper names no integrator).
+* Eqs. 3-4: damped normal and tangential spring-dashpot forces, with the
+  tangential overlap carried over a contact's life.
+* Eq. 5: Coulomb truncation of the tangential overlap, |f_t| <= mu |f_n|.
+* Eq. 6: non-linear damped Hertz coefficients and beta(e).
+* Sec. 2.2: coarse-grain scaling (r -> alpha r with rho, e, E, mu kept).
+
+Pins (tests/test_oracle_*.py) tie it to closed forms and invariants rather
+than to itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dem_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+NPARAM = 24
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C source with gcc (plain -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    i64 = ctypes.c_int64
+    lib.orc_beta.restype = ctypes.c_double
+    lib.orc_beta.argtypes = [ctypes.c_double]
+    lib.orc_pair_coeffs.restype = None
+    lib.orc_pair_coeffs.argtypes = [dp] + [ctypes.c_double] * 5 + [ctypes.c_int32, dp]
+    for fn in (lib.orc_pairs_brute, lib.orc_pairs_cells):
+        fn.restype = i64
+        fn.argtypes = [dp, i64, dp, dp, ctypes.c_double, i64, i64p, i64p]
+    lib.orc_eval.restype = i64
+    lib.orc_eval.argtypes = [dp, i64, dp, dp, dp, dp, dp, i64p, i64, i64p, i64p, dp,
+                             ctypes.c_double, ctypes.c_int32, dp, dp, i64, i64p, i64p, dp,
+                             i32p, dp]
+    lib.orc_run.restype = ctypes.c_int32
+    lib.orc_run.argtypes = [dp, i64, dp, dp, dp, dp, dp, i64p, i64p, i64, i64p, i64p, dp,
+                            i32p, dp, dp, i64, ctypes.c_int32, ctypes.c_int32]
+    _lib = lib
+    return lib
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i64(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _i32(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def make_params(*, E, nu, e, mu, dt, g=(0.0, 0.0, 0.0), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
+                periodic=(False, False, False), mu_wall=None, floor=False, floor_z=0.0,
+                floor_v=(0.0, 0.0, 0.0), clamp_fn=False) -> np.ndarray:
+    """The oracle's flat parameter block (layout documented in dem_oracle.c)."""
+    P = np.zeros(NPARAM, dtype=np.float64)
+    P[0], P[1], P[2], P[3] = E, nu, e, mu
+    P[4] = mu if mu_wall is None else mu_wall
+    P[5] = dt
+    P[6:9] = g
+    P[9:12] = lo
+    P[12:15] = hi
+    P[15:18] = [1.0 if p else 0.0 for p in periodic]
+    P[18] = 1.0 if floor else 0.0
+    P[19] = floor_z
+    P[20:23] = floor_v
+    P[23] = 1.0 if clamp_fn else 0.0
+    return P
+
+
+def beta(e: float) -> float:
+    """beta(e) = ln e / sqrt(ln^2 e + pi^2) (Eq. 6)."""
+    return _load().orc_beta(float(e))
+
+
+def pair_coeffs(P, ri, rj, mi, mj, delta, wall=False) -> dict:
+    """E_eff, G_eff, R_eff, m_eff, k_n, gamma_n, k_t, gamma_t of one contact (Eq. 6)."""
+    out = np.zeros(8)
+    _load().orc_pair_coeffs(_d(np.ascontiguousarray(P, dtype=np.float64)), ri, rj, mi, mj,
+                            delta, 1 if wall else 0, _d(out))
+    keys = ["Eeff", "Geff", "Reff", "meff", "kn", "gn", "kt", "gt"]
+    return dict(zip(keys, out.tolist()))
+
+
+def pairs(P, x, r, extra=0.0, method="cells") -> np.ndarray:
+    """Index pairs (i < j) with |x_ij| < r_i + r_j + extra, sorted; shape (n, 2)."""
+    lib = _load()
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    fn = lib.orc_pairs_brute if method == "brute" else lib.orc_pairs_cells
+    cap = max(16, 8 * len(r))
+    while True:
+        pi = np.zeros(cap, dtype=np.int64)
+        pj = np.zeros(cap, dtype=np.int64)
+        cnt = fn(_d(P), len(r), _d(x), _d(r), float(extra), cap, _i64(pi), _i64(pj))
+        if cnt <= cap:
+            return np.stack([pi[:cnt], pj[:cnt]], axis=1)
+        cap = int(cnt)
+
+
+class Sim:
+    """A DEM system advanced by the oracle (all arrays float64 / int64, SI units).
+
+    State at an integer step n: x, v, w (angular velocity), and -- once
+    evaluated -- F, T and the contact history (one record per contact, keyed by
+    the particle IDs (a < b), or (a, -1) for the floor).
+    """
+
+    def __init__(self, P, x, v, w, r, m, ids=None, use_cells=True):
+        self.P = np.ascontiguousarray(P, dtype=np.float64)
+        self.x = np.array(x, dtype=np.float64).reshape(-1, 3)
+        n = self.x.shape[0]
+        self.v = np.array(v, dtype=np.float64).reshape(n, 3)
+        self.w = np.array(w, dtype=np.float64).reshape(n, 3)
+        self.r = np.array(r, dtype=np.float64).reshape(n)
+        self.m = np.array(m, dtype=np.float64).reshape(n)
+        self.id = (np.arange(n, dtype=np.int64) if ids is None
+                   else np.array(ids, dtype=np.int64).reshape(n))
+        self.use_cells = 1 if use_cells else 0
+        self.cap = max(64, 16 * n)
+        self.ha = np.zeros(self.cap, dtype=np.int64)
+        self.hb = np.zeros(self.cap, dtype=np.int64)
+        self.hxi = np.zeros((self.cap, 3), dtype=np.float64)
+        self.slip = np.zeros(self.cap, dtype=np.int32)
+        self.nh = np.zeros(1, dtype=np.int64)
+        self.F = np.zeros((n, 3))
+        self.T = np.zeros((n, 3))
+        self.primed = 0
+
+    @property
+    def n(self):
+        return self.x.shape[0]
+
+    def set_history(self, a, b, xi):
+        """Replace the stored history by records (a, b, xi); sorted here."""
+        a = np.asarray(a, dtype=np.int64)
+        b = np.asarray(b, dtype=np.int64)
+        order = np.lexsort((b, a))
+        k = len(a)
+        self.ha[:k] = a[order]
+        self.hb[:k] = b[order]
+        self.hxi[:k] = np.asarray(xi, dtype=np.float64).reshape(-1, 3)[order]
+        self.nh[0] = k
+
+    def history(self):
+        k = int(self.nh[0])
+        return self.ha[:k].copy(), self.hb[:k].copy(), self.hxi[:k].copy(), self.slip[:k].copy()
+
+    def evaluate(self, dt_hist=0.0):
+        """Forces at the current state without changing it.
+
+        Returns (F, T, (a, b, xi, slip), fabs) where fabs[i] = sum_j |F_ij| + |m_i g|.
+        """
+        lib = _load()
+        n = self.n
+        F = np.zeros((n, 3))
+        T = np.zeros((n, 3))
+        fabs = np.zeros(n)
+        ha = np.zeros(self.cap, dtype=np.int64)
+        hb = np.zeros(self.cap, dtype=np.int64)
+        hxi = np.zeros((self.cap, 3))
+        slip = np.zeros(self.cap, dtype=np.int32)
+        c = lib.orc_eval(_d(self.P), n, _d(self.x), _d(self.v), _d(self.w), _d(self.r), _d(self.m),
+                         _i64(self.id), int(self.nh[0]), _i64(self.ha), _i64(self.hb), _d(self.hxi),
+                         float(dt_hist), self.use_cells, _d(F), _d(T), self.cap, _i64(ha), _i64(hb),
+                         _d(hxi), _i32(slip), _d(fabs))
+        if c < 0:
+            raise RuntimeError("oracle history capacity exceeded")
+        return F, T, (ha[:c], hb[:c], hxi[:c], slip[:c]), fabs
+
+    def run(self, nsteps: int):
+        lib = _load()
+        rc = lib.orc_run(_d(self.P), self.n, _d(self.x), _d(self.v), _d(self.w), _d(self.r),
+                         _d(self.m), _i64(self.id), _i64(self.nh), self.cap, _i64(self.ha),
+                         _i64(self.hb), _d(self.hxi), _i32(self.slip), _d(self.F), _d(self.T),
+                         int(nsteps), self.primed, self.use_cells)
+        if rc != 0:
+            raise RuntimeError("oracle history capacity exceeded")
+        self.primed = 1
+        return self

@@ -1,0 +1,200 @@
+"""Seeded synthetic inputs for the DEM workloads.
+
+This module only places particles and draws random numbers: lattices,
+jitter, size draws, boxes and material constants.  It holds none of the
+method's arithmetic, and both the CUDA path and the FP64 oracle take their
+inputs from it (neither imports the other).
+
+Every input is exactly representable on both sides: positions, radii and
+box bounds are multiples of GRID = 2**-26 m (about 15 nm), and velocities,
+masses, gravity and the time step are rounded to float32 values.  Masses are
+those of solid spheres of the stated density.
+
+Workloads (sizes and materials as stated for each configuration):
+
+* ``column``  -- 1,000 spheres d = 2 mm in a 20 x 20 x 60 mm box, periodic in
+  x/y, floor at z = 0, E = 1e7 Pa, nu = 0.25, e = 0.9, mu = 0.5,
+  rho = 2500 kg/m^3, dt = 2e-6 s.  The box cannot hold a 10 x 10 lattice of
+  2 mm spheres without contact, so the start is an 8 x 8 lattice at 2.5 mm
+  spacing, layers 2.5 mm apart from z = 1.25 mm, first 1,000 sites, each
+  jittered uniformly by +-0.2 mm per axis.
+* ``shear_bed`` -- N polydisperse spheres d ~ U[1.6, 2.4] mm (N = 1,000,000 at
+  full size) in a 0.2 x 0.2 m footprint (box height 0.6 m), periodic x/y,
+  floor; start on an FCC lattice whose nearest-neighbour distance exceeds
+  d_max, to be settled under gravity before the floor is sheared at 0.5 m/s.
+* ``dense_block`` -- jittered lattice at spacing slightly below 2 r with
+  random velocities and spins, so that most neighbours overlap by 0.01-1 %
+  of r: the input for single-evaluation force parity.
+* ``batch`` -- 256 settling boxes, N_k log-uniform in [2e3, 2e5], d = 2 mm,
+  e ~ U[0.5, 0.95], mu ~ U[0.2, 0.8], E log-uniform in [5e6, 5e7] Pa.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GRID = 2.0 ** -26
+
+
+def qgrid(a):
+    """Round lengths to multiples of GRID (exact in float64, float32 and the device's fixed point)."""
+    return np.round(np.asarray(a, dtype=np.float64) / GRID) * GRID
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+@dataclass
+class Material:
+    E: float = 1.0e7
+    nu: float = 0.25
+    e: float = 0.9
+    mu: float = 0.5
+    mu_wall: float | None = None
+    rho: float = 2500.0
+
+
+@dataclass
+class Workload:
+    name: str
+    x: np.ndarray                      # (n, 3) positions [m]
+    v: np.ndarray                      # (n, 3) velocities [m/s]
+    w: np.ndarray                      # (n, 3) angular velocities [1/s]
+    r: np.ndarray                      # (n,) radii [m]
+    m: np.ndarray                      # (n,) masses [kg]
+    lo: tuple                          # box lower corner [m]
+    hi: tuple                          # box upper corner [m]
+    periodic: tuple                    # (bool, bool, bool)
+    material: Material
+    dt: float
+    g: tuple = (0.0, 0.0, 0.0)
+    floor: bool = True
+    floor_v: tuple = (0.0, 0.0, 0.0)
+    skin: float = 2.0e-4
+    steps: int = 100
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+
+def sphere_masses(r, rho):
+    return f32(rho * (4.0 / 3.0) * math.pi * np.asarray(r, dtype=np.float64) ** 3)
+
+
+def _finish(name, x, v, w, r, mat, lo, hi, periodic, dt, g, floor, floor_v, skin, steps, **meta):
+    lo = tuple(qgrid(lo).tolist())
+    hi = tuple(qgrid(hi).tolist())
+    x = qgrid(x)
+    for a in range(3):
+        if periodic[a]:
+            L = hi[a] - lo[a]
+            x[:, a] = lo[a] + np.mod(x[:, a] - lo[a], L)
+            x[:, a] = qgrid(x[:, a])
+            x[x[:, a] >= hi[a], a] -= L
+    r = qgrid(r)
+    return Workload(name=name, x=x, v=f32(v), w=f32(w), r=r, m=sphere_masses(r, mat.rho), lo=lo, hi=hi,
+                    periodic=tuple(bool(p) for p in periodic), material=mat, dt=float(f32(dt)),
+                    g=tuple(f32(g).tolist()), floor=floor, floor_v=tuple(f32(floor_v).tolist()),
+                    skin=float(qgrid(skin)), steps=steps, meta=meta)
+
+
+def column(n: int = 1000, seed: int = 1) -> Workload:
+    rng = np.random.default_rng(seed)
+    d, sp = 2.0e-3, 2.5e-3
+    k = np.arange(n)
+    ix, iy, iz = k % 8, (k // 8) % 8, k // 64
+    x = np.column_stack([1.25e-3 + sp * ix, 1.25e-3 + sp * iy, 1.25e-3 + sp * iz])
+    x += rng.uniform(-0.2e-3, 0.2e-3, (n, 3))
+    r = np.full(n, d / 2)
+    z = np.zeros((n, 3))
+    return _finish("column_1k", x, z, z, r, Material(E=1e7, nu=0.25, e=0.9, mu=0.5, rho=2500.0),
+                   (0, 0, 0), (0.02, 0.02, 0.06), (True, True, False), 2e-6, (0, 0, -9.81), True,
+                   (0, 0, 0), 0.1 * d, 5000)
+
+
+def _fcc(nx, ny, a, nlayers):
+    base = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    gx, gy, gz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nlayers), indexing="ij")
+    cells = np.column_stack([gx.ravel(), gy.ravel(), gz.ravel()]).astype(np.float64)
+    pts = (cells[:, None, :] + base[None, :, :]).reshape(-1, 3) * a
+    order = np.lexsort((pts[:, 0], pts[:, 1], pts[:, 2]))
+    return pts[order]
+
+
+def shear_bed(n: int = 1_000_000, seed: int = 2, footprint: float = 0.2, height: float = 0.6,
+              dmin: float = 1.6e-3, dmax: float = 2.4e-3) -> Workload:
+    """Polydisperse bed before settling (see the module docstring)."""
+    rng = np.random.default_rng(seed)
+    nn = dmax + 0.05e-3                       # nearest-neighbour distance of the start lattice
+    ncell = max(1, int(math.floor(footprint / (nn * math.sqrt(2.0)))))
+    a = footprint / ncell
+    nlayers = int(math.ceil(n / (4 * ncell * ncell)))
+    pts = _fcc(ncell, ncell, a, nlayers)[:n]
+    pts += np.array([a / 4, a / 4, dmax / 2 + 0.05e-3])
+    pts += rng.uniform(-0.02e-3, 0.02e-3, pts.shape)
+    d = rng.uniform(dmin, dmax, n)
+    z = np.zeros((n, 3))
+    return _finish(f"shear_bed_{n}", pts, z, z, d / 2, Material(E=1e7, nu=0.25, e=0.9, mu=0.5, rho=2500.0),
+                   (0, 0, 0), (footprint, footprint, height), (True, True, False), 1e-6, (0, 0, -9.81),
+                   True, (0, 0, 0), 0.1 * 0.5 * (dmin + dmax), 10_000, lattice_a=a, layers=nlayers)
+
+
+def dense_block(nx: int = 12, ny: int = 12, nz: int = 10, r: float = 1.0e-3, seed: int = 7,
+                squeeze: float = 2e-3, rjit: float = 2e-3, vel: float = 0.05, spin: float = 20.0,
+                mat: Material | None = None, floor_v=(0.5, 0.0, 0.0), g=(0.0, 0.0, -9.81),
+                dt: float = 1e-6) -> Workload:
+    """Overlapping jittered lattice for force parity (random v, spin; floor in contact)."""
+    rng = np.random.default_rng(seed)
+    sp = 2.0 * r * (1.0 - squeeze)
+    gx, gy, gz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    x = np.column_stack([gx.ravel(), gy.ravel(), gz.ravel()]).astype(np.float64) * sp
+    x += np.array([sp / 2, sp / 2, r * (1.0 - squeeze)])
+    x += rng.uniform(-0.25, 0.25, x.shape) * squeeze * r
+    n = x.shape[0]
+    rad = r * (1.0 + rng.uniform(-rjit, rjit, n))
+    v = rng.normal(0.0, vel, (n, 3))
+    w = rng.normal(0.0, spin, (n, 3))
+    return _finish(f"dense_block_{n}", x, v, w, rad, mat or Material(E=1e7, nu=0.25, e=0.6, mu=0.4, rho=2500.0),
+                   (0, 0, 0), (nx * sp, ny * sp, nz * sp * 2 + 4 * r), (True, True, False), dt, g, True,
+                   floor_v, 0.1 * 2 * r, 100)
+
+
+def batch_sizes(count: int = 256, seed: int = 4, nmin: float = 2e3, nmax: float = 2e5) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.round(np.exp(rng.uniform(math.log(nmin), math.log(nmax), count))).astype(np.int64)
+
+
+def settling_box(n: int, seed: int, mat: Material, d: float = 2.0e-3, spacing: float = 2.1e-3,
+                 phi: float = 0.45, dt: float = 1e-6, steps: int = 2000) -> Workload:
+    """One settling box: footprint s x s with s = (n V_p / phi)^(1/3), periodic x/y, floor;
+    jittered simple-cubic lattice at the given spacing."""
+    rng = np.random.default_rng(seed)
+    vp = math.pi / 6.0 * d ** 3
+    s = (n * vp / phi) ** (1.0 / 3.0)
+    per = max(3, int(math.floor(s / spacing)))
+    s = per * spacing
+    k = np.arange(n)
+    x = np.column_stack([(k % per + 0.5) * spacing, ((k // per) % per + 0.5) * spacing,
+                         (k // (per * per)) * spacing + d / 2 + 0.02e-3])
+    x += rng.uniform(-0.03e-3, 0.03e-3, x.shape)
+    height = max(3 * s, float(x[:, 2].max()) + 2 * d)
+    z = np.zeros((n, 3))
+    return _finish(f"box_{n}", x, z, z, np.full(n, d / 2), mat, (0, 0, 0), (s, s, height),
+                   (True, True, False), dt, (0, 0, -9.81), True, (0, 0, 0), 0.1 * d, steps)
+
+
+def batch(count: int = 256, seed: int = 4, scale: float = 1.0, steps: int = 2000) -> list[Workload]:
+    """The batched workload: `count` independent boxes (sizes scaled by `scale` for small tests)."""
+    sizes = np.maximum(8, np.round(batch_sizes(count, seed) * scale).astype(np.int64))
+    rng = np.random.default_rng(seed + 1000)
+    out = []
+    for k, nk in enumerate(sizes):
+        mat = Material(E=float(math.exp(rng.uniform(math.log(5e6), math.log(5e7)))), nu=0.25,
+                       e=float(rng.uniform(0.5, 0.95)), mu=float(rng.uniform(0.2, 0.8)), rho=2500.0)
+        out.append(settling_box(int(nk), seed + k, mat, steps=steps))
+    return out

@@ -1,0 +1,190 @@
+/*
+ * dem.h -- C ABI of the GB300 (sm_103a) DEM hot path for the adaptive
+ * coarse-grain method of Queteschiner, Lichtenegger, Schneiderbauer and Pirker,
+ * "Adaptive Coarse-Graining for Large-Scale DEM Simulations" (CFD 2017).
+ *
+ * What a step computes (one call of dem_step advances every instance of a
+ * context by one time step per count):
+ *   - contact forces of the non-linear damped Hertzian spring-dashpot model,
+ *     normal part Eq. 3, tangential part Eq. 4 with a per-contact tangential
+ *     overlap carried over the contact's life, Coulomb truncation Eq. 5,
+ *     coefficients k_n, gamma_n, k_t, gamma_t and beta(e) of Eq. 6
+ *     (Sec. 2.1), plus gravity and an optional moving floor plane;
+ *   - Newton's equations for translation and rotation (Eqs. 1-2), advanced by
+ *     velocity Verlet with the two half kicks of consecutive steps merged;
+ *   - cell-list neighbour lists, rebuilt on the device whenever the
+ *     accumulated displacement bound reaches half the skin.  The paper names
+ *     neighbour-list rebuilds as a cost driver (Sec. 3, runtimes) but
+ *     describes no search; the design here is this library's own.
+ *
+ * Conventions shared by all calls:
+ *   - Units are SI.  Particle arrays are float64, concatenated over the
+ *     context's instances in instance order; within an instance particles
+ *     are in ID order (ID = index of the particle in the array written by
+ *     dem_write, 0 .. n_k - 1).  Vectors are row-major (n, 3).
+ *   - Device state is float32 (velocities, angular velocities, masses,
+ *     forces) and 32-bit fixed point for positions and radii: a length is
+ *     an integer multiple of the instance's quantum q = 2^k m, the smallest
+ *     power of two with (largest box extent) / q <= 2^30.  Written
+ *     positions and radii are rounded to the nearest multiple of q;
+ *     positions read back are exact multiples of q.
+ *   - Memory: every device byte the library uses is the caller's workspace
+ *     (size from dem_query_workspace), passed to dem_create and owned by the
+ *     caller until dem_destroy.  The library never allocates or frees device
+ *     memory and never frees caller memory.
+ *   - Streams: all work is ordered on the stream given to dem_create; calls
+ *     return before the GPU work completes unless stated otherwise.  A host
+ *     pointer (any pointer that cudaPointerGetAttributes does not report as
+ *     device or managed memory) makes dem_read/dem_write stage through the
+ *     workspace and synchronise the stream before returning.
+ *   - Errors: host-detectable errors return at once and leave the context
+ *     unchanged.  Errors found on the device (list overflow, non-finite
+ *     force, escaped particle) set a device status word; dem_sync_status
+ *     reads it, and once set every later call returns that status.  No
+ *     kernel traps or aborts.  dem_last_error gives a one-line message.
+ */
+#ifndef DEM_H
+#define DEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dem_ctx dem_ctx;
+
+typedef enum {
+    DEM_OK = 0,
+    DEM_ERR_ARG = 1,        /* invalid argument or configuration */
+    DEM_ERR_CAPACITY = 2,   /* neighbour-list width or particle capacity exceeded */
+    DEM_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    DEM_ERR_NONFINITE = 4,  /* a force, torque or velocity became NaN/Inf */
+    DEM_ERR_ESCAPED = 5,    /* a particle left the representable z range */
+    DEM_ERR_TIMEOUT = 6,    /* a bounded device wait gave up */
+    DEM_ERR_STATE = 7       /* call not valid in the context's current state */
+} dem_status;
+
+/* Fields of dem_read / dem_write.  n counts particles. */
+typedef enum {
+    DEM_F_POS = 0,      /* (n,3) float64 position [m]; read/write */
+    DEM_F_VEL = 1,      /* (n,3) float64 velocity at the current integer step [m/s]; read/write */
+    DEM_F_OMEGA = 2,    /* (n,3) float64 angular velocity [1/s]; read/write */
+    DEM_F_RADIUS = 3,   /* (n)   float64 radius [m]; read/write */
+    DEM_F_MASS = 4,     /* (n)   float64 mass [kg]; read/write (write after RADIUS) */
+    DEM_F_FORCE = 5,    /* (n,3) float64 total force at the current step [N]; read only */
+    DEM_F_TORQUE = 6,   /* (n,3) float64 total torque at the current step [N m]; read only */
+    DEM_F_WALL_XI = 7,  /* (n,3) float64 tangential overlap of the floor contact [m] (0 if none); read only */
+    DEM_F_NBR_COUNT = 8 /* (n)   float64 neighbour-list length of each particle; read only */
+} dem_field;
+
+/* One independent DEM system ("instance").  A context advances all of its
+ * instances together; every instance has its own box, material and count. */
+typedef struct {
+    int64_t n;            /* particles written by dem_write (IDs 0 .. n-1) */
+    int64_t capacity;     /* maximum particles (>= n) */
+    double lo[3], hi[3];  /* box; periodic axes wrap on [lo, hi), z is open above */
+    int32_t periodic[3];  /* x and y may be periodic; z must not be */
+    int32_t floor_on;     /* 1: frictional floor plane at z = lo[2] */
+    double floor_v[3];    /* floor velocity [m/s] (tangential part acts through friction) */
+    double g[3];          /* gravity [m/s^2] */
+    double dt;            /* time step [s] */
+    double skin;          /* neighbour-list skin [m] */
+    double r_max;         /* largest radius that will ever be present [m] */
+    double E, nu, e, mu;  /* Young's modulus [Pa], Poisson ratio, restitution, friction (Eq. 6) */
+    double mu_wall;       /* particle-wall friction; < 0 means use mu */
+    double rho;           /* particle density [kg/m^3]; masses default to rho 4/3 pi r^3 */
+    int32_t clamp_fn;     /* 1: drop tensile normal forces (not in Eq. 3; default 0) */
+    int32_t reserved;
+} dem_instance_desc;
+
+typedef struct {
+    int32_t n_instances;              /* >= 1 */
+    int32_t max_neighbors;            /* list width L_max, 1 .. 64 */
+    const dem_instance_desc *inst;    /* n_instances descriptors (host memory) */
+} dem_config;
+
+typedef struct {
+    double q;            /* length quantum [m] */
+    double lo[3], hi[3]; /* box as represented (hi - lo is a multiple of q) */
+    int32_t ncell[3];    /* cell grid */
+    int32_t reserved;
+    int64_t n;           /* current particle count */
+    int64_t capacity;
+} dem_instance_info;
+
+typedef struct {
+    int64_t steps;           /* steps taken since dem_create */
+    int64_t rebuilds;        /* neighbour-list builds (all instances) */
+    int64_t list_entries;    /* sum of list lengths at the last dem_stats call */
+    int64_t contacts;        /* contacts (particle pairs counted from both sides + floor) at that call */
+    int64_t particles;       /* live particles */
+} dem_stats_t;
+
+/* Bytes of device workspace a context with this configuration needs. */
+dem_status dem_query_workspace(const dem_config *cfg, int64_t *bytes_out);
+
+/* Create a context on the current CUDA device.  workspace: device pointer,
+ * 256-byte aligned, >= dem_query_workspace bytes, owned by the caller.
+ * stream: cudaStream_t (NULL = legacy default stream).  The state is
+ * undefined until POS, VEL, OMEGA and RADIUS have been written. */
+dem_status dem_create(const dem_config *cfg, void *workspace, int64_t workspace_bytes,
+                      void *stream, dem_ctx **out);
+
+/* Release the context (not the workspace).  Synchronises the stream. */
+dem_status dem_destroy(dem_ctx *ctx);
+
+/* Write a field for all particles (n = sum of the instances' counts).
+ * Writing POS, VEL, OMEGA, RADIUS or MASS starts the system afresh from this
+ * state: contact histories are cleared, the neighbour lists rebuilt and the
+ * first step begins with a half kick from the forces at this state. */
+dem_status dem_write(dem_ctx *ctx, int32_t field, const void *src, int64_t n);
+
+/* Read a field at the current integer step.  VEL, OMEGA, FORCE, TORQUE and
+ * WALL_XI evaluate the contact forces at the current state (no state change). */
+dem_status dem_read(dem_ctx *ctx, int32_t field, void *dst, int64_t n);
+
+/* Contacts at the current step, per particle in ID order: partner IDs
+ * (ascending, -1 padded; width entries per particle) of the particles it
+ * overlaps, and the tangential overlap xi (Eq. 4) of each such contact, in
+ * the frame of the pair's lower ID (xi of pair (a, b) with a < b is the same
+ * vector in both rows).  partner: int32 (n, width); xi: float64 (n, width, 3).
+ * Single-instance contexts only. */
+dem_status dem_read_contacts(dem_ctx *ctx, int32_t *partner, double *xi, int32_t width, int64_t n);
+
+/* Set tangential overlaps of existing neighbour pairs (same layout as
+ * dem_read_contacts); pairs not within the neighbour skin are ignored.  Use
+ * after dem_write to resume a run; the lists are built first if needed. */
+dem_status dem_write_contacts(dem_ctx *ctx, const int32_t *partner, const double *xi, int32_t width,
+                              int64_t n);
+
+/* Advance nsteps time steps (asynchronous). */
+dem_status dem_step(dem_ctx *ctx, int64_t nsteps);
+
+/* Synchronise the stream and return the device status word as a dem_status. */
+dem_status dem_sync_status(dem_ctx *ctx);
+
+/* Per-instance description of the represented system. */
+dem_status dem_instance_info_get(dem_ctx *ctx, int32_t instance, dem_instance_info *out);
+
+/* Counters (synchronises). */
+dem_status dem_stats(dem_ctx *ctx, dem_stats_t *out);
+
+/* Capture dem_step in CUDA graphs of `steps_per_graph` steps (0 disables).
+ * The neighbour-list rebuild sits in a conditional node set by the step
+ * kernel, so a captured run needs no host round trip. */
+dem_status dem_set_graph(dem_ctx *ctx, int32_t steps_per_graph);
+
+/* CUDA-event time of the step kernels of the most recent graph launch:
+ * total_ms = sum over its steps_per_graph step kernels, count = that number.
+ * Synchronises the stream.  DEM_ERR_STATE if no graph was built. */
+dem_status dem_graph_step_kernel_ms(dem_ctx *ctx, double *total_ms, int32_t *count);
+
+/* Last error message of the context; with ctx == NULL, the last configuration
+ * error (dem_query_workspace / dem_create) of the calling thread.  Never NULL. */
+const char *dem_last_error(const dem_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEM_H */

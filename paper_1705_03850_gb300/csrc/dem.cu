@@ -1,0 +1,1486 @@
+// GB300 (sm_103a) kernels and C ABI of the DEM hot path: contact forces of
+// Eqs. 3-6 with tangential history (Sec. 2.1), velocity Verlet of Eqs. 1-2,
+// and device-side neighbour-list rebuilds.  See include/dem.h for the
+// interface and dem_internal.cuh for the data layout.
+#include "dem.h"
+#include "dem_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace cgdem;
+
+// ====================================================================== scan
+// Exclusive scan of the per-cell counts into cell starts: three passes over
+// tiles of SCAN_TILE entries (per-tile sums, scan of the sums, tile scans).
+
+namespace {
+
+constexpr int SCAN_T = 256;
+constexpr int SCAN_V = 8;
+constexpr int SCAN_TILE = SCAN_T * SCAN_V;
+
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* total)
+{
+    __shared__ unsigned wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (warp == 0) {
+        unsigned w = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) wsum[lane] = w;
+    }
+    __syncthreads();
+    unsigned base = warp ? wsum[warp - 1] : 0u;
+    *total = wsum[nw - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(Dev d)
+{
+    if (!d.g->any) return;
+    const unsigned b = blockIdx.x;
+    const unsigned base = b * SCAN_TILE;
+    unsigned s = 0;
+    for (int k = 0; k < SCAN_V; ++k) {
+        unsigned i = base + k * SCAN_T + threadIdx.x;
+        if (i < d.ncodes) s += d.ccount[i];
+    }
+    unsigned tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) d.part[b] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(Dev d)
+{
+    if (!d.g->any) return;
+    __shared__ unsigned carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (unsigned c0 = 0; c0 < d.nparts; c0 += blockDim.x) {
+        unsigned i = c0 + threadIdx.x;
+        unsigned v = i < d.nparts ? d.part[i] : 0u;
+        unsigned tot;
+        unsigned ex = block_exclusive_scan(v, &tot);
+        if (i < d.nparts) d.part[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_down(Dev d)
+{
+    if (!d.g->any) return;
+    const unsigned base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_V;
+    unsigned v[SCAN_V];
+    unsigned s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
+        unsigned i = base + k;
+        v[k] = i < d.ncodes ? d.ccount[i] : 0u;
+        s += v[k];
+    }
+    unsigned tot;
+    unsigned ex = block_exclusive_scan(s, &tot) + d.part[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
+        unsigned i = base + k;
+        if (i < d.ncodes) d.cstart[i] = ex;
+        ex += v[k];
+    }
+}
+
+// ==================================================================== cells
+
+__device__ __forceinline__ int axis_cell(const InstC& c, int a, int x)
+{
+    if (x <= 0) return 0;
+    long long t = (long long)x * c.nc[a] / c.ext[a];
+    return t >= c.nc[a] ? c.nc[a] - 1 : (int)t;
+}
+
+__device__ __forceinline__ unsigned cell_code(const Dev& d, const InstC& c, int cx, int cy, int cz)
+{
+    return (unsigned)c.code0 + d.spread[c.spread_off[0] + cx] + d.spread[c.spread_off[1] + cy] +
+           d.spread[c.spread_off[2] + cz];
+}
+
+__device__ __forceinline__ int min_image(int dx, int per, int L, int half)
+{
+    if (per) {
+        if (dx > half) dx -= L;
+        else if (dx < -half) dx += L;
+    }
+    return dx;
+}
+
+// ================================================================ rebuild
+// Triggered per instance by the displacement bound (flag != 0).  Sequence:
+// clear counts -> bin (atomic slot in cell) -> scan -> scatter -> order each
+// cell by particle ID -> build lists, permute state, carry histories.
+
+__global__ void k_rb_clear(Dev d)
+{
+    if (!d.g->any) return;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < d.ncodes; i += gridDim.x * blockDim.x)
+        d.ccount[i] = 0;
+}
+
+__global__ void k_rb_bin(Dev d)
+{
+    if (!d.g->any) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.ncap) return;
+    const int k = d.tile_inst[s / TILE];
+    const InstD D = d.id[k];
+    if (!D.flag) return;
+    const InstC& c = d.ic[k];
+    if (s - c.slot0 >= D.n) return;
+    const int4 p = d.pos[D.cur][s];
+    const unsigned code = cell_code(d, c, axis_cell(c, 0, p.x), axis_cell(c, 1, p.y), axis_cell(c, 2, p.z));
+    d.cellcode[s] = code;
+    d.cslot[s] = atomicAdd(&d.ccount[code], 1u);
+}
+
+__global__ void k_rb_scatter(Dev d)
+{
+    if (!d.g->any) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.ncap) return;
+    const int k = d.tile_inst[s / TILE];
+    const InstD D = d.id[k];
+    if (!D.flag) return;
+    const InstC& c = d.ic[k];
+    if (s - c.slot0 >= D.n) return;
+    const unsigned code = d.cellcode[s];
+    const int np = c.slot0 + (int)(d.cstart[code] - d.cstart[c.code0]) + (int)d.cslot[s];
+    d.perm[np] = s;
+}
+
+// The first member of every cell orders the cell by particle ID, so that the
+// final order depends only on the cells and the IDs.
+__global__ void k_rb_cellsort(Dev d)
+{
+    if (!d.g->any) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.ncap) return;
+    const int k = d.tile_inst[s / TILE];
+    const InstD D = d.id[k];
+    if (!D.flag) return;
+    const InstC& c = d.ic[k];
+    if (s - c.slot0 >= D.n || d.cslot[s] != 0u) return;
+    const unsigned code = d.cellcode[s];
+    const int cntc = (int)d.ccount[code];
+    if (cntc < 2) return;
+    int* a = d.perm + c.slot0 + (int)(d.cstart[code] - d.cstart[c.code0]);
+    const float4* v = d.vel[D.cur];
+    for (int i = 1; i < cntc; ++i) {
+        const int x = a[i];
+        const unsigned xid = __float_as_uint(v[x].w) & ID_MASK;
+        int j = i - 1;
+        while (j >= 0 && (__float_as_uint(v[a[j]].w) & ID_MASK) > xid) {
+            a[j + 1] = a[j];
+            --j;
+        }
+        a[j + 1] = x;
+    }
+}
+
+// One thread per new slot: move the particle into the other state buffer,
+// collect neighbours within r_i + r_j + skin (exact integer test), order the
+// row by ID, and carry the tangential overlaps of pairs that were already
+// listed (merge-join on IDs with the particle's previous row).
+__global__ void __launch_bounds__(128) k_rb_build(Dev d)
+{
+    if (!d.g->any) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.ncap) return;
+    const int k = d.tile_inst[s / TILE];
+    const InstD D = d.id[k];
+    if (!D.flag) return;
+    const InstC& c = d.ic[k];
+    if (s - c.slot0 >= D.n) return;
+    const int cur = D.cur, nxt = cur ^ 1, lp = D.lp, nlp = lp ^ 1;
+    const int ncap = d.ncap;
+    const int old = d.perm[s];
+    const int4 p = d.pos[cur][old];
+    float4 v = d.vel[cur][old];
+    const float4 w = d.omg[cur][old];
+    const unsigned myid = __float_as_uint(v.w) & ID_MASK;
+    if (D.flag == 2) v.w = __uint_as_float(myid);   // fresh start: no floor history
+    d.pos[nxt][s] = p;
+    d.vel[nxt][s] = v;
+    d.omg[nxt][s] = w;
+    d.slot_of_id[c.slot0 + (int)myid] = s;
+
+    int cand_id[MAXL];
+    int cand_slot[MAXL];
+    int nc = 0;
+    bool overflow = false;
+    const int ccx = axis_cell(c, 0, p.x), ccy = axis_cell(c, 1, p.y), ccz = axis_cell(c, 2, p.z);
+    const unsigned cbase = d.cstart[c.code0];
+    const int Lmax = d.Lmax;
+    for (int dz = -1; dz <= 1; ++dz) {
+        int cz = ccz + dz;
+        if (cz < 0 || cz >= c.nc[2]) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int cy = ccy + dy;
+            if (cy < 0 || cy >= c.nc[1]) {
+                if (!c.per[1]) continue;
+                cy = (cy + c.nc[1]) % c.nc[1];
+            }
+            for (int dx = -1; dx <= 1; ++dx) {
+                int cx = ccx + dx;
+                if (cx < 0 || cx >= c.nc[0]) {
+                    if (!c.per[0]) continue;
+                    cx = (cx + c.nc[0]) % c.nc[0];
+                }
+                const unsigned code = cell_code(d, c, cx, cy, cz);
+                const int start = c.slot0 + (int)(d.cstart[code] - cbase);
+                const int cnt = (int)d.ccount[code];
+                for (int t = 0; t < cnt; ++t) {
+                    const int m = start + t;
+                    if (m == s) continue;
+                    const int o = d.perm[m];
+                    const int4 q = d.pos[cur][o];
+                    const long long ddx = min_image(p.x - q.x, c.per[0], c.ext[0], c.half[0]);
+                    const long long ddy = min_image(p.y - q.y, c.per[1], c.ext[1], c.half[1]);
+                    const long long ddz = (long long)p.z - q.z;
+                    const long long cut = (long long)p.w + q.w + c.skin;
+                    if (ddx * ddx + ddy * ddy + ddz * ddz >= cut * cut) continue;
+                    const int qid = (int)(__float_as_uint(d.vel[cur][o].w) & ID_MASK);
+                    if (nc == Lmax) { overflow = true; continue; }
+                    int j = nc - 1;
+                    while (j >= 0 && cand_id[j] > qid) {
+                        cand_id[j + 1] = cand_id[j];
+                        cand_slot[j + 1] = cand_slot[j];
+                        --j;
+                    }
+                    cand_id[j + 1] = qid;
+                    cand_slot[j + 1] = m;
+                    ++nc;
+                }
+            }
+        }
+    }
+    if (overflow) {
+        atomicOr(&d.g->status, ST_CAPACITY);
+        d.g->err_slot = s;
+    }
+    int* nrow = d.nbr[nlp] + s;
+    float* hn = d.hist[nlp] + s;
+    const size_t plane = (size_t)Lmax * ncap;
+    const int* orow = d.nbr[lp] + old;
+    const float* ho = d.hist[lp] + old;
+    const int ocnt = D.flag == 2 ? 0 : d.cnt[lp][old];
+    int eo = 0;
+    unsigned oid = 0xffffffffu;
+    if (eo < ocnt) oid = __float_as_uint(d.vel[cur][orow[0]].w) & ID_MASK;
+    for (int e = 0; e < nc; ++e) {
+        nrow[(size_t)e * ncap] = cand_slot[e];
+        const unsigned id = (unsigned)cand_id[e];
+        while (eo < ocnt && oid < id) {
+            ++eo;
+            oid = eo < ocnt ? (__float_as_uint(d.vel[cur][orow[(size_t)eo * ncap]].w) & ID_MASK) : 0xffffffffu;
+        }
+        float hx = 0.f, hy = 0.f, hz = 0.f;
+        if (eo < ocnt && oid == id) {
+            hx = ho[(size_t)eo * ncap];
+            hy = ho[plane + (size_t)eo * ncap];
+            hz = ho[2 * plane + (size_t)eo * ncap];
+        }
+        hn[(size_t)e * ncap] = hx;
+        hn[plane + (size_t)e * ncap] = hy;
+        hn[2 * plane + (size_t)e * ncap] = hz;
+    }
+    d.cnt[nlp][s] = nc;
+    d.whist[nlp][s] = D.flag == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : d.whist[lp][old];
+}
+
+__global__ void k_rb_finish(Dev d)
+{
+    if (!d.g->any) return;
+    for (int k = threadIdx.x; k < d.B; k += blockDim.x) {
+        InstD& D = d.id[k];
+        if (D.flag) {
+            D.cur ^= 1;
+            D.lp ^= 1;
+            D.flag = 0;
+            D.disp = 0.f;
+            atomicAdd(&d.g->rebuilds, 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) d.g->any = 0u;
+}
+
+// ============================================================= contact law
+
+struct V3 {
+    float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b)
+{
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// One contact in canonical order (a = lower ID, n from b to a, delta > 0 in
+// metres).  Eq. 6 coefficients, Eq. 3 normal force, Eq. 4 tangential force
+// with the stored overlap xi kept in the tangent plane at its length and
+// advanced by the tangential contact-point motion, Eq. 5 truncation.
+// Returns the force on a; ft receives the tangential part.
+template <bool WALL>
+__device__ __forceinline__ V3 contact(const InstC& c, float delta, V3 n, float ra, float rb, float ma,
+                                      float mb, V3 va, V3 vb, V3 wa, V3 wb, V3& xi, float dt_hist,
+                                      V3& ft, bool& slip)
+{
+    float R, meff;
+    if (WALL) {
+        R = ra;
+        meff = ma;
+    } else {
+        R = ra * rb / (ra + rb);
+        meff = ma * mb / (ma + mb);
+    }
+    const float sRd = sqrtf(R * delta);
+    const float kn = c.c_kn * sRd;
+    const float kt = c.c_kt * sRd;
+    const float gn = c.nbeta * sqrtf(5.0f * meff * kn);
+    const float gt = c.nbeta * sqrtf((10.0f / 3.0f) * meff * kt);
+    const V3 vr = va - vb;
+    const float vn = dot(vr, n);
+    const V3 rw = WALL ? ra * wa : ra * wa + rb * wb;
+    const V3 vc = vr - cross(rw, n);
+    const V3 vt = vc - dot(vc, n) * n;
+    float fnm = kn * delta - gn * vn;
+    if (c.clamp_fn && fnm < 0.f) fnm = 0.f;
+    // keep xi in the tangent plane at its previous length
+    const float xin = dot(xi, n);
+    const V3 xr = xi - xin * n;
+    const float l0 = dot(xi, xi), l1 = dot(xr, xr);
+    xi = l1 > 0.f ? sqrtf(l0 / l1) * xr : v3(0.f, 0.f, 0.f);
+    xi = xi + dt_hist * vt;
+    ft = (-kt) * xi - gt * vt;
+    const float ft2 = dot(ft, ft);
+    const float lim = (WALL ? c.mu_w : c.mu) * fabsf(fnm);
+    slip = ft2 > lim * lim;
+    if (slip) {
+        const float sc = lim / sqrtf(ft2);
+        ft = sc * ft;
+        xi = (-1.0f / kt) * (ft + gt * vt);
+    }
+    return fnm * n + ft;
+}
+
+// ================================================================== step
+// MODE 0: one velocity-Verlet step (force at x^n with v^{n-1/2}, merged kick,
+// drift to x^{n+1}, displacement bound, rebuild decision by the last block).
+// MODE 1: forces at the current state only, written to the output arrays.
+template <int MODE>
+__global__ void __launch_bounds__(TILE) k_step(Dev d, int prime, cudaGraphConditionalHandle hnext, int use_cond)
+{
+    const int t = blockIdx.x;
+    const int k = d.tile_inst[t];
+    const InstC& c = d.ic[k];
+    const InstD D = d.id[k];
+    const int s = t * TILE + threadIdx.x;
+    const bool live = (s - c.slot0) < D.n;
+    float mydisp = 0.f;
+    if (live) {
+        const int cur = D.cur, lp = D.lp, ncap = d.ncap;
+        const size_t plane = (size_t)d.Lmax * ncap;
+        const int4 P = d.pos[cur][s];
+        float4 Vv = d.vel[cur][s];
+        float4 Wv = d.omg[cur][s];
+        const unsigned idw = __float_as_uint(Vv.w);
+        const unsigned myid = idw & ID_MASK;
+        const bool wall_prev = (idw & WALL_BIT) != 0u;
+        const float m = Wv.w;
+        const float q = c.q;
+        const float r = (float)P.w * q;
+        const V3 vme = v3(Vv.x, Vv.y, Vv.z), wme = v3(Wv.x, Wv.y, Wv.z);
+        const float dt_hist = prime ? 0.f : c.dt;
+        V3 F = m * v3(c.g[0], c.g[1], c.g[2]);
+        V3 T = v3(0.f, 0.f, 0.f);
+        const int ncnt = d.cnt[lp][s];
+        const int* nb = d.nbr[lp] + s;
+        float* h = d.hist[lp] + s;
+        float* ho = MODE == 1 ? d.xi_out + s : h;
+        unsigned long long cm = 0ull;
+        for (int e = 0; e < ncnt; ++e) {
+            const int j = nb[(size_t)e * ncap];
+            const int4 Q = d.pos[cur][j];
+            const int dx = min_image(P.x - Q.x, c.per[0], c.ext[0], c.half[0]);
+            const int dy = min_image(P.y - Q.y, c.per[1], c.ext[1], c.half[1]);
+            const int dz = P.z - Q.z;
+            const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+            const int S = P.w + Q.w;
+            const long long S2 = (long long)S * S;
+            V3 xi = v3(0.f, 0.f, 0.f);
+            if (d2 < S2) {
+                const float4 Vj = d.vel[cur][j];
+                const float4 Wj = d.omg[cur][j];
+                const unsigned idj = __float_as_uint(Vj.w) & ID_MASK;
+                const bool own_a = myid < idj;
+                // canonical operands (identical on both sides of the pair)
+                const float sx = own_a ? 1.f : -1.f;
+                const int ax = own_a ? dx : -dx, ay = own_a ? dy : -dy, az = own_a ? dz : -dz;
+                const int rai = own_a ? P.w : Q.w, rbi = own_a ? Q.w : P.w;
+                const V3 vj = v3(Vj.x, Vj.y, Vj.z), wj = v3(Wj.x, Wj.y, Wj.z);
+                const V3 va = own_a ? vme : vj, vb = own_a ? vj : vme;
+                const V3 wa = own_a ? wme : wj, wb = own_a ? wj : wme;
+                const float ma = own_a ? m : Wj.w, mb = own_a ? Wj.w : m;
+                const float dist = sqrtf((float)d2);
+                const float delta = (float)(S2 - d2) / ((float)S + dist) * q;
+                const float inv = 1.0f / dist;
+                const V3 n = v3((float)ax * inv, (float)ay * inv, (float)az * inv);
+                xi = v3(h[(size_t)e * ncap], h[plane + (size_t)e * ncap], h[2 * plane + (size_t)e * ncap]);
+                V3 ft;
+                bool slip;
+                const V3 fa = contact<false>(c, delta, n, (float)rai * q, (float)rbi * q, ma, mb, va, vb, wa, wb,
+                                             xi, dt_hist, ft, slip);
+                F = F + sx * fa;
+                T = T - r * cross(n, ft);
+                cm |= 1ull << e;
+            }
+            ho[(size_t)e * ncap] = xi.x;
+            ho[plane + (size_t)e * ncap] = xi.y;
+            ho[2 * plane + (size_t)e * ncap] = xi.z;
+        }
+        // floor plane z = 0 (the box bottom)
+        bool wall_now = false;
+        V3 wxi = v3(0.f, 0.f, 0.f);
+        if (c.floor_on) {
+            const int dw = P.w - P.z;
+            if (dw > 0) {
+                wall_now = true;
+                if (wall_prev) {
+                    const float4 hw = d.whist[lp][s];
+                    wxi = v3(hw.x, hw.y, hw.z);
+                }
+                const V3 n = v3(0.f, 0.f, 1.f);
+                V3 ft;
+                bool slip;
+                const V3 fa = contact<true>(c, (float)dw * q, n, r, 0.f, m, 0.f, vme,
+                                            v3(c.floor_v[0], c.floor_v[1], c.floor_v[2]), wme,
+                                            v3(0.f, 0.f, 0.f), wxi, dt_hist, ft, slip);
+                F = F + fa;
+                T = T - r * cross(n, ft);
+                if (MODE == 0) d.whist[lp][s] = make_float4(wxi.x, wxi.y, wxi.z, 0.f);
+            }
+        }
+        const float inv_m = 1.0f / m;
+        const float inv_I = 2.5f / (m * r * r);
+        if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(T.x) && isfinite(T.y) &&
+              isfinite(T.z))) {
+            atomicOr(&d.g->status, ST_NONFINITE);
+            d.g->err_slot = s;
+        }
+        if (MODE == 1) {
+            const float hk = prime ? 0.f : 0.5f * c.dt;
+            d.outF[s] = make_float4(F.x, F.y, F.z, 0.f);
+            d.outT[s] = make_float4(T.x, T.y, T.z, 0.f);
+            d.outV[s] = make_float4(Vv.x + hk * F.x * inv_m, Vv.y + hk * F.y * inv_m, Vv.z + hk * F.z * inv_m, 0.f);
+            d.outW[s] = make_float4(Wv.x + hk * T.x * inv_I, Wv.y + hk * T.y * inv_I, Wv.z + hk * T.z * inv_I, 0.f);
+            d.outWX[s] = make_float4(wxi.x, wxi.y, wxi.z, wall_now ? 1.f : 0.f);
+            d.cmask[s] = cm;
+        } else {
+            const float kick = prime ? 0.5f * c.dt : c.dt;
+            Vv.x += kick * F.x * inv_m;
+            Vv.y += kick * F.y * inv_m;
+            Vv.z += kick * F.z * inv_m;
+            Wv.x += kick * T.x * inv_I;
+            Wv.y += kick * T.y * inv_I;
+            Wv.z += kick * T.z * inv_I;
+            const float sx = Vv.x * c.dt_over_q, sy = Vv.y * c.dt_over_q, sz = Vv.z * c.dt_over_q;
+            int4 Pn = P;
+            bool bad = !(fabsf(sx) < 5.0e8f && fabsf(sy) < 5.0e8f && fabsf(sz) < 5.0e8f);
+            if (!bad) {
+                const int ix = __float2int_rn(sx), iy = __float2int_rn(sy), iz = __float2int_rn(sz);
+                int x = P.x + ix, y = P.y + iy;
+                if (c.per[0]) {
+                    if (x >= c.ext[0]) x -= c.ext[0];
+                    else if (x < 0) x += c.ext[0];
+                }
+                if (c.per[1]) {
+                    if (y >= c.ext[1]) y -= c.ext[1];
+                    else if (y < 0) y += c.ext[1];
+                }
+                const long long z = (long long)P.z + iz;
+                if (z > 2000000000ll || z < -2000000000ll) bad = true;
+                Pn = make_int4(x, y, (int)z, P.w);
+                mydisp = sqrtf((float)ix * (float)ix + (float)iy * (float)iy + (float)iz * (float)iz);
+            }
+            if (bad) {
+                atomicOr(&d.g->status, ST_ESCAPED);
+                d.g->err_slot = s;
+            }
+            const int nxt = cur ^ 1;
+            d.pos[nxt][s] = Pn;
+            d.vel[nxt][s] = make_float4(Vv.x, Vv.y, Vv.z, __uint_as_float(myid | (wall_now ? WALL_BIT : 0u)));
+            d.omg[nxt][s] = Wv;
+        }
+    }
+    if (MODE == 0) {
+        // block maximum of the displacement, then the last block to finish
+        // accumulates the bound per instance and decides on rebuilds
+        __shared__ float smax[TILE / 32];
+        __shared__ bool am_last;
+        float mx = mydisp;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float bm = smax[0];
+            for (int i = 1; i < TILE / 32; ++i) bm = fmaxf(bm, smax[i]);
+            if (bm > 0.f) atomicMax(&d.id[k].stepmax, __float_as_uint(bm));
+            __threadfence();
+            const unsigned prev = atomicAdd(&d.g->counter, 1u);
+            am_last = prev == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (am_last) {
+            __threadfence();
+            for (int kk = threadIdx.x; kk < d.B; kk += blockDim.x) {
+                InstD* Dk = d.id + kk;
+                const float sm = __uint_as_float(atomicExch(&Dk->stepmax, 0u));
+                const float disp = Dk->disp + sm;
+                Dk->disp = disp;
+                Dk->cur ^= 1;
+                if (2.0f * disp >= 0.99f * d.ic[kk].skin_f && Dk->flag == 0) {
+                    Dk->flag = 1;
+                    atomicOr(&d.g->any, 1u);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                d.g->counter = 0u;
+                if (use_cond) cudaGraphSetConditional(hnext, atomicOr(&d.g->any, 0u) ? 1u : 0u);
+            }
+        }
+    }
+}
+
+__global__ void k_set_cond(Dev d, cudaGraphConditionalHandle h)
+{
+    cudaGraphSetConditional(h, d.g->any ? 1u : 0u);
+}
+
+// =========================================================== field I/O
+
+__device__ __forceinline__ int find_inst(const long long* goff, int B, long long g)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (goff[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct HostInstLo {
+    double lo[3];
+    double q;
+    double rho;
+};
+
+__global__ void k_init_ids(Dev d)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.ncap) return;
+    const int k = d.tile_inst[s / TILE];
+    const int id = s - d.ic[k].slot0;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int b = 0; b < 2; ++b) {
+        d.pos[b][s] = make_int4(0, 0, 0, 0);
+        d.vel[b][s] = make_float4(0.f, 0.f, 0.f, __uint_as_float((unsigned)id));
+        d.omg[b][s] = z;
+        d.cnt[b][s] = 0;
+        d.whist[b][s] = z;
+    }
+    d.slot_of_id[s] = s;
+}
+
+// field writes: src holds float64 values in the user layout
+__global__ void k_write_field(Dev d, int field, const double* __restrict__ src, long long total,
+                              const HostInstLo* __restrict__ hl)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int k = find_inst(d.goff, d.B, g);
+    const InstC& c = d.ic[k];
+    const int id = (int)(g - d.goff[k]);
+    const int s = d.slot_of_id[c.slot0 + id];
+    const int cur = d.id[k].cur;
+    const double q = hl[k].q;
+    if (field == DEM_F_POS) {
+        int4 p = d.pos[cur][s];
+        int xi[3];
+        for (int a = 0; a < 3; ++a) {
+            double u = rint((src[3 * g + a] - hl[k].lo[a]) / q);
+            if (c.per[a]) {
+                double L = (double)c.ext[a];
+                u = u - L * floor(u / L);
+                if (u >= L) u -= L;
+            }
+            if (!(u > -2.0e9 && u < 2.0e9)) {
+                atomicOr(&d.g->status, ST_ESCAPED);
+                u = 0.0;
+            }
+            xi[a] = (int)u;
+        }
+        p.x = xi[0]; p.y = xi[1]; p.z = xi[2];
+        d.pos[cur][s] = p;
+    } else if (field == DEM_F_VEL) {
+        float4 v = d.vel[cur][s];
+        v.x = (float)src[3 * g]; v.y = (float)src[3 * g + 1]; v.z = (float)src[3 * g + 2];
+        d.vel[cur][s] = v;
+    } else if (field == DEM_F_OMEGA) {
+        float4 w = d.omg[cur][s];
+        w.x = (float)src[3 * g]; w.y = (float)src[3 * g + 1]; w.z = (float)src[3 * g + 2];
+        d.omg[cur][s] = w;
+    } else if (field == DEM_F_RADIUS) {
+        int4 p = d.pos[cur][s];
+        const double r = src[g];
+        p.w = (int)rint(r / q);
+        d.pos[cur][s] = p;
+        float4 w = d.omg[cur][s];
+        w.w = (float)(hl[k].rho * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r);
+        d.omg[cur][s] = w;
+    } else if (field == DEM_F_MASS) {
+        float4 w = d.omg[cur][s];
+        w.w = (float)src[g];
+        d.omg[cur][s] = w;
+    }
+}
+
+__global__ void k_read_field(Dev d, int field, double* __restrict__ dst, long long total,
+                             const HostInstLo* __restrict__ hl)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int k = find_inst(d.goff, d.B, g);
+    const InstC& c = d.ic[k];
+    const int id = (int)(g - d.goff[k]);
+    const int s = d.slot_of_id[c.slot0 + id];
+    const int cur = d.id[k].cur;
+    const double q = hl[k].q;
+    float4 f;
+    switch (field) {
+    case DEM_F_POS: {
+        const int4 p = d.pos[cur][s];
+        dst[3 * g] = hl[k].lo[0] + (double)p.x * q;
+        dst[3 * g + 1] = hl[k].lo[1] + (double)p.y * q;
+        dst[3 * g + 2] = hl[k].lo[2] + (double)p.z * q;
+        return;
+    }
+    case DEM_F_RADIUS: dst[g] = (double)d.pos[cur][s].w * q; return;
+    case DEM_F_MASS: dst[g] = (double)d.omg[cur][s].w; return;
+    case DEM_F_NBR_COUNT: dst[g] = (double)d.cnt[d.id[k].lp][s]; return;
+    case DEM_F_VEL: f = d.outV[s]; break;
+    case DEM_F_OMEGA: f = d.outW[s]; break;
+    case DEM_F_FORCE: f = d.outF[s]; break;
+    case DEM_F_TORQUE: f = d.outT[s]; break;
+    case DEM_F_WALL_XI: f = d.outWX[s]; break;
+    default: return;
+    }
+    dst[3 * g] = f.x;
+    dst[3 * g + 1] = f.y;
+    dst[3 * g + 2] = f.z;
+}
+
+__global__ void k_read_contacts(Dev d, int* __restrict__ partner, double* __restrict__ xi, int width)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.ncap) return;
+    const int k = d.tile_inst[s / TILE];
+    const InstD D = d.id[k];
+    const InstC& c = d.ic[k];
+    if (s - c.slot0 >= D.n) return;
+    const unsigned id = __float_as_uint(d.vel[D.cur][s].w) & ID_MASK;
+    const size_t plane = (size_t)d.Lmax * d.ncap;
+    const int cnt = d.cnt[D.lp][s];
+    const unsigned long long cm = d.cmask[s];
+    int t = 0;
+    for (int e = 0; e < cnt; ++e) {
+        if (!((cm >> e) & 1ull)) continue;
+        if (t == width) {
+            atomicOr(&d.g->status, ST_TRUNC);
+            break;
+        }
+        const int j = d.nbr[D.lp][(size_t)e * d.ncap + s];
+        const size_t o = (size_t)id * width + t;
+        partner[o] = (int)(__float_as_uint(d.vel[D.cur][j].w) & ID_MASK);
+        xi[3 * o] = d.xi_out[(size_t)e * d.ncap + s];
+        xi[3 * o + 1] = d.xi_out[plane + (size_t)e * d.ncap + s];
+        xi[3 * o + 2] = d.xi_out[2 * plane + (size_t)e * d.ncap + s];
+        ++t;
+    }
+    for (; t < width; ++t) {
+        const size_t o = (size_t)id * width + t;
+        partner[o] = -1;
+        xi[3 * o] = xi[3 * o + 1] = xi[3 * o + 2] = 0.0;
+    }
+}
+
+__global__ void k_write_contacts(Dev d, const int* __restrict__ partner, const double* __restrict__ xi, int width)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.ncap) return;
+    const int k = d.tile_inst[s / TILE];
+    const InstD D = d.id[k];
+    const InstC& c = d.ic[k];
+    if (s - c.slot0 >= D.n) return;
+    const unsigned id = __float_as_uint(d.vel[D.cur][s].w) & ID_MASK;
+    const size_t plane = (size_t)d.Lmax * d.ncap;
+    const int cnt = d.cnt[D.lp][s];
+    float* h = d.hist[D.lp] + s;
+    int t = 0;
+    for (int e = 0; e < cnt; ++e) {
+        const int j = d.nbr[D.lp][(size_t)e * d.ncap + s];
+        const int pid = (int)(__float_as_uint(d.vel[D.cur][j].w) & ID_MASK);
+        while (t < width && partner[(size_t)id * width + t] >= 0 && partner[(size_t)id * width + t] < pid) ++t;
+        if (t < width && partner[(size_t)id * width + t] == pid) {
+            const size_t o = (size_t)id * width + t;
+            h[(size_t)e * d.ncap] = (float)xi[3 * o];
+            h[plane + (size_t)e * d.ncap] = (float)xi[3 * o + 1];
+            h[2 * plane + (size_t)e * d.ncap] = (float)xi[3 * o + 2];
+        }
+    }
+}
+
+__global__ void k_stats(Dev d)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long l = 0, cc = 0;
+    if (s < d.ncap) {
+        const int k = d.tile_inst[s / TILE];
+        const InstD D = d.id[k];
+        if (s - d.ic[k].slot0 < D.n) {
+            l = (unsigned long long)d.cnt[D.lp][s];
+            cc = (unsigned long long)__popcll(d.cmask[s]) + (d.outWX[s].w != 0.f ? 1ull : 0ull);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        l += __shfl_xor_sync(0xffffffffu, l, o);
+        cc += __shfl_xor_sync(0xffffffffu, cc, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (l || cc)) {
+        atomicAdd(&d.g->sum_list, l);
+        atomicAdd(&d.g->sum_contacts, cc);
+    }
+}
+
+}  // namespace
+
+// ============================================================== host side
+
+struct dem_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    Dev dev{};
+    int B = 0, Lmax = 0;
+    int ncap = 0, ntiles = 0;
+    unsigned ncodes = 0, nparts = 0;
+    std::vector<InstC> ic;
+    std::vector<HostInstLo> hl;
+    std::vector<long long> count;     // host mirror of live counts
+    HostInstLo* d_hl = nullptr;
+    bool fresh = true;                // velocities at an integer step (next step primes)
+    bool have_state = false;
+    long long steps = 0;
+    unsigned status = 0;
+    std::string err;
+    // graphs
+    int graph_steps = 0;
+    cudaGraph_t rb_graph = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<cudaEvent_t> ev0, ev1;   // around each step kernel of the graph
+};
+
+namespace {
+
+thread_local std::string g_cfg_err = "no error";
+
+dem_status fail(dem_ctx* c, dem_status st, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+#define CU(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ctx, DEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Layout {
+    size_t total = 0;
+    size_t take(size_t bytes)
+    {
+        size_t o = total;
+        total += (bytes + 255) & ~size_t(255);
+        return o;
+    }
+};
+
+struct Plan {
+    std::vector<InstC> ic;
+    std::vector<HostInstLo> hl;
+    std::vector<unsigned> spread;
+    std::vector<int> tile_inst;
+    std::vector<long long> count;
+    int ncap = 0, ntiles = 0, Lmax = 0, B = 0;
+    unsigned ncodes = 0, nparts = 0;
+    // offsets
+    size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_whist[2];
+    size_t o_cellcode, o_cslot, o_perm, o_ccount, o_cstart, o_part, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
+        o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl;
+    size_t bytes = 0;
+};
+
+int ceil_log2(long long v)
+{
+    int b = 0;
+    while ((1ll << b) < v) ++b;
+    return b;
+}
+
+dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
+{
+    if (!cfg || cfg->n_instances < 1 || !cfg->inst) { err = "config needs n_instances >= 1"; return DEM_ERR_ARG; }
+    if (cfg->max_neighbors < 1 || cfg->max_neighbors > MAXL) { err = "max_neighbors must be in 1..64"; return DEM_ERR_ARG; }
+    p.B = cfg->n_instances;
+    p.Lmax = cfg->max_neighbors;
+    long long slot = 0;
+    unsigned code = 0;
+    for (int k = 0; k < p.B; ++k) {
+        const dem_instance_desc& s = cfg->inst[k];
+        char buf[256];
+        if (s.n < 0 || s.capacity < s.n || s.capacity < 1) { snprintf(buf, sizeof buf, "instance %d: need 0 <= n <= capacity, capacity >= 1", k); err = buf; return DEM_ERR_ARG; }
+        if (s.periodic[2]) { snprintf(buf, sizeof buf, "instance %d: z cannot be periodic", k); err = buf; return DEM_ERR_ARG; }
+        if (!(s.dt > 0) || !(s.skin > 0) || !(s.r_max > 0) || !(s.E > 0) || !(s.e > 0 && s.e <= 1) || !(s.mu >= 0) ||
+            !(s.nu > -1 && s.nu < 0.5) || !(s.rho > 0)) {
+            snprintf(buf, sizeof buf, "instance %d: dt, skin, r_max, E, rho > 0; 0 < e <= 1; mu >= 0; -1 < nu < 0.5", k);
+            err = buf;
+            return DEM_ERR_ARG;
+        }
+        double ext[3], emax = 0;
+        for (int a = 0; a < 3; ++a) {
+            ext[a] = s.hi[a] - s.lo[a];
+            if (!(ext[a] > 0)) { snprintf(buf, sizeof buf, "instance %d: empty box", k); err = buf; return DEM_ERR_ARG; }
+            emax = std::max(emax, ext[a]);
+        }
+        // quantum: smallest power of two with emax / q <= 2^30
+        int e2 = (int)std::ceil(std::log2(emax / 1073741824.0));
+        double q = std::ldexp(1.0, e2);
+        while (emax / q > 1073741824.0) q *= 2.0;
+        InstC c{};
+        HostInstLo h{};
+        c.slot0 = (int)slot;
+        c.cap = (int)s.capacity;
+        const long long rmax_u = (long long)std::ceil(s.r_max / q);
+        const long long skin_u = (long long)std::llround(s.skin / q);
+        const long long hcell = 2 * rmax_u + skin_u;
+        for (int a = 0; a < 3; ++a) {
+            long long eu = (long long)std::llround(ext[a] / q);
+            c.ext[a] = (int)eu;
+            c.per[a] = s.periodic[a] ? 1 : 0;
+            c.half[a] = (int)(eu / 2);
+            long long n = eu / hcell;
+            if (c.per[a] && n < 3) { snprintf(buf, sizeof buf, "instance %d: periodic axis %d shorter than 3 cells (2 r_max + skin)", k, a); err = buf; return DEM_ERR_ARG; }
+            if (n < 1) n = 1;
+            if (n > 4096) n = 4096;
+            c.nc[a] = (int)n;
+            h.lo[a] = s.lo[a];
+        }
+        int bits[3], tb = 0;
+        for (int a = 0; a < 3; ++a) { bits[a] = ceil_log2(c.nc[a]); tb += bits[a]; }
+        if (tb > 28) { snprintf(buf, sizeof buf, "instance %d: cell grid too large", k); err = buf; return DEM_ERR_ARG; }
+        // Morton spread tables
+        int pos_of[3][32];
+        {
+            int pos = 0;
+            for (int b = 0; b < 32; ++b)
+                for (int a = 0; a < 3; ++a)
+                    if (b < bits[a]) pos_of[a][b] = pos++;
+        }
+        for (int a = 0; a < 3; ++a) {
+            c.spread_off[a] = (int)p.spread.size();
+            for (int v = 0; v < c.nc[a]; ++v) {
+                unsigned sv = 0;
+                for (int b = 0; b < bits[a]; ++b)
+                    if ((v >> b) & 1) sv |= 1u << pos_of[a][b];
+                p.spread.push_back(sv);
+            }
+        }
+        c.code0 = (int)code;
+        c.ncode = 1 << tb;
+        code += (unsigned)c.ncode;
+        c.floor_on = s.floor_on ? 1 : 0;
+        c.skin = (int)skin_u;
+        c.skin_f = (float)skin_u;
+        c.clamp_fn = s.clamp_fn ? 1 : 0;
+        c.q = (float)q;
+        c.dt = (float)s.dt;
+        c.dt_over_q = (float)(s.dt / q);
+        for (int a = 0; a < 3; ++a) { c.g[a] = (float)s.g[a]; c.floor_v[a] = (float)s.floor_v[a]; }
+        const double nu = s.nu, E = s.E;
+        const double Eeff = 1.0 / (2.0 * (1.0 - nu * nu) / E);
+        const double Geff = 1.0 / (2.0 * 2.0 * (2.0 - nu) * (1.0 + nu) / E);
+        const double le = std::log(s.e);
+        const double beta = le / std::sqrt(le * le + M_PI * M_PI);
+        c.c_kn = (float)(4.0 / 3.0 * Eeff);
+        c.c_kt = (float)(8.0 * Geff);
+        c.nbeta = (float)(-beta);
+        c.mu = (float)s.mu;
+        c.mu_w = (float)(s.mu_wall < 0 ? s.mu : s.mu_wall);
+        h.q = q;
+        h.rho = s.rho;
+        p.ic.push_back(c);
+        p.hl.push_back(h);
+        p.count.push_back(s.n);
+        const long long tiles = (s.capacity + TILE - 1) / TILE;
+        for (long long t = 0; t < tiles; ++t) p.tile_inst.push_back(k);
+        slot += tiles * TILE;
+        if (slot > (1ll << 30)) { err = "total capacity too large"; return DEM_ERR_ARG; }
+    }
+    p.ncap = (int)slot;
+    p.ntiles = (int)(slot / TILE);
+    p.ncodes = code;
+    p.nparts = (code + SCAN_TILE - 1) / SCAN_TILE;
+    Layout L;
+    const size_t N = (size_t)p.ncap, Lm = (size_t)p.Lmax;
+    for (int b = 0; b < 2; ++b) {
+        p.o_pos[b] = L.take(N * 16);
+        p.o_vel[b] = L.take(N * 16);
+        p.o_omg[b] = L.take(N * 16);
+        p.o_nbr[b] = L.take(N * Lm * 4);
+        p.o_hist[b] = L.take(N * Lm * 12);
+        p.o_cnt[b] = L.take(N * 4);
+        p.o_whist[b] = L.take(N * 16);
+    }
+    p.o_cellcode = L.take(N * 4);
+    p.o_cslot = L.take(N * 4);
+    p.o_perm = L.take(N * 4);
+    p.o_ccount = L.take((size_t)p.ncodes * 4);
+    p.o_cstart = L.take((size_t)p.ncodes * 4);
+    p.o_part = L.take((size_t)std::max(1u, p.nparts) * 4);
+    p.o_soi = L.take(N * 4);
+    p.o_tile = L.take((size_t)p.ntiles * 4);
+    p.o_ic = L.take(sizeof(InstC) * p.B);
+    p.o_id = L.take(sizeof(InstD) * p.B);
+    p.o_spread = L.take(p.spread.size() * 4);
+    p.o_g = L.take(sizeof(Glob));
+    p.o_goff = L.take(sizeof(long long) * (p.B + 1));
+    p.o_outF = L.take(N * 16);
+    p.o_outT = L.take(N * 16);
+    p.o_outV = L.take(N * 16);
+    p.o_outW = L.take(N * 16);
+    p.o_outWX = L.take(N * 16);
+    p.o_xi = L.take(N * Lm * 12);
+    p.o_cmask = L.take(N * 8);
+    p.o_stage = L.take(N * 24);
+    p.o_hl = L.take(sizeof(HostInstLo) * p.B);
+    p.bytes = L.total;
+    return DEM_OK;
+}
+
+inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+dem_status upload_goff(dem_ctx* ctx)
+{
+    std::vector<long long> goff(ctx->B + 1, 0);
+    for (int k = 0; k < ctx->B; ++k) goff[k + 1] = goff[k] + ctx->count[k];
+    CU(cudaMemcpyAsync(ctx->dev.goff, goff.data(), sizeof(long long) * (ctx->B + 1), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+long long total_count(const dem_ctx* ctx)
+{
+    long long t = 0;
+    for (long long c : ctx->count) t += c;
+    return t;
+}
+
+dem_status check_status(dem_ctx* ctx)
+{
+    if (!ctx->status) return DEM_OK;
+    if (ctx->status & ST_NONFINITE) return fail(ctx, DEM_ERR_NONFINITE, "non-finite force, torque or velocity on the device");
+    if (ctx->status & ST_ESCAPED) return fail(ctx, DEM_ERR_ESCAPED, "a particle left the representable range");
+    if (ctx->status & ST_CAPACITY) return fail(ctx, DEM_ERR_CAPACITY, "neighbour list wider than max_neighbors");
+    if (ctx->status & ST_TIMEOUT) return fail(ctx, DEM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (ctx->status & ST_TRUNC) return fail(ctx, DEM_ERR_CAPACITY, "more contacts than the output width");
+    return DEM_ERR_STATE;
+}
+
+// launch the rebuild chain (each kernel returns at once when no instance is flagged)
+dem_status launch_rebuild(dem_ctx* ctx, cudaStream_t st)
+{
+    const Dev& d = ctx->dev;
+    k_rb_clear<<<std::min(nblk(ctx->ncodes, 256), 152u * 16u), 256, 0, st>>>(d);
+    k_rb_bin<<<nblk(ctx->ncap, 256), 256, 0, st>>>(d);
+    k_scan_reduce<<<std::max(1u, ctx->nparts), SCAN_T, 0, st>>>(d);
+    k_scan_top<<<1, 1024, 0, st>>>(d);
+    k_scan_down<<<std::max(1u, ctx->nparts), SCAN_T, 0, st>>>(d);
+    k_rb_scatter<<<nblk(ctx->ncap, 256), 256, 0, st>>>(d);
+    k_rb_cellsort<<<nblk(ctx->ncap, 256), 256, 0, st>>>(d);
+    k_rb_build<<<nblk(ctx->ncap, 128), 128, 0, st>>>(d);
+    k_rb_finish<<<1, 256, 0, st>>>(d);
+    CU(cudaGetLastError());
+    return DEM_OK;
+}
+
+dem_status launch_eval(dem_ctx* ctx)
+{
+    dem_status st = launch_rebuild(ctx, ctx->stream);
+    if (st) return st;
+    k_step<1><<<ctx->ntiles, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
+    CU(cudaGetLastError());
+    return DEM_OK;
+}
+
+// mark every instance for a rebuild with cleared histories (fresh state)
+__global__ void k_mark_fresh(Dev d)
+{
+    for (int k = threadIdx.x; k < d.B; k += blockDim.x) {
+        d.id[k].flag = 2;
+        d.id[k].disp = 0.f;
+        d.id[k].stepmax = 0u;
+    }
+    if (threadIdx.x == 0) d.g->any = 1u;
+}
+
+void destroy_graph(dem_ctx* ctx)
+{
+    for (cudaEvent_t e : ctx->ev0) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->ev1) cudaEventDestroy(e);
+    ctx->ev0.clear();
+    ctx->ev1.clear();
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->rb_graph) cudaGraphDestroy(ctx->rb_graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+    ctx->rb_graph = nullptr;
+}
+
+dem_status build_graph(dem_ctx* ctx, int S)
+{
+    destroy_graph(ctx);
+    if (S <= 0) return DEM_OK;
+    // the rebuild chain, captured once
+    cudaStream_t cs;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    dem_status st = launch_rebuild(ctx, cs);
+    cudaGraph_t rb = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &rb);
+    cudaStreamDestroy(cs);
+    if (st) return st;
+    if (ce != cudaSuccess) return fail(ctx, DEM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    ctx->rb_graph = rb;
+    cudaGraph_t g;
+    CU(cudaGraphCreate(&g, 0));
+    ctx->graph = g;
+    std::vector<cudaGraphConditionalHandle> h(S);
+    for (int i = 0; i < S; ++i) CU(cudaGraphConditionalHandleCreate(&h[i], g, 0, 0));
+    Dev dv = ctx->dev;
+    cudaGraphNode_t prev;
+    {
+        cudaKernelNodeParams kp{};
+        void* args[] = {&dv, &h[0]};
+        kp.func = (void*)k_set_cond;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = args;
+        CU(cudaGraphAddKernelNode(&prev, g, nullptr, 0, &kp));
+    }
+    ctx->ev0.resize(S);
+    ctx->ev1.resize(S);
+    for (int i = 0; i < S; ++i) {
+        CU(cudaEventCreate(&ctx->ev0[i]));
+        CU(cudaEventCreate(&ctx->ev1[i]));
+    }
+    for (int i = 0; i < S; ++i) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h[i];
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        CU(cudaGraphAddNode(&cn, g, &prev, nullptr, 1, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t child;
+        CU(cudaGraphAddChildGraphNode(&child, body, nullptr, 0, rb));
+        int prime = 0;
+        int use_cond = i + 1 < S ? 1 : 0;
+        cudaGraphConditionalHandle hn = i + 1 < S ? h[i + 1] : h[i];
+        void* args[] = {&dv, &prime, &hn, &use_cond};
+        cudaKernelNodeParams kp{};
+        kp.func = (void*)k_step<0>;
+        kp.gridDim = dim3(ctx->ntiles);
+        kp.blockDim = dim3(TILE);
+        kp.kernelParams = args;
+        cudaGraphNode_t e0, kn, e1;
+        CU(cudaGraphAddEventRecordNode(&e0, g, &cn, 1, ctx->ev0[i]));
+        CU(cudaGraphAddKernelNode(&kn, g, &e0, 1, &kp));
+        CU(cudaGraphAddEventRecordNode(&e1, g, &kn, 1, ctx->ev1[i]));
+        prev = e1;
+    }
+    CU(cudaGraphInstantiate(&ctx->gexec, g, 0));
+    ctx->graph_steps = S;
+    return DEM_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+dem_status dem_query_workspace(const dem_config* cfg, int64_t* bytes_out)
+{
+    if (!bytes_out) return DEM_ERR_ARG;
+    Plan p;
+    dem_status st = make_plan(cfg, p, g_cfg_err);
+    if (st) return st;
+    *bytes_out = (int64_t)p.bytes;
+    return DEM_OK;
+}
+
+dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_bytes, void* stream, dem_ctx** out)
+{
+    if (!out) return DEM_ERR_ARG;
+    *out = nullptr;
+    Plan p;
+    dem_status st = make_plan(cfg, p, g_cfg_err);
+    if (st) return st;
+    if (!workspace || (size_t)workspace_bytes < p.bytes || ((uintptr_t)workspace & 255)) {
+        g_cfg_err = "workspace missing, too small or not 256-byte aligned";
+        return DEM_ERR_ARG;
+    }
+    dem_ctx* ctx = new dem_ctx();
+    ctx->stream = (cudaStream_t)stream;
+    cudaGetDevice(&ctx->device);
+    ctx->B = p.B;
+    ctx->Lmax = p.Lmax;
+    ctx->ncap = p.ncap;
+    ctx->ntiles = p.ntiles;
+    ctx->ncodes = p.ncodes;
+    ctx->nparts = p.nparts;
+    ctx->ic = p.ic;
+    ctx->hl = p.hl;
+    ctx->count = p.count;
+    char* base = (char*)workspace;
+    Dev& d = ctx->dev;
+    for (int b = 0; b < 2; ++b) {
+        d.pos[b] = (int4*)(base + p.o_pos[b]);
+        d.vel[b] = (float4*)(base + p.o_vel[b]);
+        d.omg[b] = (float4*)(base + p.o_omg[b]);
+        d.nbr[b] = (int*)(base + p.o_nbr[b]);
+        d.hist[b] = (float*)(base + p.o_hist[b]);
+        d.cnt[b] = (int*)(base + p.o_cnt[b]);
+        d.whist[b] = (float4*)(base + p.o_whist[b]);
+    }
+    d.cellcode = (unsigned*)(base + p.o_cellcode);
+    d.cslot = (unsigned*)(base + p.o_cslot);
+    d.perm = (int*)(base + p.o_perm);
+    d.ccount = (unsigned*)(base + p.o_ccount);
+    d.cstart = (unsigned*)(base + p.o_cstart);
+    d.part = (unsigned*)(base + p.o_part);
+    d.slot_of_id = (int*)(base + p.o_soi);
+    d.tile_inst = (int*)(base + p.o_tile);
+    d.ic = (const InstC*)(base + p.o_ic);
+    d.id = (InstD*)(base + p.o_id);
+    d.spread = (const unsigned*)(base + p.o_spread);
+    d.g = (Glob*)(base + p.o_g);
+    d.goff = (long long*)(base + p.o_goff);
+    d.outF = (float4*)(base + p.o_outF);
+    d.outT = (float4*)(base + p.o_outT);
+    d.outV = (float4*)(base + p.o_outV);
+    d.outW = (float4*)(base + p.o_outW);
+    d.outWX = (float4*)(base + p.o_outWX);
+    d.xi_out = (float*)(base + p.o_xi);
+    d.cmask = (unsigned long long*)(base + p.o_cmask);
+    d.stage = (double*)(base + p.o_stage);
+    ctx->d_hl = (HostInstLo*)(base + p.o_hl);
+    d.ncap = p.ncap;
+    d.ntiles = p.ntiles;
+    d.B = p.B;
+    d.Lmax = p.Lmax;
+    d.ncodes = p.ncodes;
+    d.nparts = p.nparts;
+    std::vector<InstD> idv(p.B);
+    for (int k = 0; k < p.B; ++k) {
+        idv[k] = InstD{};
+        idv[k].n = (int)p.count[k];
+        idv[k].flag = 2;
+    }
+    Glob gl{};
+    gl.any = 1u;
+    cudaStream_t s = ctx->stream;
+#define CUC(call)                                                    \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) {                                     \
+            delete ctx;                                              \
+            return DEM_ERR_CUDA;                                     \
+        }                                                            \
+    } while (0)
+    CUC(cudaMemcpyAsync((void*)d.ic, p.ic.data(), sizeof(InstC) * p.B, cudaMemcpyHostToDevice, s));
+    CUC(cudaMemcpyAsync(d.id, idv.data(), sizeof(InstD) * p.B, cudaMemcpyHostToDevice, s));
+    CUC(cudaMemcpyAsync((void*)d.spread, p.spread.data(), p.spread.size() * 4, cudaMemcpyHostToDevice, s));
+    CUC(cudaMemcpyAsync(d.tile_inst, p.tile_inst.data(), p.tile_inst.size() * 4, cudaMemcpyHostToDevice, s));
+    CUC(cudaMemcpyAsync(d.g, &gl, sizeof(Glob), cudaMemcpyHostToDevice, s));
+    CUC(cudaMemcpyAsync(ctx->d_hl, p.hl.data(), sizeof(HostInstLo) * p.B, cudaMemcpyHostToDevice, s));
+    CUC(cudaMemsetAsync(d.hist[0], 0, (size_t)p.ncap * p.Lmax * 12, s));
+    CUC(cudaMemsetAsync(d.hist[1], 0, (size_t)p.ncap * p.Lmax * 12, s));
+    k_init_ids<<<nblk(p.ncap, 256), 256, 0, s>>>(d);
+    CUC(cudaGetLastError());
+    CUC(cudaStreamSynchronize(s));
+#undef CUC
+    if (upload_goff(ctx)) {
+        delete ctx;
+        return DEM_ERR_CUDA;
+    }
+    *out = ctx;
+    return DEM_OK;
+}
+
+dem_status dem_destroy(dem_ctx* ctx)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    destroy_graph(ctx);
+    delete ctx;
+    return DEM_OK;
+}
+
+static bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int field_width(int f)
+{
+    switch (f) {
+    case DEM_F_POS: case DEM_F_VEL: case DEM_F_OMEGA: case DEM_F_FORCE: case DEM_F_TORQUE: case DEM_F_WALL_XI: return 3;
+    case DEM_F_RADIUS: case DEM_F_MASS: case DEM_F_NBR_COUNT: return 1;
+    default: return 0;
+    }
+}
+
+dem_status dem_write(dem_ctx* ctx, int32_t field, const void* src, int64_t n)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    const int w = field_width(field);
+    if (w == 0 || field == DEM_F_FORCE || field == DEM_F_TORQUE || field == DEM_F_WALL_XI || field == DEM_F_NBR_COUNT)
+        return fail(ctx, DEM_ERR_ARG, "field is not writable");
+    if (n != total_count(ctx)) return fail(ctx, DEM_ERR_ARG, "n must equal the total particle count");
+    if (n == 0) return DEM_OK;
+    if (!src) return fail(ctx, DEM_ERR_ARG, "null source");
+    const double* dsrc = (const double*)src;
+    if (!is_device_ptr(src)) {
+        CU(cudaMemcpyAsync(ctx->dev.stage, src, (size_t)n * w * 8, cudaMemcpyHostToDevice, ctx->stream));
+        dsrc = ctx->dev.stage;
+    }
+    k_write_field<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->dev, field, dsrc, n, ctx->d_hl);
+    CU(cudaGetLastError());
+    k_mark_fresh<<<1, 256, 0, ctx->stream>>>(ctx->dev);
+    CU(cudaGetLastError());
+    if (dsrc == ctx->dev.stage) CU(cudaStreamSynchronize(ctx->stream));
+    ctx->fresh = true;
+    ctx->have_state = true;
+    return DEM_OK;
+}
+
+dem_status dem_read(dem_ctx* ctx, int32_t field, void* dst, int64_t n)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    const int w = field_width(field);
+    if (w == 0) return fail(ctx, DEM_ERR_ARG, "unknown field");
+    if (n != total_count(ctx)) return fail(ctx, DEM_ERR_ARG, "n must equal the total particle count");
+    if (n == 0) return DEM_OK;
+    if (!dst) return fail(ctx, DEM_ERR_ARG, "null destination");
+    if (field == DEM_F_VEL || field == DEM_F_OMEGA || field == DEM_F_FORCE || field == DEM_F_TORQUE ||
+        field == DEM_F_WALL_XI || field == DEM_F_NBR_COUNT) {
+        dem_status st = launch_eval(ctx);
+        if (st) return st;
+    }
+    const bool dev = is_device_ptr(dst);
+    double* ddst = dev ? (double*)dst : ctx->dev.stage;
+    k_read_field<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->dev, field, ddst, n, ctx->d_hl);
+    CU(cudaGetLastError());
+    if (!dev) {
+        CU(cudaMemcpyAsync(dst, ddst, (size_t)n * w * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return DEM_OK;
+}
+
+dem_status dem_read_contacts(dem_ctx* ctx, int32_t* partner, double* xi, int32_t width, int64_t n)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    if (ctx->B != 1) return fail(ctx, DEM_ERR_ARG, "contacts I/O needs a single-instance context");
+    if (n != total_count(ctx) || width < 1 || !partner || !xi) return fail(ctx, DEM_ERR_ARG, "bad contacts arguments");
+    if (!is_device_ptr(partner) || !is_device_ptr(xi)) return fail(ctx, DEM_ERR_ARG, "contacts buffers must be device memory");
+    dem_status st = launch_eval(ctx);
+    if (st) return st;
+    k_read_contacts<<<nblk(ctx->ncap, 256), 256, 0, ctx->stream>>>(ctx->dev, partner, xi, width);
+    CU(cudaGetLastError());
+    return DEM_OK;
+}
+
+dem_status dem_write_contacts(dem_ctx* ctx, const int32_t* partner, const double* xi, int32_t width, int64_t n)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    if (ctx->B != 1) return fail(ctx, DEM_ERR_ARG, "contacts I/O needs a single-instance context");
+    if (n != total_count(ctx) || width < 1 || !partner || !xi) return fail(ctx, DEM_ERR_ARG, "bad contacts arguments");
+    if (!is_device_ptr(partner) || !is_device_ptr(xi)) return fail(ctx, DEM_ERR_ARG, "contacts buffers must be device memory");
+    dem_status st = launch_rebuild(ctx, ctx->stream);
+    if (st) return st;
+    k_write_contacts<<<nblk(ctx->ncap, 256), 256, 0, ctx->stream>>>(ctx->dev, partner, xi, width);
+    CU(cudaGetLastError());
+    return DEM_OK;
+}
+
+dem_status dem_step(dem_ctx* ctx, int64_t nsteps)
+{
+    if (!ctx || nsteps < 0) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    if (!ctx->have_state) return fail(ctx, DEM_ERR_STATE, "write the state before stepping");
+    int64_t done = 0;
+    while (done < nsteps) {
+        if (!ctx->fresh && ctx->gexec && nsteps - done >= ctx->graph_steps) {
+            CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
+            done += ctx->graph_steps;
+            continue;
+        }
+        dem_status st = launch_rebuild(ctx, ctx->stream);
+        if (st) return st;
+        k_step<0><<<ctx->ntiles, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
+        CU(cudaGetLastError());
+        ctx->fresh = false;
+        ++done;
+    }
+    ctx->steps += nsteps;
+    return DEM_OK;
+}
+
+dem_status dem_sync_status(dem_ctx* ctx)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    CU(cudaStreamSynchronize(ctx->stream));
+    unsigned stv = 0;
+    CU(cudaMemcpy(&stv, &ctx->dev.g->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    ctx->status |= stv;
+    return check_status(ctx);
+}
+
+dem_status dem_instance_info_get(dem_ctx* ctx, int32_t k, dem_instance_info* out)
+{
+    if (!ctx || !out || k < 0 || k >= ctx->B) return DEM_ERR_ARG;
+    const InstC& c = ctx->ic[k];
+    const HostInstLo& h = ctx->hl[k];
+    out->q = h.q;
+    for (int a = 0; a < 3; ++a) {
+        out->lo[a] = h.lo[a];
+        out->hi[a] = h.lo[a] + (double)c.ext[a] * h.q;
+        out->ncell[a] = c.nc[a];
+    }
+    out->n = ctx->count[k];
+    out->capacity = c.cap;
+    return DEM_OK;
+}
+
+dem_status dem_stats(dem_ctx* ctx, dem_stats_t* out)
+{
+    if (!ctx || !out) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    memset(out, 0, sizeof(*out));
+    out->steps = ctx->steps;
+    out->particles = total_count(ctx);
+    if (!ctx->have_state) return DEM_OK;
+    dem_status st = launch_eval(ctx);
+    if (st) return st;
+    CU(cudaMemsetAsync(&ctx->dev.g->sum_list, 0, 16, ctx->stream));
+    k_stats<<<nblk(ctx->ncap, 256), 256, 0, ctx->stream>>>(ctx->dev);
+    CU(cudaGetLastError());
+    Glob gl;
+    CU(cudaMemcpyAsync(&gl, ctx->dev.g, sizeof(Glob), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    out->rebuilds = (int64_t)gl.rebuilds;
+    out->list_entries = (int64_t)gl.sum_list;
+    out->contacts = (int64_t)gl.sum_contacts;
+    ctx->status |= gl.status;
+    return check_status(ctx);
+}
+
+dem_status dem_set_graph(dem_ctx* ctx, int32_t steps_per_graph)
+{
+    if (!ctx || steps_per_graph < 0 || steps_per_graph > 4096) return DEM_ERR_ARG;
+    return build_graph(ctx, steps_per_graph);
+}
+
+dem_status dem_graph_step_kernel_ms(dem_ctx* ctx, double* total_ms, int32_t* count)
+{
+    if (!ctx || !total_ms || !count) return DEM_ERR_ARG;
+    if (!ctx->gexec) return fail(ctx, DEM_ERR_STATE, "no step graph has been built");
+    CU(cudaStreamSynchronize(ctx->stream));
+    double t = 0.0;
+    for (size_t i = 0; i < ctx->ev0.size(); ++i) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, ctx->ev0[i], ctx->ev1[i]));
+        t += ms;
+    }
+    *total_ms = t;
+    *count = (int32_t)ctx->ev0.size();
+    return DEM_OK;
+}
+
+const char* dem_last_error(const dem_ctx* ctx)
+{
+    if (!ctx) return g_cfg_err.c_str();
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

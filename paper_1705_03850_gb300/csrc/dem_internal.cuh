@@ -1,0 +1,119 @@
+// Internal layout shared by the library's translation units (never by the oracle).
+//
+// Device data of a context (all carved from the caller's workspace):
+//   slots      particles of instance k live in slots [slot0_k, slot0_k + n_k);
+//              slot0_k is a multiple of TILE so that a thread block of the step
+//              kernel never straddles two instances.
+//   state      double-buffered SoA, 48 B per particle:
+//                pos int4   {x, y, z, r}  32-bit fixed point, units of q
+//                vel float4 {vx, vy, vz, id | floor-contact bit 31}
+//                omg float4 {wx, wy, wz, m}
+//              buffer cur_k holds step n, the step kernel writes cur_k ^ 1.
+//   lists      double-buffered (parity lp_k), entry-major for coalescing:
+//                nbr  int32 [Lmax][ncap]      slot of the e-th neighbour
+//                hist float  [3][Lmax][ncap]  tangential overlap of entry e,
+//                                             in the frame of the pair's lower ID
+//                cnt  int32 [ncap]            row length; rows are sorted by
+//                                             neighbour ID
+//                whist float4 [ncap]          floor-contact tangential overlap
+//   cells      per instance a Morton-ordered code range [code0_k, code0_k + ncode_k)
+//              with counts and exclusive starts, rebuilt with the lists.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cgdem {
+
+constexpr int TILE = 128;      // step-kernel block size = slot alignment of an instance
+constexpr int MAXL = 64;       // largest list width
+constexpr unsigned ID_MASK = 0x7fffffffu;
+constexpr unsigned WALL_BIT = 0x80000000u;
+
+// device status bits
+constexpr unsigned ST_CAPACITY = 1u;
+constexpr unsigned ST_NONFINITE = 2u;
+constexpr unsigned ST_ESCAPED = 4u;
+constexpr unsigned ST_TIMEOUT = 8u;
+constexpr unsigned ST_TRUNC = 16u;
+
+// constant description of one instance (host-computed at create)
+struct InstC {
+    int slot0, cap;
+    int ext[3];          // box extent per axis in units of q
+    int per[3];          // periodic flags
+    int half[3];         // ext / 2 on periodic axes
+    int nc[3];           // cells per axis
+    int spread_off[3];   // offsets of the per-axis Morton spread tables
+    int code0, ncode;
+    int floor_on;
+    int skin;            // skin in units
+    int clamp_fn;
+    int pad0;
+    float q, dt, dt_over_q, skin_f;
+    float g[3];
+    float floor_v[3];
+    float c_kn, c_kt, nbeta, mu, mu_w;   // 4/3 E_eff, 8 G_eff, -beta, mu, mu_wall
+    float pad1;
+};
+
+// dynamic state of one instance (device-resident)
+struct InstD {
+    int n;               // live particles
+    int cur;             // state buffer holding the current step
+    int lp;              // list buffer parity
+    int flag;            // 0 none, 1 rebuild pending, 2 rebuild with cleared history
+    float disp;          // accumulated per-step displacement bound since the last build [units]
+    unsigned stepmax;    // this step's largest displacement (float bits)
+    int pad[2];
+};
+
+struct Glob {
+    unsigned status;
+    unsigned any;              // some instance has flag != 0
+    unsigned counter;          // last-block detection of the step kernel
+    unsigned pad;
+    unsigned long long rebuilds;
+    unsigned long long sum_list;
+    unsigned long long sum_contacts;
+    long long err_slot;
+};
+
+// kernel-visible pointers of a context
+struct Dev {
+    int4* pos[2];
+    float4* vel[2];
+    float4* omg[2];
+    int* nbr[2];
+    float* hist[2];
+    int* cnt[2];
+    float4* whist[2];
+    unsigned* cellcode;
+    unsigned* cslot;
+    int* perm;
+    unsigned* ccount;
+    unsigned* cstart;
+    unsigned* part;
+    int* slot_of_id;
+    int* tile_inst;
+    const InstC* ic;
+    InstD* id;
+    const unsigned* spread;
+    Glob* g;
+    long long* goff;           // [B+1] global offsets of instances in user arrays
+    float4* outF;
+    float4* outT;
+    float4* outV;
+    float4* outW;
+    float4* outWX;             // floor-contact xi at the evaluated step
+    float* xi_out;             // [3][Lmax][ncap]
+    unsigned long long* cmask; // contact bits per list entry at the evaluated step
+    double* stage;             // [3 * ncap] staging for host transfers
+    int ncap;
+    int ntiles;
+    int B;
+    int Lmax;
+    unsigned ncodes;
+    unsigned nparts;
+};
+
+}  // namespace cgdem

@@ -1,0 +1,263 @@
+"""Thin ctypes binding of the C ABI in include/dem.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA library ``_build/libcgdem.so``;
+this module only allocates the caller-owned workspace with PyTorch, passes
+PyTorch's current stream, and converts arrays.  There is no CPU fallback: if
+the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+# field ids (dem_field)
+POS, VEL, OMEGA, RADIUS, MASS, FORCE, TORQUE, WALL_XI, NBR_COUNT = range(9)
+_WIDTH = {POS: 3, VEL: 3, OMEGA: 3, RADIUS: 1, MASS: 1, FORCE: 3, TORQUE: 3, WALL_XI: 3, NBR_COUNT: 1}
+STATUS = {0: "DEM_OK", 1: "DEM_ERR_ARG", 2: "DEM_ERR_CAPACITY", 3: "DEM_ERR_CUDA", 4: "DEM_ERR_NONFINITE",
+          5: "DEM_ERR_ESCAPED", 6: "DEM_ERR_TIMEOUT", 7: "DEM_ERR_STATE"}
+
+
+class DemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class InstanceDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("capacity", ctypes.c_int64), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("periodic", ctypes.c_int32 * 3), ("floor_on", ctypes.c_int32),
+                ("floor_v", ctypes.c_double * 3), ("g", ctypes.c_double * 3), ("dt", ctypes.c_double),
+                ("skin", ctypes.c_double), ("r_max", ctypes.c_double), ("E", ctypes.c_double),
+                ("nu", ctypes.c_double), ("e", ctypes.c_double), ("mu", ctypes.c_double),
+                ("mu_wall", ctypes.c_double), ("rho", ctypes.c_double), ("clamp_fn", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
+                ("inst", ctypes.POINTER(InstanceDesc))]
+
+
+class InstanceInfo(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_double), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("ncell", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("capacity", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("list_entries", ctypes.c_int64),
+                ("contacts", ctypes.c_int64), ("particles", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcgdem.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError(f"CUDA library not built: {LIB} (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "dem_query_workspace": [ctypes.POINTER(Config), ctypes.POINTER(i64)],
+        "dem_create": [ctypes.POINTER(Config), vp, i64, vp, ctypes.POINTER(vp)],
+        "dem_destroy": [vp],
+        "dem_write": [vp, i32, vp, i64],
+        "dem_read": [vp, i32, vp, i64],
+        "dem_read_contacts": [vp, vp, vp, i32, i64],
+        "dem_write_contacts": [vp, vp, vp, i32, i64],
+        "dem_step": [vp, i64],
+        "dem_sync_status": [vp],
+        "dem_instance_info_get": [vp, i32, ctypes.POINTER(InstanceInfo)],
+        "dem_stats": [vp, ctypes.POINTER(Stats)],
+        "dem_set_graph": [vp, i32],
+        "dem_graph_step_kernel_ms": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.dem_last_error.argtypes = [vp]
+    L.dem_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    return ["dem_query_workspace", "dem_create", "dem_destroy", "dem_write", "dem_read", "dem_read_contacts",
+            "dem_write_contacts", "dem_step", "dem_sync_status", "dem_instance_info_get", "dem_stats",
+            "dem_set_graph", "dem_graph_step_kernel_ms", "dem_last_error"]
+
+
+def desc(*, n, lo, hi, periodic, dt, skin, r_max, E, nu, e, mu, rho, g=(0, 0, 0), floor=True,
+         floor_v=(0, 0, 0), mu_wall=None, capacity=None, clamp_fn=False) -> InstanceDesc:
+    d = InstanceDesc()
+    d.n = int(n)
+    d.capacity = int(capacity if capacity is not None else max(1, n))
+    for a in range(3):
+        d.lo[a], d.hi[a] = float(lo[a]), float(hi[a])
+        d.periodic[a] = 1 if periodic[a] else 0
+        d.floor_v[a] = float(floor_v[a])
+        d.g[a] = float(g[a])
+    d.floor_on = 1 if floor else 0
+    d.dt, d.skin, d.r_max = float(dt), float(skin), float(r_max)
+    d.E, d.nu, d.e, d.mu = float(E), float(nu), float(e), float(mu)
+    d.mu_wall = -1.0 if mu_wall is None else float(mu_wall)
+    d.rho = float(rho)
+    d.clamp_fn = 1 if clamp_fn else 0
+    return d
+
+
+def desc_from_workload(wl, capacity=None, r_max=None) -> InstanceDesc:
+    m = wl.material
+    return desc(n=wl.n, lo=wl.lo, hi=wl.hi, periodic=wl.periodic, dt=wl.dt, skin=wl.skin,
+                r_max=r_max if r_max is not None else float(np.max(wl.r)) if wl.n else 1e-3,
+                E=m.E, nu=m.nu, e=m.e, mu=m.mu, rho=m.rho, g=wl.g, floor=wl.floor, floor_v=wl.floor_v,
+                mu_wall=m.mu_wall, capacity=capacity)
+
+
+class DEM:
+    """A context of one or more DEM instances on the current CUDA device."""
+
+    def __init__(self, descs, max_neighbors=32, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("DEM needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.L = lib()
+        self.device = torch.device(device or "cuda")
+        if isinstance(descs, InstanceDesc):
+            descs = [descs]
+        self._descs = (InstanceDesc * len(descs))(*descs)
+        self.cfg = Config(len(descs), int(max_neighbors), self._descs)
+        nbytes = ctypes.c_int64()
+        self._check(self.L.dem_query_workspace(ctypes.byref(self.cfg), ctypes.byref(nbytes)), "query workspace")
+        self.workspace_bytes = int(nbytes.value)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+            self.stream = stream or torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        self._check(self.L.dem_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.workspace.data_ptr()),
+                                      self.workspace_bytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.byref(h)), "create")
+        self.h = h
+        self.counts = [int(d.n) for d in descs]
+
+    # ------------------------------------------------------------------
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = self.L.dem_last_error(getattr(self, "h", None)).decode()
+            raise DemError(rc, f"{what}: {msg}")
+
+    @property
+    def n(self):
+        return sum(self.counts)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.dem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _as_f64(self, a, width):
+        torch = self.torch
+        if isinstance(a, torch.Tensor):
+            t = a.to(dtype=torch.float64).contiguous()
+        else:
+            t = torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float64)))
+        if t.numel() != self.n * width:
+            raise ValueError(f"expected {self.n * width} values, got {t.numel()}")
+        return t
+
+    def write(self, field, values):
+        t = self._as_f64(values, _WIDTH[field])
+        self._check(self.L.dem_write(self.h, field, ctypes.c_void_p(t.data_ptr()), self.n), "write")
+        self._keep = t  # device-side source must outlive the asynchronous copy kernel
+        return self
+
+    def write_state(self, x, v, w, r, m=None):
+        self.write(POS, x).write(VEL, v).write(OMEGA, w).write(RADIUS, r)
+        if m is not None:
+            self.write(MASS, m)
+        return self
+
+    def read(self, field, out=None, host=True):
+        """Read a field; returns a float64 numpy array (host) or CUDA tensor."""
+        torch = self.torch
+        shape = (self.n, 3) if _WIDTH[field] == 3 else (self.n,)
+        if out is None:
+            out = (torch.empty(shape, dtype=torch.float64, device=self.device) if not host
+                   else torch.empty(shape, dtype=torch.float64).pin_memory())
+        self._check(self.L.dem_read(self.h, field, ctypes.c_void_p(out.data_ptr()), self.n), "read")
+        return out.numpy() if host and out.device.type == "cpu" else out
+
+    def read_contacts(self, width=16):
+        torch = self.torch
+        partner = torch.empty((self.n, width), dtype=torch.int32, device=self.device)
+        xi = torch.empty((self.n, width, 3), dtype=torch.float64, device=self.device)
+        self._check(self.L.dem_read_contacts(self.h, ctypes.c_void_p(partner.data_ptr()),
+                                             ctypes.c_void_p(xi.data_ptr()), width, self.n), "read contacts")
+        self.sync()
+        return partner.cpu().numpy(), xi.cpu().numpy()
+
+    def write_contacts(self, partner, xi):
+        torch = self.torch
+        p = torch.as_tensor(np.ascontiguousarray(partner, dtype=np.int32)).to(self.device)
+        x = torch.as_tensor(np.ascontiguousarray(xi, dtype=np.float64)).to(self.device)
+        width = p.shape[1]
+        self._check(self.L.dem_write_contacts(self.h, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                              width, self.n), "write contacts")
+        self.sync()
+        return self
+
+    def step(self, nsteps=1):
+        self._check(self.L.dem_step(self.h, int(nsteps)), "step")
+        return self
+
+    def sync(self):
+        self._check(self.L.dem_sync_status(self.h), "sync")
+        return self
+
+    def status(self):
+        return self.L.dem_sync_status(self.h)
+
+    def set_graph(self, steps_per_graph):
+        self._check(self.L.dem_set_graph(self.h, int(steps_per_graph)), "set graph")
+        return self
+
+    def graph_step_kernel_ms(self):
+        """(sum of step-kernel CUDA-event times in the last graph launch [ms], number of step kernels)."""
+        t, c = ctypes.c_double(), ctypes.c_int32()
+        self._check(self.L.dem_graph_step_kernel_ms(self.h, ctypes.byref(t), ctypes.byref(c)), "kernel times")
+        return t.value, c.value
+
+    def info(self, k=0):
+        inf = InstanceInfo()
+        self._check(self.L.dem_instance_info_get(self.h, k, ctypes.byref(inf)), "info")
+        return dict(q=inf.q, lo=tuple(inf.lo), hi=tuple(inf.hi), ncell=tuple(inf.ncell), n=inf.n,
+                    capacity=inf.capacity)
+
+    def stats(self):
+        st = Stats()
+        self._check(self.L.dem_stats(self.h, ctypes.byref(st)), "stats")
+        return dict(steps=st.steps, rebuilds=st.rebuilds, list_entries=st.list_entries, contacts=st.contacts,
+                    particles=st.particles)
+
+
+def from_workload(wl, max_neighbors=32, capacity=None, **kw) -> DEM:
+    """A single-instance context loaded with a workload's state."""
+    d = DEM([desc_from_workload(wl, capacity=capacity)], max_neighbors=max_neighbors, **kw)
+    d.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
+    return d

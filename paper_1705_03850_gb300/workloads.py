@@ -164,6 +164,14 @@ def dense_block(nx: int = 12, ny: int = 12, nz: int = 10, r: float = 1.0e-3, see
                    floor_v, 0.1 * 2 * r, 100)
 
 
+def single_sphere(r: float = 1.0e-3, z: float = 0.999e-3, v=(0.2, 0.05, -0.1), w=(30.0, -50.0, 10.0),
+                  mat: Material | None = None, dt: float = 1e-6) -> Workload:
+    """One sphere just touching the floor of a 10 mm periodic box, sliding and spinning."""
+    return _finish("single_sphere", np.array([[5e-3, 5e-3, z]]), np.array([v]), np.array([w]), np.array([r]),
+                   mat or Material(E=1e7, nu=0.25, e=0.6, mu=0.4, rho=2500.0), (0, 0, 0), (0.01, 0.01, 0.01),
+                   (True, True, False), dt, (0, 0, -9.81), True, (0.3, 0.0, 0.0), 0.1 * 2 * r, 400)
+
+
 def batch_sizes(count: int = 256, seed: int = 4, nmin: float = 2e3, nmax: float = 2e5) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.round(np.exp(rng.uniform(math.log(nmin), math.log(nmax), count))).astype(np.int64)

@@ -180,6 +180,37 @@ dem_status dem_set_graph(dem_ctx *ctx, int32_t steps_per_graph);
  * Synchronises the stream.  DEM_ERR_STATE if no graph was built. */
 dem_status dem_graph_step_kernel_ms(dem_ctx *ctx, double *total_ms, int32_t *count);
 
+/*
+ * Neighbour counts without any allocation or workspace.  The paper has no
+ * counterpart; this is a service for callers that cannot give the library
+ * device memory: a host solver or plugin framework that owns every device
+ * byte through its own pool and passes only its particle buffers, or a
+ * real-time loop that must not allocate after start-up.
+ *
+ * For n particles of one box it writes counts[i] = the number of j != i with
+ * |x_i - x_j| < r_i + r_j + skin (minimum image on periodic axes), with the
+ * positions, radii and skin rounded to the same length quantum and tested by
+ * the same exact integer arithmetic as a context built from this box, so the
+ * counts equal that context's neighbour-list lengths (DEM_F_NBR_COUNT).
+ *   x: device float64 (n,3); r: device float64 (n); counts: device int32 (n),
+ *   written asynchronously on `stream` (cudaStream_t, NULL = legacy default).
+ *   lo, hi, periodic: host arrays of 3; skin >= 0; r_max >= every r.
+ * Limits: n <= 262,144 particles and a cell grid (cell width >= 2 r_max +
+ * skin) of at most 262,144 cells; larger inputs return DEM_ERR_CAPACITY with
+ * a message in dem_last_error(NULL), before any GPU work.
+ * Memory: scratch is one fixed 9 MiB device array inside the library, held by
+ * every GPU that loads it until the process exits; nothing is allocated or
+ * freed.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with that device current; make this first call
+ * before any stream capture.  All calls share the array and each call
+ * re-initialises what it reads, so calls that overlap on the GPU (other
+ * streams, other threads, or concurrent contexts on the same device) race
+ * and must be serialised by the caller.
+ */
+dem_status dem_neighbor_counts_noalloc(const double *x, const double *r, int64_t n, const double lo[3],
+                                       const double hi[3], const int32_t periodic[3], double skin,
+                                       double r_max, int32_t *counts, void *stream);
+
 /* Last error message of the context; with ctx == NULL, the last configuration
  * error (dem_query_workspace / dem_create) of the calling thread.  Never NULL. */
 const char *dem_last_error(const dem_ctx *ctx);

@@ -1164,6 +1164,11 @@ dem_status build_graph(dem_ctx* ctx, int S)
 
 }  // namespace
 
+namespace cgdem {
+// error text reported by dem_last_error(NULL) for calls made without a context
+void set_thread_error(const std::string& msg) { g_cfg_err = msg; }
+}  // namespace cgdem
+
 // ================================================================== C ABI
 
 extern "C" {

@@ -79,6 +79,8 @@ def lib():
         "dem_stats": [vp, ctypes.POINTER(Stats)],
         "dem_set_graph": [vp, i32],
         "dem_graph_step_kernel_ms": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)],
+        "dem_neighbor_counts_noalloc": [vp, vp, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(i32), ctypes.c_double, ctypes.c_double, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -93,7 +95,7 @@ def lib():
 def exported_symbols():
     return ["dem_query_workspace", "dem_create", "dem_destroy", "dem_write", "dem_read", "dem_read_contacts",
             "dem_write_contacts", "dem_step", "dem_sync_status", "dem_instance_info_get", "dem_stats",
-            "dem_set_graph", "dem_graph_step_kernel_ms", "dem_last_error"]
+            "dem_set_graph", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_last_error"]
 
 
 def desc(*, n, lo, hi, periodic, dt, skin, r_max, E, nu, e, mu, rho, g=(0, 0, 0), floor=True,
@@ -254,6 +256,29 @@ class DEM:
         self._check(self.L.dem_stats(self.h, ctypes.byref(st)), "stats")
         return dict(steps=st.steps, rebuilds=st.rebuilds, list_entries=st.list_entries, contacts=st.contacts,
                     particles=st.particles)
+
+
+def neighbor_counts_noalloc(x, r, lo, hi, periodic, skin, r_max, out=None, stream=None):
+    """Neighbour counts through the allocation-free entry point (see include/dem.h).
+
+    x (n,3) and r (n,) are float64 CUDA tensors; the result is an int32 CUDA tensor
+    (the caller's `out` if given).  The library allocates nothing for this call.
+    """
+    import torch
+    L = lib()
+    n = int(r.shape[0])
+    if out is None:
+        out = torch.empty((n,), dtype=torch.int32, device=r.device)
+    st = stream or torch.cuda.current_stream(r.device)
+    lo3 = (ctypes.c_double * 3)(*[float(v) for v in lo])
+    hi3 = (ctypes.c_double * 3)(*[float(v) for v in hi])
+    per3 = (ctypes.c_int32 * 3)(*[1 if p else 0 for p in periodic])
+    rc = L.dem_neighbor_counts_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(r.data_ptr()), n, lo3, hi3,
+                                       per3, float(skin), float(r_max), ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise DemError(rc, L.dem_last_error(None).decode())
+    return out
 
 
 def from_workload(wl, max_neighbors=32, capacity=None, **kw) -> DEM:

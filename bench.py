@@ -38,8 +38,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
-    ap.add_argument("--settle", type=int, default=20_000)
-    ap.add_argument("--graph", type=int, default=50, help="steps per captured CUDA graph")
+    ap.add_argument("--settle", type=int, default=30_000, help="settling steps at dt 5e-6, e 0.5 (not timed)")
+    ap.add_argument("--graph", type=int, default=50, help="steps per captured CUDA graph (0: direct launches)")
+    ap.add_argument("--settle-graph", type=int, default=50, help="steps per graph while settling")
     ap.add_argument("--lmax", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
@@ -203,16 +204,20 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     S = args.graph
-    K = max(S, (args.steps // S) * S)
+    K = max(S, (args.steps // S) * S) if S > 0 else max(1, args.steps)
     W = max(3, args.warmup)
 
-    # ---- build and settle the bed (not timed)
+    # ---- build and settle the bed (not timed): larger step and more damping
+    # than the sheared run, so that the lattice collapses into a dense bed quickly
     wl = workloads.shear_bed(args.n, seed=2)
     desc = dem.desc_from_workload(wl, r_max=1.2e-3)
-    settle = dem.DEM([desc], max_neighbors=args.lmax, device=dev)
+    sdesc = dem.desc_from_workload(wl, r_max=1.2e-3)
+    sdesc.dt, sdesc.e = 5e-6, 0.5
+    settle = dem.DEM([sdesc], max_neighbors=args.lmax, device=dev)
     settle.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
     settle.step(1)
-    settle.set_graph(S)
+    if args.settle_graph > 0:
+        settle.set_graph(args.settle_graph)
     settle.step(max(0, args.settle - 1))
     settle.sync()
     x = settle.read(dem.POS, host=False)
@@ -228,8 +233,11 @@ def run_ours(args):
     sim = dem.DEM([desc], max_neighbors=args.lmax, device=dev)
     sim.write_state(x, v, w, r, m)
     sim.step(1)
-    sim.set_graph(S)
-    sim.step(((W + S - 1) // S) * S)
+    if S > 0:
+        sim.set_graph(S)
+        sim.step(((W + S - 1) // S) * S)
+    else:
+        sim.step(W)
     sim.sync()
     st0 = sim.stats()
 
@@ -244,7 +252,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
-    kern_ms, kern_n = sim.graph_step_kernel_ms()
+    kern_ms, kern_n = sim.graph_step_kernel_ms() if S > 0 else (float("nan"), 1)
     st1 = sim.stats()
     sim.sync()
     if world > 1:
@@ -255,8 +263,14 @@ def run_ours(args):
     value = n * K * world / (ms / 1e3)
     L = st1["list_entries"] / max(1, st1["particles"])
     C = st1["contacts"] / max(1, st1["particles"])
+    Wc = st1["wall_contacts"] / max(1, st1["particles"])
     rebuilds = st1["rebuilds"] - st0["rebuilds"]
-    B_step = 96.0 + 28.0 * L                   # algorithmic bytes per particle-step of the step kernel
+    # algorithmic bytes per particle-step of the step kernel, SURVEY.md 8(d):
+    # 48 B own state read + 48 B written, per list entry 4 B index + 12 B history read + 12 B written
+    B_step = 96.0 + 28.0 * L
+    # what this design must move at least: the same state, count and history mask,
+    # indices of every entry, history only of entries in contact, floor history
+    B_design = 96.0 + 4.0 + 8.0 + 4.0 * L + 24.0 * (C - Wc) + 32.0 * Wc
     t_kernel = kern_ms / max(1, kern_n) / 1e3
     achieved = n * B_step / t_kernel / 1e9
     peaks = _peaks()
@@ -264,7 +278,7 @@ def run_ours(args):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     traffic = _profile_traffic(_kernel_hash())
-    launches = K + K // S + 9 * rebuilds
+    launches = K + (K // S if S > 0 else 9 * K) + 9 * rebuilds
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -303,8 +317,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "shear_bed_1M: 1,000,000 polydisperse spheres, settled then floor-sheared",
+        "config": {"workload": f"shear_bed: {n:,} polydisperse spheres, settled then floor-sheared",
                    "n_particles": n, "dt": wl.dt, "skin_m": wl.skin, "settle_steps": args.settle,
+                   "settle": "dt 5e-6 s, e 0.5, from the FCC start",
                    "steps_per_graph": S, "max_neighbors": args.lmax,
                    "l2": "inputs larger than L2 (state + lists + histories > 129 MB)",
                    "mean_list_length": L, "mean_contacts_per_particle": C, "rebuilds_in_timed_region": rebuilds,
@@ -312,6 +327,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_src, "kernel": "k_step<0> (fused force + Verlet)",
                      "bytes_per_particle_step": B_step, "kernel_ms_avg": t_kernel * 1e3,
+                     "design_bytes_per_particle_step": B_design,
+                     "design_achieved": n * B_design / t_kernel / 1e9,
                      "kernel_share_of_step": t_kernel * 1e3 / (ms / K)},
         "clocks": clocks.summary(),
         "e2e": e2e,

@@ -100,7 +100,7 @@ typedef struct {
 
 typedef struct {
     int32_t n_instances;              /* >= 1 */
-    int32_t max_neighbors;            /* list width L_max, 1 .. 64 */
+    int32_t max_neighbors;            /* list width L_max, 1 .. 32 */
     const dem_instance_desc *inst;    /* n_instances descriptors (host memory) */
 } dem_config;
 
@@ -119,6 +119,7 @@ typedef struct {
     int64_t list_entries;    /* sum of list lengths at the last dem_stats call */
     int64_t contacts;        /* contacts (particle pairs counted from both sides + floor) at that call */
     int64_t particles;       /* live particles */
+    int64_t wall_contacts;   /* floor contacts among `contacts` */
 } dem_stats_t;
 
 /* Bytes of device workspace a context with this configuration needs. */

@@ -14,6 +14,11 @@
 
 using namespace cgdem;
 
+// minimum resident blocks per SM requested for the step kernel (register budget)
+#ifndef DEM_STEP_MINB
+#define DEM_STEP_MINB 8
+#endif
+
 // ====================================================================== scan
 // Exclusive scan of the per-cell counts into cell starts: three passes over
 // tiles of SCAN_TILE entries (per-tile sums, scan of the sums, tile scans).
@@ -206,8 +211,8 @@ __global__ void k_rb_cellsort(Dev d)
 
 // One thread per new slot: move the particle into the other state buffer,
 // collect neighbours within r_i + r_j + skin (exact integer test), order the
-// row by ID, and carry the tangential overlaps of pairs that were already
-// listed (merge-join on IDs with the particle's previous row).
+// row by overlap depth, and carry the tangential overlaps of pairs that were
+// already listed (found by ID in the particle's previous row).
 __global__ void __launch_bounds__(128) k_rb_build(Dev d)
 {
     if (!d.g->any) return;
@@ -231,6 +236,9 @@ __global__ void __launch_bounds__(128) k_rb_build(Dev d)
     d.omg[nxt][s] = w;
     d.slot_of_id[c.slot0 + (int)myid] = s;
 
+    // candidates ordered by (d^2 - (r_i + r_j)^2, ID): deepest overlaps first, so
+    // that within a warp the contacts sit in the leading entries of every row
+    long long cand_key[MAXL];
     int cand_id[MAXL];
     int cand_slot[MAXL];
     int nc = 0;
@@ -264,16 +272,21 @@ __global__ void __launch_bounds__(128) k_rb_build(Dev d)
                     const long long ddx = min_image(p.x - q.x, c.per[0], c.ext[0], c.half[0]);
                     const long long ddy = min_image(p.y - q.y, c.per[1], c.ext[1], c.half[1]);
                     const long long ddz = (long long)p.z - q.z;
+                    const long long d2 = ddx * ddx + ddy * ddy + ddz * ddz;
                     const long long cut = (long long)p.w + q.w + c.skin;
-                    if (ddx * ddx + ddy * ddy + ddz * ddz >= cut * cut) continue;
+                    if (d2 >= cut * cut) continue;
+                    const long long S = (long long)p.w + q.w;
+                    const long long key = d2 - S * S;
                     const int qid = (int)(__float_as_uint(d.vel[cur][o].w) & ID_MASK);
                     if (nc == Lmax) { overflow = true; continue; }
                     int j = nc - 1;
-                    while (j >= 0 && cand_id[j] > qid) {
+                    while (j >= 0 && (cand_key[j] > key || (cand_key[j] == key && cand_id[j] > qid))) {
+                        cand_key[j + 1] = cand_key[j];
                         cand_id[j + 1] = cand_id[j];
                         cand_slot[j + 1] = cand_slot[j];
                         --j;
                     }
+                    cand_key[j + 1] = key;
                     cand_id[j + 1] = qid;
                     cand_slot[j + 1] = m;
                     ++nc;
@@ -291,27 +304,31 @@ __global__ void __launch_bounds__(128) k_rb_build(Dev d)
     const int* orow = d.nbr[lp] + old;
     const float* ho = d.hist[lp] + old;
     const int ocnt = D.flag == 2 ? 0 : d.cnt[lp][old];
-    int eo = 0;
-    unsigned oid = 0xffffffffu;
-    if (eo < ocnt) oid = __float_as_uint(d.vel[cur][orow[0]].w) & ID_MASK;
+    int oid[MAXL];
+    for (int e = 0; e < ocnt; ++e) oid[e] = (int)(__float_as_uint(d.vel[cur][orow[(size_t)e * ncap]].w) & ID_MASK);
+    const unsigned ohm = D.flag == 2 ? 0u : d.hmask[lp][old];
+    unsigned nhm = 0u;
     for (int e = 0; e < nc; ++e) {
         nrow[(size_t)e * ncap] = cand_slot[e];
-        const unsigned id = (unsigned)cand_id[e];
-        while (eo < ocnt && oid < id) {
-            ++eo;
-            oid = eo < ocnt ? (__float_as_uint(d.vel[cur][orow[(size_t)eo * ncap]].w) & ID_MASK) : 0xffffffffu;
-        }
+        const int id = cand_id[e];
         float hx = 0.f, hy = 0.f, hz = 0.f;
-        if (eo < ocnt && oid == id) {
-            hx = ho[(size_t)eo * ncap];
-            hy = ho[plane + (size_t)eo * ncap];
-            hz = ho[2 * plane + (size_t)eo * ncap];
+        for (int eo = 0; eo < ocnt; ++eo) {
+            if (oid[eo] == id) {
+                if ((ohm >> eo) & 1u) {
+                    hx = ho[(size_t)eo * ncap];
+                    hy = ho[plane + (size_t)eo * ncap];
+                    hz = ho[2 * plane + (size_t)eo * ncap];
+                    if (hx != 0.f || hy != 0.f || hz != 0.f) nhm |= 1u << e;
+                }
+                break;
+            }
         }
         hn[(size_t)e * ncap] = hx;
         hn[plane + (size_t)e * ncap] = hy;
         hn[2 * plane + (size_t)e * ncap] = hz;
     }
     d.cnt[nlp][s] = nc;
+    d.hmask[nlp][s] = nhm;
     d.whist[nlp][s] = D.flag == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : d.whist[lp][old];
 }
 
@@ -347,50 +364,55 @@ __device__ __forceinline__ V3 cross(V3 a, V3 b)
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
-// One contact in canonical order (a = lower ID, n from b to a, delta > 0 in
-// metres).  Eq. 6 coefficients, Eq. 3 normal force, Eq. 4 tangential force
-// with the stored overlap xi kept in the tangent plane at its length and
-// advanced by the tangential contact-point motion, Eq. 5 truncation.
+// One contact seen from body a (n from b to a, delta > 0 in metres): Eq. 6
+// coefficients, Eq. 3 normal force, Eq. 4 tangential force with the stored
+// overlap xi kept in the tangent plane at its length and advanced by the
+// tangential contact-point motion, Eq. 5 truncation.
 // Returns the force on a; ft receives the tangential part.
 template <bool WALL>
-__device__ __forceinline__ V3 contact(const InstC& c, float delta, V3 n, float ra, float rb, float ma,
-                                      float mb, V3 va, V3 vb, V3 wa, V3 wb, V3& xi, float dt_hist,
-                                      V3& ft, bool& slip)
+__device__ __forceinline__ V3 contact(const InstC& c, float delta, V3 n, float ra, float rb, float ma, float mb,
+                                      V3 va, V3 vb, V3 wa, V3 wb, V3& xi, float dt_hist, V3& ft, bool& slip)
 {
     float R, meff;
     if (WALL) {
         R = ra;
         meff = ma;
     } else {
-        R = ra * rb / (ra + rb);
-        meff = ma * mb / (ma + mb);
+        R = __fdividef(ra * rb, ra + rb);
+        meff = __fdividef(ma * mb, ma + mb);
     }
-    const float sRd = sqrtf(R * delta);
+    const float Rd = R * delta;
+    const float sRd = Rd * rsqrtf(Rd);                 // sqrt(R_eff delta), Rd > 0
     const float kn = c.c_kn * sRd;
     const float kt = c.c_kt * sRd;
-    const float gn = c.nbeta * sqrtf(5.0f * meff * kn);
-    const float gt = c.nbeta * sqrtf((10.0f / 3.0f) * meff * kt);
+    const float x5 = 5.0f * meff * kn;
+    const float gn = c.nbeta * (x5 * rsqrtf(x5));       // -beta sqrt(5 m_eff k_n)
+    const float gt = gn * c.gt_ratio;                   // -beta sqrt(10/3 m_eff k_t)
     const V3 vr = va - vb;
     const float vn = dot(vr, n);
-    const V3 rw = WALL ? ra * wa : ra * wa + rb * wb;
+    // r_a w_a + r_b w_b rounded term by term (no contraction), so that it is the
+    // same number whichever body evaluates the pair
+    const V3 rw = WALL ? ra * wa
+                       : v3(__fadd_rn(__fmul_rn(ra, wa.x), __fmul_rn(rb, wb.x)),
+                            __fadd_rn(__fmul_rn(ra, wa.y), __fmul_rn(rb, wb.y)),
+                            __fadd_rn(__fmul_rn(ra, wa.z), __fmul_rn(rb, wb.z)));
     const V3 vc = vr - cross(rw, n);
     const V3 vt = vc - dot(vc, n) * n;
     float fnm = kn * delta - gn * vn;
     if (c.clamp_fn && fnm < 0.f) fnm = 0.f;
-    // keep xi in the tangent plane at its previous length
+    // keep xi in the tangent plane at its previous length (|xr| <= |xi|)
     const float xin = dot(xi, n);
     const V3 xr = xi - xin * n;
     const float l0 = dot(xi, xi), l1 = dot(xr, xr);
-    xi = l1 > 0.f ? sqrtf(l0 / l1) * xr : v3(0.f, 0.f, 0.f);
+    xi = l1 > 0.f ? rsqrtf(__fdividef(l1, l0)) * xr : v3(0.f, 0.f, 0.f);
     xi = xi + dt_hist * vt;
     ft = (-kt) * xi - gt * vt;
     const float ft2 = dot(ft, ft);
     const float lim = (WALL ? c.mu_w : c.mu) * fabsf(fnm);
     slip = ft2 > lim * lim;
     if (slip) {
-        const float sc = lim / sqrtf(ft2);
-        ft = sc * ft;
-        xi = (-1.0f / kt) * (ft + gt * vt);
+        ft = (lim * rsqrtf(ft2)) * ft;
+        xi = __fdividef(-1.0f, kt) * (ft + gt * vt);
     }
     return fnm * n + ft;
 }
@@ -399,22 +421,63 @@ __device__ __forceinline__ V3 contact(const InstC& c, float delta, V3 n, float r
 // MODE 0: one velocity-Verlet step (force at x^n with v^{n-1/2}, merged kick,
 // drift to x^{n+1}, displacement bound, rebuild decision by the last block).
 // MODE 1: forces at the current state only, written to the output arrays.
+//
+// Persistent grid: block b owns the contiguous tile range [b T / G, (b+1) T / G)
+// (neighbouring tiles share neighbours, which then hit in L1), one thread per
+// particle.  The row walk is software-pipelined: the index of entry e+2 and the
+// state of entry e+1 are loaded while entry e is computed; the stored overlap is
+// loaded only for entries whose history is non-zero (bit mask hmask), and stored
+// only where it changes.  Each particle evaluates its contacts from its own side; the
+// contact law has a single call site, so both particles of a pair run the same
+// instructions on operands that differ only in the sign of the antisymmetric
+// ones.
 template <int MODE>
-__global__ void __launch_bounds__(TILE) k_step(Dev d, int prime, cudaGraphConditionalHandle hnext, int use_cond)
+__global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, cudaGraphConditionalHandle hnext, int use_cond)
 {
-    const int t = blockIdx.x;
-    const int k = d.tile_inst[t];
-    const InstC& c = d.ic[k];
-    const InstD D = d.id[k];
-    const int s = t * TILE + threadIdx.x;
-    const bool live = (s - c.slot0) < D.n;
-    float mydisp = 0.f;
-    if (live) {
-        const int cur = D.cur, lp = D.lp, ncap = d.ncap;
-        const size_t plane = (size_t)d.Lmax * ncap;
-        const int4 P = d.pos[cur][s];
-        float4 Vv = d.vel[cur][s];
-        float4 Wv = d.omg[cur][s];
+    __shared__ InstC sc;
+    __shared__ InstD sd;
+    __shared__ float smax[TILE / 32];
+    __shared__ bool am_last;
+    const int T = d.ntiles;
+    const int t0 = (int)((long long)blockIdx.x * T / gridDim.x);
+    const int t1 = (int)((long long)(blockIdx.x + 1) * T / gridDim.x);
+    const int ncap = d.ncap;
+    const size_t plane = (size_t)d.Lmax * ncap;
+    int kprev = -1;
+    float runmax = 0.f;
+    for (int t = t0; t < t1; ++t) {
+        const int k = __ldg(d.tile_inst + t);
+        if (k != kprev) {
+            if (MODE == 0 && kprev >= 0) {
+                // flush the displacement maximum of the previous instance
+                float mx = runmax;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    float bm = smax[0];
+                    for (int i = 1; i < TILE / 32; ++i) bm = fmaxf(bm, smax[i]);
+                    if (bm > 0.f) atomicMax(&d.id[kprev].stepmax, __float_as_uint(bm));
+                }
+                runmax = 0.f;
+            }
+            __syncthreads();
+            if (threadIdx.x < (int)(sizeof(InstC) / 4)) ((int*)&sc)[threadIdx.x] = ((const int*)(d.ic + k))[threadIdx.x];
+            if (threadIdx.x < (int)(sizeof(InstD) / 4)) ((int*)&sd)[threadIdx.x] = ((const int*)(d.id + k))[threadIdx.x];
+            __syncthreads();
+            kprev = k;
+        }
+        const InstC& c = sc;
+        const int s = t * TILE + threadIdx.x;
+        if (s - c.slot0 >= sd.n) continue;
+        const int cur = sd.cur, lp = sd.lp;
+        const int4* __restrict__ pos = d.pos[cur];
+        const float4* __restrict__ vel = d.vel[cur];
+        const float4* __restrict__ omg = d.omg[cur];
+        const int4 P = pos[s];
+        float4 Vv = vel[s];
+        float4 Wv = omg[s];
         const unsigned idw = __float_as_uint(Vv.w);
         const unsigned myid = idw & ID_MASK;
         const bool wall_prev = (idw & WALL_BIT) != 0u;
@@ -424,52 +487,86 @@ __global__ void __launch_bounds__(TILE) k_step(Dev d, int prime, cudaGraphCondit
         const V3 vme = v3(Vv.x, Vv.y, Vv.z), wme = v3(Wv.x, Wv.y, Wv.z);
         const float dt_hist = prime ? 0.f : c.dt;
         V3 F = m * v3(c.g[0], c.g[1], c.g[2]);
-        V3 T = v3(0.f, 0.f, 0.f);
+        V3 Tq = v3(0.f, 0.f, 0.f);
         const int ncnt = d.cnt[lp][s];
         const int* nb = d.nbr[lp] + s;
         float* h = d.hist[lp] + s;
         float* ho = MODE == 1 ? d.xi_out + s : h;
-        unsigned long long cm = 0ull;
+        const int per0 = c.per[0], per1 = c.per[1], ext0 = c.ext[0], ext1 = c.ext[1], hf0 = c.half[0],
+                  hf1 = c.half[1];
+
+        // ---- one pass over the row, software-pipelined one entry ahead; the
+        // stored overlap is read only where hmask says it is non-zero
+        const unsigned hm = d.hmask[lp][s];
+        unsigned cm = 0u;
+        int jn = s;
+        int4 Qn = P;
+        float4 Vn = Vv, Wn = Wv;
+        float hxn = 0.f, hyn = 0.f, hzn = 0.f;
+        int j2 = s;
+        if (ncnt > 0) {
+            jn = __ldg(nb);
+            Qn = __ldg(pos + jn);
+            Vn = __ldg(vel + jn);
+            Wn = __ldg(omg + jn);
+            if (hm & 1u) {
+                hxn = h[0];
+                hyn = h[plane];
+                hzn = h[2 * plane];
+            }
+        }
+        if (ncnt > 1) j2 = __ldg(nb + ncap);
         for (int e = 0; e < ncnt; ++e) {
-            const int j = nb[(size_t)e * ncap];
-            const int4 Q = d.pos[cur][j];
-            const int dx = min_image(P.x - Q.x, c.per[0], c.ext[0], c.half[0]);
-            const int dy = min_image(P.y - Q.y, c.per[1], c.ext[1], c.half[1]);
+            const int4 Q = Qn;
+            const float4 Vb = Vn, Wb = Wn;
+            V3 xi = v3(hxn, hyn, hzn);
+            if (e + 1 < ncnt) {
+                const size_t o1 = (size_t)(e + 1) * ncap;
+                Qn = __ldg(pos + j2);
+                Vn = __ldg(vel + j2);
+                Wn = __ldg(omg + j2);
+                hxn = hyn = hzn = 0.f;
+                if ((hm >> (e + 1)) & 1u) {
+                    hxn = h[o1];
+                    hyn = h[plane + o1];
+                    hzn = h[2 * plane + o1];
+                }
+                if (e + 2 < ncnt) j2 = __ldg(nb + (size_t)(e + 2) * ncap);
+            }
+            const int dx = min_image(P.x - Q.x, per0, ext0, hf0);
+            const int dy = min_image(P.y - Q.y, per1, ext1, hf1);
             const int dz = P.z - Q.z;
             const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
             const int S = P.w + Q.w;
             const long long S2 = (long long)S * S;
-            V3 xi = v3(0.f, 0.f, 0.f);
-            if (d2 < S2) {
-                const float4 Vj = d.vel[cur][j];
-                const float4 Wj = d.omg[cur][j];
-                const unsigned idj = __float_as_uint(Vj.w) & ID_MASK;
-                const bool own_a = myid < idj;
-                // canonical operands (identical on both sides of the pair)
-                const float sx = own_a ? 1.f : -1.f;
-                const int ax = own_a ? dx : -dx, ay = own_a ? dy : -dy, az = own_a ? dz : -dz;
-                const int rai = own_a ? P.w : Q.w, rbi = own_a ? Q.w : P.w;
-                const V3 vj = v3(Vj.x, Vj.y, Vj.z), wj = v3(Wj.x, Wj.y, Wj.z);
-                const V3 va = own_a ? vme : vj, vb = own_a ? vj : vme;
-                const V3 wa = own_a ? wme : wj, wb = own_a ? wj : wme;
-                const float ma = own_a ? m : Wj.w, mb = own_a ? Wj.w : m;
-                const float dist = sqrtf((float)d2);
-                const float delta = (float)(S2 - d2) / ((float)S + dist) * q;
-                const float inv = 1.0f / dist;
-                const V3 n = v3((float)ax * inv, (float)ay * inv, (float)az * inv);
-                xi = v3(h[(size_t)e * ncap], h[plane + (size_t)e * ncap], h[2 * plane + (size_t)e * ncap]);
+            const bool touch = d2 < S2;
+            if (touch) {
+                // Own perspective (a = this particle, n from the neighbour to it).
+                // Every operation is either symmetric in (a, b) or odd under the
+                // exchange, and round-to-nearest is sign-symmetric, so the
+                // neighbour computes exactly the negated force and overlap.
+                const float d2f = (float)d2;
+                const float inv = rsqrtf(d2f);
+                const float dist = d2f * inv;
+                const float delta = __fdividef((float)(S2 - d2), (float)S + dist) * q;
+                const V3 n = v3((float)dx * inv, (float)dy * inv, (float)dz * inv);
                 V3 ft;
                 bool slip;
-                const V3 fa = contact<false>(c, delta, n, (float)rai * q, (float)rbi * q, ma, mb, va, vb, wa, wb,
-                                             xi, dt_hist, ft, slip);
-                F = F + sx * fa;
-                T = T - r * cross(n, ft);
-                cm |= 1ull << e;
+                const V3 fa = contact<false>(c, delta, n, r, (float)Q.w * q, m, Wb.w, vme, v3(Vb.x, Vb.y, Vb.z),
+                                             wme, v3(Wb.x, Wb.y, Wb.z), xi, dt_hist, ft, slip);
+                F = F + fa;
+                Tq = Tq - r * cross(n, ft);
+                cm |= 1u << e;
+            } else {
+                xi = v3(0.f, 0.f, 0.f);   // out of contact: no history
             }
-            ho[(size_t)e * ncap] = xi.x;
-            ho[plane + (size_t)e * ncap] = xi.y;
-            ho[2 * plane + (size_t)e * ncap] = xi.z;
+            if (MODE == 1 || touch || ((hm >> e) & 1u)) {
+                ho[(size_t)e * ncap] = xi.x;
+                ho[plane + (size_t)e * ncap] = xi.y;
+                ho[2 * plane + (size_t)e * ncap] = xi.z;
+            }
         }
+        if (MODE == 0) d.hmask[lp][s] = cm;
         // floor plane z = 0 (the box bottom)
         bool wall_now = false;
         V3 wxi = v3(0.f, 0.f, 0.f);
@@ -488,23 +585,23 @@ __global__ void __launch_bounds__(TILE) k_step(Dev d, int prime, cudaGraphCondit
                                             v3(c.floor_v[0], c.floor_v[1], c.floor_v[2]), wme,
                                             v3(0.f, 0.f, 0.f), wxi, dt_hist, ft, slip);
                 F = F + fa;
-                T = T - r * cross(n, ft);
+                Tq = Tq - r * cross(n, ft);
                 if (MODE == 0) d.whist[lp][s] = make_float4(wxi.x, wxi.y, wxi.z, 0.f);
             }
         }
         const float inv_m = 1.0f / m;
         const float inv_I = 2.5f / (m * r * r);
-        if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(T.x) && isfinite(T.y) &&
-              isfinite(T.z))) {
+        if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(Tq.x) && isfinite(Tq.y) &&
+              isfinite(Tq.z))) {
             atomicOr(&d.g->status, ST_NONFINITE);
             d.g->err_slot = s;
         }
         if (MODE == 1) {
             const float hk = prime ? 0.f : 0.5f * c.dt;
             d.outF[s] = make_float4(F.x, F.y, F.z, 0.f);
-            d.outT[s] = make_float4(T.x, T.y, T.z, 0.f);
+            d.outT[s] = make_float4(Tq.x, Tq.y, Tq.z, 0.f);
             d.outV[s] = make_float4(Vv.x + hk * F.x * inv_m, Vv.y + hk * F.y * inv_m, Vv.z + hk * F.z * inv_m, 0.f);
-            d.outW[s] = make_float4(Wv.x + hk * T.x * inv_I, Wv.y + hk * T.y * inv_I, Wv.z + hk * T.z * inv_I, 0.f);
+            d.outW[s] = make_float4(Wv.x + hk * Tq.x * inv_I, Wv.y + hk * Tq.y * inv_I, Wv.z + hk * Tq.z * inv_I, 0.f);
             d.outWX[s] = make_float4(wxi.x, wxi.y, wxi.z, wall_now ? 1.f : 0.f);
             d.cmask[s] = cm;
         } else {
@@ -512,27 +609,27 @@ __global__ void __launch_bounds__(TILE) k_step(Dev d, int prime, cudaGraphCondit
             Vv.x += kick * F.x * inv_m;
             Vv.y += kick * F.y * inv_m;
             Vv.z += kick * F.z * inv_m;
-            Wv.x += kick * T.x * inv_I;
-            Wv.y += kick * T.y * inv_I;
-            Wv.z += kick * T.z * inv_I;
+            Wv.x += kick * Tq.x * inv_I;
+            Wv.y += kick * Tq.y * inv_I;
+            Wv.z += kick * Tq.z * inv_I;
             const float sx = Vv.x * c.dt_over_q, sy = Vv.y * c.dt_over_q, sz = Vv.z * c.dt_over_q;
             int4 Pn = P;
             bool bad = !(fabsf(sx) < 5.0e8f && fabsf(sy) < 5.0e8f && fabsf(sz) < 5.0e8f);
             if (!bad) {
                 const int ix = __float2int_rn(sx), iy = __float2int_rn(sy), iz = __float2int_rn(sz);
                 int x = P.x + ix, y = P.y + iy;
-                if (c.per[0]) {
-                    if (x >= c.ext[0]) x -= c.ext[0];
-                    else if (x < 0) x += c.ext[0];
+                if (per0) {
+                    if (x >= ext0) x -= ext0;
+                    else if (x < 0) x += ext0;
                 }
-                if (c.per[1]) {
-                    if (y >= c.ext[1]) y -= c.ext[1];
-                    else if (y < 0) y += c.ext[1];
+                if (per1) {
+                    if (y >= ext1) y -= ext1;
+                    else if (y < 0) y += ext1;
                 }
                 const long long z = (long long)P.z + iz;
                 if (z > 2000000000ll || z < -2000000000ll) bad = true;
                 Pn = make_int4(x, y, (int)z, P.w);
-                mydisp = sqrtf((float)ix * (float)ix + (float)iy * (float)iy + (float)iz * (float)iz);
+                runmax = fmaxf(runmax, sqrtf((float)ix * (float)ix + (float)iy * (float)iy + (float)iz * (float)iz));
             }
             if (bad) {
                 atomicOr(&d.g->status, ST_ESCAPED);
@@ -545,19 +642,18 @@ __global__ void __launch_bounds__(TILE) k_step(Dev d, int prime, cudaGraphCondit
         }
     }
     if (MODE == 0) {
-        // block maximum of the displacement, then the last block to finish
-        // accumulates the bound per instance and decides on rebuilds
-        __shared__ float smax[TILE / 32];
-        __shared__ bool am_last;
-        float mx = mydisp;
+        // last instance's maximum, then the last block to finish accumulates the
+        // bound per instance and decides on rebuilds
+        float mx = runmax;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        __syncthreads();
         if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
         __syncthreads();
         if (threadIdx.x == 0) {
             float bm = smax[0];
             for (int i = 1; i < TILE / 32; ++i) bm = fmaxf(bm, smax[i]);
-            if (bm > 0.f) atomicMax(&d.id[k].stepmax, __float_as_uint(bm));
+            if (bm > 0.f && kprev >= 0) atomicMax(&d.id[kprev].stepmax, __float_as_uint(bm));
             __threadfence();
             const unsigned prev = atomicAdd(&d.g->counter, 1u);
             am_last = prev == gridDim.x - 1;
@@ -621,6 +717,7 @@ __global__ void k_init_ids(Dev d)
         d.vel[b][s] = make_float4(0.f, 0.f, 0.f, __uint_as_float((unsigned)id));
         d.omg[b][s] = z;
         d.cnt[b][s] = 0;
+        d.hmask[b][s] = 0u;
         d.whist[b][s] = z;
     }
     d.slot_of_id[s] = s;
@@ -726,25 +823,38 @@ __global__ void k_read_contacts(Dev d, int* __restrict__ partner, double* __rest
     const size_t plane = (size_t)d.Lmax * d.ncap;
     const int cnt = d.cnt[D.lp][s];
     const unsigned long long cm = d.cmask[s];
-    int t = 0;
+    // contacts of the row, ordered by partner ID
+    int pid[MAXL], ent[MAXL];
+    int nct = 0;
     for (int e = 0; e < cnt; ++e) {
         if (!((cm >> e) & 1ull)) continue;
-        if (t == width) {
-            atomicOr(&d.g->status, ST_TRUNC);
-            break;
-        }
         const int j = d.nbr[D.lp][(size_t)e * d.ncap + s];
-        const size_t o = (size_t)id * width + t;
-        partner[o] = (int)(__float_as_uint(d.vel[D.cur][j].w) & ID_MASK);
-        xi[3 * o] = d.xi_out[(size_t)e * d.ncap + s];
-        xi[3 * o + 1] = d.xi_out[plane + (size_t)e * d.ncap + s];
-        xi[3 * o + 2] = d.xi_out[2 * plane + (size_t)e * d.ncap + s];
-        ++t;
+        const int p = (int)(__float_as_uint(d.vel[D.cur][j].w) & ID_MASK);
+        int t = nct - 1;
+        while (t >= 0 && pid[t] > p) {
+            pid[t + 1] = pid[t];
+            ent[t + 1] = ent[t];
+            --t;
+        }
+        pid[t + 1] = p;
+        ent[t + 1] = e;
+        ++nct;
     }
-    for (; t < width; ++t) {
+    if (nct > width) atomicOr(&d.g->status, ST_TRUNC);
+    for (int t = 0; t < width; ++t) {
         const size_t o = (size_t)id * width + t;
-        partner[o] = -1;
-        xi[3 * o] = xi[3 * o + 1] = xi[3 * o + 2] = 0.0;
+        if (t < nct) {
+            const int e = ent[t];
+            partner[o] = pid[t];
+            // stored from this particle's side; reported in the frame of the lower ID
+            const double sg = (int)id < pid[t] ? 1.0 : -1.0;
+            xi[3 * o] = sg * d.xi_out[(size_t)e * d.ncap + s];
+            xi[3 * o + 1] = sg * d.xi_out[plane + (size_t)e * d.ncap + s];
+            xi[3 * o + 2] = sg * d.xi_out[2 * plane + (size_t)e * d.ncap + s];
+        } else {
+            partner[o] = -1;
+            xi[3 * o] = xi[3 * o + 1] = xi[3 * o + 2] = 0.0;
+        }
     }
 }
 
@@ -760,39 +870,49 @@ __global__ void k_write_contacts(Dev d, const int* __restrict__ partner, const d
     const size_t plane = (size_t)d.Lmax * d.ncap;
     const int cnt = d.cnt[D.lp][s];
     float* h = d.hist[D.lp] + s;
-    int t = 0;
+    unsigned hm = d.hmask[D.lp][s];
     for (int e = 0; e < cnt; ++e) {
         const int j = d.nbr[D.lp][(size_t)e * d.ncap + s];
         const int pid = (int)(__float_as_uint(d.vel[D.cur][j].w) & ID_MASK);
-        while (t < width && partner[(size_t)id * width + t] >= 0 && partner[(size_t)id * width + t] < pid) ++t;
-        if (t < width && partner[(size_t)id * width + t] == pid) {
+        for (int t = 0; t < width; ++t) {
             const size_t o = (size_t)id * width + t;
-            h[(size_t)e * d.ncap] = (float)xi[3 * o];
-            h[plane + (size_t)e * d.ncap] = (float)xi[3 * o + 1];
-            h[2 * plane + (size_t)e * d.ncap] = (float)xi[3 * o + 2];
+            const int p = partner[o];
+            if (p < 0 || p > pid) break;
+            if (p == pid) {
+                const double sg = (int)id < pid ? 1.0 : -1.0;   // input is in the lower ID's frame
+                h[(size_t)e * d.ncap] = (float)(sg * xi[3 * o]);
+                h[plane + (size_t)e * d.ncap] = (float)(sg * xi[3 * o + 1]);
+                h[2 * plane + (size_t)e * d.ncap] = (float)(sg * xi[3 * o + 2]);
+                hm |= 1u << e;
+                break;
+            }
         }
     }
+    d.hmask[D.lp][s] = hm;
 }
 
 __global__ void k_stats(Dev d)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long l = 0, cc = 0;
+    unsigned long long l = 0, cc = 0, wc = 0;
     if (s < d.ncap) {
         const int k = d.tile_inst[s / TILE];
         const InstD D = d.id[k];
         if (s - d.ic[k].slot0 < D.n) {
             l = (unsigned long long)d.cnt[D.lp][s];
-            cc = (unsigned long long)__popcll(d.cmask[s]) + (d.outWX[s].w != 0.f ? 1ull : 0ull);
+            wc = d.outWX[s].w != 0.f ? 1ull : 0ull;
+            cc = (unsigned long long)__popcll(d.cmask[s]) + wc;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
         l += __shfl_xor_sync(0xffffffffu, l, o);
         cc += __shfl_xor_sync(0xffffffffu, cc, o);
+        wc += __shfl_xor_sync(0xffffffffu, wc, o);
     }
     if ((threadIdx.x & 31) == 0 && (l || cc)) {
         atomicAdd(&d.g->sum_list, l);
         atomicAdd(&d.g->sum_contacts, cc);
+        atomicAdd(&d.g->sum_wall, wc);
     }
 }
 
@@ -806,6 +926,7 @@ struct dem_ctx {
     Dev dev{};
     int B = 0, Lmax = 0;
     int ncap = 0, ntiles = 0;
+    int grid0 = 1, grid1 = 1;         // persistent grids of the step / evaluation kernels
     unsigned ncodes = 0, nparts = 0;
     std::vector<InstC> ic;
     std::vector<HostInstLo> hl;
@@ -860,7 +981,7 @@ struct Plan {
     int ncap = 0, ntiles = 0, Lmax = 0, B = 0;
     unsigned ncodes = 0, nparts = 0;
     // offsets
-    size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_whist[2];
+    size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_whist[2];
     size_t o_cellcode, o_cslot, o_perm, o_ccount, o_cstart, o_part, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
         o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl;
     size_t bytes = 0;
@@ -876,7 +997,7 @@ int ceil_log2(long long v)
 dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
 {
     if (!cfg || cfg->n_instances < 1 || !cfg->inst) { err = "config needs n_instances >= 1"; return DEM_ERR_ARG; }
-    if (cfg->max_neighbors < 1 || cfg->max_neighbors > MAXL) { err = "max_neighbors must be in 1..64"; return DEM_ERR_ARG; }
+    if (cfg->max_neighbors < 1 || cfg->max_neighbors > MAXL) { err = "max_neighbors must be in 1..32"; return DEM_ERR_ARG; }
     p.B = cfg->n_instances;
     p.Lmax = cfg->max_neighbors;
     long long slot = 0;
@@ -962,6 +1083,7 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
         c.nbeta = (float)(-beta);
         c.mu = (float)s.mu;
         c.mu_w = (float)(s.mu_wall < 0 ? s.mu : s.mu_wall);
+        c.gt_ratio = (float)std::sqrt(2.0 * (8.0 * Geff) / (3.0 * (4.0 / 3.0 * Eeff)));
         h.q = q;
         h.rho = s.rho;
         p.ic.push_back(c);
@@ -985,6 +1107,7 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
         p.o_nbr[b] = L.take(N * Lm * 4);
         p.o_hist[b] = L.take(N * Lm * 12);
         p.o_cnt[b] = L.take(N * 4);
+        p.o_hmask[b] = L.take(N * 4);
         p.o_whist[b] = L.take(N * 16);
     }
     p.o_cellcode = L.take(N * 4);
@@ -1064,7 +1187,7 @@ dem_status launch_eval(dem_ctx* ctx)
 {
     dem_status st = launch_rebuild(ctx, ctx->stream);
     if (st) return st;
-    k_step<1><<<ctx->ntiles, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
+    k_step<1><<<ctx->grid1, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
     CU(cudaGetLastError());
     return DEM_OK;
 }
@@ -1148,7 +1271,7 @@ dem_status build_graph(dem_ctx* ctx, int S)
         void* args[] = {&dv, &prime, &hn, &use_cond};
         cudaKernelNodeParams kp{};
         kp.func = (void*)k_step<0>;
-        kp.gridDim = dim3(ctx->ntiles);
+        kp.gridDim = dim3(ctx->grid0);
         kp.blockDim = dim3(TILE);
         kp.kernelParams = args;
         cudaGraphNode_t e0, kn, e1;
@@ -1215,6 +1338,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
         d.nbr[b] = (int*)(base + p.o_nbr[b]);
         d.hist[b] = (float*)(base + p.o_hist[b]);
         d.cnt[b] = (int*)(base + p.o_cnt[b]);
+        d.hmask[b] = (unsigned*)(base + p.o_hmask[b]);
         d.whist[b] = (float4*)(base + p.o_whist[b]);
     }
     d.cellcode = (unsigned*)(base + p.o_cellcode);
@@ -1277,6 +1401,15 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     if (upload_goff(ctx)) {
         delete ctx;
         return DEM_ERR_CUDA;
+    }
+    {
+        int nsm = 0, b0 = 0, b1 = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_step<0>, TILE, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_step<1>, TILE, 0);
+        ctx->grid0 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b0)));
+        ctx->grid1 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b1)));
+        cudaGetLastError();
     }
     *out = ctx;
     return DEM_OK;
@@ -1402,7 +1535,7 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps)
         }
         dem_status st = launch_rebuild(ctx, ctx->stream);
         if (st) return st;
-        k_step<0><<<ctx->ntiles, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
+        k_step<0><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
         CU(cudaGetLastError());
         ctx->fresh = false;
         ++done;
@@ -1447,7 +1580,7 @@ dem_status dem_stats(dem_ctx* ctx, dem_stats_t* out)
     if (!ctx->have_state) return DEM_OK;
     dem_status st = launch_eval(ctx);
     if (st) return st;
-    CU(cudaMemsetAsync(&ctx->dev.g->sum_list, 0, 16, ctx->stream));
+    CU(cudaMemsetAsync(&ctx->dev.g->sum_list, 0, 24, ctx->stream));
     k_stats<<<nblk(ctx->ncap, 256), 256, 0, ctx->stream>>>(ctx->dev);
     CU(cudaGetLastError());
     Glob gl;
@@ -1456,6 +1589,7 @@ dem_status dem_stats(dem_ctx* ctx, dem_stats_t* out)
     out->rebuilds = (int64_t)gl.rebuilds;
     out->list_entries = (int64_t)gl.sum_list;
     out->contacts = (int64_t)gl.sum_contacts;
+    out->wall_contacts = (int64_t)gl.sum_wall;
     ctx->status |= gl.status;
     return check_status(ctx);
 }

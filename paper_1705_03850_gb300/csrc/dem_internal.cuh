@@ -12,9 +12,13 @@
 //   lists      double-buffered (parity lp_k), entry-major for coalescing:
 //                nbr  int32 [Lmax][ncap]      slot of the e-th neighbour
 //                hist float  [3][Lmax][ncap]  tangential overlap of entry e,
-//                                             in the frame of the pair's lower ID
-//                cnt  int32 [ncap]            row length; rows are sorted by
-//                                             neighbour ID
+//                                             seen from the row's particle (the
+//                                             partner's row holds its negative)
+//                hmask u32  [ncap]            bit e set: entry e holds a non-zero
+//                                             overlap (the contact was active)
+//                cnt  int32 [ncap]            row length; rows are ordered by
+//                                             d^2 - (r_i + r_j)^2 at the build,
+//                                             then by neighbour ID
 //                whist float4 [ncap]          floor-contact tangential overlap
 //   cells      per instance a Morton-ordered code range [code0_k, code0_k + ncode_k)
 //              with counts and exclusive starts, rebuilt with the lists.
@@ -25,7 +29,7 @@
 namespace cgdem {
 
 constexpr int TILE = 128;      // step-kernel block size = slot alignment of an instance
-constexpr int MAXL = 64;       // largest list width
+constexpr int MAXL = 32;       // largest list width (one bit per entry in a 32-bit mask)
 constexpr unsigned ID_MASK = 0x7fffffffu;
 constexpr unsigned WALL_BIT = 0x80000000u;
 
@@ -53,7 +57,7 @@ struct InstC {
     float g[3];
     float floor_v[3];
     float c_kn, c_kt, nbeta, mu, mu_w;   // 4/3 E_eff, 8 G_eff, -beta, mu, mu_wall
-    float pad1;
+    float gt_ratio;                      // gamma_t / gamma_n = sqrt(2 c_kt / (3 c_kn))
 };
 
 // dynamic state of one instance (device-resident)
@@ -75,6 +79,7 @@ struct Glob {
     unsigned long long rebuilds;
     unsigned long long sum_list;
     unsigned long long sum_contacts;
+    unsigned long long sum_wall;
     long long err_slot;
 };
 
@@ -86,6 +91,7 @@ struct Dev {
     int* nbr[2];
     float* hist[2];
     int* cnt[2];
+    unsigned* hmask[2];        // bit e: entry e holds a non-zero tangential overlap
     float4* whist[2];
     unsigned* cellcode;
     unsigned* cslot;

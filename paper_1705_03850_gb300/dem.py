@@ -50,7 +50,7 @@ class InstanceInfo(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("list_entries", ctypes.c_int64),
-                ("contacts", ctypes.c_int64), ("particles", ctypes.c_int64)]
+                ("contacts", ctypes.c_int64), ("particles", ctypes.c_int64), ("wall_contacts", ctypes.c_int64)]
 
 
 _lib = None
@@ -255,7 +255,7 @@ class DEM:
         st = Stats()
         self._check(self.L.dem_stats(self.h, ctypes.byref(st)), "stats")
         return dict(steps=st.steps, rebuilds=st.rebuilds, list_entries=st.list_entries, contacts=st.contacts,
-                    particles=st.particles)
+                    particles=st.particles, wall_contacts=st.wall_contacts)
 
 
 def neighbor_counts_noalloc(x, r, lo, hi, periodic, skin, r_max, out=None, stream=None):

@@ -1,0 +1,112 @@
+"""Autotuner for multi-instance (batched) runs.
+
+Chooses the neighbour-list skin (the rebuild interval), the cell width, the
+number of steps captured per CUDA graph and the list width by timing each
+candidate through the C ABI on a representative subset of the instances
+(evenly spread over their sizes) for the run's full length, so that the cost of
+list rebuilds is part of what is measured: create a context, load the same
+state, time the start-up step (including the first list build) and the
+remaining steps, and keep the fastest candidate that ran without a device
+error.
+"""
+from __future__ import annotations
+
+import itertools
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import dem
+
+
+@dataclass
+class Choice:
+    skin_factor: float      # skin = skin_factor * d (d = 2 r_max of each instance)
+    cell_factor: float      # cell width >= cell_factor * 2 r_max + skin
+    graph_steps: int
+    max_neighbors: int
+    ms_start: float = float("nan")
+    ms_per_step: float = float("nan")
+    ok: bool = False
+
+    def as_dict(self):
+        return dict(skin_factor=self.skin_factor, cell_factor=self.cell_factor, graph_steps=self.graph_steps,
+                    max_neighbors=self.max_neighbors, ms_start=self.ms_start, ms_per_step=self.ms_per_step)
+
+
+def descs_for(workloads, choice: Choice, floor_v=None):
+    out = []
+    for wl in workloads:
+        rmax = float(np.max(wl.r)) if wl.n else 1e-3
+        d = dem.desc_from_workload(wl, r_max=rmax * choice.cell_factor)
+        d.skin = choice.skin_factor * 2.0 * rmax
+        if floor_v is not None:
+            for a in range(3):
+                d.floor_v[a] = floor_v[a]
+        out.append(d)
+    return out
+
+
+def concat_state(workloads):
+    cat = lambda f: np.concatenate([getattr(w, f) for w in workloads]) if workloads else np.zeros((0, 3))
+    return cat("x"), cat("v"), cat("w"), cat("r"), cat("m")
+
+
+def make_context(workloads, choice: Choice, device=None, state=None):
+    sim = dem.DEM(descs_for(workloads, choice), max_neighbors=choice.max_neighbors, device=device)
+    x, v, w, r, m = state if state is not None else concat_state(workloads)
+    sim.write_state(x, v, w, r, m)
+    return sim
+
+
+def subset(workloads, count):
+    """`count` instances evenly spread over the sizes (all of them if fewer)."""
+    if len(workloads) <= count:
+        return list(workloads)
+    order = sorted(range(len(workloads)), key=lambda k: workloads[k].n)
+    pick = sorted({order[int(round(i * (len(order) - 1) / (count - 1)))] for i in range(count)})
+    return [workloads[k] for k in pick]
+
+
+def tune(workloads, skin_factors=(0.025, 0.05, 0.1), cell_factors=(1.0, 1.25), graph_steps=(50, 100),
+         max_neighbors=(32,), window=2000, sample=32, device=None, state=None, log=None):
+    """Time every candidate on `sample` instances for `window` steps; return (best, all)."""
+    import torch
+    workloads = subset(workloads, sample)
+    state = [torch.as_tensor(a, dtype=torch.float64, device=device or "cuda") for a in concat_state(workloads)]
+    results = []
+    for sf, cf, gs, lm in itertools.product(skin_factors, cell_factors, graph_steps, max_neighbors):
+        ch = Choice(sf, cf, gs, lm)
+        sim = None
+        try:
+            sim = make_context(workloads, ch, device=device, state=state)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.step(1)
+            sim.sync()
+            ch.ms_start = (time.perf_counter() - t0) * 1e3
+            sim.set_graph(gs)
+            n = max(gs, (window // gs) * gs)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(sim.stream)
+            sim.step(n)
+            ev1.record(sim.stream)
+            sim.sync()
+            ch.ms_per_step = ev0.elapsed_time(ev1) / n
+            ch.ok = True
+        except dem.DemError as e:
+            ch.ok = False
+            if log:
+                log(f"candidate {ch.as_dict()} rejected: {e}")
+        finally:
+            if sim is not None:
+                sim.close()
+        results.append(ch)
+        if log:
+            log(f"candidate {ch.as_dict()} ok={ch.ok}")
+    good = [c for c in results if c.ok]
+    if not good:
+        raise RuntimeError("no autotuner candidate ran without a device error")
+    best = min(good, key=lambda c: c.ms_start + c.ms_per_step * window)
+    return best, results

@@ -58,10 +58,22 @@ __device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* t
     return base + x - v;
 }
 
+// A scan chunk belongs to one instance (code ranges are aligned to chunks);
+// chunks of instances that are not rebuilding are skipped.
+__device__ __forceinline__ bool chunk_active(const Dev& d, unsigned b)
+{
+    const int k = d.part_inst[b];
+    return k >= 0 && d.id[k].flag != 0;
+}
+
 __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(Dev d)
 {
     if (!d.g->any) return;
     const unsigned b = blockIdx.x;
+    if (!chunk_active(d, b)) {
+        if (threadIdx.x == 0) d.part[b] = 0u;
+        return;
+    }
     const unsigned base = b * SCAN_TILE;
     unsigned s = 0;
     for (int k = 0; k < SCAN_V; ++k) {
@@ -93,7 +105,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(Dev d)
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_down(Dev d)
 {
-    if (!d.g->any) return;
+    if (!d.g->any || !chunk_active(d, blockIdx.x)) return;
     const unsigned base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_V;
     unsigned v[SCAN_V];
     unsigned s = 0;
@@ -142,87 +154,84 @@ __device__ __forceinline__ int min_image(int dx, int per, int L, int half)
 // clear counts -> bin (atomic slot in cell) -> scan -> scatter -> order each
 // cell by particle ID -> build lists, permute state, carry histories.
 
+// Per-slot rebuild work runs on a persistent grid of TILE-thread blocks that
+// strides over the tiles and skips tiles of instances that are not rebuilding.
+template <typename Fn>
+__device__ __forceinline__ void for_rebuilding_slots(const Dev& d, Fn fn)
+{
+    for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
+        const int k = d.tile_inst[t];
+        const InstD D = d.id[k];
+        if (!D.flag) continue;
+        const InstC& c = d.ic[k];
+        const int s = t * TILE + threadIdx.x;
+        if (s - c.slot0 >= D.n) continue;
+        fn(s, D, c);
+    }
+}
+
 __global__ void k_rb_clear(Dev d)
 {
     if (!d.g->any) return;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < d.ncodes; i += gridDim.x * blockDim.x)
-        d.ccount[i] = 0;
+    for (unsigned b = blockIdx.x; b < d.nparts; b += gridDim.x) {
+        if (!chunk_active(d, b)) continue;
+        for (unsigned i = b * SCAN_TILE + threadIdx.x; i < (b + 1) * SCAN_TILE && i < d.ncodes; i += blockDim.x)
+            d.ccount[i] = 0u;
+    }
 }
 
-__global__ void k_rb_bin(Dev d)
+__global__ void __launch_bounds__(TILE) k_rb_bin(Dev d)
 {
     if (!d.g->any) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.ncap) return;
-    const int k = d.tile_inst[s / TILE];
-    const InstD D = d.id[k];
-    if (!D.flag) return;
-    const InstC& c = d.ic[k];
-    if (s - c.slot0 >= D.n) return;
-    const int4 p = d.pos[D.cur][s];
-    const unsigned code = cell_code(d, c, axis_cell(c, 0, p.x), axis_cell(c, 1, p.y), axis_cell(c, 2, p.z));
-    d.cellcode[s] = code;
-    d.cslot[s] = atomicAdd(&d.ccount[code], 1u);
+    for_rebuilding_slots(d, [&](int s, const InstD& D, const InstC& c) {
+        const int4 p = d.pos[D.cur][s];
+        const unsigned code = cell_code(d, c, axis_cell(c, 0, p.x), axis_cell(c, 1, p.y), axis_cell(c, 2, p.z));
+        d.cellcode[s] = code;
+        d.cslot[s] = atomicAdd(&d.ccount[code], 1u);
+    });
 }
 
-__global__ void k_rb_scatter(Dev d)
+__global__ void __launch_bounds__(TILE) k_rb_scatter(Dev d)
 {
     if (!d.g->any) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.ncap) return;
-    const int k = d.tile_inst[s / TILE];
-    const InstD D = d.id[k];
-    if (!D.flag) return;
-    const InstC& c = d.ic[k];
-    if (s - c.slot0 >= D.n) return;
-    const unsigned code = d.cellcode[s];
-    const int np = c.slot0 + (int)(d.cstart[code] - d.cstart[c.code0]) + (int)d.cslot[s];
-    d.perm[np] = s;
+    for_rebuilding_slots(d, [&](int s, const InstD& D, const InstC& c) {
+        const unsigned code = d.cellcode[s];
+        const int np = c.slot0 + (int)(d.cstart[code] - d.cstart[c.code0]) + (int)d.cslot[s];
+        d.perm[np] = s;
+    });
 }
 
 // The first member of every cell orders the cell by particle ID, so that the
 // final order depends only on the cells and the IDs.
-__global__ void k_rb_cellsort(Dev d)
+__global__ void __launch_bounds__(TILE) k_rb_cellsort(Dev d)
 {
     if (!d.g->any) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.ncap) return;
-    const int k = d.tile_inst[s / TILE];
-    const InstD D = d.id[k];
-    if (!D.flag) return;
-    const InstC& c = d.ic[k];
-    if (s - c.slot0 >= D.n || d.cslot[s] != 0u) return;
-    const unsigned code = d.cellcode[s];
-    const int cntc = (int)d.ccount[code];
-    if (cntc < 2) return;
-    int* a = d.perm + c.slot0 + (int)(d.cstart[code] - d.cstart[c.code0]);
-    const float4* v = d.vel[D.cur];
-    for (int i = 1; i < cntc; ++i) {
-        const int x = a[i];
-        const unsigned xid = __float_as_uint(v[x].w) & ID_MASK;
-        int j = i - 1;
-        while (j >= 0 && (__float_as_uint(v[a[j]].w) & ID_MASK) > xid) {
-            a[j + 1] = a[j];
-            --j;
+    for_rebuilding_slots(d, [&](int s, const InstD& D, const InstC& c) {
+        if (d.cslot[s] != 0u) return;
+        const unsigned code = d.cellcode[s];
+        const int cntc = (int)d.ccount[code];
+        if (cntc < 2) return;
+        int* a = d.perm + c.slot0 + (int)(d.cstart[code] - d.cstart[c.code0]);
+        const float4* v = d.vel[D.cur];
+        for (int i = 1; i < cntc; ++i) {
+            const int x = a[i];
+            const unsigned xid = __float_as_uint(v[x].w) & ID_MASK;
+            int j = i - 1;
+            while (j >= 0 && (__float_as_uint(v[a[j]].w) & ID_MASK) > xid) {
+                a[j + 1] = a[j];
+                --j;
+            }
+            a[j + 1] = x;
         }
-        a[j + 1] = x;
-    }
+    });
 }
 
 // One thread per new slot: move the particle into the other state buffer,
 // collect neighbours within r_i + r_j + skin (exact integer test), order the
 // row by overlap depth, and carry the tangential overlaps of pairs that were
 // already listed (found by ID in the particle's previous row).
-__global__ void __launch_bounds__(128) k_rb_build(Dev d)
+__device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, const InstC& c)
 {
-    if (!d.g->any) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.ncap) return;
-    const int k = d.tile_inst[s / TILE];
-    const InstD D = d.id[k];
-    if (!D.flag) return;
-    const InstC& c = d.ic[k];
-    if (s - c.slot0 >= D.n) return;
     const int cur = D.cur, nxt = cur ^ 1, lp = D.lp, nlp = lp ^ 1;
     const int ncap = d.ncap;
     const int old = d.perm[s];
@@ -330,6 +339,12 @@ __global__ void __launch_bounds__(128) k_rb_build(Dev d)
     d.cnt[nlp][s] = nc;
     d.hmask[nlp][s] = nhm;
     d.whist[nlp][s] = D.flag == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : d.whist[lp][old];
+}
+
+__global__ void __launch_bounds__(TILE) k_rb_build(Dev d)
+{
+    if (!d.g->any) return;
+    for_rebuilding_slots(d, [&](int s, const InstD& D, const InstC& c) { build_row(d, s, D, c); });
 }
 
 __global__ void k_rb_finish(Dev d)
@@ -927,6 +942,7 @@ struct dem_ctx {
     int B = 0, Lmax = 0;
     int ncap = 0, ntiles = 0;
     int grid0 = 1, grid1 = 1;         // persistent grids of the step / evaluation kernels
+    int grid_rb = 1;                  // persistent grid of the per-slot rebuild kernels
     unsigned ncodes = 0, nparts = 0;
     std::vector<InstC> ic;
     std::vector<HostInstLo> hl;
@@ -977,12 +993,13 @@ struct Plan {
     std::vector<HostInstLo> hl;
     std::vector<unsigned> spread;
     std::vector<int> tile_inst;
+    std::vector<int> part_inst;
     std::vector<long long> count;
     int ncap = 0, ntiles = 0, Lmax = 0, B = 0;
     unsigned ncodes = 0, nparts = 0;
     // offsets
     size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_whist[2];
-    size_t o_cellcode, o_cslot, o_perm, o_ccount, o_cstart, o_part, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
+    size_t o_cellcode, o_cslot, o_perm, o_ccount, o_cstart, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
         o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl;
     size_t bytes = 0;
 };
@@ -1062,6 +1079,7 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
                 p.spread.push_back(sv);
             }
         }
+        code = (code + SCAN_TILE - 1) / SCAN_TILE * SCAN_TILE;   // scan chunks never straddle instances
         c.code0 = (int)code;
         c.ncode = 1 << tb;
         code += (unsigned)c.ncode;
@@ -1098,6 +1116,11 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
     p.ntiles = (int)(slot / TILE);
     p.ncodes = code;
     p.nparts = (code + SCAN_TILE - 1) / SCAN_TILE;
+    p.part_inst.assign(std::max(1u, p.nparts), -1);
+    for (int k = 0; k < p.B; ++k)
+        for (unsigned b = (unsigned)p.ic[k].code0 / SCAN_TILE;
+             b < ((unsigned)p.ic[k].code0 + (unsigned)p.ic[k].ncode + SCAN_TILE - 1) / SCAN_TILE; ++b)
+            p.part_inst[b] = k;
     Layout L;
     const size_t N = (size_t)p.ncap, Lm = (size_t)p.Lmax;
     for (int b = 0; b < 2; ++b) {
@@ -1116,6 +1139,7 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
     p.o_ccount = L.take((size_t)p.ncodes * 4);
     p.o_cstart = L.take((size_t)p.ncodes * 4);
     p.o_part = L.take((size_t)std::max(1u, p.nparts) * 4);
+    p.o_pinst = L.take((size_t)std::max(1u, p.nparts) * 4);
     p.o_soi = L.take(N * 4);
     p.o_tile = L.take((size_t)p.ntiles * 4);
     p.o_ic = L.take(sizeof(InstC) * p.B);
@@ -1170,14 +1194,15 @@ dem_status check_status(dem_ctx* ctx)
 dem_status launch_rebuild(dem_ctx* ctx, cudaStream_t st)
 {
     const Dev& d = ctx->dev;
-    k_rb_clear<<<std::min(nblk(ctx->ncodes, 256), 152u * 16u), 256, 0, st>>>(d);
-    k_rb_bin<<<nblk(ctx->ncap, 256), 256, 0, st>>>(d);
+    const unsigned gt = (unsigned)ctx->grid_rb;
+    k_rb_clear<<<std::min(std::max(1u, ctx->nparts), 152u * 8u), 256, 0, st>>>(d);
+    k_rb_bin<<<gt, TILE, 0, st>>>(d);
     k_scan_reduce<<<std::max(1u, ctx->nparts), SCAN_T, 0, st>>>(d);
     k_scan_top<<<1, 1024, 0, st>>>(d);
     k_scan_down<<<std::max(1u, ctx->nparts), SCAN_T, 0, st>>>(d);
-    k_rb_scatter<<<nblk(ctx->ncap, 256), 256, 0, st>>>(d);
-    k_rb_cellsort<<<nblk(ctx->ncap, 256), 256, 0, st>>>(d);
-    k_rb_build<<<nblk(ctx->ncap, 128), 128, 0, st>>>(d);
+    k_rb_scatter<<<gt, TILE, 0, st>>>(d);
+    k_rb_cellsort<<<gt, TILE, 0, st>>>(d);
+    k_rb_build<<<gt, TILE, 0, st>>>(d);
     k_rb_finish<<<1, 256, 0, st>>>(d);
     CU(cudaGetLastError());
     return DEM_OK;
@@ -1347,6 +1372,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     d.ccount = (unsigned*)(base + p.o_ccount);
     d.cstart = (unsigned*)(base + p.o_cstart);
     d.part = (unsigned*)(base + p.o_part);
+    d.part_inst = (int*)(base + p.o_pinst);
     d.slot_of_id = (int*)(base + p.o_soi);
     d.tile_inst = (int*)(base + p.o_tile);
     d.ic = (const InstC*)(base + p.o_ic);
@@ -1390,6 +1416,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     CUC(cudaMemcpyAsync(d.id, idv.data(), sizeof(InstD) * p.B, cudaMemcpyHostToDevice, s));
     CUC(cudaMemcpyAsync((void*)d.spread, p.spread.data(), p.spread.size() * 4, cudaMemcpyHostToDevice, s));
     CUC(cudaMemcpyAsync(d.tile_inst, p.tile_inst.data(), p.tile_inst.size() * 4, cudaMemcpyHostToDevice, s));
+    CUC(cudaMemcpyAsync(d.part_inst, p.part_inst.data(), p.part_inst.size() * 4, cudaMemcpyHostToDevice, s));
     CUC(cudaMemcpyAsync(d.g, &gl, sizeof(Glob), cudaMemcpyHostToDevice, s));
     CUC(cudaMemcpyAsync(ctx->d_hl, p.hl.data(), sizeof(HostInstLo) * p.B, cudaMemcpyHostToDevice, s));
     CUC(cudaMemsetAsync(d.hist[0], 0, (size_t)p.ncap * p.Lmax * 12, s));
@@ -1409,6 +1436,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_step<1>, TILE, 0);
         ctx->grid0 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b0)));
         ctx->grid1 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b1)));
+        ctx->grid_rb = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * 8));
         cudaGetLastError();
     }
     *out = ctx;

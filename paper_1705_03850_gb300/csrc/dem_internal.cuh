@@ -99,6 +99,7 @@ struct Dev {
     unsigned* ccount;
     unsigned* cstart;
     unsigned* part;
+    int* part_inst;            // instance owning each scan chunk of cell codes (-1: padding)
     int* slot_of_id;
     int* tile_inst;
     const InstC* ic;

@@ -180,17 +180,17 @@ def batch_sizes(count: int = 256, seed: int = 4, nmin: float = 2e3, nmax: float 
 def settling_box(n: int, seed: int, mat: Material, d: float = 2.0e-3, spacing: float = 2.1e-3,
                  phi: float = 0.45, dt: float = 1e-6, steps: int = 2000) -> Workload:
     """One settling box: footprint s x s with s = (n V_p / phi)^(1/3), periodic x/y, floor;
-    jittered simple-cubic lattice at the given spacing."""
+    jittered simple-cubic lattice at the given spacing; box height = lattice top + 4 d."""
     rng = np.random.default_rng(seed)
     vp = math.pi / 6.0 * d ** 3
     s = (n * vp / phi) ** (1.0 / 3.0)
-    per = max(3, int(math.floor(s / spacing)))
+    per = max(4, int(math.floor(s / spacing)))     # at least 3 cells across for any tuned cell width
     s = per * spacing
     k = np.arange(n)
     x = np.column_stack([(k % per + 0.5) * spacing, ((k // per) % per + 0.5) * spacing,
                          (k // (per * per)) * spacing + d / 2 + 0.02e-3])
     x += rng.uniform(-0.03e-3, 0.03e-3, x.shape)
-    height = max(3 * s, float(x[:, 2].max()) + 2 * d)
+    height = float(x[:, 2].max()) + 4 * d       # particles only settle: the cell grid need not reach higher
     z = np.zeros((n, 3))
     return _finish(f"box_{n}", x, z, z, np.full(n, d / 2), mat, (0, 0, 0), (s, s, height),
                    (True, True, False), dt, (0, 0, -9.81), True, (0, 0, 0), 0.1 * d, steps)

@@ -5,8 +5,11 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
 product path (``paper_1705_03850_gb300``) never imports it, and it imports
 nothing from the product path.
 
-The arithmetic lives in ``dem_oracle.c`` (plain C, double precision), compiled
-here with gcc into ``oracle/_build/liboracle.so`` and called through ctypes.
+The arithmetic lives in ``dem_oracle.c`` and ``dem_oracle_dyn.h`` (plain C,
+double precision), compiled here with gcc into ``oracle/_build/liboracle.so``
+and called through ctypes.  ``dem_oracle_cs.c`` compiles the same dynamics
+with complex numbers for complex-step derivatives (the FP64 reference
+gradient of rollouts with respect to E, e and mu).
 What it follows, by section and equation of Queteschiner et al. (2017):
 
 * Sec. 2.1, Eqs. 1-2: Newton's equations for translation and rotation,
@@ -29,7 +32,8 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "dem_oracle.c")
+_SRCS = [os.path.join(_HERE, f) for f in ("dem_oracle.c", "dem_oracle_cs.c")]
+_HDRS = [os.path.join(_HERE, f) for f in ("dem_oracle_common.h", "dem_oracle_dyn.h")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lib = None
@@ -40,10 +44,11 @@ NPARAM = 24
 def build(force: bool = False) -> str:
     """Compile the oracle's C source with gcc (plain -O2, no fast-math)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS + _HDRS)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -68,6 +73,9 @@ def _load():
     lib.orc_eval.argtypes = [dp, i64, dp, dp, dp, dp, dp, i64p, i64, i64p, i64p, dp,
                              ctypes.c_double, ctypes.c_int32, dp, dp, i64, i64p, i64p, dp,
                              i32p, dp]
+    lib.orc_cs_run_derivative.restype = ctypes.c_int32
+    lib.orc_cs_run_derivative.argtypes = [dp, ctypes.c_int32, ctypes.c_double, i64, dp, dp, dp, dp, dp, i64p, i64,
+                                          ctypes.c_int32, i64] + [dp] * 10
     lib.orc_run.restype = ctypes.c_int32
     lib.orc_run.argtypes = [dp, i64, dp, dp, dp, dp, dp, i64p, i64p, i64, i64p, i64p, dp,
                             i32p, dp, dp, i64, ctypes.c_int32, ctypes.c_int32]
@@ -135,6 +143,35 @@ def pairs(P, x, r, extra=0.0, method="cells") -> np.ndarray:
         if cnt <= cap:
             return np.stack([pi[:cnt], pj[:cnt]], axis=1)
         cap = int(cnt)
+
+
+PARAM_INDEX = {"E": 0, "e": 1, "mu": 2}
+
+
+def rollout_derivative(P, x, v, w, r, m, nsteps, param, h=None, ids=None, use_cells=True):
+    """State after `nsteps` from (x, v, w) with empty history, and its derivative with
+    respect to one material parameter ("E", "e" or "mu") by a complex step.
+
+    Returns dict with x, v, w, F, T (step nsteps) and dx, dv, dw, dF, dT.
+    """
+    lib = _load()
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    which = PARAM_INDEX[param]
+    base = float(P[[0, 2, 3][which]])
+    h = h if h is not None else 1e-30 * max(abs(base), 1e-300)
+    ids = np.arange(n, dtype=np.int64) if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
+    outs = {k: np.zeros((n, 3)) for k in ("x", "v", "w", "F", "T", "dx", "dv", "dw", "dF", "dT")}
+    rc = lib.orc_cs_run_derivative(_d(P), which, float(h), n, _d(x), _d(np.ascontiguousarray(v, dtype=np.float64)),
+                                   _d(np.ascontiguousarray(w, dtype=np.float64)),
+                                   _d(np.ascontiguousarray(r, dtype=np.float64)),
+                                   _d(np.ascontiguousarray(m, dtype=np.float64)), _i64(ids), int(nsteps),
+                                   1 if use_cells else 0, max(64, 16 * n),
+                                   *[_d(outs[k]) for k in ("x", "v", "w", "F", "T", "dx", "dv", "dw", "dF", "dT")])
+    if rc != 0:
+        raise RuntimeError("oracle history capacity exceeded")
+    return outs
 
 
 class Sim:

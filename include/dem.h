@@ -181,6 +181,41 @@ dem_status dem_set_graph(dem_ctx *ctx, int32_t steps_per_graph);
  * Synchronises the stream.  DEM_ERR_STATE if no graph was built. */
 dem_status dem_graph_step_kernel_ms(dem_ctx *ctx, double *total_ms, int32_t *count);
 
+/* ---------------------------------------------------------------------------
+ * Differentiable rollouts (gradients of observables with respect to the
+ * material parameters E, e and mu of Eq. 6, per instance).
+ *
+ * dem_rollout_forward runs nsteps steps with the neighbour lists frozen (built
+ * once at the start; if a particle moves more than half the skin the run stops
+ * with DEM_ERR_CAPACITY) and saves the full state every checkpoint_every steps
+ * in the caller's rollout workspace (device memory, 256-byte aligned, size from
+ * dem_rollout_workspace).  dem_rollout_adjoint then computes, by a hand-written
+ * reverse pass through the contact law and the integrator, the gradient of
+ *     J = sum_k ( w_KE,k KE_k + w_R,k runout_k )
+ * at the final step, where KE = sum 1/2 m v^2 + 1/2 I w^2 and runout = the
+ * largest horizontal distance of a particle from the instance's axis.  Each
+ * checkpointed segment is recomputed forward (bit-identical) and walked
+ * backwards; which contacts exist and which slip is taken from that forward
+ * pass (the derivative is that of the discrete map with the contact pattern
+ * held fixed).  The context ends in the rollout's final state.
+ *   weights: host (B, 2) {w_KE, w_R}; axis: host (B, 2) {x, y} [m];
+ *   grad: host (B, 3) {dJ/dE, dJ/de, dJ/dmu} (mu also moves the floor friction
+ *   when mu_wall was left unset).
+ * ------------------------------------------------------------------------- */
+dem_status dem_rollout_workspace(dem_ctx *ctx, int64_t nsteps, int64_t checkpoint_every, int64_t *bytes);
+dem_status dem_rollout_forward(dem_ctx *ctx, int64_t nsteps, int64_t checkpoint_every, void *workspace,
+                               int64_t workspace_bytes);
+dem_status dem_rollout_adjoint(dem_ctx *ctx, const double *weights, const double *axis, double *grad);
+
+/* Observables at the current step: out (B, 2) = {KE, runout} with axis (B, 2)
+ * as above (host arrays; synchronises). */
+dem_status dem_observables(dem_ctx *ctx, const double *axis, double *out);
+
+/* Replace the material parameters {E, e, mu} of every instance (host (B, 3));
+ * nu, rho and the state are kept.  mu also sets the floor friction when
+ * mu_wall was left unset. */
+dem_status dem_set_material(dem_ctx *ctx, const double *params);
+
 /*
  * Neighbour counts without any allocation or workspace.  The paper has no
  * counterpart; this is a service for callers that cannot give the library

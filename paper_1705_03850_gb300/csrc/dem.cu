@@ -4,6 +4,7 @@
 // interface and dem_internal.cuh for the data layout.
 #include "dem.h"
 #include "dem_internal.cuh"
+#include "dem_contact.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -365,71 +366,13 @@ __global__ void k_rb_finish(Dev d)
 }
 
 // ============================================================= contact law
+// (contact_fwd / contact_vjp in dem_contact.cuh)
 
-struct V3 {
-    float x, y, z;
-};
+using V3 = Vec3<float>;
 __device__ __forceinline__ V3 v3(float x, float y, float z) { return {x, y, z}; }
-__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
-__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ V3 operator*(float s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
-__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ V3 cross(V3 a, V3 b)
+__device__ __forceinline__ Coef<float> coef_of(const InstC& c)
 {
-    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
-}
-
-// One contact seen from body a (n from b to a, delta > 0 in metres): Eq. 6
-// coefficients, Eq. 3 normal force, Eq. 4 tangential force with the stored
-// overlap xi kept in the tangent plane at its length and advanced by the
-// tangential contact-point motion, Eq. 5 truncation.
-// Returns the force on a; ft receives the tangential part.
-template <bool WALL>
-__device__ __forceinline__ V3 contact(const InstC& c, float delta, V3 n, float ra, float rb, float ma, float mb,
-                                      V3 va, V3 vb, V3 wa, V3 wb, V3& xi, float dt_hist, V3& ft, bool& slip)
-{
-    float R, meff;
-    if (WALL) {
-        R = ra;
-        meff = ma;
-    } else {
-        R = __fdividef(ra * rb, ra + rb);
-        meff = __fdividef(ma * mb, ma + mb);
-    }
-    const float Rd = R * delta;
-    const float sRd = Rd * rsqrtf(Rd);                 // sqrt(R_eff delta), Rd > 0
-    const float kn = c.c_kn * sRd;
-    const float kt = c.c_kt * sRd;
-    const float x5 = 5.0f * meff * kn;
-    const float gn = c.nbeta * (x5 * rsqrtf(x5));       // -beta sqrt(5 m_eff k_n)
-    const float gt = gn * c.gt_ratio;                   // -beta sqrt(10/3 m_eff k_t)
-    const V3 vr = va - vb;
-    const float vn = dot(vr, n);
-    // r_a w_a + r_b w_b rounded term by term (no contraction), so that it is the
-    // same number whichever body evaluates the pair
-    const V3 rw = WALL ? ra * wa
-                       : v3(__fadd_rn(__fmul_rn(ra, wa.x), __fmul_rn(rb, wb.x)),
-                            __fadd_rn(__fmul_rn(ra, wa.y), __fmul_rn(rb, wb.y)),
-                            __fadd_rn(__fmul_rn(ra, wa.z), __fmul_rn(rb, wb.z)));
-    const V3 vc = vr - cross(rw, n);
-    const V3 vt = vc - dot(vc, n) * n;
-    float fnm = kn * delta - gn * vn;
-    if (c.clamp_fn && fnm < 0.f) fnm = 0.f;
-    // keep xi in the tangent plane at its previous length (|xr| <= |xi|)
-    const float xin = dot(xi, n);
-    const V3 xr = xi - xin * n;
-    const float l0 = dot(xi, xi), l1 = dot(xr, xr);
-    xi = l1 > 0.f ? rsqrtf(__fdividef(l1, l0)) * xr : v3(0.f, 0.f, 0.f);
-    xi = xi + dt_hist * vt;
-    ft = (-kt) * xi - gt * vt;
-    const float ft2 = dot(ft, ft);
-    const float lim = (WALL ? c.mu_w : c.mu) * fabsf(fnm);
-    slip = ft2 > lim * lim;
-    if (slip) {
-        ft = (lim * rsqrtf(ft2)) * ft;
-        xi = __fdividef(-1.0f, kt) * (ft + gt * vt);
-    }
-    return fnm * n + ft;
+    return Coef<float>{c.c_kn, c.c_kt, c.nbeta, c.gt_ratio, c.mu, c.mu_w, c.clamp_fn};
 }
 
 // ================================================================== step
@@ -567,8 +510,9 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                 const V3 n = v3((float)dx * inv, (float)dy * inv, (float)dz * inv);
                 V3 ft;
                 bool slip;
-                const V3 fa = contact<false>(c, delta, n, r, (float)Q.w * q, m, Wb.w, vme, v3(Vb.x, Vb.y, Vb.z),
-                                             wme, v3(Wb.x, Wb.y, Wb.z), xi, dt_hist, ft, slip);
+                const V3 fa = contact_fwd<float, false>(coef_of(c), delta, n, r, (float)Q.w * q, m, Wb.w, vme,
+                                                        v3(Vb.x, Vb.y, Vb.z), wme, v3(Wb.x, Wb.y, Wb.z), xi, dt_hist,
+                                                        ft, slip);
                 F = F + fa;
                 Tq = Tq - r * cross(n, ft);
                 cm |= 1u << e;
@@ -596,9 +540,9 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                 const V3 n = v3(0.f, 0.f, 1.f);
                 V3 ft;
                 bool slip;
-                const V3 fa = contact<true>(c, (float)dw * q, n, r, 0.f, m, 0.f, vme,
-                                            v3(c.floor_v[0], c.floor_v[1], c.floor_v[2]), wme,
-                                            v3(0.f, 0.f, 0.f), wxi, dt_hist, ft, slip);
+                const V3 fa = contact_fwd<float, true>(coef_of(c), (float)dw * q, n, r, 0.f, m, 0.f, vme,
+                                                       v3(c.floor_v[0], c.floor_v[1], c.floor_v[2]), wme,
+                                                       v3(0.f, 0.f, 0.f), wxi, dt_hist, ft, slip);
                 F = F + fa;
                 Tq = Tq - r * cross(n, ft);
                 if (MODE == 0) d.whist[lp][s] = make_float4(wxi.x, wxi.y, wxi.z, 0.f);
@@ -683,8 +627,12 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                 Dk->disp = disp;
                 Dk->cur ^= 1;
                 if (2.0f * disp >= 0.99f * d.ic[kk].skin_f && Dk->flag == 0) {
-                    Dk->flag = 1;
-                    atomicOr(&d.g->any, 1u);
+                    if (d.g->frozen) {
+                        atomicOr(&d.g->status, ST_SKIN);
+                    } else {
+                        Dk->flag = 1;
+                        atomicOr(&d.g->any, 1u);
+                    }
                 }
             }
             __syncthreads();
@@ -931,6 +879,316 @@ __global__ void k_stats(Dev d)
     }
 }
 
+// ================================================================ adjoint
+// Reverse mode of the step for a differentiable rollout (lists frozen):
+//   x^{n+1} = x^n + dt v^{n+1/2},  v^{n+1/2} = v^{n-1/2} + kick F^n / m,
+//   w^{n+1/2} = w^{n-1/2} + kick T^n / I,  (F^n, T^n, xi^n) = forces at
+//   (x^n, v^{n-1/2}, w^{n-1/2}, xi^{n-1}; E, e, mu),
+// with the contact and slip pattern of the forward pass.  The adjoint of the
+// stored overlap is kept from each row's side, so the two rows of a pair hold
+// opposite values and every particle can compute its part of a pair's
+// derivative alone (no atomics; the parameter part is split evenly).
+
+struct Snap {
+    int4* pos;
+    float4* vel;
+    float4* omg;
+    float* hist;
+    unsigned* hmask;
+    float4* whist;
+    float* disp;       // per instance: displacement bound accumulated since the list build
+};
+
+struct AdjBufs {
+    float4* xb;        // adjoint of x^n [1/m units of the objective]
+    float4* vb;        // adjoint of v^{n-1/2}
+    float4* wb;        // adjoint of w^{n-1/2}
+    float4* Fb;        // adjoint of F^n
+    float4* Tb;        // adjoint of T^n
+    float* xib;        // adjoint of the stored overlaps, [3][Lmax][ncap], from each row's side
+    float4* wxib;      // adjoint of the floor overlap
+    double* thb;       // per slot: accumulated d/dE, d/de, d/dmu
+};
+
+template <typename Fn>
+__device__ __forceinline__ void for_live_slots(const Dev& d, Fn fn)
+{
+    for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
+        const int k = d.tile_inst[t];
+        const InstD D = d.id[k];
+        const int s = t * TILE + threadIdx.x;
+        if (s - d.ic[k].slot0 >= D.n) continue;
+        fn(s, k, D);
+    }
+}
+
+template <bool SAVE>
+__global__ void __launch_bounds__(TILE) k_snap(Dev d, Snap S)
+{
+    const size_t plane = (size_t)d.Lmax * d.ncap;
+    for_live_slots(d, [&](int s, int k, const InstD& D) {
+        const int cur = D.cur, lp = D.lp;
+        const int cnt = d.cnt[lp][s];
+        float* h = d.hist[lp] + s;
+        float* hs = S.hist + s;
+        if (SAVE) {
+            S.pos[s] = d.pos[cur][s];
+            S.vel[s] = d.vel[cur][s];
+            S.omg[s] = d.omg[cur][s];
+            S.hmask[s] = d.hmask[lp][s];
+            S.whist[s] = d.whist[lp][s];
+            for (int e = 0; e < cnt; ++e)
+                for (int c3 = 0; c3 < 3; ++c3) hs[c3 * plane + (size_t)e * d.ncap] = h[c3 * plane + (size_t)e * d.ncap];
+        } else {
+            d.pos[cur][s] = S.pos[s];
+            d.vel[cur][s] = S.vel[s];
+            d.omg[cur][s] = S.omg[s];
+            d.hmask[lp][s] = S.hmask[s];
+            d.whist[lp][s] = S.whist[s];
+            for (int e = 0; e < cnt; ++e)
+                for (int c3 = 0; c3 < 3; ++c3) h[c3 * plane + (size_t)e * d.ncap] = hs[c3 * plane + (size_t)e * d.ncap];
+        }
+        (void)k;
+    });
+    if (blockIdx.x == 0) {
+        for (int k = threadIdx.x; k < d.B; k += blockDim.x) {
+            if (SAVE) S.disp[k] = d.id[k].disp;
+            else d.id[k].disp = S.disp[k];
+        }
+    }
+}
+
+// F-bar, T-bar of this step from the velocity adjoints (and the drift)
+__global__ void __launch_bounds__(TILE) k_adj_prep(Dev d, AdjBufs a, float kick, int drift)
+{
+    for_live_slots(d, [&](int s, int k, const InstD& D) {
+        const InstC& c = d.ic[k];
+        const float dt = c.dt;
+        float4 vb = a.vb[s];
+        if (drift) {
+            const float4 xb = a.xb[s];
+            vb.x += dt * xb.x;
+            vb.y += dt * xb.y;
+            vb.z += dt * xb.z;
+            a.vb[s] = vb;
+        }
+        const float4 wb = a.wb[s];
+        const float m = d.omg[D.cur][s].w;
+        const float r = (float)d.pos[D.cur][s].w * c.q;
+        const float fk = kick * dt / m, tk = kick * dt / (0.4f * m * r * r);
+        a.Fb[s] = make_float4(fk * vb.x, fk * vb.y, fk * vb.z, 0.f);
+        a.Tb[s] = make_float4(tk * wb.x, tk * wb.y, tk * wb.z, 0.f);
+    });
+}
+
+// pull the force adjoints back to x^n, v^{n-1/2}, w^{n-1/2}, xi^{n-1} and (E, e, mu)
+__global__ void __launch_bounds__(TILE) k_adj_force(Dev d, AdjBufs a, Snap S, int prime)
+{
+    const size_t plane = (size_t)d.Lmax * d.ncap;
+    const int ncap = d.ncap;
+    for_live_slots(d, [&](int s, int k, const InstD& D) {
+        const InstC& c = d.ic[k];
+        const Coef<float> cf = coef_of(c);
+        const int lp = D.lp;
+        const float q = c.q;
+        const int4 P = S.pos[s];
+        const float4 Vv = S.vel[s], Wv = S.omg[s];
+        const float m = Wv.w, r = (float)P.w * q;
+        const V3 vme = v3(Vv.x, Vv.y, Vv.z), wme = v3(Wv.x, Wv.y, Wv.z);
+        const unsigned hm = S.hmask[s];
+        const float dt_hist = prime ? 0.f : c.dt;
+        const float4 Fi = a.Fb[s], Ti = a.Tb[s];
+        float4 xb = a.xb[s], vb = a.vb[s], wb = a.wb[s];
+        double thE = 0.0, the = 0.0, thm = 0.0;
+        const int ncnt = d.cnt[lp][s];
+        const int* nb = d.nbr[lp] + s;
+        float* xbr = a.xib + s;
+        const float* hs = S.hist + s;
+        for (int e = 0; e < ncnt; ++e) {
+            const size_t o = (size_t)e * ncap;
+            const int j = nb[o];
+            const int4 Q = S.pos[j];
+            const int dx = min_image(P.x - Q.x, c.per[0], c.ext[0], c.half[0]);
+            const int dy = min_image(P.y - Q.y, c.per[1], c.ext[1], c.half[1]);
+            const int dz = P.z - Q.z;
+            const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+            const int Sr = P.w + Q.w;
+            const long long S2 = (long long)Sr * Sr;
+            if (d2 >= S2) {
+                xbr[o] = 0.f;
+                xbr[plane + o] = 0.f;
+                xbr[2 * plane + o] = 0.f;
+                continue;
+            }
+            const float4 Vj = S.vel[j], Wj = S.omg[j];
+            const float4 Fj = a.Fb[j], Tj = a.Tb[j];
+            const float d2f = (float)d2;
+            const float inv = rsqrtf(d2f);
+            const float dist = d2f * inv;
+            const float delta = __fdividef((float)(S2 - d2), (float)Sr + dist) * q;
+            const V3 n = v3((float)dx * inv, (float)dy * inv, (float)dz * inv);
+            const float rj = (float)Q.w * q;
+            const V3 xio = ((hm >> e) & 1u) ? v3(hs[o], hs[plane + o], hs[2 * plane + o]) : v3(0.f, 0.f, 0.f);
+            const V3 G = v3(Fi.x - Fj.x, Fi.y - Fj.y, Fi.z - Fj.z);
+            const V3 H = v3(r * Ti.x + rj * Tj.x, r * Ti.y + rj * Tj.y, r * Ti.z + rj * Tj.z);
+            const V3 xibar = v3(xbr[o], xbr[plane + o], xbr[2 * plane + o]);
+            PairGrad<float> g;
+            contact_vjp<float, false>(cf, delta, n, dist * q, r, rj, m, Wj.w, vme, v3(Vj.x, Vj.y, Vj.z), wme,
+                                      v3(Wj.x, Wj.y, Wj.z), xio, dt_hist, G, H, xibar, g);
+            xb.x += g.r.x; xb.y += g.r.y; xb.z += g.r.z;
+            vb.x += g.va.x; vb.y += g.va.y; vb.z += g.va.z;
+            wb.x += g.wa.x; wb.y += g.wa.y; wb.z += g.wa.z;
+            xbr[o] = g.xi.x;
+            xbr[plane + o] = g.xi.y;
+            xbr[2 * plane + o] = g.xi.z;
+            // each side of the pair adds half of the parameter derivative
+            thE += 0.5 * ((double)g.c_kn * c.c_kn + (double)g.c_kt * c.c_kt) * c.inv_E;
+            the += 0.5 * (double)g.nbeta * c.dnb_de;
+            thm += 0.5 * (double)g.mu;
+        }
+        float4 wx = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c.floor_on) {
+            const int dw = P.w - P.z;
+            if (dw > 0) {
+                const bool wall_prev = (__float_as_uint(Vv.w) & WALL_BIT) != 0u;
+                const float4 hw = S.whist[s];
+                const V3 xio = wall_prev ? v3(hw.x, hw.y, hw.z) : v3(0.f, 0.f, 0.f);
+                const float4 wxo = a.wxib[s];
+                PairGrad<float> g;
+                contact_vjp<float, true>(cf, (float)dw * q, v3(0.f, 0.f, 1.f), (float)P.z * q, r, 0.f, m, 0.f, vme,
+                                         v3(c.floor_v[0], c.floor_v[1], c.floor_v[2]), wme, v3(0.f, 0.f, 0.f), xio,
+                                         dt_hist, v3(Fi.x, Fi.y, Fi.z), v3(r * Ti.x, r * Ti.y, r * Ti.z),
+                                         v3(wxo.x, wxo.y, wxo.z), g);
+                xb.z += g.r.z;
+                vb.x += g.va.x; vb.y += g.va.y; vb.z += g.va.z;
+                wb.x += g.wa.x; wb.y += g.wa.y; wb.z += g.wa.z;
+                wx = make_float4(g.xi.x, g.xi.y, g.xi.z, 0.f);
+                thE += ((double)g.c_kn * c.c_kn + (double)g.c_kt * c.c_kt) * c.inv_E;
+                the += (double)g.nbeta * c.dnb_de;
+                if (c.mu_w_follows) thm += (double)g.mu;
+            }
+        }
+        a.wxib[s] = wx;
+        a.xb[s] = xb;
+        a.vb[s] = vb;
+        a.wb[s] = wb;
+        a.thb[3 * (size_t)s] += thE;
+        a.thb[3 * (size_t)s + 1] += the;
+        a.thb[3 * (size_t)s + 2] += thm;
+    });
+}
+
+// Observables at the evaluated step, one block per instance (deterministic
+// fixed-order reductions): kinetic energy sum 1/2 m v^2 + 1/2 I w^2, and the
+// runout max_i |(x_i, y_i) - axis| with the particle attaining it (lowest ID on
+// ties).  small[16 k + ...]: 0-1 axis (in), 2 KE, 3 runout, 4 argmax slot.
+__global__ void __launch_bounds__(256) k_obs(Dev d, const HostInstLo* __restrict__ hl)
+{
+    const int k = blockIdx.x;
+    const InstC& c = d.ic[k];
+    const InstD D = d.id[k];
+    double* sm = d.small + 16 * k;
+    const double cx = sm[0], cy = sm[1];
+    double ke = 0.0, best = -1.0;
+    int bslot = -1;
+    unsigned bid = 0xffffffffu;
+    for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
+        const int s = c.slot0 + i;
+        const float4 v = d.outV[s], w = d.outW[s];
+        const float m = d.omg[D.cur][s].w;
+        const int4 p = d.pos[D.cur][s];
+        const double r = (double)p.w * hl[k].q;
+        const double I = 0.4 * m * r * r;
+        ke += 0.5 * m * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z) +
+              0.5 * I * ((double)w.x * w.x + (double)w.y * w.y + (double)w.z * w.z);
+        const double x = hl[k].lo[0] + (double)p.x * hl[k].q - cx;
+        const double y = hl[k].lo[1] + (double)p.y * hl[k].q - cy;
+        const double rho = sqrt(x * x + y * y);
+        const unsigned id = __float_as_uint(d.vel[D.cur][s].w) & ID_MASK;
+        if (rho > best || (rho == best && id < bid)) {
+            best = rho;
+            bslot = s;
+            bid = id;
+        }
+    }
+    __shared__ double ske[256], sbest[256];
+    __shared__ int sslot[256];
+    __shared__ unsigned sid[256];
+    ske[threadIdx.x] = ke;
+    sbest[threadIdx.x] = best;
+    sslot[threadIdx.x] = bslot;
+    sid[threadIdx.x] = bid;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const int t = threadIdx.x + o;
+            ske[threadIdx.x] += ske[t];
+            if (sbest[t] > sbest[threadIdx.x] || (sbest[t] == sbest[threadIdx.x] && sid[t] < sid[threadIdx.x])) {
+                sbest[threadIdx.x] = sbest[t];
+                sslot[threadIdx.x] = sslot[t];
+                sid[threadIdx.x] = sid[t];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sm[2] = ske[0];
+        sm[3] = sbest[0] < 0.0 ? 0.0 : sbest[0];
+        sm[4] = (double)sslot[0];
+    }
+}
+
+// Adjoint seeds of  sum_k w_KE,k KE_k + w_R,k runout_k  at the final step
+// (small[16 k + 5..6] = weights), and zeroed history and parameter adjoints.
+__global__ void __launch_bounds__(TILE) k_adj_seed(Dev d, AdjBufs a, const HostInstLo* __restrict__ hl)
+{
+    const size_t plane = (size_t)d.Lmax * d.ncap;
+    for_live_slots(d, [&](int s, int k, const InstD& D) {
+        const double* sm = d.small + 16 * k;
+        const float wke = (float)sm[5], wro = (float)sm[6];
+        const float4 v = d.outV[s], w = d.outW[s];
+        const float m = d.omg[D.cur][s].w;
+        const int4 p = d.pos[D.cur][s];
+        const float r = (float)(p.w * hl[k].q);
+        const float I = 0.4f * m * r * r;
+        float4 xb = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((int)sm[4] == s && sm[3] > 0.0) {
+            const double x = hl[k].lo[0] + (double)p.x * hl[k].q - sm[0];
+            const double y = hl[k].lo[1] + (double)p.y * hl[k].q - sm[1];
+            xb.x = (float)(wro * x / sm[3]);
+            xb.y = (float)(wro * y / sm[3]);
+        }
+        a.xb[s] = xb;
+        a.vb[s] = make_float4(wke * m * v.x, wke * m * v.y, wke * m * v.z, 0.f);
+        a.wb[s] = make_float4(wke * I * w.x, wke * I * w.y, wke * I * w.z, 0.f);
+        a.wxib[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = 0; e < d.Lmax; ++e)
+            for (int c3 = 0; c3 < 3; ++c3) a.xib[c3 * plane + (size_t)e * d.ncap + s] = 0.f;
+        a.thb[3 * (size_t)s] = a.thb[3 * (size_t)s + 1] = a.thb[3 * (size_t)s + 2] = 0.0;
+    });
+}
+
+// per-instance sum of the parameter adjoints (fixed order) into small[16 k + 8..10]
+__global__ void __launch_bounds__(256) k_adj_reduce(Dev d, AdjBufs a)
+{
+    const int k = blockIdx.x;
+    const InstC& c = d.ic[k];
+    const int n = d.id[k].n;
+    __shared__ double sh[3][256];
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int q3 = 0; q3 < 3; ++q3) t[q3] += a.thb[3 * (size_t)(c.slot0 + i) + q3];
+    for (int q3 = 0; q3 < 3; ++q3) sh[q3][threadIdx.x] = t[q3];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int q3 = 0; q3 < 3; ++q3) sh[q3][threadIdx.x] += sh[q3][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q3 = 0; q3 < 3; ++q3) d.small[16 * k + 8 + q3] = sh[q3][0];
+}
+
 }  // namespace
 
 // ============================================================== host side
@@ -959,7 +1217,17 @@ struct dem_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<cudaEvent_t> ev0, ev1;   // around each step kernel of the graph
+    std::vector<double> nu;              // Poisson ratio per instance (for material updates)
+    struct Rollout {
+        bool ready = false;
+        long long nsteps = 0, K = 0;
+        int ncp = 0;
+        bool prime0 = false;
+        std::vector<Snap> ck, seg;       // checkpoints (every K steps and the end), segment steps
+        AdjBufs a{};
+    } ro;
 };
+using Rollout = dem_ctx::Rollout;
 
 namespace {
 
@@ -1000,7 +1268,7 @@ struct Plan {
     // offsets
     size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_whist[2];
     size_t o_cellcode, o_cslot, o_perm, o_ccount, o_cstart, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
-        o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl;
+        o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl, o_small;
     size_t bytes = 0;
 };
 
@@ -1102,6 +1370,10 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
         c.mu = (float)s.mu;
         c.mu_w = (float)(s.mu_wall < 0 ? s.mu : s.mu_wall);
         c.gt_ratio = (float)std::sqrt(2.0 * (8.0 * Geff) / (3.0 * (4.0 / 3.0 * Eeff)));
+        c.mu_w_follows = s.mu_wall < 0 ? 1 : 0;
+        c.inv_E = (float)(1.0 / E);
+        // beta = ln e / sqrt(ln^2 e + pi^2): dbeta/de = pi^2 / (e (ln^2 e + pi^2)^(3/2))
+        c.dnb_de = (float)(-(M_PI * M_PI) / (s.e * std::pow(le * le + M_PI * M_PI, 1.5)));
         h.q = q;
         h.rho = s.rho;
         p.ic.push_back(c);
@@ -1156,6 +1428,7 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
     p.o_cmask = L.take(N * 8);
     p.o_stage = L.take(N * 24);
     p.o_hl = L.take(sizeof(HostInstLo) * p.B);
+    p.o_small = L.take(sizeof(double) * 16 * p.B);
     p.bytes = L.total;
     return DEM_OK;
 }
@@ -1187,6 +1460,10 @@ dem_status check_status(dem_ctx* ctx)
     if (ctx->status & ST_CAPACITY) return fail(ctx, DEM_ERR_CAPACITY, "neighbour list wider than max_neighbors");
     if (ctx->status & ST_TIMEOUT) return fail(ctx, DEM_ERR_TIMEOUT, "a bounded device wait gave up");
     if (ctx->status & ST_TRUNC) return fail(ctx, DEM_ERR_CAPACITY, "more contacts than the output width");
+    if (ctx->status & ST_SKIN)
+        return fail(ctx, DEM_ERR_CAPACITY,
+                    "a particle moved more than half the skin while the lists were frozen for a differentiable "
+                    "rollout: use a larger skin");
     return DEM_ERR_STATE;
 }
 
@@ -1353,6 +1630,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     ctx->nparts = p.nparts;
     ctx->ic = p.ic;
     ctx->hl = p.hl;
+    for (int k = 0; k < p.B; ++k) ctx->nu.push_back(cfg->inst[k].nu);
     ctx->count = p.count;
     char* base = (char*)workspace;
     Dev& d = ctx->dev;
@@ -1389,6 +1667,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     d.cmask = (unsigned long long*)(base + p.o_cmask);
     d.stage = (double*)(base + p.o_stage);
     ctx->d_hl = (HostInstLo*)(base + p.o_hl);
+    d.small = (double*)(base + p.o_small);
     d.ncap = p.ncap;
     d.ntiles = p.ntiles;
     d.B = p.B;
@@ -1648,6 +1927,218 @@ const char* dem_last_error(const dem_ctx* ctx)
 {
     if (!ctx) return g_cfg_err.c_str();
     return ctx->err.c_str();
+}
+
+}  // extern "C"
+
+// ================================================================ rollout (host)
+
+namespace {
+
+size_t snap_layout(const dem_ctx* ctx, Layout& L, Snap* S, char* base)
+{
+    const size_t N = (size_t)ctx->ncap, Lm = (size_t)ctx->Lmax;
+    size_t o_pos = L.take(N * 16), o_vel = L.take(N * 16), o_omg = L.take(N * 16), o_h = L.take(N * Lm * 12),
+           o_hm = L.take(N * 4), o_wh = L.take(N * 16), o_disp = L.take(sizeof(float) * ctx->B);
+    if (S && base) {
+        S->pos = (int4*)(base + o_pos);
+        S->vel = (float4*)(base + o_vel);
+        S->omg = (float4*)(base + o_omg);
+        S->hist = (float*)(base + o_h);
+        S->hmask = (unsigned*)(base + o_hm);
+        S->whist = (float4*)(base + o_wh);
+        S->disp = (float*)(base + o_disp);
+    }
+    return L.total;
+}
+
+size_t rollout_layout(dem_ctx* ctx, long long nsteps, long long K, char* base)
+{
+    Layout L;
+    const int ncp = (int)((nsteps + K - 1) / K) + 1;
+    const int nseg = (int)std::min<long long>(K, nsteps);
+    if (base) {
+        ctx->ro.ck.assign(ncp, Snap{});
+        ctx->ro.seg.assign(nseg, Snap{});
+    }
+    for (int i = 0; i < ncp; ++i) snap_layout(ctx, L, base ? &ctx->ro.ck[i] : nullptr, base);
+    for (int i = 0; i < nseg; ++i) snap_layout(ctx, L, base ? &ctx->ro.seg[i] : nullptr, base);
+    const size_t N = (size_t)ctx->ncap, Lm = (size_t)ctx->Lmax;
+    size_t o_xb = L.take(N * 16), o_vb = L.take(N * 16), o_wb = L.take(N * 16), o_Fb = L.take(N * 16),
+           o_Tb = L.take(N * 16), o_xib = L.take(N * Lm * 12), o_wxib = L.take(N * 16), o_thb = L.take(N * 24);
+    if (base) {
+        AdjBufs& a = ctx->ro.a;
+        a.xb = (float4*)(base + o_xb);
+        a.vb = (float4*)(base + o_vb);
+        a.wb = (float4*)(base + o_wb);
+        a.Fb = (float4*)(base + o_Fb);
+        a.Tb = (float4*)(base + o_Tb);
+        a.xib = (float*)(base + o_xib);
+        a.wxib = (float4*)(base + o_wxib);
+        a.thb = (double*)(base + o_thb);
+    }
+    return L.total;
+}
+
+dem_status set_frozen(dem_ctx* ctx, unsigned v)
+{
+    CU(cudaMemcpyAsync(&ctx->dev.g->frozen, &v, sizeof(unsigned), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+dem_status snap(dem_ctx* ctx, const Snap& S, bool save)
+{
+    if (save) k_snap<true><<<ctx->grid_rb, TILE, 0, ctx->stream>>>(ctx->dev, S);
+    else k_snap<false><<<ctx->grid_rb, TILE, 0, ctx->stream>>>(ctx->dev, S);
+    CU(cudaGetLastError());
+    return DEM_OK;
+}
+
+dem_status step_once(dem_ctx* ctx, int prime)
+{
+    k_step<0><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, prime, 0, 0);
+    CU(cudaGetLastError());
+    return DEM_OK;
+}
+
+dem_status upload_material(dem_ctx* ctx)
+{
+    CU(cudaMemcpyAsync((void*)ctx->dev.ic, ctx->ic.data(), sizeof(InstC) * ctx->B, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dem_status dem_set_material(dem_ctx* ctx, const double* params)
+{
+    if (!ctx || !params) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    for (int k = 0; k < ctx->B; ++k) {
+        const double E = params[3 * k], e = params[3 * k + 1], mu = params[3 * k + 2];
+        if (!(E > 0) || !(e > 0 && e <= 1) || !(mu >= 0)) return fail(ctx, DEM_ERR_ARG, "need E > 0, 0 < e <= 1, mu >= 0");
+        InstC& c = ctx->ic[k];
+        const double nu = ctx->nu[k];
+        const double Eeff = 1.0 / (2.0 * (1.0 - nu * nu) / E);
+        const double Geff = 1.0 / (2.0 * 2.0 * (2.0 - nu) * (1.0 + nu) / E);
+        const double le = std::log(e);
+        c.c_kn = (float)(4.0 / 3.0 * Eeff);
+        c.c_kt = (float)(8.0 * Geff);
+        c.nbeta = (float)(-(le / std::sqrt(le * le + M_PI * M_PI)));
+        c.mu = (float)mu;
+        if (c.mu_w_follows) c.mu_w = (float)mu;
+        c.inv_E = (float)(1.0 / E);
+        c.dnb_de = (float)(-(M_PI * M_PI) / (e * std::pow(le * le + M_PI * M_PI, 1.5)));
+    }
+    return upload_material(ctx);
+}
+
+dem_status dem_rollout_workspace(dem_ctx* ctx, int64_t nsteps, int64_t checkpoint_every, int64_t* bytes)
+{
+    if (!ctx || !bytes || nsteps < 1 || checkpoint_every < 1) return DEM_ERR_ARG;
+    *bytes = (int64_t)rollout_layout(ctx, nsteps, checkpoint_every, nullptr);
+    return DEM_OK;
+}
+
+dem_status dem_rollout_forward(dem_ctx* ctx, int64_t nsteps, int64_t checkpoint_every, void* ws, int64_t ws_bytes)
+{
+    if (!ctx || nsteps < 1 || checkpoint_every < 1 || !ws) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    if (!ctx->have_state) return fail(ctx, DEM_ERR_STATE, "write the state before a rollout");
+    const size_t need = rollout_layout(ctx, nsteps, checkpoint_every, nullptr);
+    if ((size_t)ws_bytes < need || ((uintptr_t)ws & 255)) return fail(ctx, DEM_ERR_ARG, "rollout workspace too small");
+    rollout_layout(ctx, nsteps, checkpoint_every, (char*)ws);
+    Rollout& ro = ctx->ro;
+    ro.nsteps = nsteps;
+    ro.K = checkpoint_every;
+    ro.ncp = (int)ro.ck.size();
+    ro.prime0 = ctx->fresh;
+    dem_status st = launch_rebuild(ctx, ctx->stream);       // the lists the whole rollout uses
+    if (st) return st;
+    if ((st = set_frozen(ctx, 1u))) return st;
+    for (long long s = 0; s < nsteps; ++s) {
+        if (s % ro.K == 0 && (st = snap(ctx, ro.ck[s / ro.K], true))) return st;
+        if ((st = step_once(ctx, (s == 0 && ro.prime0) ? 1 : 0))) return st;
+    }
+    if ((st = snap(ctx, ro.ck[ro.ncp - 1], true))) return st;
+    if ((st = set_frozen(ctx, 0u))) return st;
+    ctx->fresh = false;
+    ctx->steps += nsteps;
+    ro.ready = true;
+    return dem_sync_status(ctx);
+}
+
+dem_status dem_observables(dem_ctx* ctx, const double* axis, double* out)
+{
+    if (!ctx || !axis || !out) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    if (!ctx->have_state) return fail(ctx, DEM_ERR_STATE, "write the state first");
+    dem_status st = launch_eval(ctx);
+    if (st) return st;
+    std::vector<double> sm(16 * ctx->B, 0.0);
+    for (int k = 0; k < ctx->B; ++k) { sm[16 * k] = axis[2 * k]; sm[16 * k + 1] = axis[2 * k + 1]; }
+    CU(cudaMemcpyAsync(ctx->dev.small, sm.data(), sizeof(double) * sm.size(), cudaMemcpyHostToDevice, ctx->stream));
+    k_obs<<<ctx->B, 256, 0, ctx->stream>>>(ctx->dev, ctx->d_hl);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(sm.data(), ctx->dev.small, sizeof(double) * sm.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < ctx->B; ++k) { out[2 * k] = sm[16 * k + 2]; out[2 * k + 1] = sm[16 * k + 3]; }
+    return dem_sync_status(ctx);
+}
+
+dem_status dem_rollout_adjoint(dem_ctx* ctx, const double* weights, const double* axis, double* grad)
+{
+    if (!ctx || !weights || !axis || !grad) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    Rollout& ro = ctx->ro;
+    if (!ro.ready) return fail(ctx, DEM_ERR_STATE, "run dem_rollout_forward first");
+    cudaStream_t s = ctx->stream;
+    // observables and their seeds at the final step N
+    dem_status st = launch_eval(ctx);
+    if (st) return st;
+    std::vector<double> sm(16 * ctx->B, 0.0);
+    for (int k = 0; k < ctx->B; ++k) {
+        sm[16 * k] = axis[2 * k];
+        sm[16 * k + 1] = axis[2 * k + 1];
+        sm[16 * k + 5] = weights[2 * k];
+        sm[16 * k + 6] = weights[2 * k + 1];
+    }
+    CU(cudaMemcpyAsync(ctx->dev.small, sm.data(), sizeof(double) * sm.size(), cudaMemcpyHostToDevice, s));
+    k_obs<<<ctx->B, 256, 0, s>>>(ctx->dev, ctx->d_hl);
+    k_adj_seed<<<ctx->grid_rb, TILE, 0, s>>>(ctx->dev, ro.a, ctx->d_hl);
+    CU(cudaGetLastError());
+    if ((st = set_frozen(ctx, 1u))) return st;
+    const long long N = ro.nsteps, K = ro.K;
+    // v^N = v^{N-1/2} + dt/2 F^N / m: the evaluation at N with a half kick and no drift
+    k_adj_prep<<<ctx->grid_rb, TILE, 0, s>>>(ctx->dev, ro.a, 0.5f, 0);
+    k_adj_force<<<ctx->grid_rb, TILE, 0, s>>>(ctx->dev, ro.a, ro.ck[ro.ncp - 1], 0);
+    CU(cudaGetLastError());
+    for (int c = ro.ncp - 2; c >= 0; --c) {
+        const long long s0 = (long long)c * K, s1 = std::min(s0 + K, N);
+        if ((st = snap(ctx, ro.ck[c], false))) return st;          // restore step s0
+        for (long long t = s0; t < s1; ++t) {                      // recompute the segment
+            if ((st = snap(ctx, ro.seg[t - s0], true))) return st;
+            if ((st = step_once(ctx, (t == 0 && ro.prime0) ? 1 : 0))) return st;
+        }
+        for (long long t = s1 - 1; t >= s0; --t) {
+            const bool pr = t == 0 && ro.prime0;
+            k_adj_prep<<<ctx->grid_rb, TILE, 0, s>>>(ctx->dev, ro.a, pr ? 0.5f : 1.0f, 1);
+            k_adj_force<<<ctx->grid_rb, TILE, 0, s>>>(ctx->dev, ro.a, ro.seg[t - s0], pr ? 1 : 0);
+            CU(cudaGetLastError());
+        }
+    }
+    k_adj_reduce<<<ctx->B, 256, 0, s>>>(ctx->dev, ro.a);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(sm.data(), ctx->dev.small, sizeof(double) * sm.size(), cudaMemcpyDeviceToHost, s));
+    if ((st = snap(ctx, ro.ck[ro.ncp - 1], false))) return st;    // back to the final state
+    if ((st = set_frozen(ctx, 0u))) return st;
+    for (int k = 0; k < ctx->B; ++k)
+        for (int q = 0; q < 3; ++q) grad[3 * k + q] = sm[16 * k + 8 + q];
+    return dem_sync_status(ctx);
 }
 
 }  // extern "C"

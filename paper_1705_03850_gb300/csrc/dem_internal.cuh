@@ -39,6 +39,7 @@ constexpr unsigned ST_NONFINITE = 2u;
 constexpr unsigned ST_ESCAPED = 4u;
 constexpr unsigned ST_TIMEOUT = 8u;
 constexpr unsigned ST_TRUNC = 16u;
+constexpr unsigned ST_SKIN = 32u;     // displacement exceeded the skin while lists were frozen
 
 // constant description of one instance (host-computed at create)
 struct InstC {
@@ -52,12 +53,14 @@ struct InstC {
     int floor_on;
     int skin;            // skin in units
     int clamp_fn;
-    int pad0;
+    int mu_w_follows;    // 1: the wall friction is mu (it follows mu in derivatives)
     float q, dt, dt_over_q, skin_f;
     float g[3];
     float floor_v[3];
     float c_kn, c_kt, nbeta, mu, mu_w;   // 4/3 E_eff, 8 G_eff, -beta, mu, mu_wall
     float gt_ratio;                      // gamma_t / gamma_n = sqrt(2 c_kt / (3 c_kn))
+    float inv_E;                         // 1 / E (c_kn and c_kt are proportional to E)
+    float dnb_de;                        // d(-beta)/de
 };
 
 // dynamic state of one instance (device-resident)
@@ -75,7 +78,7 @@ struct Glob {
     unsigned status;
     unsigned any;              // some instance has flag != 0
     unsigned counter;          // last-block detection of the step kernel
-    unsigned pad;
+    unsigned frozen;           // 1: lists are frozen (differentiable rollout), no rebuilds
     unsigned long long rebuilds;
     unsigned long long sum_list;
     unsigned long long sum_contacts;
@@ -115,6 +118,7 @@ struct Dev {
     float* xi_out;             // [3][Lmax][ncap]
     unsigned long long* cmask; // contact bits per list entry at the evaluated step
     double* stage;             // [3 * ncap] staging for host transfers
+    double* small;             // [16 * B] per-instance scratch of observables and gradients
     int ncap;
     int ntiles;
     int B;

@@ -79,6 +79,11 @@ def lib():
         "dem_stats": [vp, ctypes.POINTER(Stats)],
         "dem_set_graph": [vp, i32],
         "dem_graph_step_kernel_ms": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)],
+        "dem_rollout_workspace": [vp, i64, i64, ctypes.POINTER(i64)],
+        "dem_rollout_forward": [vp, i64, i64, vp, i64],
+        "dem_rollout_adjoint": [vp, vp, vp, vp],
+        "dem_observables": [vp, vp, vp],
+        "dem_set_material": [vp, vp],
         "dem_neighbor_counts_noalloc": [vp, vp, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i32), ctypes.c_double, ctypes.c_double, vp, vp],
     }
@@ -95,7 +100,8 @@ def lib():
 def exported_symbols():
     return ["dem_query_workspace", "dem_create", "dem_destroy", "dem_write", "dem_read", "dem_read_contacts",
             "dem_write_contacts", "dem_step", "dem_sync_status", "dem_instance_info_get", "dem_stats",
-            "dem_set_graph", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_last_error"]
+            "dem_set_graph", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
+            "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material", "dem_last_error"]
 
 
 def desc(*, n, lo, hi, periodic, dt, skin, r_max, E, nu, e, mu, rho, g=(0, 0, 0), floor=True,
@@ -244,6 +250,48 @@ class DEM:
         t, c = ctypes.c_double(), ctypes.c_int32()
         self._check(self.L.dem_graph_step_kernel_ms(self.h, ctypes.byref(t), ctypes.byref(c)), "kernel times")
         return t.value, c.value
+
+    # ---- differentiable rollouts -------------------------------------------------
+    @staticmethod
+    def _host(a, shape):
+        arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+        return arr, ctypes.c_void_p(arr.ctypes.data)
+
+    def set_material(self, params):
+        """params (B, 3) = {E, e, mu} per instance."""
+        arr, ptr = self._host(params, (len(self.counts), 3))
+        self._check(self.L.dem_set_material(self.h, ptr), "set material")
+        return self
+
+    def rollout_forward(self, nsteps, checkpoint_every):
+        torch = self.torch
+        nb = ctypes.c_int64()
+        self._check(self.L.dem_rollout_workspace(self.h, int(nsteps), int(checkpoint_every), ctypes.byref(nb)),
+                    "rollout workspace")
+        if getattr(self, "_ro_ws", None) is None or self._ro_ws.numel() < nb.value:
+            self._ro_ws = None
+            self._ro_ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        self._check(self.L.dem_rollout_forward(self.h, int(nsteps), int(checkpoint_every),
+                                               ctypes.c_void_p(self._ro_ws.data_ptr()), int(self._ro_ws.numel())),
+                    "rollout forward")
+        return self
+
+    def observables(self, axis):
+        """(B, 2) = {kinetic energy, runout} at the current step; axis (B, 2) [m]."""
+        B = len(self.counts)
+        ax, axp = self._host(axis, (B, 2))
+        out = np.zeros((B, 2))
+        self._check(self.L.dem_observables(self.h, axp, ctypes.c_void_p(out.ctypes.data)), "observables")
+        return out
+
+    def rollout_adjoint(self, weights, axis):
+        """(B, 3) gradient of sum_k w_KE KE_k + w_R runout_k w.r.t. {E, e, mu} per instance."""
+        B = len(self.counts)
+        w, wp = self._host(weights, (B, 2))
+        ax, axp = self._host(axis, (B, 2))
+        grad = np.zeros((B, 3))
+        self._check(self.L.dem_rollout_adjoint(self.h, wp, axp, ctypes.c_void_p(grad.ctypes.data)), "rollout adjoint")
+        return grad
 
     def info(self, k=0):
         inf = InstanceInfo()

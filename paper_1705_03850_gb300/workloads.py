@@ -172,6 +172,33 @@ def single_sphere(r: float = 1.0e-3, z: float = 0.999e-3, v=(0.2, 0.05, -0.1), w
                    (True, True, False), dt, (0, 0, -9.81), True, (0.3, 0.0, 0.0), 0.1 * 2 * r, 400)
 
 
+def column_collapse(n: int = 10_000, seed: int = 5, mat: Material | None = None, side: int = 14,
+                    spacing: float = 2.1e-3, d: float = 2.0e-3, dt: float = 5e-6, steps: int = 500,
+                    box: float = 0.1) -> Workload:
+    """A granular column released onto a floor: side x side jittered simple-cubic
+    lattice at `spacing` (30 x 30 mm footprint for 14 x 2.1 mm), layers from the
+    floor up until n particles; open x/y in a `box` wide domain centred on the column."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(n)
+    x = np.column_stack([(k % side - (side - 1) / 2) * spacing, ((k // side) % side - (side - 1) / 2) * spacing,
+                         (k // (side * side)) * spacing + d / 2 + 0.02e-3])
+    x += rng.uniform(-0.03e-3, 0.03e-3, x.shape)
+    x[:, :2] += box / 2
+    top = float(x[:, 2].max()) + 4 * d
+    z = np.zeros((n, 3))
+    return _finish(f"column_{n}", x, z, z, np.full(n, d / 2), mat or Material(), (0, 0, 0), (box, box, top),
+                   (False, False, False), dt, (0, 0, -9.81), True, (0, 0, 0), 0.1 * d, steps,
+                   axis=(box / 2, box / 2))
+
+
+def column_materials(count: int = 64, seed: int = 5) -> list[Material]:
+    """Per-instance E log-uniform in [5e6, 5e7] Pa, e ~ U[0.5, 0.95], mu ~ U[0.2, 0.8]."""
+    rng = np.random.default_rng(seed + 2000)
+    return [Material(E=float(math.exp(rng.uniform(math.log(5e6), math.log(5e7)))), nu=0.25,
+                     e=float(rng.uniform(0.5, 0.95)), mu=float(rng.uniform(0.2, 0.8)), rho=2500.0)
+            for _ in range(count)]
+
+
 def batch_sizes(count: int = 256, seed: int = 4, nmin: float = 2e3, nmax: float = 2e5) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.round(np.exp(rng.uniform(math.log(nmin), math.log(nmax), count))).astype(np.int64)

@@ -181,7 +181,7 @@ def column_collapse(n: int = 10_000, seed: int = 5, mat: Material | None = None,
     rng = np.random.default_rng(seed)
     k = np.arange(n)
     x = np.column_stack([(k % side - (side - 1) / 2) * spacing, ((k // side) % side - (side - 1) / 2) * spacing,
-                         (k // (side * side)) * spacing + d / 2 + 0.02e-3])
+                         (k // (side * side)) * spacing + d / 2 + 0.05e-3])
     x += rng.uniform(-0.03e-3, 0.03e-3, x.shape)
     x[:, :2] += box / 2
     top = float(x[:, 2].max()) + 4 * d
@@ -215,7 +215,7 @@ def settling_box(n: int, seed: int, mat: Material, d: float = 2.0e-3, spacing: f
     s = per * spacing
     k = np.arange(n)
     x = np.column_stack([(k % per + 0.5) * spacing, ((k // per) % per + 0.5) * spacing,
-                         (k // (per * per)) * spacing + d / 2 + 0.02e-3])
+                         (k // (per * per)) * spacing + d / 2 + 0.05e-3])
     x += rng.uniform(-0.03e-3, 0.03e-3, x.shape)
     height = float(x[:, 2].max()) + 4 * d       # particles only settle: the cell grid need not reach higher
     z = np.zeros((n, 3))

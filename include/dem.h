@@ -75,7 +75,8 @@ typedef enum {
     DEM_F_FORCE = 5,    /* (n,3) float64 total force at the current step [N]; read only */
     DEM_F_TORQUE = 6,   /* (n,3) float64 total torque at the current step [N m]; read only */
     DEM_F_WALL_XI = 7,  /* (n,3) float64 tangential overlap of the floor contact [m] (0 if none); read only */
-    DEM_F_NBR_COUNT = 8 /* (n)   float64 neighbour-list length of each particle; read only */
+    DEM_F_NBR_COUNT = 8,/* (n)   float64 neighbour-list length of each particle; read only */
+    DEM_F_FEXT = 9      /* (n,3) float64 external (coupling-controller) force held on each particle [N]; read only */
 } dem_field;
 
 /* One independent DEM system ("instance").  A context advances all of its
@@ -246,6 +247,102 @@ dem_status dem_set_material(dem_ctx *ctx, const double *params);
 dem_status dem_neighbor_counts_noalloc(const double *x, const double *r, int64_t n, const double lo[3],
                                        const double hi[3], const int32_t periodic[3], double skin,
                                        double r_max, int32_t *counts, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Two-way volumetric coupling of a coarse-grain level and an embedded fine
+ * level (Sec. 2.3).  Both contexts hold one instance each and share one frame
+ * of reference; both advance `interval` steps between calls of dem_couple.
+ *
+ * Geometry: the fine region is the box [lo, hi].  Each face named in
+ * feed_faces (coarse material flows in through it) is divided into square
+ * surface cells of side >= surface_cell; behind each surface cell, inside the
+ * region, lies one hexahedral transition cell of thickness `layer`.  The
+ * region is also divided into cubic correction cells of edge >= corr_cell.
+ *
+ * One call of dem_couple, in the paper's order:
+ *  - measurement on the coarse level: mass of coarse particles whose centre
+ *    entered the region through each surface cell since the previous call
+ *    (integer multiples of mass_unit), their diameter histogram (`bins` bins
+ *    over [0, 2 r_max of the fine level] after division by alpha), and the
+ *    Favre (mass-weighted) velocity of coarse particles within one diameter
+ *    of the face (Sec. 2.3);
+ *  - per transition and correction cell on both levels: volume fraction,
+ *    Favre velocity, largest speed, and the granular stress of Eq. 7
+ *    (contact part 1/2 r_ij f_ij over contacts, floor contacts with the branch
+ *    vector to the contact point, plus m v' v');
+ *  - stress PI controller per transition cell on the normal stress along the
+ *    face normal (setpoint: coarse, process variable: fine):
+ *    e = s_cg - s_fine, I += e T_c, u = kp e + ki I; every fine particle in
+ *    the cell receives F = u pi r^2 max(0, 1 - s / (1.5 d)) n_in (s: distance
+ *    from the face, n_in: inward normal), shortened so that its speed after one
+ *    step stays below the coarse cell's largest speed; held until the next call;
+ *  - fine-to-coarse P controller per correction cell: target velocity v* =
+ *    fine Favre velocity (mode 0) or that times min(phi_fine / phi_cg, 4)
+ *    (mode 1, mass flow); every coarse particle in the cell receives
+ *    F = kv m (v* - v_cg) / T_c, held until the next call;
+ *  - insertion of fine particles per surface cell by simple sequential
+ *    inhibition: until the inserted mass reaches the entered mass plus the
+ *    carry of earlier intervals, draw a diameter from the histogram (uniform
+ *    within the bin) and a position uniformly in the slab behind the cell
+ *    (depth max(d, |v_n| T_c)), reject it if it overlaps any fine particle or
+ *    an earlier insertion, give up after max_attempts rejections; inserted
+ *    particles take the cell's Favre velocity; random numbers come from the
+ *    SplitMix64 generator on counters (seed, cell, interval, attempt, draw);
+ *  - fine particles whose centre left the region through a drain face are
+ *    removed.  Inserted and removed particles take effect at the fine level's
+ *    next list build, which the call requests.  Fine particle IDs are never
+ *    reused: inserted particles get new IDs, removed IDs read as NaN.
+ * ------------------------------------------------------------------------- */
+typedef struct dem_coupler dem_coupler;
+
+typedef struct {
+    double lo[3], hi[3];    /* fine region [m] */
+    int32_t feed_faces;     /* bit 2a: face at lo[a], bit 2a+1: face at hi[a] */
+    int32_t drain_faces;    /* same bits: fine particles past these faces are removed */
+    double surface_cell;    /* surface / transition cell side [m] (3 to 10 coarse diameters) */
+    double layer;           /* transition layer thickness [m] */
+    double corr_cell;       /* correction cell edge [m] */
+    int32_t interval;       /* steps between calls (T_c = interval dt) */
+    int32_t bins;           /* diameter histogram bins, 1 .. 32 */
+    double alpha;           /* coarse diameter / fine diameter */
+    double kp, ki;          /* stress PI gains [-], [1/s] */
+    double kv;              /* fine-to-coarse P gain [-] */
+    int32_t mode;           /* 0: velocity, 1: mass flow */
+    int32_t max_attempts;   /* SSI rejections per cell and call before giving up */
+    uint64_t seed;          /* random seed of the insertion */
+    double mass_unit;       /* unit of the integer mass bookkeeping [kg] */
+    int32_t max_insert;     /* most particles inserted per surface cell and call */
+    int32_t reserved;
+} dem_coupling;
+
+typedef enum {
+    DEM_CPL_SURFACE_MASS = 0,    /* (S)   mass entered through each surface cell at the last call [kg] */
+    DEM_CPL_SURFACE_CARRY = 1,   /* (S)   mass still to insert [kg] */
+    DEM_CPL_SURFACE_INSERTED = 2,/* (S)   particles inserted at the last call */
+    DEM_CPL_SURFACE_VEL = 3,     /* (S,3) Favre velocity at the face [m/s] */
+    DEM_CPL_SURFACE_HIST = 4,    /* (S,bins) diameter histogram of the entered particles */
+    DEM_CPL_LAYER_STRESS = 5,    /* (H,2,6) stress {xx,yy,zz,xy,xz,yz} [Pa], coarse then fine */
+    DEM_CPL_LAYER_PHI = 6,       /* (H,2) volume fraction */
+    DEM_CPL_LAYER_VEL = 7,       /* (H,2,3) Favre velocity */
+    DEM_CPL_LAYER_VMAX = 8,      /* (H,2) largest speed */
+    DEM_CPL_LAYER_CTRL = 9,      /* (H,3) {error, integral, u} of the stress controller */
+    DEM_CPL_CORR_PHI = 10,       /* (C,2) volume fraction, coarse then fine */
+    DEM_CPL_CORR_VEL = 11,       /* (C,2,3) Favre velocity */
+    DEM_CPL_SIZES = 12           /* (4) {S, H, C, calls so far} */
+} dem_coupler_field;
+
+dem_status dem_coupler_workspace(dem_ctx *coarse, dem_ctx *fine, const dem_coupling *spec, int64_t *bytes);
+dem_status dem_coupler_create(dem_ctx *coarse, dem_ctx *fine, const dem_coupling *spec, void *workspace,
+                              int64_t workspace_bytes, dem_coupler **out);
+dem_status dem_couple(dem_coupler *cp);
+dem_status dem_coupler_read(dem_coupler *cp, int32_t field, double *dst, int64_t n);
+/* Free the coupler (not its workspace).  It does not touch the two contexts,
+ * which may be destroyed before or after it; call it when no dem_couple of
+ * this coupler is running. */
+dem_status dem_coupler_destroy(dem_coupler *cp);
+
+/* Live particles and IDs handed out, per instance (host arrays of B; synchronises). */
+dem_status dem_counts(dem_ctx *ctx, int64_t *live, int64_t *ids);
 
 /* Last error message of the context; with ctx == NULL, the last configuration
  * error (dem_query_workspace / dem_create) of the calling thread.  Never NULL. */

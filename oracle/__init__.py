@@ -32,7 +32,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, f) for f in ("dem_oracle.c", "dem_oracle_cs.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("dem_oracle.c", "dem_oracle_cs.c", "dem_oracle_couple.c")]
 _HDRS = [os.path.join(_HERE, f) for f in ("dem_oracle_common.h", "dem_oracle_dyn.h")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
@@ -76,6 +76,12 @@ def _load():
     lib.orc_cs_run_derivative.restype = ctypes.c_int32
     lib.orc_cs_run_derivative.argtypes = [dp, ctypes.c_int32, ctypes.c_double, i64, dp, dp, dp, dp, dp, i64p, i64,
                                           ctypes.c_int32, i64] + [dp] * 10
+    u64 = ctypes.c_uint64
+    lib.orc_couple.restype = ctypes.c_int32
+    lib.orc_couple.argtypes = ([dp, u64, ctypes.c_int32, dp, i64, dp, dp, dp, dp, dp, i64p, dp, i64, dp, dp, dp, dp,
+                                dp, i64p, dp, ctypes.c_double, i64, dp, i32p, i64p, dp, ctypes.c_double,
+                                ctypes.c_double, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_uint32), dp, dp, dp, dp,
+                                dp, dp, i32p, i64p, dp, i32p])
     lib.orc_run.restype = ctypes.c_int32
     lib.orc_run.argtypes = [dp, i64, dp, dp, dp, dp, dp, i64p, i64p, i64, i64p, i64p, dp,
                             i32p, dp, dp, i64, ctypes.c_int32, ctypes.c_int32]
@@ -172,6 +178,114 @@ def rollout_derivative(P, x, v, w, r, m, nsteps, param, h=None, ids=None, use_ce
     if rc != 0:
         raise RuntimeError("oracle history capacity exceeded")
     return outs
+
+
+def quantum(lo, hi):
+    """Length unit of a level's integer positions: the smallest power of two with
+    (largest box extent) / q <= 2^30 (the rule the library documents)."""
+    import math
+    emax = max(h - l for l, h in zip(lo, hi))
+    q = 2.0 ** math.ceil(math.log2(emax / 2.0 ** 30))
+    while emax / q > 2.0 ** 30:
+        q *= 2.0
+    return q
+
+
+class Coupler:
+    """FP64 oracle of the coarse/fine coupling (see dem_oracle_couple.c).
+
+    spec: dict with the fields of dem_coupling; Pc, Pf: parameter blocks of the
+    levels; the fine frame (lof, qf) and largest fine radius rmaxf_u in fine units.
+    """
+
+    def __init__(self, spec, Pc, Pf, lof, qf, rmaxf_u, rho_f, idcap):
+        self.CP = np.zeros(24)
+        self.CP[0:3] = spec["lo"]
+        self.CP[3:6] = spec["hi"]
+        self.CP[6] = spec["feed_faces"]
+        self.CP[7] = spec.get("drain_faces", 0)
+        self.CP[8] = spec["surface_cell"]
+        self.CP[9] = spec["layer"]
+        self.CP[10] = spec["corr_cell"]
+        self.CP[11] = spec["interval"]
+        self.CP[12] = spec["bins"]
+        self.CP[13] = spec["alpha"]
+        self.CP[14] = spec["kp"]
+        self.CP[15] = spec["ki"]
+        self.CP[16] = spec["kv"]
+        self.CP[17] = spec["mode"]
+        self.CP[18] = spec["max_attempts"]
+        self.CP[20] = spec["mass_unit"]
+        self.CP[21] = spec["max_insert"]
+        self.CP[22] = spec["dt"]
+        self.CP[23] = rho_f
+        self.seed = int(spec["seed"])
+        self.Pc = np.ascontiguousarray(Pc, dtype=np.float64)
+        self.Pf = np.ascontiguousarray(Pf, dtype=np.float64)
+        self.lof = np.ascontiguousarray(lof, dtype=np.float64)
+        self.qf = float(qf)
+        self.rmaxf_u = int(rmaxf_u)
+        self.prev = np.zeros((idcap, 3))
+        self.prev_ok = np.zeros(idcap, dtype=np.int32)
+        self.calls = 0
+        self.S = None
+
+    def _sizes(self):
+        lo, hi, sc, cc = self.CP[0:3], self.CP[3:6], self.CP[8], self.CP[10]
+        S = 0
+        for bit in range(6):
+            if not (int(self.CP[6]) >> bit) & 1:
+                continue
+            a = bit // 2
+            b, c = sorted(((a + 1) % 3, (a + 2) % 3))
+            S += max(1, int(np.floor((hi[b] - lo[b]) / sc))) * max(1, int(np.floor((hi[c] - lo[c]) / sc)))
+        C = 1
+        for a in range(3):
+            C *= max(1, int(np.floor((hi[a] - lo[a]) / cc)))
+        return S, C
+
+    def record(self, xc, idc):
+        for i, k in enumerate(np.asarray(idc)):
+            self.prev[k] = xc[i]
+            self.prev_ok[k] = 1
+
+    def call(self, coarse, fine, dth_c, dth_f):
+        """coarse, fine: dicts x, v, w, r, m, id (float64 / int64 arrays). Returns a dict of outputs."""
+        lib = _load()
+        S, C = self._sizes()
+        if self.S is None:
+            self.S = S
+            self.carry = np.zeros(S, dtype=np.int64)
+            self.integ = np.zeros(S)
+        self.calls += 1
+        bins, mi = int(self.CP[12]), int(self.CP[21])
+        nc, nf = len(coarse["r"]), len(fine["r"])
+        out = dict(cross=np.zeros(S, dtype=np.uint64), hist=np.zeros(S * bins, dtype=np.uint32), fav=np.zeros(S * 4),
+                   lay=np.zeros(2 * S * 11), ctrl=np.zeros(S * 3), cor=np.zeros(2 * C * 5), fext_c=np.zeros(nc * 3),
+                   fext_f=np.zeros(nf * 3), removed=np.zeros(nf, dtype=np.int32),
+                   ins_u=np.zeros(S * mi * 4, dtype=np.int64), ins_m=np.zeros(S * mi), nins=np.zeros(S, dtype=np.int32))
+        c = {k: np.ascontiguousarray(v, dtype=np.int64 if k == "id" else np.float64) for k, v in coarse.items()}
+        f = {k: np.ascontiguousarray(v, dtype=np.int64 if k == "id" else np.float64) for k, v in fine.items()}
+        u64p = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        u32p = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+        lib.orc_couple(_d(self.CP), self.seed, self.calls, _d(self.Pc), nc, _d(c["x"]), _d(c["v"]), _d(c["w"]),
+                       _d(c["r"]), _d(c["m"]), _i64(c["id"]), _d(self.Pf), nf, _d(f["x"]), _d(f["v"]), _d(f["w"]),
+                       _d(f["r"]), _d(f["m"]), _i64(f["id"]), _d(self.lof), self.qf, self.rmaxf_u, _d(self.prev),
+                       _i32(self.prev_ok), _i64(self.carry), _d(self.integ), float(dth_c), float(dth_f),
+                       u64p(out["cross"]), u32p(out["hist"]), _d(out["fav"]), _d(out["lay"]), _d(out["ctrl"]),
+                       _d(out["cor"]), _d(out["fext_c"]), _d(out["fext_f"]), _i32(out["removed"]), _i64(out["ins_u"]),
+                       _d(out["ins_m"]), _i32(out["nins"]))
+        out["carry"] = self.carry.copy()
+        out["hist"] = out["hist"].reshape(S, bins)
+        out["fav"] = out["fav"].reshape(S, 4)
+        out["lay"] = out["lay"].reshape(2, S, 11)
+        out["ctrl"] = out["ctrl"].reshape(S, 3)
+        out["cor"] = out["cor"].reshape(2, C, 5)
+        out["ins_u"] = out["ins_u"].reshape(S, mi, 4)
+        out["ins_m"] = out["ins_m"].reshape(S, mi)
+        out["fext_c"] = out["fext_c"].reshape(nc, 3)
+        out["fext_f"] = out["fext_f"].reshape(nf, 3)
+        return out
 
 
 class Sim:

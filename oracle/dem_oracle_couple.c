@@ -1,0 +1,484 @@
+/*
+ * FP64 oracle of the two-way volumetric coupling between a coarse-grain level
+ * and an embedded fine level (Sec. 2.3 of Queteschiner et al. 2017).
+ * TEST INFRASTRUCTURE ONLY (see dem_oracle.c).
+ *
+ * One call, in the paper's order and with the readings stated for the
+ * library (the paper fixes neither cell sizes, bins, gains, fade shape nor the
+ * random generator):
+ *   1. boundary surface (feed faces split into square cells): mass of coarse
+ *      particles whose centre entered the region through each cell since the
+ *      previous call (integer mass units), their fine-scale diameter
+ *      histogram (r / alpha), and the mass-weighted (Favre) velocity of coarse
+ *      particles within one diameter of the face;
+ *   2. transition layer (one hexahedral cell behind each surface cell) on both
+ *      levels: volume fraction, Favre velocity, largest speed and the granular
+ *      stress of Eq. 7 (1/2 r_ij f_ij over contacts, floor contacts with the
+ *      branch vector to the contact point, plus m v'v', symmetrised);
+ *   3. stress PI controller on the face-normal stress (setpoint coarse,
+ *      process variable fine) and its force on fine particles, faded out
+ *      linearly over 3/2 fine diameters and limited by the coarse cell's
+ *      largest speed;
+ *   4. fine-to-coarse P controller per correction cell (velocity or mass flow
+ *      with the volume-fraction ratio capped at 4);
+ *   5. simple sequential inhibition (Diggle et al. 1976) of fine particles per
+ *      surface cell with SplitMix64 random numbers on counters;
+ *   6. removal of fine particles that left through drain faces.
+ *
+ * Spec block CP (doubles): 0..2 lo, 3..5 hi, 6 feed bits, 7 drain bits,
+ * 8 surface_cell, 9 layer, 10 corr_cell, 11 interval, 12 bins, 13 alpha,
+ * 14 kp, 15 ki, 16 kv, 17 mode, 18 max_attempts, 19 (unused: the seed is passed
+ * separately), 20 mass_unit, 21 max_insert, 22 dt, 23 fine particle density.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "dem_oracle_common.h"
+
+int orc_contact_pair(const double *P, double ra, double rb, double ma, double mb, int32_t wall, double delta,
+                     const double *n, const double *va, const double *vb, const double *wa, const double *wb,
+                     double *xi, double dt_hist, double *fa, double *ft);
+
+typedef struct {
+    int axis, side, b, c, nb, nc, off;
+    double plane, wb, wc;
+} cface_t;
+
+typedef struct {
+    double lo[3], hi[3];
+    int nface;
+    cface_t face[6];
+    int S, ncr[3], C;
+    double wcr[3];
+} cgeo_t;
+
+static void make_geo(const double *CP, cgeo_t *g)
+{
+    memset(g, 0, sizeof(*g));
+    for (int a = 0; a < 3; ++a) { g->lo[a] = CP[a]; g->hi[a] = CP[3 + a]; }
+    int feed = (int)CP[6], off = 0;
+    for (int bit = 0; bit < 6; ++bit) {
+        if (!((feed >> bit) & 1)) continue;
+        cface_t *f = &g->face[g->nface++];
+        f->axis = bit / 2;
+        f->side = bit % 2;
+        int o1 = (f->axis + 1) % 3, o2 = (f->axis + 2) % 3;
+        f->b = o1 < o2 ? o1 : o2;
+        f->c = o1 < o2 ? o2 : o1;
+        f->plane = f->side == 0 ? g->lo[f->axis] : g->hi[f->axis];
+        f->nb = (int)floor((g->hi[f->b] - g->lo[f->b]) / CP[8]);
+        f->nc = (int)floor((g->hi[f->c] - g->lo[f->c]) / CP[8]);
+        if (f->nb < 1) f->nb = 1;
+        if (f->nc < 1) f->nc = 1;
+        f->wb = (g->hi[f->b] - g->lo[f->b]) / f->nb;
+        f->wc = (g->hi[f->c] - g->lo[f->c]) / f->nc;
+        f->off = off;
+        off += f->nb * f->nc;
+    }
+    g->S = off;
+    g->C = 1;
+    for (int a = 0; a < 3; ++a) {
+        g->ncr[a] = (int)floor((g->hi[a] - g->lo[a]) / CP[10]);
+        if (g->ncr[a] < 1) g->ncr[a] = 1;
+        g->wcr[a] = (g->hi[a] - g->lo[a]) / g->ncr[a];
+        g->C *= g->ncr[a];
+    }
+}
+
+static int in_box(const cgeo_t *g, const double *x)
+{
+    for (int a = 0; a < 3; ++a)
+        if (!(x[a] >= g->lo[a] && x[a] < g->hi[a])) return 0;
+    return 1;
+}
+
+static int face_cell(const cgeo_t *g, const cface_t *f, double pb, double pc)
+{
+    if (pb < g->lo[f->b] || pb >= g->hi[f->b] || pc < g->lo[f->c] || pc >= g->hi[f->c]) return -1;
+    int ib = (int)floor((pb - g->lo[f->b]) / f->wb), ic = (int)floor((pc - g->lo[f->c]) / f->wc);
+    if (ib < 0) ib = 0;
+    if (ib > f->nb - 1) ib = f->nb - 1;
+    if (ic < 0) ic = 0;
+    if (ic > f->nc - 1) ic = f->nc - 1;
+    return f->off + ib + f->nb * ic;
+}
+
+static int layer_cell(const cgeo_t *g, double layer, const double *x, int *fk)
+{
+    if (!in_box(g, x)) return -1;
+    for (int k = 0; k < g->nface; ++k) {
+        const cface_t *f = &g->face[k];
+        double s = f->side == 0 ? x[f->axis] - f->plane : f->plane - x[f->axis];
+        if (s >= 0.0 && s < layer) {
+            int c = face_cell(g, f, x[f->b], x[f->c]);
+            if (c >= 0) { *fk = k; return c; }
+        }
+    }
+    return -1;
+}
+
+static int corr_cell(const cgeo_t *g, const double *x)
+{
+    if (!in_box(g, x)) return -1;
+    int i[3];
+    for (int a = 0; a < 3; ++a) {
+        i[a] = (int)floor((x[a] - g->lo[a]) / g->wcr[a]);
+        if (i[a] < 0) i[a] = 0;
+        if (i[a] > g->ncr[a] - 1) i[a] = g->ncr[a] - 1;
+    }
+    return (i[2] * g->ncr[1] + i[1]) * g->ncr[0] + i[0];
+}
+
+static void min_image_d(const double *P, double *d)
+{
+    for (int a = 0; a < 3; ++a)
+        if (P[P_PER + a] != 0.0) {
+            double L = P[P_HI + a] - P[P_LO + a];
+            d[a] -= L * floor(d[a] / L + 0.5);
+        }
+}
+
+/* Eq. 7 contributions of the particles of one level to the transition cells.
+ * lay[(cell)*20 + k]: 0 m, 1..3 m v, 4..9 m v v, 10 V, 11..16 contact stress. */
+static void level_layer(const double *CP, const cgeo_t *g, const double *P, int64_t n, const double *x,
+                        const double *v, const double *w, const double *r, const double *m, const int64_t *id,
+                        double dt_hist, double *lay, double *vmax)
+{
+    const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    int64_t np = 0;
+    pair_t *pairs = orc_find_pairs(P, n, x, r, 0.0, 1, &np);
+    int fk;
+    for (int64_t i = 0; i < n; ++i) {
+        int c = layer_cell(g, CP[9], x + 3 * i, &fk);
+        if (c < 0) continue;
+        double *A = lay + 20 * (size_t)c;
+        A[0] += m[i];
+        for (int a = 0; a < 3; ++a) A[1 + a] += m[i] * v[3 * i + a];
+        for (int k = 0; k < 6; ++k) A[4 + k] += m[i] * v[3 * i + ij[k][0]] * v[3 * i + ij[k][1]];
+        A[10] += 4.0 / 3.0 * ORC_PI * r[i] * r[i] * r[i];
+        double sp = sqrt(v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);
+        if (sp > vmax[c]) vmax[c] = sp;
+    }
+    /* contacts: the pair force acts on both particles; each particle in a cell
+     * adds 1/2 r_ij f_ij with r_ij = x_i - x_j and f_ij the force on i */
+    for (int64_t k = 0; k < np; ++k) {
+        int64_t a = pairs[k].i, b = pairs[k].j;
+        double d[3] = {x[3 * a] - x[3 * b], x[3 * a + 1] - x[3 * b + 1], x[3 * a + 2] - x[3 * b + 2]};
+        min_image_d(P, d);
+        double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double nvec[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+        double xi[3] = {0, 0, 0}, fa[3], ft[3];
+        orc_contact_pair(P, r[a], r[b], m[a], m[b], 0, r[a] + r[b] - dist, nvec, v + 3 * a, v + 3 * b, w + 3 * a,
+                         w + 3 * b, xi, dt_hist, fa, ft);
+        int ca = layer_cell(g, CP[9], x + 3 * a, &fk), cb = layer_cell(g, CP[9], x + 3 * b, &fk);
+        for (int q = 0; q < 6; ++q) {
+            int s = ij[q][0], t = ij[q][1];
+            double val = 0.25 * (d[s] * fa[t] + d[t] * fa[s]);   /* same for both ends */
+            if (ca >= 0) lay[20 * (size_t)ca + 11 + q] += val;
+            if (cb >= 0) lay[20 * (size_t)cb + 11 + q] += val;
+        }
+    }
+    free(pairs);
+    if (P[P_FLOOR] != 0.0) {
+        const double nz[3] = {0, 0, 1}, zero3[3] = {0, 0, 0};
+        for (int64_t i = 0; i < n; ++i) {
+            double h = x[3 * i + 2] - P[P_FLOORZ];
+            if (!(r[i] - h > 0)) continue;
+            int c = layer_cell(g, CP[9], x + 3 * i, &fk);
+            if (c < 0) continue;
+            double xi[3] = {0, 0, 0}, fa[3], ft[3];
+            orc_contact_pair(P, r[i], 0.0, m[i], 0.0, 1, r[i] - h, nz, v + 3 * i, P + P_FLOORV, w + 3 * i, zero3, xi,
+                             dt_hist, fa, ft);
+            double rv[3] = {0, 0, h};
+            for (int q = 0; q < 6; ++q) {
+                int s = ij[q][0], t = ij[q][1];
+                lay[20 * (size_t)c + 11 + q] += 0.5 * (rv[s] * fa[t] + rv[t] * fa[s]);
+            }
+        }
+    }
+    (void)id;
+}
+
+static void level_corr(const cgeo_t *g, int64_t n, const double *x, const double *v, const double *r,
+                       const double *m, double *cor)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int c = corr_cell(g, x + 3 * i);
+        if (c < 0) continue;
+        double *o = cor + 5 * (size_t)c;
+        o[0] += m[i];
+        for (int a = 0; a < 3; ++a) o[1 + a] += m[i] * v[3 * i + a];
+        o[4] += 4.0 / 3.0 * ORC_PI * r[i] * r[i] * r[i];
+    }
+}
+
+/* SplitMix64 (Steele, Lea and Flood 2014) */
+static uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+static uint64_t draw(uint64_t seed, int cell, int call, int attempt, int k)
+{
+    uint64_t ctr = (((uint64_t)cell * 1048576ull + (uint64_t)call) * 16777216ull + (uint64_t)attempt) * 8ull + (uint64_t)k;
+    return splitmix64(seed ^ splitmix64(ctr));
+}
+
+static int64_t below(uint64_t u, int64_t n) { return (int64_t)(((u >> 32) * (uint64_t)n) >> 32); }
+
+static int64_t min_image_i(int64_t dx, const double *Pf, double qf, int a)
+{
+    if (Pf[P_PER + a] == 0.0) return dx;
+    int64_t L = llround((Pf[P_HI + a] - Pf[P_LO + a]) / qf), h = L / 2;
+    if (dx > h) dx -= L;
+    else if (dx < -h) dx += L;
+    return dx;
+}
+
+/*
+ * One coupling call.  Inputs: spec CP and seed; the call number; both levels'
+ * parameter blocks (Pc, Pf) and states; the fine frame (lof, qf, rmaxf_u); the
+ * coarse positions at the previous call by ID (prev, prev_ok; updated); the
+ * carried mass per surface cell (carry; updated) and the controller integral
+ * (integ; updated); dt_hist of the stress evaluation per level.
+ * Outputs: cross[S] (mass units), hist[S*bins], fav[S*4], layout[2*S*11],
+ * ctrl[S*3], corout[2*C*5], fext_c[nc*3], fext_f[nf*3], removed[nf],
+ * inserted particles ins_u[S*max_insert*4] (fine units, radius last),
+ * ins_m[S*max_insert], nins[S].  Returns 0.
+ */
+int32_t orc_couple(const double *CP, uint64_t seed, int32_t call, const double *Pc, int64_t nc, const double *xc,
+                   const double *vc, const double *wc, const double *rc, const double *mc, const int64_t *idc,
+                   const double *Pf, int64_t nf, const double *xf, const double *vf, const double *wf,
+                   const double *rf, const double *mf, const int64_t *idf, const double *lof, double qf,
+                   int64_t rmaxf_u, double *prev, int32_t *prev_ok, int64_t *carry, double *integ, double dth_c,
+                   double dth_f, uint64_t *cross, uint32_t *hist, double *fav, double *layout, double *ctrl,
+                   double *corout, double *fext_c, double *fext_f, int32_t *removed, int64_t *ins_u, double *ins_m,
+                   int32_t *nins)
+{
+    cgeo_t g;
+    make_geo(CP, &g);
+    const int S = g.S, C = g.C, bins = (int)CP[12], max_ins = (int)CP[21], max_att = (int)CP[18];
+    const double alpha = CP[13], mass_unit = CP[20], dt = CP[22], Tc = CP[11] * dt, layer = CP[9];
+    memset(cross, 0, sizeof(uint64_t) * S);
+    memset(hist, 0, sizeof(uint32_t) * S * bins);
+    memset(fav, 0, sizeof(double) * S * 4);
+    double *lay = (double *)calloc((size_t)2 * S * 20, sizeof(double));
+    double *vmax = (double *)calloc((size_t)2 * S, sizeof(double));
+    double *cor = (double *)calloc((size_t)2 * C * 5, sizeof(double));
+    double L[3];
+    for (int a = 0; a < 3; ++a) L[a] = Pc[P_HI + a] - Pc[P_LO + a];
+
+    /* 1. coarse level: entries, histogram, Favre samples */
+    for (int64_t i = 0; i < nc; ++i) {
+        const double *x = xc + 3 * i;
+        int64_t id = idc[i];
+        const double *p = prev + 3 * id;
+        if (prev_ok[id] && in_box(&g, x)) {
+            double seg = 0.0;
+            for (int k = 0; k < 3; ++k) seg = fmax(seg, fabs(x[k] - p[k]));
+            double span = 0.25 * ((g.hi[0] - g.lo[0]) + (g.hi[1] - g.lo[1]) + (g.hi[2] - g.lo[2]));
+            if (!in_box(&g, p) && seg < span) {
+                double tbest = 2.0;
+                int cbest = -1;
+                for (int k = 0; k < g.nface; ++k) {
+                    const cface_t *f = &g.face[k];
+                    double p0 = p[f->axis], p1 = x[f->axis];
+                    int enters = f->side == 0 ? (p0 < f->plane && p1 >= f->plane) : (p0 >= f->plane && p1 < f->plane);
+                    if (!enters) continue;
+                    double t = (f->plane - p0) / (p1 - p0);
+                    int cc = face_cell(&g, f, p[f->b] + t * (x[f->b] - p[f->b]), p[f->c] + t * (x[f->c] - p[f->c]));
+                    if (cc >= 0 && t < tbest) { tbest = t; cbest = cc; }
+                }
+                if (cbest >= 0) {
+                    cross[cbest] += (uint64_t)llrint(mc[i] / mass_unit);
+                    int64_t ru = llrint(rc[i] / alpha / qf);
+                    if (ru > rmaxf_u) ru = rmaxf_u;
+                    hist[(size_t)cbest * bins + (int)(ru * bins / (rmaxf_u + 1))] += 1;
+                }
+            }
+        }
+        for (int k = 0; k < g.nface; ++k) {
+            const cface_t *f = &g.face[k];
+            if (fabs(x[f->axis] - f->plane) >= 2.0 * rc[i]) continue;
+            int cc = face_cell(&g, f, x[f->b], x[f->c]);
+            if (cc < 0) continue;
+            fav[4 * cc] += mc[i];
+            for (int a = 0; a < 3; ++a) fav[4 * cc + 1 + a] += mc[i] * vc[3 * i + a];
+            break;
+        }
+    }
+    (void)L;
+
+    /* 2. transition and correction cells on both levels */
+    level_layer(CP, &g, Pc, nc, xc, vc, wc, rc, mc, idc, dth_c, lay, vmax);
+    level_layer(CP, &g, Pf, nf, xf, vf, wf, rf, mf, idf, dth_f, lay + (size_t)S * 20, vmax + S);
+    level_corr(&g, nc, xc, vc, rc, mc, cor);
+    level_corr(&g, nf, xf, vf, rf, mf, cor + (size_t)C * 5);
+    const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int i = 0; i < S; ++i) {
+        int fk = 0;
+        for (int k = 0; k < g.nface; ++k)
+            if (i >= g.face[k].off && i < g.face[k].off + g.face[k].nb * g.face[k].nc) fk = k;
+        const cface_t *f = &g.face[fk];
+        double Vc = f->wb * f->wc * layer, saa[2];
+        for (int lv = 0; lv < 2; ++lv) {
+            const double *A = lay + 20 * ((size_t)lv * S + i);
+            double *o = layout + 11 * ((size_t)lv * S + i);
+            double M = A[0], vv[3] = {0, 0, 0};
+            if (M > 0) for (int a = 0; a < 3; ++a) vv[a] = A[1 + a] / M;
+            for (int k = 0; k < 6; ++k) o[k] = (A[11 + k] + A[4 + k] - M * vv[ij[k][0]] * vv[ij[k][1]]) / Vc;
+            o[6] = A[10] / Vc;
+            for (int a = 0; a < 3; ++a) o[7 + a] = vv[a];
+            o[10] = vmax[lv * S + i];
+            saa[lv] = o[f->axis];
+        }
+        /* 3. stress PI controller */
+        double e = saa[0] - saa[1];
+        integ[i] += e * Tc;
+        ctrl[3 * i] = e;
+        ctrl[3 * i + 1] = integ[i];
+        ctrl[3 * i + 2] = CP[14] * e + CP[15] * integ[i];
+    }
+    /* 4. fine-to-coarse correction */
+    double *dv = (double *)calloc((size_t)C * 3, sizeof(double));
+    for (int i = 0; i < C; ++i) {
+        const double *Ac = cor + 5 * (size_t)i, *Af = cor + 5 * ((size_t)C + i);
+        double *oc = corout + 5 * (size_t)i, *of = corout + 5 * ((size_t)C + i);
+        memcpy(oc, Ac, 5 * sizeof(double));
+        memcpy(of, Af, 5 * sizeof(double));
+        if (Ac[0] > 0 && Af[0] > 0) {
+            double fac = 1.0;
+            if ((int)CP[17] == 1) fac = fmin(Af[4] / Ac[4], 4.0);
+            for (int a = 0; a < 3; ++a) dv[3 * i + a] = Af[1 + a] / Af[0] * fac - Ac[1 + a] / Ac[0];
+        }
+    }
+    for (int64_t i = 0; i < nc; ++i) {
+        int c = corr_cell(&g, xc + 3 * i);
+        for (int a = 0; a < 3; ++a) fext_c[3 * i + a] = c >= 0 ? CP[16] * mc[i] * dv[3 * c + a] / Tc : 0.0;
+    }
+    for (int64_t i = 0; i < nf; ++i) {
+        int fk = 0;
+        int c = layer_cell(&g, layer, xf + 3 * i, &fk);
+        for (int a = 0; a < 3; ++a) fext_f[3 * i + a] = 0.0;
+        if (c < 0) continue;
+        const cface_t *f = &g.face[fk];
+        double s = f->side == 0 ? xf[3 * i + f->axis] - f->plane : f->plane - xf[3 * i + f->axis];
+        double wfade = fmax(0.0, 1.0 - s / (1.5 * 2.0 * rf[i]));
+        double Fv[3] = {0, 0, 0};
+        Fv[f->axis] = (f->side == 0 ? 1.0 : -1.0) * ctrl[3 * c + 2] * ORC_PI * rf[i] * rf[i] * wfade;
+        double vm = vmax[c], acc[3], A2 = 0, VA = 0, V2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            acc[a] = dt * Fv[a] / mf[i];
+            A2 += acc[a] * acc[a];
+            VA += vf[3 * i + a] * acc[a];
+            V2 += vf[3 * i + a] * vf[3 * i + a];
+        }
+        double lam = 1.0;
+        if (A2 > 0 && V2 + 2 * VA + A2 > vm * vm) {
+            if (V2 >= vm * vm) lam = 0.0;
+            else lam = fmin(1.0, (-VA + sqrt(VA * VA - A2 * (V2 - vm * vm))) / A2);
+        }
+        for (int a = 0; a < 3; ++a) fext_f[3 * i + a] = lam * Fv[a];
+    }
+
+    /* 5. simple sequential inhibition per surface cell, faces in order */
+    int64_t *fu = (int64_t *)malloc(sizeof(int64_t) * 4 * (nf > 0 ? nf : 1));
+    for (int64_t j = 0; j < nf; ++j) {
+        for (int a = 0; a < 3; ++a) fu[4 * j + a] = llrint((xf[3 * j + a] - lof[a]) / qf);
+        fu[4 * j + 3] = llrint(rf[j] / qf);
+    }
+    for (int k = 0; k < g.nface; ++k) {
+        const cface_t *f = &g.face[k];
+        for (int local = 0; local < f->nb * f->nc; ++local) {
+            int cell = f->off + local, ib = local % f->nb, ic = local / f->nb;
+            int64_t quota = (int64_t)cross[cell] + carry[cell];
+            uint64_t total = 0;
+            for (int b = 0; b < bins; ++b) total += hist[(size_t)cell * bins + b];
+            double M = fav[4 * cell], vn = 0.0;
+            if (M > 0) vn = fav[4 * cell + 1 + f->axis] / M;
+            int n_in = 0, fails = 0, attempt = 0;
+            int64_t *mine = ins_u + (size_t)cell * max_ins * 4;
+            double b0 = g.lo[f->b] + ib * f->wb, c0 = g.lo[f->c] + ic * f->wc;
+            while (quota > 0 && total > 0 && fails < max_att && n_in < max_ins) {
+                int64_t pick = below(draw(seed, cell, call, attempt, 0), (int64_t)total);
+                int b = 0;
+                while (pick >= (int64_t)hist[(size_t)cell * bins + b]) { pick -= hist[(size_t)cell * bins + b]; ++b; }
+                int64_t R1 = rmaxf_u + 1;
+                int64_t rlo = (b * R1 + bins - 1) / bins, rhi = ((b + 1) * R1 + bins - 1) / bins - 1;
+                int64_t ru = rlo + below(draw(seed, cell, call, attempt, 1), rhi - rlo + 1);
+                if (ru <= 0) { ++attempt; ++fails; continue; }
+                double r = (double)ru * qf;
+                double depth = fmax(2.0 * r, fabs(vn) * Tc);
+                int64_t bl = llrint(ceil((b0 + r - lof[f->b]) / qf)), bh = llrint(floor((b0 + f->wb - r - lof[f->b]) / qf));
+                int64_t cl = llrint(ceil((c0 + r - lof[f->c]) / qf)), ch = llrint(floor((c0 + f->wc - r - lof[f->c]) / qf));
+                double nlo = f->side == 0 ? f->plane + r : f->plane - r - depth;
+                double nhi = f->side == 0 ? f->plane + r + depth : f->plane - r;
+                int64_t al = llrint(ceil((nlo - lof[f->axis]) / qf)), ah = llrint(floor((nhi - lof[f->axis]) / qf));
+                if (bh < bl || ch < cl || ah < al) { ++attempt; ++fails; continue; }
+                int64_t u[3];
+                u[f->b] = bl + below(draw(seed, cell, call, attempt, 2), bh - bl + 1);
+                u[f->c] = cl + below(draw(seed, cell, call, attempt, 3), ch - cl + 1);
+                u[f->axis] = al + below(draw(seed, cell, call, attempt, 4), ah - al + 1);
+                ++attempt;
+                int ok = 1;
+                for (int64_t j = 0; j < nf && ok; ++j) {
+                    int64_t ex = min_image_i(u[0] - fu[4 * j], Pf, qf, 0), ey = min_image_i(u[1] - fu[4 * j + 1], Pf, qf, 1);
+                    int64_t ez = u[2] - fu[4 * j + 2], S2 = (ru + fu[4 * j + 3]) * (ru + fu[4 * j + 3]);
+                    if (ex * ex + ey * ey + ez * ez < S2) ok = 0;
+                }
+                for (int t = 0; t < n_in && ok; ++t) {
+                    int64_t ex = u[0] - mine[4 * t], ey = u[1] - mine[4 * t + 1], ez = u[2] - mine[4 * t + 2];
+                    int64_t S2 = (ru + mine[4 * t + 3]) * (ru + mine[4 * t + 3]);
+                    if (ex * ex + ey * ey + ez * ez < S2) ok = 0;
+                }
+                for (int kk = 0; kk < k && ok; ++kk) {
+                    const cface_t *o = &g.face[kk];
+                    for (int oc = o->off; oc < o->off + o->nb * o->nc && ok; ++oc) {
+                        const int64_t *other = ins_u + (size_t)oc * max_ins * 4;
+                        for (int t = 0; t < nins[oc] && ok; ++t) {
+                            int64_t ex = u[0] - other[4 * t], ey = u[1] - other[4 * t + 1], ez = u[2] - other[4 * t + 2];
+                            int64_t S2 = (ru + other[4 * t + 3]) * (ru + other[4 * t + 3]);
+                            if (ex * ex + ey * ey + ez * ez < S2) ok = 0;
+                        }
+                    }
+                }
+                if (!ok) { ++fails; continue; }
+                /* mass of a solid sphere of the fine density */
+                double m = CP[23] * (4.0 / 3.0 * ORC_PI) * r * r * r;
+                mine[4 * n_in] = u[0]; mine[4 * n_in + 1] = u[1]; mine[4 * n_in + 2] = u[2]; mine[4 * n_in + 3] = ru;
+                ins_m[(size_t)cell * max_ins + n_in] = m;
+                ++n_in;
+                quota -= llrint(m / mass_unit);
+            }
+            nins[cell] = n_in;
+            carry[cell] = quota;
+        }
+    }
+    free(fu);
+
+    /* 6. removal through drain faces */
+    int drain = (int)CP[7];
+    for (int64_t i = 0; i < nf; ++i) {
+        int gone = 0;
+        for (int a = 0; a < 3; ++a) {
+            if ((drain >> (2 * a)) & 1) gone |= xf[3 * i + a] < g.lo[a];
+            if ((drain >> (2 * a + 1)) & 1) gone |= xf[3 * i + a] >= g.hi[a];
+        }
+        removed[i] = gone;
+    }
+    /* remember the coarse positions */
+    for (int64_t i = 0; i < nc; ++i) {
+        for (int a = 0; a < 3; ++a) prev[3 * idc[i] + a] = xc[3 * i + a];
+        prev_ok[idc[i]] = 1;
+    }
+    free(lay);
+    free(vmax);
+    free(cor);
+    free(dv);
+    return 0;
+}

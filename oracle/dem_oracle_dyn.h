@@ -397,6 +397,17 @@ void orc_pair_coeffs(const double *P, double ri, double rj, double mi, double mj
     orc_coeffs(&M, ri, rj, mi, mj, delta, wall, out);
 }
 
+/* One contact of the contact law (Eqs. 3-6) for the coupling oracle: force on
+ * a (fa) and tangential part (ft); xi is updated in place; returns 1 on slip. */
+int orc_contact_pair(const double *P, double ra, double rb, double ma, double mb, int32_t wall, double delta,
+                     const double *n, const double *va, const double *vb, const double *wa, const double *wb,
+                     double *xi, double dt_hist, double *fa, double *ft)
+{
+    orc_mat_t M = orc_mat_from(P);
+    return orc_contact_law(P, &M, ra, rb, ma, mb, wall, delta, n, va, vb, wa, wb, xi, dt_hist,
+                           wall ? M.mu_w : M.mu, fa, ft);
+}
+
 int64_t orc_eval(const double *P, int64_t n, const double *x, const double *v, const double *w, const double *r,
                  const double *m, const int64_t *id, int64_t nh, const int64_t *ha, const int64_t *hb,
                  const double *hxi, double dt_hist, int32_t use_cells, double *F, double *T, int64_t cap,

@@ -4,6 +4,7 @@
 // interface and dem_internal.cuh for the data layout.
 #include "dem.h"
 #include "dem_internal.cuh"
+#include "dem_ctx.h"
 #include "dem_contact.cuh"
 
 #include <algorithm>
@@ -127,28 +128,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(Dev d)
 }
 
 // ==================================================================== cells
-
-__device__ __forceinline__ int axis_cell(const InstC& c, int a, int x)
-{
-    if (x <= 0) return 0;
-    long long t = (long long)x * c.nc[a] / c.ext[a];
-    return t >= c.nc[a] ? c.nc[a] - 1 : (int)t;
-}
-
-__device__ __forceinline__ unsigned cell_code(const Dev& d, const InstC& c, int cx, int cy, int cz)
-{
-    return (unsigned)c.code0 + d.spread[c.spread_off[0] + cx] + d.spread[c.spread_off[1] + cy] +
-           d.spread[c.spread_off[2] + cz];
-}
-
-__device__ __forceinline__ int min_image(int dx, int per, int L, int half)
-{
-    if (per) {
-        if (dx > half) dx -= L;
-        else if (dx < -half) dx += L;
-    }
-    return dx;
-}
+// (axis_cell, cell_code, min_image in dem_internal.cuh)
 
 // ================================================================ rebuild
 // Triggered per instance by the displacement bound (flag != 0).  Sequence:
@@ -185,6 +165,12 @@ __global__ void __launch_bounds__(TILE) k_rb_bin(Dev d)
 {
     if (!d.g->any) return;
     for_rebuilding_slots(d, [&](int s, const InstD& D, const InstC& c) {
+        const unsigned idw = __float_as_uint(d.vel[D.cur][s].w);
+        if (idw & GONE_BIT) {               // removed particle: not binned, its ID unmapped
+            d.slot_of_id[c.slot0 + (int)(idw & ID_MASK)] = -1;
+            d.cslot[s] = 0xffffffffu;
+            return;
+        }
         const int4 p = d.pos[D.cur][s];
         const unsigned code = cell_code(d, c, axis_cell(c, 0, p.x), axis_cell(c, 1, p.y), axis_cell(c, 2, p.z));
         d.cellcode[s] = code;
@@ -196,6 +182,7 @@ __global__ void __launch_bounds__(TILE) k_rb_scatter(Dev d)
 {
     if (!d.g->any) return;
     for_rebuilding_slots(d, [&](int s, const InstD& D, const InstC& c) {
+        if (d.cslot[s] == 0xffffffffu) return;   // removed
         const unsigned code = d.cellcode[s];
         const int np = c.slot0 + (int)(d.cstart[code] - d.cstart[c.code0]) + (int)d.cslot[s];
         d.perm[np] = s;
@@ -208,7 +195,7 @@ __global__ void __launch_bounds__(TILE) k_rb_cellsort(Dev d)
 {
     if (!d.g->any) return;
     for_rebuilding_slots(d, [&](int s, const InstD& D, const InstC& c) {
-        if (d.cslot[s] != 0u) return;
+        if (d.cslot[s] != 0u) return;   // not the first of its cell, or removed
         const unsigned code = d.cellcode[s];
         const int cntc = (int)d.ccount[code];
         if (cntc < 2) return;
@@ -339,13 +326,35 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
     }
     d.cnt[nlp][s] = nc;
     d.hmask[nlp][s] = nhm;
+    if (D.fext) d.fext[nlp][s] = D.flag == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : d.fext[lp][old];
     d.whist[nlp][s] = D.flag == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : d.whist[lp][old];
 }
 
 __global__ void __launch_bounds__(TILE) k_rb_build(Dev d)
 {
     if (!d.g->any) return;
-    for_rebuilding_slots(d, [&](int s, const InstD& D, const InstC& c) { build_row(d, s, D, c); });
+    for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {   // over the new slots
+        const int k = d.tile_inst[t];
+        const InstD D = d.id[k];
+        if (!D.flag) continue;
+        const InstC& c = d.ic[k];
+        const int s = t * TILE + threadIdx.x;
+        if (s - c.slot0 >= D.n_new) continue;
+        build_row(d, s, D, c);
+    }
+}
+
+// live particles after the rebuild: the binned ones (removed particles dropped)
+__global__ void k_rb_count(Dev d)
+{
+    if (!d.g->any) return;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.B; k += gridDim.x * blockDim.x) {
+        InstD& D = d.id[k];
+        if (!D.flag) continue;
+        const InstC& c = d.ic[k];
+        const unsigned last = (unsigned)(c.code0 + c.ncode - 1);
+        D.n_new = (int)(d.cstart[last] + d.ccount[last] - d.cstart[c.code0]);
+    }
 }
 
 __global__ void k_rb_finish(Dev d)
@@ -357,6 +366,7 @@ __global__ void k_rb_finish(Dev d)
             D.cur ^= 1;
             D.lp ^= 1;
             D.flag = 0;
+            D.n = D.n_new;
             D.disp = 0.f;
             atomicAdd(&d.g->rebuilds, 1ull);
         }
@@ -526,6 +536,10 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
             }
         }
         if (MODE == 0) d.hmask[lp][s] = cm;
+        if (sd.fext) {   // coupling controllers' force, held over the coupling interval
+            const float4 fe = d.fext[lp][s];
+            F = F + v3(fe.x, fe.y, fe.z);
+        }
         // floor plane z = 0 (the box bottom)
         bool wall_now = false;
         V3 wxi = v3(0.f, 0.f, 0.f);
@@ -662,11 +676,6 @@ __device__ __forceinline__ int find_inst(const long long* goff, int B, long long
     return lo;
 }
 
-struct HostInstLo {
-    double lo[3];
-    double q;
-    double rho;
-};
 
 __global__ void k_init_ids(Dev d)
 {
@@ -681,6 +690,7 @@ __global__ void k_init_ids(Dev d)
         d.omg[b][s] = z;
         d.cnt[b][s] = 0;
         d.hmask[b][s] = 0u;
+        d.fext[b][s] = z;
         d.whist[b][s] = z;
     }
     d.slot_of_id[s] = s;
@@ -696,6 +706,7 @@ __global__ void k_write_field(Dev d, int field, const double* __restrict__ src, 
     const InstC& c = d.ic[k];
     const int id = (int)(g - d.goff[k]);
     const int s = d.slot_of_id[c.slot0 + id];
+    if (s < 0) return;                       // removed particle
     const int cur = d.id[k].cur;
     const double q = hl[k].q;
     if (field == DEM_F_POS) {
@@ -748,6 +759,11 @@ __global__ void k_read_field(Dev d, int field, double* __restrict__ dst, long lo
     const InstC& c = d.ic[k];
     const int id = (int)(g - d.goff[k]);
     const int s = d.slot_of_id[c.slot0 + id];
+    if (s < 0) {                             // removed particle
+        const int w = (field == DEM_F_RADIUS || field == DEM_F_MASS || field == DEM_F_NBR_COUNT) ? 1 : 3;
+        for (int a = 0; a < w; ++a) dst[w * g + a] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     const int cur = d.id[k].cur;
     const double q = hl[k].q;
     float4 f;
@@ -767,6 +783,7 @@ __global__ void k_read_field(Dev d, int field, double* __restrict__ dst, long lo
     case DEM_F_FORCE: f = d.outF[s]; break;
     case DEM_F_TORQUE: f = d.outT[s]; break;
     case DEM_F_WALL_XI: f = d.outWX[s]; break;
+    case DEM_F_FEXT: f = d.fext[d.id[k].lp][s]; break;
     default: return;
     }
     dst[3 * g] = f.x;
@@ -889,26 +906,7 @@ __global__ void k_stats(Dev d)
 // opposite values and every particle can compute its part of a pair's
 // derivative alone (no atomics; the parameter part is split evenly).
 
-struct Snap {
-    int4* pos;
-    float4* vel;
-    float4* omg;
-    float* hist;
-    unsigned* hmask;
-    float4* whist;
-    float* disp;       // per instance: displacement bound accumulated since the list build
-};
 
-struct AdjBufs {
-    float4* xb;        // adjoint of x^n [1/m units of the objective]
-    float4* vb;        // adjoint of v^{n-1/2}
-    float4* wb;        // adjoint of w^{n-1/2}
-    float4* Fb;        // adjoint of F^n
-    float4* Tb;        // adjoint of T^n
-    float* xib;        // adjoint of the stored overlaps, [3][Lmax][ncap], from each row's side
-    float4* wxib;      // adjoint of the floor overlap
-    double* thb;       // per slot: accumulated d/dE, d/de, d/dmu
-};
 
 template <typename Fn>
 __device__ __forceinline__ void for_live_slots(const Dev& d, Fn fn)
@@ -1193,43 +1191,8 @@ __global__ void __launch_bounds__(256) k_adj_reduce(Dev d, AdjBufs a)
 
 // ============================================================== host side
 
-struct dem_ctx {
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    Dev dev{};
-    int B = 0, Lmax = 0;
-    int ncap = 0, ntiles = 0;
-    int grid0 = 1, grid1 = 1;         // persistent grids of the step / evaluation kernels
-    int grid_rb = 1;                  // persistent grid of the per-slot rebuild kernels
-    unsigned ncodes = 0, nparts = 0;
-    std::vector<InstC> ic;
-    std::vector<HostInstLo> hl;
-    std::vector<long long> count;     // host mirror of live counts
-    HostInstLo* d_hl = nullptr;
-    bool fresh = true;                // velocities at an integer step (next step primes)
-    bool have_state = false;
-    long long steps = 0;
-    unsigned status = 0;
-    std::string err;
-    // graphs
-    int graph_steps = 0;
-    cudaGraph_t rb_graph = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<cudaEvent_t> ev0, ev1;   // around each step kernel of the graph
-    std::vector<double> nu;              // Poisson ratio per instance (for material updates)
-    struct Rollout {
-        bool ready = false;
-        long long nsteps = 0, K = 0;
-        int ncp = 0;
-        bool prime0 = false;
-        std::vector<Snap> ck, seg;       // checkpoints (every K steps and the end), segment steps
-        AdjBufs a{};
-    } ro;
-};
-using Rollout = dem_ctx::Rollout;
 
-namespace {
+namespace cgdem {
 
 thread_local std::string g_cfg_err = "no error";
 
@@ -1239,12 +1202,6 @@ dem_status fail(dem_ctx* c, dem_status st, const std::string& msg)
     return st;
 }
 
-#define CU(call)                                                                               \
-    do {                                                                                       \
-        cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess)                                                                 \
-            return fail(ctx, DEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
 
 struct Layout {
     size_t total = 0;
@@ -1266,7 +1223,7 @@ struct Plan {
     int ncap = 0, ntiles = 0, Lmax = 0, B = 0;
     unsigned ncodes = 0, nparts = 0;
     // offsets
-    size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_whist[2];
+    size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_fext[2], o_whist[2];
     size_t o_cellcode, o_cslot, o_perm, o_ccount, o_cstart, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
         o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl, o_small;
     size_t bytes = 0;
@@ -1403,6 +1360,7 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
         p.o_hist[b] = L.take(N * Lm * 12);
         p.o_cnt[b] = L.take(N * 4);
         p.o_hmask[b] = L.take(N * 4);
+        p.o_fext[b] = L.take(N * 16);
         p.o_whist[b] = L.take(N * 16);
     }
     p.o_cellcode = L.take(N * 4);
@@ -1479,6 +1437,7 @@ dem_status launch_rebuild(dem_ctx* ctx, cudaStream_t st)
     k_scan_down<<<std::max(1u, ctx->nparts), SCAN_T, 0, st>>>(d);
     k_rb_scatter<<<gt, TILE, 0, st>>>(d);
     k_rb_cellsort<<<gt, TILE, 0, st>>>(d);
+    k_rb_count<<<1, 256, 0, st>>>(d);
     k_rb_build<<<gt, TILE, 0, st>>>(d);
     k_rb_finish<<<1, 256, 0, st>>>(d);
     CU(cudaGetLastError());
@@ -1587,7 +1546,7 @@ dem_status build_graph(dem_ctx* ctx, int S)
     return DEM_OK;
 }
 
-}  // namespace
+}  // namespace cgdem
 
 namespace cgdem {
 // error text reported by dem_last_error(NULL) for calls made without a context
@@ -1630,7 +1589,10 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     ctx->nparts = p.nparts;
     ctx->ic = p.ic;
     ctx->hl = p.hl;
-    for (int k = 0; k < p.B; ++k) ctx->nu.push_back(cfg->inst[k].nu);
+    for (int k = 0; k < p.B; ++k) {
+        ctx->nu.push_back(cfg->inst[k].nu);
+        ctx->rmax.push_back(cfg->inst[k].r_max);
+    }
     ctx->count = p.count;
     char* base = (char*)workspace;
     Dev& d = ctx->dev;
@@ -1642,6 +1604,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
         d.hist[b] = (float*)(base + p.o_hist[b]);
         d.cnt[b] = (int*)(base + p.o_cnt[b]);
         d.hmask[b] = (unsigned*)(base + p.o_hmask[b]);
+        d.fext[b] = (float4*)(base + p.o_fext[b]);
         d.whist[b] = (float4*)(base + p.o_whist[b]);
     }
     d.cellcode = (unsigned*)(base + p.o_cellcode);
@@ -1678,6 +1641,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     for (int k = 0; k < p.B; ++k) {
         idv[k] = InstD{};
         idv[k].n = (int)p.count[k];
+        idv[k].nid = (int)p.count[k];
         idv[k].flag = 2;
     }
     Glob gl{};
@@ -1744,7 +1708,8 @@ static bool is_device_ptr(const void* p)
 static int field_width(int f)
 {
     switch (f) {
-    case DEM_F_POS: case DEM_F_VEL: case DEM_F_OMEGA: case DEM_F_FORCE: case DEM_F_TORQUE: case DEM_F_WALL_XI: return 3;
+    case DEM_F_POS: case DEM_F_VEL: case DEM_F_OMEGA: case DEM_F_FORCE: case DEM_F_TORQUE: case DEM_F_WALL_XI:
+    case DEM_F_FEXT: return 3;
     case DEM_F_RADIUS: case DEM_F_MASS: case DEM_F_NBR_COUNT: return 1;
     default: return 0;
     }
@@ -1755,7 +1720,8 @@ dem_status dem_write(dem_ctx* ctx, int32_t field, const void* src, int64_t n)
     if (!ctx) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     const int w = field_width(field);
-    if (w == 0 || field == DEM_F_FORCE || field == DEM_F_TORQUE || field == DEM_F_WALL_XI || field == DEM_F_NBR_COUNT)
+    if (w == 0 || field == DEM_F_FORCE || field == DEM_F_TORQUE || field == DEM_F_WALL_XI || field == DEM_F_NBR_COUNT ||
+        field == DEM_F_FEXT)
         return fail(ctx, DEM_ERR_ARG, "field is not writable");
     if (n != total_count(ctx)) return fail(ctx, DEM_ERR_ARG, "n must equal the total particle count");
     if (n == 0) return DEM_OK;

@@ -1,0 +1,973 @@
+// Two-way volumetric coupling of a coarse-grain level and an embedded fine
+// level (Sec. 2.3): boundary-surface measurement, transition-layer stress (Eq. 7)
+// with a PI controller acting on the fine particles, fine-to-coarse P
+// correction, insertion of fine particles by simple sequential inhibition, and
+// removal through drain faces.  The interface and the readings of the paper are
+// documented in include/dem.h (dem_coupling).
+#include "dem.h"
+#include "dem_contact.cuh"
+#include "dem_ctx.h"
+#include "dem_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace cgdem;
+
+namespace {
+
+constexpr int MAXBINS = 32;
+
+struct Face {
+    int axis, side;      // side 0: the face at lo[axis] (inward normal +e_axis), 1: at hi[axis]
+    int b, c;            // in-plane axes
+    int nb, nc, off;     // cells along b and c, first cell index
+    double plane, wb, wc;
+};
+
+struct Geo {
+    double lo[3], hi[3];
+    int nface;
+    Face face[6];
+    int S;               // surface cells (= transition cells)
+    int ncr[3];
+    double wcr[3];
+    int C;               // correction cells
+    double layer, alpha, Tc, dt, kp, ki, kv, mass_unit;
+    int bins, mode, max_attempts, max_insert, drain;
+    unsigned long long seed;
+    int call;            // coupling interval counter (random-number counter)
+    // the two levels' frames: x = lo + u q
+    double loc[3], qc, lof[3], qf;
+    int rmaxf_u;         // largest fine radius in fine units (histogram range)
+    int fresh_c, fresh_f;
+};
+
+struct Acc {
+    // surface cells
+    unsigned long long* cross;   // entered mass [mass units]
+    unsigned* hist;              // [S][MAXBINS]
+    double* fav;                 // [S][4]: sum m, sum m v
+    long long* carry;            // [S]
+    int* nins;                   // [S]
+    int4* ins;                   // [S][max_insert] inserted particles, fine units (r in w)
+    double* insm;                // [S][max_insert] their masses [kg]
+    // transition cells, level L = 0 coarse, 1 fine
+    double* lay;                 // [2][S][20]: m, mv(3), mvv(6), V, contact stress(6), -, -, -
+    unsigned* vmax;              // [2][S] largest speed (float bits)
+    double* ctrl;                // [S][3]: e, I, u
+    double* out;                 // [2][S][11]: sigma(6), phi, v(3), vmax
+    // correction cells
+    double* cor;                 // [2][C][5]: m, mv(3), V
+    double* dv;                  // [C][3] velocity change asked of the coarse particles
+    // coarse particles by ID: position at the previous call [m], validity
+    double* prev;                // [idcap][3]
+    int* prev_ok;
+    int* removed;                // [1] fine particles removed at this call
+};
+
+__device__ __forceinline__ double posm(const double* lo, double q, int u, int a) { return lo[a] + (double)u * q; }
+
+__device__ __forceinline__ bool inside_box(const Geo& g, const double* x)
+{
+    return x[0] >= g.lo[0] && x[0] < g.hi[0] && x[1] >= g.lo[1] && x[1] < g.hi[1] && x[2] >= g.lo[2] &&
+           x[2] < g.hi[2];
+}
+
+// surface / transition cell of an in-plane point of face f (-1 outside the face)
+__device__ __forceinline__ int face_cell(const Face& f, double pb, double pc, const Geo& g)
+{
+    if (pb < g.lo[f.b] || pb >= g.hi[f.b] || pc < g.lo[f.c] || pc >= g.hi[f.c]) return -1;
+    int ib = (int)floor((pb - g.lo[f.b]) / f.wb), ic = (int)floor((pc - g.lo[f.c]) / f.wc);
+    ib = min(max(ib, 0), f.nb - 1);
+    ic = min(max(ic, 0), f.nc - 1);
+    return f.off + ib + f.nb * ic;
+}
+
+// transition cell holding a point (first face in order wins at corners), or -1
+__device__ __forceinline__ int layer_cell(const Geo& g, const double* x, int* fidx)
+{
+    if (!inside_box(g, x)) return -1;
+    for (int k = 0; k < g.nface; ++k) {
+        const Face& f = g.face[k];
+        const double s = f.side == 0 ? x[f.axis] - f.plane : f.plane - x[f.axis];
+        if (s >= 0.0 && s < g.layer) {
+            const int c = face_cell(f, x[f.b], x[f.c], g);
+            if (c >= 0) {
+                *fidx = k;
+                return c;
+            }
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int corr_cell(const Geo& g, const double* x)
+{
+    if (!inside_box(g, x)) return -1;
+    int i[3];
+    for (int a = 0; a < 3; ++a) i[a] = min(max((int)floor((x[a] - g.lo[a]) / g.wcr[a]), 0), g.ncr[a] - 1);
+    return (i[2] * g.ncr[1] + i[1]) * g.ncr[0] + i[0];
+}
+
+__device__ __forceinline__ void atomic_max_f(unsigned* a, float v)
+{
+    if (v > 0.f) atomicMax(a, __float_as_uint(v));
+}
+
+// Eq. 7 accumulation of one particle into a transition cell: mass, momentum,
+// m v v, volume, and the contact part 1/2 r_ij (x) f_ij over its contacts
+// (floor contact: branch vector to the contact point, no 1/2), symmetrised.
+__device__ void layer_add(const Dev& d, const InstC& c, const InstD& D, int s, double* acc, unsigned* vmax, int fresh)
+{
+    const int cur = D.cur, lp = D.lp, ncap = d.ncap;
+    const size_t plane = (size_t)d.Lmax * ncap;
+    const int4 P = d.pos[cur][s];
+    const float4 Vv = d.vel[cur][s], Wv = d.omg[cur][s];
+    const double m = Wv.w, q = c.q;
+    const double r = (double)P.w * q;
+    const double v[3] = {Vv.x, Vv.y, Vv.z};
+    atomicAdd(acc + 0, m);
+    for (int a = 0; a < 3; ++a) atomicAdd(acc + 1 + a, m * v[a]);
+    const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int k = 0; k < 6; ++k) atomicAdd(acc + 4 + k, m * v[ij[k][0]] * v[ij[k][1]]);
+    atomicAdd(acc + 10, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
+    atomic_max_f(vmax, sqrtf(Vv.x * Vv.x + Vv.y * Vv.y + Vv.z * Vv.z));
+    const Coef<float> cf{c.c_kn, c.c_kt, c.nbeta, c.gt_ratio, c.mu, c.mu_w, c.clamp_fn};
+    const float dt_hist = fresh ? 0.f : c.dt;
+    const unsigned hm = d.hmask[lp][s];
+    double st[6] = {0, 0, 0, 0, 0, 0};
+    const int ncnt = d.cnt[lp][s];
+    for (int e = 0; e < ncnt; ++e) {
+        const int j = d.nbr[lp][(size_t)e * ncap + s];
+        const int4 Q = d.pos[cur][j];
+        const int dx = min_image(P.x - Q.x, c.per[0], c.ext[0], c.half[0]);
+        const int dy = min_image(P.y - Q.y, c.per[1], c.ext[1], c.half[1]);
+        const int dz = P.z - Q.z;
+        const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+        const int S = P.w + Q.w;
+        const long long S2 = (long long)S * S;
+        if (d2 >= S2) continue;
+        const float4 Vj = d.vel[cur][j], Wj = d.omg[cur][j];
+        const float d2f = (float)d2;
+        const float inv = rsqrtf(d2f);
+        const float dist = d2f * inv;
+        const float delta = __fdividef((float)(S2 - d2), (float)S + dist) * (float)q;
+        const Vec3<float> n = mk3((float)dx * inv, (float)dy * inv, (float)dz * inv);
+        const float* h = d.hist[lp] + s + (size_t)e * ncap;
+        Vec3<float> xi = ((hm >> e) & 1u) ? mk3(h[0], h[plane], h[2 * plane]) : mk3(0.f, 0.f, 0.f);
+        Vec3<float> ft;
+        bool slip;
+        const Vec3<float> fa = contact_fwd<float, false>(cf, delta, n, (float)r, (float)((double)Q.w * q), (float)m,
+                                                         Wj.w, mk3(Vv.x, Vv.y, Vv.z), mk3(Vj.x, Vj.y, Vj.z),
+                                                         mk3(Wv.x, Wv.y, Wv.z), mk3(Wj.x, Wj.y, Wj.z), xi, dt_hist,
+                                                         ft, slip);
+        const double rv[3] = {dx * q, dy * q, dz * q}, f[3] = {fa.x, fa.y, fa.z};
+        for (int k = 0; k < 6; ++k) {
+            const int a = ij[k][0], b = ij[k][1];
+            st[k] += 0.25 * (rv[a] * f[b] + rv[b] * f[a]);
+        }
+    }
+    if (c.floor_on && P.w - P.z > 0) {
+        const float4 hw = d.whist[lp][s];
+        const bool wall_prev = (__float_as_uint(Vv.w) & WALL_BIT) != 0u;
+        Vec3<float> xi = wall_prev ? mk3(hw.x, hw.y, hw.z) : mk3(0.f, 0.f, 0.f);
+        Vec3<float> ft;
+        bool slip;
+        const Vec3<float> fa = contact_fwd<float, true>(cf, (float)((P.w - P.z) * q), mk3(0.f, 0.f, 1.f), (float)r, 0.f,
+                                                        (float)m, 0.f, mk3(Vv.x, Vv.y, Vv.z),
+                                                        mk3(c.floor_v[0], c.floor_v[1], c.floor_v[2]),
+                                                        mk3(Wv.x, Wv.y, Wv.z), mk3(0.f, 0.f, 0.f), xi, dt_hist, ft, slip);
+        const double rv[3] = {0.0, 0.0, (double)P.z * q}, f[3] = {fa.x, fa.y, fa.z};
+        for (int k = 0; k < 6; ++k) {
+            const int a = ij[k][0], b = ij[k][1];
+            st[k] += 0.5 * (rv[a] * f[b] + rv[b] * f[a]);
+        }
+    }
+    for (int k = 0; k < 6; ++k) atomicAdd(acc + 11 + k, st[k]);
+}
+
+template <typename Fn>
+__device__ __forceinline__ void for_live(const Dev& d, Fn fn)
+{
+    for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
+        const int k = d.tile_inst[t];
+        const InstD D = d.id[k];
+        const int s = t * TILE + threadIdx.x;
+        if (s - d.ic[k].slot0 >= D.n) continue;
+        fn(s, d.ic[k], D);
+    }
+}
+
+__global__ void k_cp_clear(Geo g, Acc a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < g.S) {
+        a.cross[i] = 0ull;
+        for (int b = 0; b < MAXBINS; ++b) a.hist[(size_t)i * MAXBINS + b] = 0u;
+        for (int k = 0; k < 4; ++k) a.fav[4 * i + k] = 0.0;
+        a.nins[i] = 0;
+        for (int L = 0; L < 2; ++L) {
+            for (int k = 0; k < 20; ++k) a.lay[((size_t)L * g.S + i) * 20 + k] = 0.0;
+            a.vmax[L * g.S + i] = 0u;
+        }
+    }
+    if (i < g.C)
+        for (int L = 0; L < 2; ++L)
+            for (int k = 0; k < 5; ++k) a.cor[((size_t)L * g.C + i) * 5 + k] = 0.0;
+    if (i == 0) a.removed[0] = 0;
+}
+
+// coarse level: entries through the feed faces, Favre samples at the faces,
+// transition and correction cells; remember the positions for the next call
+__global__ void __launch_bounds__(TILE) k_cp_coarse(Dev d, Geo g, Acc a, int record_only)
+{
+    for_live(d, [&](int s, const InstC& c, const InstD& D) {
+        const int4 P = d.pos[D.cur][s];
+        const float4 V = d.vel[D.cur][s];
+        const unsigned id = __float_as_uint(V.w) & ID_MASK;
+        const double x[3] = {posm(g.loc, g.qc, P.x, 0), posm(g.loc, g.qc, P.y, 1), posm(g.loc, g.qc, P.z, 2)};
+        const double r = (double)P.w * g.qc, m = d.omg[D.cur][s].w;
+        if (!record_only) {
+            // entry through a feed face since the previous call
+            if (a.prev_ok[id] && inside_box(g, x)) {
+                const double* p = a.prev + 3 * (size_t)id;
+                double seg = 0.0;
+                for (int k = 0; k < 3; ++k) seg = fmax(seg, fabs(x[k] - p[k]));
+                if (!inside_box(g, p) && seg < 0.25 * (g.hi[0] - g.lo[0] + g.hi[1] - g.lo[1] + g.hi[2] - g.lo[2])) {
+                    double tbest = 2.0;
+                    int cbest = -1;
+                    for (int k = 0; k < g.nface; ++k) {
+                        const Face& f = g.face[k];
+                        const double p0 = p[f.axis], p1 = x[f.axis];
+                        const bool enters = f.side == 0 ? (p0 < f.plane && p1 >= f.plane) : (p0 >= f.plane && p1 < f.plane);
+                        if (!enters) continue;
+                        const double t = (f.plane - p0) / (p1 - p0);
+                        const int cc = face_cell(f, p[f.b] + t * (x[f.b] - p[f.b]), p[f.c] + t * (x[f.c] - p[f.c]), g);
+                        if (cc >= 0 && t < tbest) {
+                            tbest = t;
+                            cbest = cc;
+                        }
+                    }
+                    if (cbest >= 0) {
+                        atomicAdd(a.cross + cbest, (unsigned long long)llrint(m / g.mass_unit));
+                        // fine radius r / alpha in fine units; bin b holds the radii u with
+                        // floor(u bins / (R + 1)) = b over [0, R], R = largest fine radius
+                        const long long rf = min(llrint(r / g.alpha / g.qf), (long long)g.rmaxf_u);
+                        const int b = (int)(rf * g.bins / (g.rmaxf_u + 1));
+                        atomicAdd(a.hist + (size_t)cbest * MAXBINS + b, 1u);
+                    }
+                }
+            }
+            // Favre sample at the faces: centres within one diameter of a feed face
+            for (int k = 0; k < g.nface; ++k) {
+                const Face& f = g.face[k];
+                if (fabs(x[f.axis] - f.plane) >= 2.0 * r) continue;
+                const int cc = face_cell(f, x[f.b], x[f.c], g);
+                if (cc < 0) continue;
+                atomicAdd(a.fav + 4 * cc, m);
+                atomicAdd(a.fav + 4 * cc + 1, m * V.x);
+                atomicAdd(a.fav + 4 * cc + 2, m * V.y);
+                atomicAdd(a.fav + 4 * cc + 3, m * V.z);
+                break;
+            }
+            int fk;
+            const int lc = layer_cell(g, x, &fk);
+            if (lc >= 0) layer_add(d, c, D, s, a.lay + (size_t)lc * 20, a.vmax + lc, g.fresh_c);
+            const int cc = corr_cell(g, x);
+            if (cc >= 0) {
+                double* o = a.cor + (size_t)cc * 5;
+                atomicAdd(o, m);
+                atomicAdd(o + 1, m * V.x);
+                atomicAdd(o + 2, m * V.y);
+                atomicAdd(o + 3, m * V.z);
+                atomicAdd(o + 4, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
+            }
+        }
+        for (int k = 0; k < 3; ++k) a.prev[3 * (size_t)id + k] = x[k];
+        a.prev_ok[id] = 1;
+    });
+}
+
+// fine level: transition and correction cells, removal through drain faces
+__global__ void __launch_bounds__(TILE) k_cp_fine(Dev d, Geo g, Acc a)
+{
+    for_live(d, [&](int s, const InstC& c, const InstD& D) {
+        const int4 P = d.pos[D.cur][s];
+        float4 V = d.vel[D.cur][s];
+        const double x[3] = {posm(g.lof, g.qf, P.x, 0), posm(g.lof, g.qf, P.y, 1), posm(g.lof, g.qf, P.z, 2)};
+        const double r = (double)P.w * g.qf, m = d.omg[D.cur][s].w;
+        int fk;
+        const int lc = layer_cell(g, x, &fk);
+        if (lc >= 0) layer_add(d, c, D, s, a.lay + ((size_t)g.S + lc) * 20, a.vmax + g.S + lc, g.fresh_f);
+        const int cc = corr_cell(g, x);
+        if (cc >= 0) {
+            double* o = a.cor + ((size_t)g.C + cc) * 5;
+            atomicAdd(o, m);
+            atomicAdd(o + 1, m * V.x);
+            atomicAdd(o + 2, m * V.y);
+            atomicAdd(o + 3, m * V.z);
+            atomicAdd(o + 4, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
+        }
+        bool gone = false;
+        for (int ax = 0; ax < 3; ++ax) {
+            if ((g.drain >> (2 * ax)) & 1) gone |= x[ax] < g.lo[ax];
+            if ((g.drain >> (2 * ax + 1)) & 1) gone |= x[ax] >= g.hi[ax];
+        }
+        if (gone) {
+            V.w = __uint_as_float(__float_as_uint(V.w) | GONE_BIT);
+            d.vel[D.cur][s] = V;
+            atomicAdd(a.removed, 1);
+        }
+    });
+}
+
+// per cell: finish the averages, update the controllers
+__global__ void k_cp_cells(Geo g, Acc a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < g.S) {
+        int fk = 0;
+        for (int k = 0; k < g.nface; ++k)
+            if (i >= g.face[k].off && i < g.face[k].off + g.face[k].nb * g.face[k].nc) fk = k;
+        const Face& f = g.face[fk];
+        const double Vc = f.wb * f.wc * g.layer;
+        double sig_aa[2];
+        for (int L = 0; L < 2; ++L) {
+            const double* A = a.lay + ((size_t)L * g.S + i) * 20;
+            double* o = a.out + ((size_t)L * g.S + i) * 11;
+            const double M = A[0];
+            double v[3] = {0, 0, 0};
+            if (M > 0) for (int k = 0; k < 3; ++k) v[k] = A[1 + k] / M;
+            const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+            for (int k = 0; k < 6; ++k) o[k] = (A[11 + k] + A[4 + k] - M * v[ij[k][0]] * v[ij[k][1]]) / Vc;
+            o[6] = A[10] / Vc;
+            for (int k = 0; k < 3; ++k) o[7 + k] = v[k];
+            o[10] = __uint_as_float(a.vmax[L * g.S + i]);
+            sig_aa[L] = o[f.axis];
+        }
+        double* ct = a.ctrl + 3 * (size_t)i;
+        const double e = sig_aa[0] - sig_aa[1];
+        ct[0] = e;
+        ct[1] += e * g.Tc;
+        ct[2] = g.kp * e + g.ki * ct[1];
+    }
+    if (i < g.C) {
+        const double* Ac = a.cor + (size_t)i * 5;
+        const double* Af = a.cor + ((size_t)g.C + i) * 5;
+        double* dv = a.dv + 3 * (size_t)i;
+        dv[0] = dv[1] = dv[2] = 0.0;
+        if (Ac[0] > 0 && Af[0] > 0) {
+            double fac = 1.0;
+            if (g.mode == 1) fac = fmin(Af[4] / Ac[4], 4.0);
+            for (int k = 0; k < 3; ++k) dv[k] = Af[1 + k] / Af[0] * fac - Ac[1 + k] / Ac[0];
+        }
+    }
+}
+
+// controller forces, held until the next call
+__global__ void __launch_bounds__(TILE) k_cp_force_fine(Dev d, Geo g, Acc a)
+{
+    for_live(d, [&](int s, const InstC& c, const InstD& D) {
+        const int4 P = d.pos[D.cur][s];
+        const float4 V = d.vel[D.cur][s];
+        const double x[3] = {posm(g.lof, g.qf, P.x, 0), posm(g.lof, g.qf, P.y, 1), posm(g.lof, g.qf, P.z, 2)};
+        float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
+        int fk = 0;
+        const int lc = layer_cell(g, x, &fk);
+        if (lc >= 0) {
+            const Face& f = g.face[fk];
+            const double r = (double)P.w * g.qf, m = d.omg[D.cur][s].w;
+            const double sdist = f.side == 0 ? x[f.axis] - f.plane : f.plane - x[f.axis];
+            const double w = fmax(0.0, 1.0 - sdist / (1.5 * 2.0 * r));
+            const double u = a.ctrl[3 * (size_t)lc + 2];
+            double Fv[3] = {0, 0, 0};
+            Fv[f.axis] = (f.side == 0 ? 1.0 : -1.0) * u * 3.14159265358979323846 * r * r * w;
+            // keep the speed after one step below the coarse cell's largest speed
+            const double vmax = __uint_as_float(a.vmax[lc]);
+            const double vv[3] = {V.x, V.y, V.z};
+            double acc[3], A2 = 0, VA = 0, V2 = 0;
+            for (int k = 0; k < 3; ++k) {
+                acc[k] = g.dt * Fv[k] / m;
+                A2 += acc[k] * acc[k];
+                VA += vv[k] * acc[k];
+                V2 += vv[k] * vv[k];
+            }
+            double lam = 1.0;
+            if (A2 > 0 && V2 + 2 * VA + A2 > vmax * vmax) {
+                if (V2 >= vmax * vmax) lam = 0.0;
+                else lam = fmin(1.0, (-VA + sqrt(VA * VA - A2 * (V2 - vmax * vmax))) / A2);
+            }
+            F = make_float4((float)(lam * Fv[0]), (float)(lam * Fv[1]), (float)(lam * Fv[2]), 0.f);
+        }
+        d.fext[D.lp][s] = F;
+    });
+}
+
+__global__ void __launch_bounds__(TILE) k_cp_force_coarse(Dev d, Geo g, Acc a)
+{
+    for_live(d, [&](int s, const InstC& c, const InstD& D) {
+        const int4 P = d.pos[D.cur][s];
+        const double x[3] = {posm(g.loc, g.qc, P.x, 0), posm(g.loc, g.qc, P.y, 1), posm(g.loc, g.qc, P.z, 2)};
+        float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int cc = corr_cell(g, x);
+        if (cc >= 0) {
+            const double m = d.omg[D.cur][s].w, k = g.kv * m / g.Tc;
+            const double* dv = a.dv + 3 * (size_t)cc;
+            F = make_float4((float)(k * dv[0]), (float)(k * dv[1]), (float)(k * dv[2]), 0.f);
+        }
+        d.fext[D.lp][s] = F;
+    });
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): finaliser of a Weyl sequence, used
+// here on a counter built from (seed, cell, interval, attempt, draw)
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ unsigned long long draw(const Geo& g, int cell, int attempt, int k)
+{
+    const unsigned long long ctr =
+        (((unsigned long long)cell * 1048576ull + (unsigned long long)g.call) * 16777216ull + (unsigned long long)attempt) *
+            8ull + (unsigned long long)k;
+    return splitmix64(g.seed ^ splitmix64(ctr));
+}
+
+// uniform integer in [0, n) from 64 random bits (n < 2^32)
+__device__ __forceinline__ long long below(unsigned long long u, long long n)
+{
+    return (long long)(((u >> 32) * (unsigned long long)n) >> 32);
+}
+
+__device__ __forceinline__ double sphere_mass(double rho, double r)
+{
+    return __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(rho, 4.0 / 3.0 * 3.14159265358979323846), r), r), r);
+}
+
+// one thread per surface cell of one face: simple sequential inhibition
+__global__ void k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
+{
+    const Face& f = g.face[fk];
+    const int local = blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= f.nb * f.nc) return;
+    const int cell = f.off + local;
+    const int ib = local % f.nb, ic = local / f.nb;
+    const InstC& c = d.ic[0];
+    const InstD D = d.id[0];
+    long long quota = (long long)a.cross[cell] + a.carry[cell];
+    unsigned total = 0;
+    const unsigned* hist = a.hist + (size_t)cell * MAXBINS;
+    for (int b = 0; b < g.bins; ++b) total += hist[b];
+    int nins = 0, fails = 0, attempt = 0;
+    const double M = a.fav[4 * cell];
+    double vn = 0.0, vf[3] = {0, 0, 0};
+    if (M > 0) {
+        for (int k = 0; k < 3; ++k) vf[k] = a.fav[4 * cell + 1 + k] / M;
+        vn = vf[f.axis];
+    }
+    int4* mine = a.ins + (size_t)cell * g.max_insert;
+    double* mym = a.insm + (size_t)cell * g.max_insert;
+    // face extent of this cell in fine units
+    const double b0 = g.lo[f.b] + ib * f.wb, c0 = g.lo[f.c] + ic * f.wc;
+    while (quota > 0 && total > 0 && fails < g.max_attempts && nins < g.max_insert) {
+        // diameter: bin by count, uniform within the bin
+        long long pick = below(draw(g, cell, attempt, 0), total);
+        int b = 0;
+        while (pick >= (long long)hist[b]) {
+            pick -= hist[b];
+            ++b;
+        }
+        const long long R1 = g.rmaxf_u + 1;
+        const long long rlo = (b * R1 + g.bins - 1) / g.bins, rhi = ((b + 1) * R1 + g.bins - 1) / g.bins - 1;
+        const long long ru = rlo + below(draw(g, cell, attempt, 1), rhi - rlo + 1);
+        if (ru <= 0) {
+            ++attempt;
+            ++fails;
+            continue;
+        }
+        const double r = (double)ru * g.qf;
+        const double depth = fmax(2.0 * r, fabs(vn) * g.Tc);
+        // position in fine units: in-plane within the cell shrunk by r, along the
+        // normal in [face + r, face + r + depth] inside the region
+        long long u[3];
+        const long long bl = llrint(ceil((b0 + r - g.lof[f.b]) / g.qf)), bh = llrint(floor((b0 + f.wb - r - g.lof[f.b]) / g.qf));
+        const long long cl = llrint(ceil((c0 + r - g.lof[f.c]) / g.qf)), ch = llrint(floor((c0 + f.wc - r - g.lof[f.c]) / g.qf));
+        double nlo, nhi;
+        if (f.side == 0) {
+            nlo = f.plane + r;
+            nhi = f.plane + r + depth;
+        } else {
+            nlo = f.plane - r - depth;
+            nhi = f.plane - r;
+        }
+        const long long al = llrint(ceil((nlo - g.lof[f.axis]) / g.qf)), ah = llrint(floor((nhi - g.lof[f.axis]) / g.qf));
+        if (bh < bl || ch < cl || ah < al) {
+            ++attempt;
+            ++fails;
+            continue;
+        }
+        u[f.b] = bl + below(draw(g, cell, attempt, 2), bh - bl + 1);
+        u[f.c] = cl + below(draw(g, cell, attempt, 3), ch - cl + 1);
+        u[f.axis] = al + below(draw(g, cell, attempt, 4), ah - al + 1);
+        ++attempt;
+        // overlap with fine particles (cell lists of the last build) and with earlier insertions
+        bool ok = true;
+        const int ru_i = (int)ru;
+        const int cx0 = axis_cell(c, 0, (int)u[0]), cy0 = axis_cell(c, 1, (int)u[1]), cz0 = axis_cell(c, 2, (int)u[2]);
+        const unsigned cbase = d.cstart[c.code0];
+        for (int dz = -1; dz <= 1 && ok; ++dz) {
+            const int cz = cz0 + dz;
+            if (cz < 0 || cz >= c.nc[2]) continue;
+            for (int dy = -1; dy <= 1 && ok; ++dy) {
+                int cy = cy0 + dy;
+                if (cy < 0 || cy >= c.nc[1]) {
+                    if (!c.per[1]) continue;
+                    cy = (cy + c.nc[1]) % c.nc[1];
+                }
+                for (int dx = -1; dx <= 1 && ok; ++dx) {
+                    int cx = cx0 + dx;
+                    if (cx < 0 || cx >= c.nc[0]) {
+                        if (!c.per[0]) continue;
+                        cx = (cx + c.nc[0]) % c.nc[0];
+                    }
+                    const unsigned code = cell_code(d, c, cx, cy, cz);
+                    const int start = c.slot0 + (int)(d.cstart[code] - cbase);
+                    const int cnt = (int)d.ccount[code];
+                    for (int t = 0; t < cnt; ++t) {
+                        const int j = start + t;
+                        if (j - c.slot0 >= D.n) continue;
+                        const int4 Q = d.pos[D.cur][j];
+                        const long long ex = min_image((int)u[0] - Q.x, c.per[0], c.ext[0], c.half[0]);
+                        const long long ey = min_image((int)u[1] - Q.y, c.per[1], c.ext[1], c.half[1]);
+                        const long long ez = (long long)u[2] - Q.z;
+                        const long long S = (long long)ru_i + Q.w;
+                        if (ex * ex + ey * ey + ez * ez < S * S) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+        // earlier insertions: this cell, and the cells of earlier faces
+        for (int t = 0; t < nins && ok; ++t) {
+            const long long ex = u[0] - mine[t].x, ey = u[1] - mine[t].y, ez = u[2] - mine[t].z;
+            const long long S = (long long)ru_i + mine[t].w;
+            if (ex * ex + ey * ey + ez * ez < S * S) ok = false;
+        }
+        for (int k = 0; k < fk && ok; ++k) {
+            const Face& o = g.face[k];
+            for (int oc = o.off; oc < o.off + o.nb * o.nc && ok; ++oc) {
+                const int4* other = a.ins + (size_t)oc * g.max_insert;
+                for (int t = 0; t < a.nins[oc] && ok; ++t) {
+                    const long long ex = u[0] - other[t].x, ey = u[1] - other[t].y, ez = u[2] - other[t].z;
+                    const long long S = (long long)ru_i + other[t].w;
+                    if (ex * ex + ey * ey + ez * ez < S * S) ok = false;
+                }
+            }
+        }
+        if (!ok) {
+            ++fails;
+            continue;
+        }
+        const double m = sphere_mass(rho, r);
+        mine[nins] = make_int4((int)u[0], (int)u[1], (int)u[2], ru_i);
+        mym[nins] = m;
+        ++nins;
+        quota -= llrint(m / g.mass_unit);
+    }
+    a.nins[cell] = nins;
+    a.carry[cell] = quota;
+}
+
+// append the inserted particles (cell order) to the fine level's tail
+__global__ void k_cp_append(Dev d, Geo g, Acc a, int* overflow)
+{
+    const InstC& c = d.ic[0];
+    InstD& D = d.id[0];
+    int tot = 0;
+    for (int i = 0; i < g.S; ++i) tot += a.nins[i];
+    if (D.n + tot > c.cap || D.nid + tot > c.cap) {
+        if (threadIdx.x == 0) *overflow = 1;
+        return;
+    }
+    __syncthreads();
+    int off = 0;
+    for (int i = 0; i < g.S; ++i) {
+        const int k = a.nins[i];
+        for (int t = threadIdx.x; t < k; t += blockDim.x) {
+            const int s = c.slot0 + D.n + off + t;
+            const int id = D.nid + off + t;
+            const int4 p = a.ins[(size_t)i * g.max_insert + t];
+            const double M = a.fav[4 * i];
+            float v[3] = {0.f, 0.f, 0.f};
+            if (M > 0)
+                for (int q = 0; q < 3; ++q) v[q] = (float)(a.fav[4 * i + 1 + q] / M);
+            d.pos[D.cur][s] = p;
+            d.vel[D.cur][s] = make_float4(v[0], v[1], v[2], __uint_as_float((unsigned)id));
+            d.omg[D.cur][s] = make_float4(0.f, 0.f, 0.f, (float)a.insm[(size_t)i * g.max_insert + t]);
+            d.cnt[D.lp][s] = 0;
+            d.hmask[D.lp][s] = 0u;
+            d.whist[D.lp][s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            d.fext[D.lp][s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            d.slot_of_id[c.slot0 + id] = s;
+        }
+        off += k;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        D.n += tot;
+        D.nid += tot;
+        if ((tot > 0 || a.removed[0] > 0) && D.flag == 0) {
+            D.flag = 1;
+            atomicOr(&d.g->any, 1u);
+        }
+    }
+}
+
+}  // namespace
+
+struct dem_coupler {
+    dem_ctx* c = nullptr;
+    dem_ctx* f = nullptr;
+    dem_coupling spec{};
+    Geo g{};
+    Acc a{};
+    int* overflow = nullptr;
+    int calls = 0;
+    double rho_f = 0.0;
+};
+
+namespace {
+
+size_t coupler_layout(dem_coupler* cp, char* base)
+{
+    struct L {
+        size_t t = 0;
+        size_t take(size_t b)
+        {
+            size_t o = t;
+            t += (b + 255) & ~size_t(255);
+            return o;
+        }
+    } L;
+    const size_t S = cp->g.S, C = cp->g.C, MI = cp->g.max_insert, ncap = (size_t)cp->c->ncap;
+    size_t o_cross = L.take(S * 8), o_hist = L.take(S * MAXBINS * 4), o_fav = L.take(S * 32), o_carry = L.take(S * 8),
+           o_nins = L.take(S * 4), o_ins = L.take(S * MI * 16), o_insm = L.take(S * MI * 8), o_lay = L.take(2 * S * 160),
+           o_vmax = L.take(2 * S * 4), o_ctrl = L.take(S * 24), o_out = L.take(2 * S * 88), o_cor = L.take(2 * C * 40),
+           o_dv = L.take(C * 24), o_prev = L.take(ncap * 24), o_pok = L.take(ncap * 4), o_rem = L.take(16),
+           o_ovf = L.take(16);
+    if (base) {
+        Acc& a = cp->a;
+        a.cross = (unsigned long long*)(base + o_cross);
+        a.hist = (unsigned*)(base + o_hist);
+        a.fav = (double*)(base + o_fav);
+        a.carry = (long long*)(base + o_carry);
+        a.nins = (int*)(base + o_nins);
+        a.ins = (int4*)(base + o_ins);
+        a.insm = (double*)(base + o_insm);
+        a.lay = (double*)(base + o_lay);
+        a.vmax = (unsigned*)(base + o_vmax);
+        a.ctrl = (double*)(base + o_ctrl);
+        a.out = (double*)(base + o_out);
+        a.cor = (double*)(base + o_cor);
+        a.dv = (double*)(base + o_dv);
+        a.prev = (double*)(base + o_prev);
+        a.prev_ok = (int*)(base + o_pok);
+        a.removed = (int*)(base + o_rem);
+        cp->overflow = (int*)(base + o_ovf);
+    }
+    return L.t;
+}
+
+dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo& g, std::string& err)
+{
+    if (!coarse || !fine || !sp) { err = "null argument"; return DEM_ERR_ARG; }
+    if (coarse->B != 1 || fine->B != 1) { err = "coupling needs single-instance contexts"; return DEM_ERR_ARG; }
+    if (sp->interval < 1 || sp->bins < 1 || sp->bins > MAXBINS || !(sp->alpha > 0) || !(sp->surface_cell > 0) ||
+        !(sp->layer > 0) || !(sp->corr_cell > 0) || !(sp->mass_unit > 0) || sp->max_insert < 1 || sp->max_attempts < 1 ||
+        sp->feed_faces <= 0 || sp->feed_faces >= 64) {
+        err = "coupling spec: interval, bins (1..32), alpha, cell sizes, layer, mass_unit, max_insert, max_attempts and "
+              "feed_faces must be positive";
+        return DEM_ERR_ARG;
+    }
+    memset(&g, 0, sizeof(g));
+    for (int a = 0; a < 3; ++a) {
+        g.lo[a] = sp->lo[a];
+        g.hi[a] = sp->hi[a];
+        if (!(g.hi[a] > g.lo[a])) { err = "empty fine region"; return DEM_ERR_ARG; }
+        g.loc[a] = coarse->hl[0].lo[a];
+        g.lof[a] = fine->hl[0].lo[a];
+    }
+    g.qc = coarse->hl[0].q;
+    g.qf = fine->hl[0].q;
+    int off = 0;
+    for (int bit = 0; bit < 6; ++bit) {
+        if (!((sp->feed_faces >> bit) & 1)) continue;
+        Face& f = g.face[g.nface++];
+        f.axis = bit / 2;
+        f.side = bit % 2;
+        f.b = (f.axis + 1) % 3;
+        f.c = (f.axis + 2) % 3;
+        if (f.b > f.c) std::swap(f.b, f.c);
+        f.plane = f.side == 0 ? g.lo[f.axis] : g.hi[f.axis];
+        f.nb = std::max(1, (int)std::floor((g.hi[f.b] - g.lo[f.b]) / sp->surface_cell));
+        f.nc = std::max(1, (int)std::floor((g.hi[f.c] - g.lo[f.c]) / sp->surface_cell));
+        f.wb = (g.hi[f.b] - g.lo[f.b]) / f.nb;
+        f.wc = (g.hi[f.c] - g.lo[f.c]) / f.nc;
+        f.off = off;
+        off += f.nb * f.nc;
+    }
+    g.S = off;
+    g.C = 1;
+    for (int a = 0; a < 3; ++a) {
+        g.ncr[a] = std::max(1, (int)std::floor((g.hi[a] - g.lo[a]) / sp->corr_cell));
+        g.wcr[a] = (g.hi[a] - g.lo[a]) / g.ncr[a];
+        g.C *= g.ncr[a];
+    }
+    g.layer = sp->layer;
+    g.alpha = sp->alpha;
+    g.dt = fine->ic[0].dt;
+    g.Tc = sp->interval * (double)fine->ic[0].dt;
+    g.kp = sp->kp;
+    g.ki = sp->ki;
+    g.kv = sp->kv;
+    g.mass_unit = sp->mass_unit;
+    g.bins = sp->bins;
+    g.mode = sp->mode;
+    g.max_attempts = sp->max_attempts;
+    g.max_insert = sp->max_insert;
+    g.drain = sp->drain_faces;
+    g.seed = sp->seed;
+    return DEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dem_status dem_coupler_workspace(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* spec, int64_t* bytes)
+{
+    if (!bytes) return DEM_ERR_ARG;
+    dem_coupler tmp;
+    std::string err;
+    dem_status st = plan_geo(coarse, fine, spec, tmp.g, err);
+    if (st) {
+        set_thread_error(err);
+        return st;
+    }
+    tmp.c = coarse;
+    tmp.f = fine;
+    *bytes = (int64_t)coupler_layout(&tmp, nullptr);
+    return DEM_OK;
+}
+
+dem_status dem_coupler_create(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* spec, void* ws, int64_t bytes,
+                              dem_coupler** out)
+{
+    if (!out) return DEM_ERR_ARG;
+    *out = nullptr;
+    dem_coupler* cp = new dem_coupler();
+    std::string err;
+    dem_status st = plan_geo(coarse, fine, spec, cp->g, err);
+    if (st) {
+        set_thread_error(err);
+        delete cp;
+        return st;
+    }
+    cp->c = coarse;
+    cp->f = fine;
+    cp->spec = *spec;
+    const size_t need = coupler_layout(cp, nullptr);
+    if (!ws || (size_t)bytes < need || ((uintptr_t)ws & 255)) {
+        set_thread_error("coupler workspace missing, too small or not 256-byte aligned");
+        delete cp;
+        return DEM_ERR_ARG;
+    }
+    coupler_layout(cp, (char*)ws);
+    cp->rho_f = fine->hl[0].rho;
+    // largest fine radius in fine units: from the fine level's r_max (cell width)
+    cp->g.rmaxf_u = (int)std::llround(std::ceil(fine->rmax[0] / cp->g.qf));
+    cudaStream_t s = fine->stream;
+    dem_ctx* ctx = fine;
+    CU(cudaMemsetAsync(ws, 0, need, s));
+    // enable the external force on both levels
+    for (dem_ctx* x : {coarse, fine}) {
+        int one = 1;
+        ctx = x;
+        CU(cudaMemcpyAsync((char*)x->dev.id + offsetof(InstD, fext), &one, sizeof(int), cudaMemcpyHostToDevice,
+                           x->stream));
+        CU(cudaStreamSynchronize(x->stream));
+    }
+    ctx = fine;
+    CU(cudaStreamSynchronize(s));
+    // first sample of the coarse positions
+    cp->g.call = 0;
+    cudaStreamSynchronize(coarse->stream);
+    k_cp_coarse<<<coarse->grid_rb, TILE, 0, s>>>(coarse->dev, cp->g, cp->a, 1);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(s));
+    *out = cp;
+    return DEM_OK;
+}
+
+dem_status dem_couple(dem_coupler* cp)
+{
+    if (!cp) return DEM_ERR_ARG;
+    dem_ctx* ctx = cp->f;
+    dem_ctx* coarse = cp->c;
+    if (coarse->status) return check_status(coarse);
+    if (ctx->status) return check_status(ctx);
+    // both levels must be current and their lists valid; work on the fine level's stream
+    CU(cudaStreamSynchronize(coarse->stream));
+    dem_status st = launch_rebuild(coarse, coarse->stream);
+    if (st) return st;
+    if ((st = launch_rebuild(ctx, ctx->stream))) return st;
+    CU(cudaStreamSynchronize(coarse->stream));
+    cudaStream_t s = ctx->stream;
+    Geo g = cp->g;
+    g.call = ++cp->calls;
+    g.fresh_c = coarse->fresh ? 1 : 0;
+    g.fresh_f = ctx->fresh ? 1 : 0;
+    const int nb = (std::max(g.S, g.C) + 255) / 256;
+    k_cp_clear<<<nb, 256, 0, s>>>(g, cp->a);
+    k_cp_coarse<<<coarse->grid_rb, TILE, 0, s>>>(coarse->dev, g, cp->a, 0);
+    k_cp_fine<<<ctx->grid_rb, TILE, 0, s>>>(ctx->dev, g, cp->a);
+    k_cp_cells<<<nb, 256, 0, s>>>(g, cp->a);
+    k_cp_force_fine<<<ctx->grid_rb, TILE, 0, s>>>(ctx->dev, g, cp->a);
+    k_cp_force_coarse<<<coarse->grid_rb, TILE, 0, s>>>(coarse->dev, g, cp->a);
+    for (int fk = 0; fk < g.nface; ++fk)
+        k_cp_insert<<<(g.face[fk].nb * g.face[fk].nc + 63) / 64, 64, 0, s>>>(ctx->dev, g, cp->a, fk, cp->rho_f);
+    CU(cudaMemsetAsync(cp->overflow, 0, sizeof(int), s));
+    k_cp_append<<<1, 256, 0, s>>>(ctx->dev, g, cp->a, cp->overflow);
+    CU(cudaGetLastError());
+    int ovf = 0;
+    CU(cudaMemcpyAsync(&ovf, cp->overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
+    InstD D;
+    CU(cudaMemcpyAsync(&D, ctx->dev.id, sizeof(InstD), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (ovf) return fail(ctx, DEM_ERR_CAPACITY, "inserted particles exceed the fine level's capacity");
+    ctx->count[0] = D.nid;
+    std::vector<long long> goff = {0, (long long)D.nid};
+    CU(cudaMemcpyAsync(ctx->dev.goff, goff.data(), sizeof(long long) * 2, cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    return DEM_OK;
+}
+
+dem_status dem_coupler_read(dem_coupler* cp, int32_t field, double* dst, int64_t n)
+{
+    if (!cp || !dst) return DEM_ERR_ARG;
+    dem_ctx* ctx = cp->f;
+    const Geo& g = cp->g;
+    const size_t S = g.S, C = g.C;
+    CU(cudaStreamSynchronize(ctx->stream));
+    auto get = [&](const void* src, size_t bytes, void* h) -> dem_status {
+        CU(cudaMemcpy(h, src, bytes, cudaMemcpyDeviceToHost));
+        return DEM_OK;
+    };
+    std::vector<double> tmp;
+    std::vector<long long> li(S);
+    std::vector<unsigned long long> lu(S);
+    std::vector<int> ii(S);
+    std::vector<unsigned> hu;
+    size_t need = 0;
+    switch (field) {
+    case DEM_CPL_SIZES: need = 4; break;
+    case DEM_CPL_SURFACE_MASS: case DEM_CPL_SURFACE_CARRY: case DEM_CPL_SURFACE_INSERTED: need = S; break;
+    case DEM_CPL_SURFACE_VEL: need = 3 * S; break;
+    case DEM_CPL_SURFACE_HIST: need = S * g.bins; break;
+    case DEM_CPL_LAYER_STRESS: need = 12 * S; break;
+    case DEM_CPL_LAYER_PHI: case DEM_CPL_LAYER_VMAX: need = 2 * S; break;
+    case DEM_CPL_LAYER_VEL: need = 6 * S; break;
+    case DEM_CPL_LAYER_CTRL: need = 3 * S; break;
+    case DEM_CPL_CORR_PHI: need = 2 * C; break;
+    case DEM_CPL_CORR_VEL: need = 6 * C; break;
+    default: return fail(ctx, DEM_ERR_ARG, "unknown coupler field");
+    }
+    if ((size_t)n != need) return fail(ctx, DEM_ERR_ARG, "wrong element count for the coupler field");
+    dem_status st = DEM_OK;
+    switch (field) {
+    case DEM_CPL_SIZES: dst[0] = (double)S; dst[1] = (double)S; dst[2] = (double)C; dst[3] = cp->calls; break;
+    case DEM_CPL_SURFACE_MASS:
+        st = get(cp->a.cross, S * 8, lu.data());
+        for (size_t i = 0; i < S; ++i) dst[i] = (double)lu[i] * g.mass_unit;
+        break;
+    case DEM_CPL_SURFACE_CARRY:
+        st = get(cp->a.carry, S * 8, li.data());
+        for (size_t i = 0; i < S; ++i) dst[i] = (double)li[i] * g.mass_unit;
+        break;
+    case DEM_CPL_SURFACE_INSERTED:
+        st = get(cp->a.nins, S * 4, ii.data());
+        for (size_t i = 0; i < S; ++i) dst[i] = ii[i];
+        break;
+    case DEM_CPL_SURFACE_VEL:
+        tmp.resize(4 * S);
+        st = get(cp->a.fav, S * 32, tmp.data());
+        for (size_t i = 0; i < S; ++i)
+            for (int k = 0; k < 3; ++k) dst[3 * i + k] = tmp[4 * i] > 0 ? tmp[4 * i + 1 + k] / tmp[4 * i] : 0.0;
+        break;
+    case DEM_CPL_SURFACE_HIST:
+        hu.resize(S * MAXBINS);
+        st = get(cp->a.hist, S * MAXBINS * 4, hu.data());
+        for (size_t i = 0; i < S; ++i)
+            for (int b = 0; b < g.bins; ++b) dst[i * g.bins + b] = hu[i * MAXBINS + b];
+        break;
+    default:
+        if (field >= DEM_CPL_LAYER_STRESS && field <= DEM_CPL_LAYER_VMAX) {
+            tmp.resize(2 * S * 11);
+            st = get(cp->a.out, 2 * S * 88, tmp.data());
+            for (size_t L = 0; L < 2; ++L)
+                for (size_t i = 0; i < S; ++i) {
+                    const double* o = &tmp[(L * S + i) * 11];
+                    if (field == DEM_CPL_LAYER_STRESS) for (int k = 0; k < 6; ++k) dst[(i * 2 + L) * 6 + k] = o[k];
+                    if (field == DEM_CPL_LAYER_PHI) dst[i * 2 + L] = o[6];
+                    if (field == DEM_CPL_LAYER_VEL) for (int k = 0; k < 3; ++k) dst[(i * 2 + L) * 3 + k] = o[7 + k];
+                    if (field == DEM_CPL_LAYER_VMAX) dst[i * 2 + L] = o[10];
+                }
+        } else if (field == DEM_CPL_LAYER_CTRL) {
+            st = get(cp->a.ctrl, S * 24, dst);
+        } else {
+            tmp.resize(2 * C * 5);
+            st = get(cp->a.cor, 2 * C * 40, tmp.data());
+            for (size_t L = 0; L < 2; ++L)
+                for (size_t i = 0; i < C; ++i) {
+                    const double* o = &tmp[(L * C + i) * 5];
+                    const double V = g.wcr[0] * g.wcr[1] * g.wcr[2];
+                    if (field == DEM_CPL_CORR_PHI) dst[i * 2 + L] = o[4] / V;
+                    if (field == DEM_CPL_CORR_VEL)
+                        for (int k = 0; k < 3; ++k) dst[(i * 2 + L) * 3 + k] = o[0] > 0 ? o[1 + k] / o[0] : 0.0;
+                }
+        }
+    }
+    return st;
+}
+
+dem_status dem_coupler_destroy(dem_coupler* cp)
+{
+    if (!cp) return DEM_ERR_ARG;
+    delete cp;   // touches neither context (they may already be gone)
+    return DEM_OK;
+}
+
+dem_status dem_counts(dem_ctx* ctx, int64_t* live, int64_t* ids)
+{
+    if (!ctx || !live || !ids) return DEM_ERR_ARG;
+    std::vector<InstD> D(ctx->B);
+    CU(cudaMemcpyAsync(D.data(), ctx->dev.id, sizeof(InstD) * ctx->B, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < ctx->B; ++k) {
+        live[k] = D[k].n;
+        ids[k] = D[k].nid;
+    }
+    return DEM_OK;
+}
+
+}  // extern "C"

@@ -30,8 +30,9 @@ namespace cgdem {
 
 constexpr int TILE = 128;      // step-kernel block size = slot alignment of an instance
 constexpr int MAXL = 32;       // largest list width (one bit per entry in a 32-bit mask)
-constexpr unsigned ID_MASK = 0x7fffffffu;
-constexpr unsigned WALL_BIT = 0x80000000u;
+constexpr unsigned ID_MASK = 0x3fffffffu;   // particle ID (< 2^30)
+constexpr unsigned GONE_BIT = 0x40000000u;  // removed: dropped at the next list build
+constexpr unsigned WALL_BIT = 0x80000000u;  // in contact with the floor at the last step
 
 // device status bits
 constexpr unsigned ST_CAPACITY = 1u;
@@ -65,13 +66,16 @@ struct InstC {
 
 // dynamic state of one instance (device-resident)
 struct InstD {
-    int n;               // live particles
+    int n;               // live particles (slots slot0 .. slot0 + n - 1)
     int cur;             // state buffer holding the current step
     int lp;              // list buffer parity
     int flag;            // 0 none, 1 rebuild pending, 2 rebuild with cleared history
     float disp;          // accumulated per-step displacement bound since the last build [units]
     unsigned stepmax;    // this step's largest displacement (float bits)
-    int pad[2];
+    int nid;             // IDs handed out so far (n plus removed particles); IDs are never reused
+    int n_new;           // live particles after the pending rebuild (removed ones dropped)
+    int fext;            // 1: add the per-particle external force fext to the contact forces
+    int pad[3];
 };
 
 struct Glob {
@@ -95,6 +99,7 @@ struct Dev {
     float* hist[2];
     int* cnt[2];
     unsigned* hmask[2];        // bit e: entry e holds a non-zero tangential overlap
+    float4* fext[2];           // external force per particle (coupling controllers), list parity
     float4* whist[2];
     unsigned* cellcode;
     unsigned* cslot;
@@ -126,5 +131,57 @@ struct Dev {
     unsigned ncodes;
     unsigned nparts;
 };
+
+// host-side description of an instance's frame (origin, quantum, density)
+struct HostInstLo {
+    double lo[3];
+    double q;
+    double rho;
+};
+
+// snapshot of the dynamic state of a context (differentiable rollouts)
+struct Snap {
+    int4* pos;
+    float4* vel;
+    float4* omg;
+    float* hist;
+    unsigned* hmask;
+    float4* whist;
+    float* disp;       // per instance: displacement bound accumulated since the list build
+};
+
+// adjoint buffers of a differentiable rollout
+struct AdjBufs {
+    float4* xb;        // adjoint of x^n [1/m units of the objective]
+    float4* vb;        // adjoint of v^{n-1/2}
+    float4* wb;        // adjoint of w^{n-1/2}
+    float4* Fb;        // adjoint of F^n
+    float4* Tb;        // adjoint of T^n
+    float* xib;        // adjoint of the stored overlaps, [3][Lmax][ncap], from each row's side
+    float4* wxib;      // adjoint of the floor overlap
+    double* thb;       // per slot: accumulated d/dE, d/de, d/dmu
+};
+
+__device__ __forceinline__ int axis_cell(const InstC& c, int a, int x)
+{
+    if (x <= 0) return 0;
+    long long t = (long long)x * c.nc[a] / c.ext[a];
+    return t >= c.nc[a] ? c.nc[a] - 1 : (int)t;
+}
+
+__device__ __forceinline__ unsigned cell_code(const Dev& d, const InstC& c, int cx, int cy, int cz)
+{
+    return (unsigned)c.code0 + d.spread[c.spread_off[0] + cx] + d.spread[c.spread_off[1] + cy] +
+           d.spread[c.spread_off[2] + cz];
+}
+
+__device__ __forceinline__ int min_image(int dx, int per, int L, int half)
+{
+    if (per) {
+        if (dx > half) dx -= L;
+        else if (dx < -half) dx += L;
+    }
+    return dx;
+}
 
 }  // namespace cgdem

@@ -9,14 +9,15 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 
 import numpy as np
 
 from .build import LIB
 
 # field ids (dem_field)
-POS, VEL, OMEGA, RADIUS, MASS, FORCE, TORQUE, WALL_XI, NBR_COUNT = range(9)
-_WIDTH = {POS: 3, VEL: 3, OMEGA: 3, RADIUS: 1, MASS: 1, FORCE: 3, TORQUE: 3, WALL_XI: 3, NBR_COUNT: 1}
+POS, VEL, OMEGA, RADIUS, MASS, FORCE, TORQUE, WALL_XI, NBR_COUNT, FEXT = range(10)
+_WIDTH = {POS: 3, VEL: 3, OMEGA: 3, RADIUS: 1, MASS: 1, FORCE: 3, TORQUE: 3, WALL_XI: 3, NBR_COUNT: 1, FEXT: 3}
 STATUS = {0: "DEM_OK", 1: "DEM_ERR_ARG", 2: "DEM_ERR_CAPACITY", 3: "DEM_ERR_CUDA", 4: "DEM_ERR_NONFINITE",
           5: "DEM_ERR_ESCAPED", 6: "DEM_ERR_TIMEOUT", 7: "DEM_ERR_STATE"}
 
@@ -53,6 +54,19 @@ class Stats(ctypes.Structure):
                 ("contacts", ctypes.c_int64), ("particles", ctypes.c_int64), ("wall_contacts", ctypes.c_int64)]
 
 
+class CouplingSpec(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("feed_faces", ctypes.c_int32),
+                ("drain_faces", ctypes.c_int32), ("surface_cell", ctypes.c_double), ("layer", ctypes.c_double),
+                ("corr_cell", ctypes.c_double), ("interval", ctypes.c_int32), ("bins", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("kp", ctypes.c_double), ("ki", ctypes.c_double), ("kv", ctypes.c_double),
+                ("mode", ctypes.c_int32), ("max_attempts", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("mass_unit", ctypes.c_double), ("max_insert", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+# coupler fields (dem_coupler_field)
+CPL_SURFACE_MASS, CPL_SURFACE_CARRY, CPL_SURFACE_INSERTED, CPL_SURFACE_VEL, CPL_SURFACE_HIST, CPL_LAYER_STRESS, \
+    CPL_LAYER_PHI, CPL_LAYER_VEL, CPL_LAYER_VMAX, CPL_LAYER_CTRL, CPL_CORR_PHI, CPL_CORR_VEL, CPL_SIZES = range(13)
+
 _lib = None
 
 
@@ -84,6 +98,12 @@ def lib():
         "dem_rollout_adjoint": [vp, vp, vp, vp],
         "dem_observables": [vp, vp, vp],
         "dem_set_material": [vp, vp],
+        "dem_coupler_workspace": [vp, vp, ctypes.POINTER(CouplingSpec), ctypes.POINTER(i64)],
+        "dem_coupler_create": [vp, vp, ctypes.POINTER(CouplingSpec), vp, i64, ctypes.POINTER(vp)],
+        "dem_couple": [vp],
+        "dem_coupler_read": [vp, i32, vp, i64],
+        "dem_coupler_destroy": [vp],
+        "dem_counts": [vp, vp, vp],
         "dem_neighbor_counts_noalloc": [vp, vp, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i32), ctypes.c_double, ctypes.c_double, vp, vp],
     }
@@ -101,7 +121,9 @@ def exported_symbols():
     return ["dem_query_workspace", "dem_create", "dem_destroy", "dem_write", "dem_read", "dem_read_contacts",
             "dem_write_contacts", "dem_step", "dem_sync_status", "dem_instance_info_get", "dem_stats",
             "dem_set_graph", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
-            "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material", "dem_last_error"]
+            "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material",
+            "dem_coupler_workspace", "dem_coupler_create", "dem_couple", "dem_coupler_read", "dem_coupler_destroy",
+            "dem_counts", "dem_last_error"]
 
 
 def desc(*, n, lo, hi, periodic, dt, skin, r_max, E, nu, e, mu, rho, g=(0, 0, 0), floor=True,
@@ -156,7 +178,7 @@ class DEM:
                                       self.workspace_bytes, ctypes.c_void_p(self.stream.cuda_stream),
                                       ctypes.byref(h)), "create")
         self.h = h
-        self.counts = [int(d.n) for d in descs]
+        self.counts_ = [int(d.n) for d in descs]
 
     # ------------------------------------------------------------------
     def _check(self, rc, what):
@@ -166,7 +188,7 @@ class DEM:
 
     @property
     def n(self):
-        return sum(self.counts)
+        return sum(self.counts_)
 
     def close(self):
         if getattr(self, "h", None):
@@ -174,6 +196,8 @@ class DEM:
             self.h = None
 
     def __del__(self):
+        if sys.is_finalizing():      # the CUDA runtime may already be torn down
+            return
         try:
             self.close()
         except Exception:
@@ -259,7 +283,7 @@ class DEM:
 
     def set_material(self, params):
         """params (B, 3) = {E, e, mu} per instance."""
-        arr, ptr = self._host(params, (len(self.counts), 3))
+        arr, ptr = self._host(params, (len(self.counts_), 3))
         self._check(self.L.dem_set_material(self.h, ptr), "set material")
         return self
 
@@ -278,7 +302,7 @@ class DEM:
 
     def observables(self, axis):
         """(B, 2) = {kinetic energy, runout} at the current step; axis (B, 2) [m]."""
-        B = len(self.counts)
+        B = len(self.counts_)
         ax, axp = self._host(axis, (B, 2))
         out = np.zeros((B, 2))
         self._check(self.L.dem_observables(self.h, axp, ctypes.c_void_p(out.ctypes.data)), "observables")
@@ -286,12 +310,22 @@ class DEM:
 
     def rollout_adjoint(self, weights, axis):
         """(B, 3) gradient of sum_k w_KE KE_k + w_R runout_k w.r.t. {E, e, mu} per instance."""
-        B = len(self.counts)
+        B = len(self.counts_)
         w, wp = self._host(weights, (B, 2))
         ax, axp = self._host(axis, (B, 2))
         grad = np.zeros((B, 3))
         self._check(self.L.dem_rollout_adjoint(self.h, wp, axp, ctypes.c_void_p(grad.ctypes.data)), "rollout adjoint")
         return grad
+
+    def counts(self):
+        """(live, ids) per instance; refreshes the binding's idea of the particle count."""
+        B = len(self.counts_)
+        live = np.zeros(B, dtype=np.int64)
+        ids = np.zeros(B, dtype=np.int64)
+        self._check(self.L.dem_counts(self.h, ctypes.c_void_p(live.ctypes.data), ctypes.c_void_p(ids.ctypes.data)),
+                    "counts")
+        self.counts_ = [int(x) for x in ids]
+        return live, ids
 
     def info(self, k=0):
         inf = InstanceInfo()
@@ -327,6 +361,70 @@ def neighbor_counts_noalloc(x, r, lo, hi, periodic, skin, r_max, out=None, strea
     if rc != 0:
         raise DemError(rc, L.dem_last_error(None).decode())
     return out
+
+
+class Coupler:
+    """Two-way coupling of a coarse and a fine single-instance context (dem_coupler_*)."""
+
+    def __init__(self, coarse, fine, **spec):
+        import torch
+        self.L = lib()
+        self.coarse, self.fine = coarse, fine
+        sp = CouplingSpec()
+        for a in range(3):
+            sp.lo[a], sp.hi[a] = float(spec["lo"][a]), float(spec["hi"][a])
+        for k in ("feed_faces", "drain_faces", "interval", "bins", "mode", "max_attempts", "max_insert"):
+            setattr(sp, k, int(spec.get(k, 0)))
+        for k in ("surface_cell", "layer", "corr_cell", "alpha", "kp", "ki", "kv", "mass_unit"):
+            setattr(sp, k, float(spec[k]))
+        sp.seed = int(spec.get("seed", 0))
+        self.spec = sp
+        nb = ctypes.c_int64()
+        rc = self.L.dem_coupler_workspace(coarse.h, fine.h, ctypes.byref(sp), ctypes.byref(nb))
+        if rc:
+            raise DemError(rc, self.L.dem_last_error(None).decode())
+        self.ws = torch.empty(int(nb.value), dtype=torch.uint8, device=fine.device)
+        h = ctypes.c_void_p()
+        rc = self.L.dem_coupler_create(coarse.h, fine.h, ctypes.byref(sp), ctypes.c_void_p(self.ws.data_ptr()),
+                                       int(nb.value), ctypes.byref(h))
+        if rc:
+            raise DemError(rc, self.L.dem_last_error(None).decode())
+        self.h = h
+        sz = self.read(CPL_SIZES)
+        self.S, self.C = int(sz[0]), int(sz[2])
+
+    def couple(self):
+        rc = self.L.dem_couple(self.h)
+        if rc:
+            raise DemError(rc, self.L.dem_last_error(self.fine.h).decode())
+        self.fine.counts()
+        return self
+
+    def read(self, field):
+        S, C = getattr(self, "S", 0), getattr(self, "C", 0)
+        bins = self.spec.bins
+        shapes = {CPL_SIZES: (4,), CPL_SURFACE_MASS: (S,), CPL_SURFACE_CARRY: (S,), CPL_SURFACE_INSERTED: (S,),
+                  CPL_SURFACE_VEL: (S, 3), CPL_SURFACE_HIST: (S, bins), CPL_LAYER_STRESS: (S, 2, 6),
+                  CPL_LAYER_PHI: (S, 2), CPL_LAYER_VEL: (S, 2, 3), CPL_LAYER_VMAX: (S, 2), CPL_LAYER_CTRL: (S, 3),
+                  CPL_CORR_PHI: (C, 2), CPL_CORR_VEL: (C, 2, 3)}
+        out = np.zeros(shapes[field])
+        rc = self.L.dem_coupler_read(self.h, field, ctypes.c_void_p(out.ctypes.data), out.size)
+        if rc:
+            raise DemError(rc, self.L.dem_last_error(self.fine.h).decode())
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.dem_coupler_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_workload(wl, max_neighbors=32, capacity=None, **kw) -> DEM:

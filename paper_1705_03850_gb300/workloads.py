@@ -199,6 +199,45 @@ def column_materials(count: int = 64, seed: int = 5) -> list[Material]:
             for _ in range(count)]
 
 
+def coupling_case(seed: int = 50, shift: float = 3.0e-3):
+    """A coarse level (d = 4 mm) above and across the top face of a fine region
+    (d = 2 mm particles) in a 24 x 24 mm periodic column, for one coupling call:
+    coarse positions before (A) and after (B, moved down by `shift`), the fine
+    level, and the coupling spec.  Returns (A, B, fine, spec)."""
+    rng = np.random.default_rng(seed)
+    L, H = 0.024, 0.06
+    mat = Material(E=1e7, nu=0.25, e=0.6, mu=0.4, rho=2500.0)
+    sp_c = 4.0e-3 * (1 - 2e-3)
+    g = np.arange(6) * sp_c + sp_c / 2
+    X, Y, Z = np.meshgrid(g, g, np.arange(11) * sp_c + 14.2e-3, indexing="ij")
+    xa = np.column_stack([X.ravel(), Y.ravel(), Z.ravel()]) + rng.uniform(-2e-6, 2e-6, (X.size, 3))
+    nc = xa.shape[0]
+    rc = 2.0e-3 * (1 + rng.uniform(-2e-3, 2e-3, nc))
+    vc = rng.normal(0.0, 0.05, (nc, 3)) + np.array([0.0, 0.0, -0.5])
+    wc = rng.normal(0.0, 10.0, (nc, 3))
+    xb = xa + np.array([0.0, 0.0, -shift]) + rng.uniform(-1e-5, 1e-5, xa.shape)
+    A = _finish("coarse_A", xa, vc, wc, rc, mat, (0, 0, 0), (L, L, H), (True, True, False), 1e-6, (0, 0, -9.81),
+                True, (0, 0, 0), 0.4e-3, 15)
+    B = _finish("coarse_B", xb, vc, wc, rc, mat, (0, 0, 0), (L, L, H), (True, True, False), 1e-6, (0, 0, -9.81),
+                True, (0, 0, 0), 0.4e-3, 15)
+    sp_f = 2.0e-3 * (1 - 2e-3)
+    gf = np.arange(12) * sp_f + sp_f / 2
+    Xf, Yf, Zf = np.meshgrid(gf, gf, np.arange(9) * sp_f + 2.0e-3, indexing="ij")   # top within the fade zone
+    xf = np.column_stack([Xf.ravel(), Yf.ravel(), Zf.ravel()]) + rng.uniform(-1e-6, 1e-6, (Xf.size, 3))
+    # the top layer (inside the controller's fade zone) covers half the face only,
+    # so that the other half has room for inserted particles
+    top = Zf.ravel() > Zf.max() - 1e-4
+    xf = xf[~top | (Xf.ravel() < L / 2)]
+    nf = xf.shape[0]
+    rf = 1.0e-3 * (1 + rng.uniform(-2e-3, 2e-3, nf))
+    fine = _finish("fine", xf, rng.normal(0.0, 0.05, (nf, 3)), rng.normal(0.0, 10.0, (nf, 3)), rf, mat, (0, 0, 0),
+                   (L, L, H), (True, True, False), 1e-6, (0, 0, -9.81), True, (0, 0, 0), 0.2e-3, 15)
+    spec = dict(lo=(0.0, 0.0, 0.0), hi=(L, L, 0.02), feed_faces=1 << 5, drain_faces=0, surface_cell=12e-3,
+                layer=12e-3, corr_cell=8e-3, interval=15, bins=16, alpha=2.0, kp=1.0, ki=1.0 / (10 * 15e-6), kv=0.5,
+                mode=1, max_attempts=100, seed=1234, mass_unit=1e-15, max_insert=256, dt=B.dt)
+    return A, B, fine, spec
+
+
 def batch_sizes(count: int = 256, seed: int = 4, nmin: float = 2e3, nmax: float = 2e5) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.round(np.exp(rng.uniform(math.log(nmin), math.log(nmax), count))).astype(np.int64)

@@ -42,7 +42,7 @@ def test_struct_layout_matches_header(tmp_path):
     import subprocess
     from paper_1705_03850_gb300 import dem
     structs = {"dem_instance_desc": dem.InstanceDesc, "dem_config": dem.Config,
-               "dem_instance_info": dem.InstanceInfo, "dem_stats_t": dem.Stats}
+               "dem_instance_info": dem.InstanceInfo, "dem_stats_t": dem.Stats, "dem_coupling": dem.CouplingSpec}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dem.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -1,0 +1,137 @@
+"""Pins of the coupling oracle (Sec. 2.3) against closed forms and invariants (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+RHO = 2500.0
+E, NU = 1e7, 0.25
+
+
+def _P(lo, hi, periodic=(True, True, False), floor=False, g=(0, 0, 0)):
+    return oracle.make_params(E=E, nu=NU, e=0.6, mu=0.4, dt=1e-6, g=g, lo=lo, hi=hi, periodic=periodic, floor=floor)
+
+
+def _spec(**kw):
+    s = dict(lo=(0.0, 0.0, 0.0), hi=(0.024, 0.024, 0.02), feed_faces=1 << 5, drain_faces=0, surface_cell=0.012,
+             layer=0.012, corr_cell=0.008, interval=15, bins=16, alpha=2.0, kp=1.0, ki=0.0, kv=0.5, mode=0,
+             max_attempts=100, seed=7, mass_unit=1e-15, max_insert=256, dt=1e-6)
+    s.update(kw)
+    return s
+
+
+def _state(x, v=None, r=None, rho=RHO):
+    x = np.atleast_2d(np.asarray(x, dtype=float))
+    n = len(x)
+    v = np.zeros((n, 3)) if v is None else np.atleast_2d(np.asarray(v, dtype=float))
+    r = np.full(n, 1e-3) if r is None else np.asarray(r, dtype=float)
+    m = rho * 4.0 / 3.0 * math.pi * r ** 3
+    return dict(x=x, v=v, w=np.zeros((n, 3)), r=r, m=m, id=np.arange(n))
+
+
+def _coupler(spec, Pc, Pf, rmax_f=1e-3, idcap=64):
+    qf = oracle.quantum(Pf[9:12], Pf[12:15])
+    return oracle.Coupler(spec, Pc, Pf, Pf[9:12], qf, int(math.ceil(rmax_f / qf)), RHO, idcap), qf
+
+
+def test_eq7_stress_of_one_compressed_pair_and_two_moving_particles():
+    # One contact inside a transition cell: both ends lie in the cell, each adds
+    # 1/2 r_ij f_ij, so sigma_zz = F d / V.  Kinetic part: two equal masses
+    # moving at +-u along z add 2 m u^2 / V.
+    lo, hi = (0, 0, 0), (0.024, 0.024, 0.06)
+    Pc, Pf = _P(lo, hi), _P(lo, hi)
+    spec = _spec()
+    cp, qf = _coupler(spec, Pc, Pf)
+    d = 2e-3 - 4e-6
+    fine = _state([[0.006, 0.006, 0.015], [0.006, 0.006, 0.015 + d]], v=[[0, 0, 0], [0, 0, 0]])
+    out = cp.call(_state([[0.006, 0.006, 0.05]]), fine, 0.0, 0.0)
+    c = oracle.pair_coeffs(Pf, 1e-3, 1e-3, fine["m"][0], fine["m"][1], 4e-6)
+    F = c["kn"] * 4e-6
+    V = 0.012 * 0.012 * 0.012
+    cell = 0                      # x, y < 12 mm
+    assert out["lay"][1, cell, 2] == pytest.approx(F * d / V, rel=1e-12)
+    assert abs(out["lay"][1, cell, 0]) < 1e-12 * F * d / V      # no xx part for a vertical contact
+    u = 0.3
+    moving = _state([[0.003, 0.003, 0.012], [0.009, 0.009, 0.012]], v=[[0, 0, u], [0, 0, -u]])
+    out = cp.call(_state([[0.006, 0.006, 0.05]]), moving, 0.0, 0.0)
+    m = moving["m"][0]
+    # same cell, <v> = 0, v' = +-u
+    assert out["lay"][1, 0, 2] == pytest.approx(2 * m * u * u / V, rel=1e-12)
+    assert out["lay"][1, 0, 0] == 0.0
+
+
+def test_entry_through_the_feed_face_only_and_histogram_bin():
+    lo, hi = (0, 0, 0), (0.024, 0.024, 0.06)
+    Pc, Pf = _P(lo, hi), _P(lo, hi)
+    cp, qf = _coupler(_spec(), Pc, Pf, idcap=4)
+    r = np.array([2e-3, 2e-3, 2e-3])
+    before = _state([[0.006, 0.006, 0.0215], [0.018, 0.018, 0.03], [0.006, 0.018, 0.025]], r=r)
+    cp.record(before["x"], before["id"])
+    after = _state([[0.006, 0.006, 0.0195], [0.018, 0.018, 0.029], [0.006, 0.018, 0.0199]], r=r)
+    out = cp.call(after, _state([[0.012, 0.012, 0.003]]), 0.0, 0.0)
+    m = after["m"][0]
+    # particles 0 and 2 entered through the top face (cells 0 and 2 of the 2 x 2 grid); particle 1 did not
+    expect = np.zeros(4, dtype=np.int64)
+    expect[0] = round(m / 1e-15)
+    expect[2] = round(m / 1e-15)
+    assert np.array_equal(out["cross"].astype(np.int64), expect)
+    # diameter histogram of r / alpha = 1 mm over [0, r_max fine]: the top bin
+    assert out["hist"][0].sum() == 1 and out["hist"][0][-1] == 1
+
+
+def test_insertion_conserves_mass_and_makes_no_overlaps():
+    lo, hi = (0, 0, 0), (0.024, 0.024, 0.06)
+    Pc, Pf = _P(lo, hi), _P(lo, hi)
+    cp, qf = _coupler(_spec(), Pc, Pf, idcap=200)
+    rng = np.random.default_rng(3)
+    xs = np.column_stack([rng.uniform(0, 0.024, 72), rng.uniform(0, 0.024, 72), np.full(72, 0.021)])
+    cg = _state(xs, r=np.full(72, 2e-3))
+    cp.record(cg["x"], cg["id"])
+    cg2 = dict(cg)
+    cg2["x"] = xs - np.array([0, 0, 0.002])
+    fine = _state([[0.012, 0.012, 0.003]])
+    out = cp.call(cg2, fine, 0.0, 0.0)
+    ins = np.concatenate([out["ins_u"][c, :out["nins"][c]] for c in range(4)])
+    assert len(ins) > 20
+    mass_in = np.array([sum(round(m / 1e-15) for m in out["ins_m"][c, :out["nins"][c]]) for c in range(4)])
+    assert np.array_equal(mass_in + out["carry"], out["cross"].astype(np.int64))
+    x = np.vstack([fine["x"], ins[:, :3] * qf])
+    r = np.concatenate([fine["r"], ins[:, 3] * qf])
+    assert len(oracle.pairs(Pf, x, r, 0.0, method="brute")) == 0
+    # inside the region, within r of nothing outside: below the top face by at least r
+    assert np.all(x[1:, 2] + r[1:] <= 0.02 + 1e-12)
+
+
+def test_controllers_special_cases():
+    lo, hi = (0, 0, 0), (0.024, 0.024, 0.06)
+    Pc, Pf = _P(lo, hi), _P(lo, hi)
+    # identical coarse and fine material in the correction cells: v* = v_cg -> no force on coarse particles
+    v = [[0.1, 0.0, -0.2]]
+    for mode in (0, 1):
+        cp, qf = _coupler(_spec(mode=mode), Pc, Pf)
+        out = cp.call(_state([[0.004, 0.004, 0.004]], v=v, r=[1e-3]), _state([[0.004, 0.004, 0.004]], v=v),
+                      0.0, 0.0)
+        assert np.abs(out["fext_c"]).max() == 0.0
+    # a velocity mismatch gives F = kv m (v_f - v_cg) / T_c (mode 0)
+    cp, qf = _coupler(_spec(mode=0), Pc, Pf)
+    c = _state([[0.004, 0.004, 0.004]], v=[[0.0, 0.0, 0.0]], r=[1e-3])
+    out = cp.call(c, _state([[0.004, 0.004, 0.004]], v=[[0.0, 0.0, -0.3]]), 0.0, 0.0)
+    assert out["fext_c"][0, 2] == pytest.approx(0.5 * c["m"][0] * (-0.3) / 15e-6, rel=1e-12)
+    # mass-flow mode multiplies the fine velocity by phi_f / phi_cg (here 8 particles vs 1: capped at 4)
+    cp, qf = _coupler(_spec(mode=1), Pc, Pf)
+    fine = _state([[0.002 + 0.002 * i, 0.002 + 0.002 * j, 0.002 + 0.002 * k] for i in range(2) for j in range(2)
+                   for k in range(2)], v=[[0.0, 0.0, -0.1]] * 8)
+    out = cp.call(_state([[0.004, 0.004, 0.004]], r=[1e-3]), fine, 0.0, 0.0)
+    assert out["fext_c"][0, 2] == pytest.approx(0.5 * c["m"][0] * (-0.1 * 4.0) / 15e-6, rel=1e-12)
+    # PI with ki = 0: the force on a fine particle is linear in the stress mismatch
+    spec = _spec(kp=2.0)
+    cp, qf = _coupler(spec, Pc, Pf)
+    d = 2e-3 - 4e-6
+    cg = _state([[0.006, 0.006, 0.0185], [0.006, 0.006, 0.0185 - d]], r=[1e-3, 1e-3])
+    probe = _state([[0.018, 0.006, 0.0195]], v=[[0, 0, -1e-3]])
+    out = cp.call(cg, probe, 0.0, 0.0)
+    ctrl = out["ctrl"]
+    e = ctrl[0, 0]
+    assert ctrl[0, 2] == pytest.approx(2.0 * e, rel=1e-14)

@@ -51,6 +51,13 @@ def _args():
     ap.add_argument("--batched-steps", type=int, default=2000)
     ap.add_argument("--batched-scale", type=float, default=1.0, help="scale of the 256 box sizes (1 = as stated)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batched-settle", type=int, default=8000, help="settling steps before the settled batched "
+                    "measurement (0: skip it)")
+    ap.add_argument("--no-coupled", action="store_true")
+    ap.add_argument("--coupled-intervals", type=int, default=100, help="timed coupling intervals of 15 steps")
+    ap.add_argument("--coupled-settle", type=int, default=4000, help="settling steps per level (dt 5e-6)")
+    ap.add_argument("--save-state", default=None, help="save the settled bed (.npz) for later --load-state runs")
+    ap.add_argument("--load-state", default=None, help="start from a saved settled bed instead of settling")
     return ap.parse_args()
 
 
@@ -125,6 +132,22 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(x, device):
+    """The largest of a per-rank float over all ranks (the time of the slowest replica)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks (weak scaling: each rank its own replica) per second of the slowest."""
+    return units_per_rank * world / seconds
+
+
 def _profile_traffic(kernel_src_hash):
     """DRAM bytes per launch of the step kernel from the committed ncu summary, if it is current."""
     path = os.path.join(ROOT, "profiles", "k_step_shear_bed.md")
@@ -140,8 +163,11 @@ def _profile_traffic(kernel_src_hash):
 
 
 def _kernel_hash():
-    p = os.path.join(ROOT, "paper_1705_03850_gb300", "csrc", "dem.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Hash of the sources the step kernel is compiled from (a stale profile gives no traffic)."""
+    h = hashlib.sha256()
+    for f in ("dem.cu", "dem_internal.cuh", "dem_contact.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1705_03850_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -217,22 +243,31 @@ def run_ours(args):
     # than the sheared run, so that the lattice collapses into a dense bed quickly
     wl = workloads.shear_bed(args.n, seed=2)
     desc = dem.desc_from_workload(wl, r_max=1.2e-3)
-    sdesc = dem.desc_from_workload(wl, r_max=1.2e-3)
-    sdesc.dt, sdesc.e = 5e-6, 0.5
-    settle = dem.DEM([sdesc], max_neighbors=args.lmax, device=dev)
-    settle.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
-    settle.step(1)
-    if args.settle_graph > 0:
-        settle.set_graph(args.settle_graph)
-    settle.step(max(0, args.settle - 1))
-    settle.sync()
-    x = settle.read(dem.POS, host=False)
-    v = settle.read(dem.VEL, host=False)
-    w = settle.read(dem.OMEGA, host=False)
-    r = settle.read(dem.RADIUS, host=False)
-    m = settle.read(dem.MASS, host=False)
-    settle.close()
-    del settle
+    if args.load_state:
+        z = np.load(args.load_state)
+        x, v, w, r, m = (torch.from_numpy(z[k]).to(dev) for k in ("x", "v", "w", "r", "m"))
+        if x.shape[0] != wl.n:
+            raise SystemExit(f"{args.load_state} holds {x.shape[0]} particles, not {wl.n}")
+    else:
+        sdesc = dem.desc_from_workload(wl, r_max=1.2e-3)
+        sdesc.dt, sdesc.e = 5e-6, 0.5
+        settle = dem.DEM([sdesc], max_neighbors=args.lmax, device=dev)
+        settle.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
+        settle.step(1)
+        if args.settle_graph > 0:
+            settle.set_graph(args.settle_graph)
+        settle.step(max(0, args.settle - 1))
+        settle.sync()
+        x = settle.read(dem.POS, host=False)
+        v = settle.read(dem.VEL, host=False)
+        w = settle.read(dem.OMEGA, host=False)
+        r = settle.read(dem.RADIUS, host=False)
+        m = settle.read(dem.MASS, host=False)
+        settle.close()
+        del settle
+    if args.save_state and rank == 0:
+        np.savez(args.save_state, x=x.cpu().numpy(), v=v.cpu().numpy(), w=w.cpu().numpy(), r=r.cpu().numpy(),
+                 m=m.cpu().numpy())
 
     # ---- sheared bed: floor moves at 0.5 m/s in x
     desc.floor_v[0] = 0.5
@@ -253,20 +288,19 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clocks:
+        torch.cuda.profiler.start()          # marks the timed region for `ncu --profile-from-start off`
         e0.record(stream)
         sim.step(K)
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
     ms = e0.elapsed_time(e1)
     kern_ms, kern_n = sim.graph_step_kernel_ms() if S > 0 else (float("nan"), 1)
     st1 = sim.stats()
     sim.sync()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     n = wl.n
-    value = n * K * world / (ms / 1e3)
+    value = whole_job_rate(n * K, world, ms / 1e3)
     L = st1["list_entries"] / max(1, st1["particles"])
     C = st1["contacts"] / max(1, st1["particles"])
     Wc = st1["wall_contacts"] / max(1, st1["particles"])
@@ -306,16 +340,20 @@ def run_ours(args):
         sim.read(dem.VEL, out=ov)
         sim.read(dem.OMEGA, out=ow)
         torch.cuda.synchronize(dev)
-        t_e2e = time.perf_counter() - t0
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dev)
         h2d = (hx.numel() + hv.numel() + hw.numel() + hr.numel() + hm.numel()) * 8
         d2h = (ox.numel() + ov.numel() + ow.numel()) * 8
-        e2e = {"value": n * K / t_e2e * world, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+        e2e = {"value": whole_job_rate(n * K, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                "d2h_bytes_per_step": d2h / K, "chunk_steps": K,
                "what": "dem_write(POS,VEL,OMEGA,RADIUS,MASS) from pinned host, dem_step(K), "
                        "dem_read(POS,VEL,OMEGA) to pinned host; bytes per DEM step = chunk bytes / K"}
 
-    batched = None if args.no_batched else run_batched(args, dev, value)
-    adj = None if args.no_adjoint else run_adjoint(args, dev, value)
+    # the batched, adjoint and coupled lines are single-GPU measurements (rank 0 alone reports;
+    # under several ranks only the plain replicas are timed)
+    single = world == 1
+    batched = run_batched(args, dev, value) if single and not args.no_batched else None
+    adj = run_adjoint(args, dev, value) if single and not args.no_adjoint else None
+    coupled = run_coupled(args, dev, value) if single and not args.no_coupled else None
 
     if rank != 0:
         return
@@ -327,8 +365,10 @@ def run_ours(args):
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"shear_bed: {n:,} polydisperse spheres, settled then floor-sheared",
-                   "n_particles": n, "dt": wl.dt, "skin_m": wl.skin, "settle_steps": args.settle,
-                   "settle": "dt 5e-6 s, e 0.5, from the FCC start",
+                   "n_particles": n, "dt": wl.dt, "skin_m": wl.skin,
+                   "settle_steps": 0 if args.load_state else args.settle,
+                   "settle": (f"loaded from {os.path.basename(args.load_state)}" if args.load_state
+                              else "dt 5e-6 s, e 0.5, from the FCC start"),
                    "steps_per_graph": S, "max_neighbors": args.lmax,
                    "l2": "inputs larger than L2 (state + lists + histories > 129 MB)",
                    "mean_list_length": L, "mean_contacts_per_particle": C, "rebuilds_in_timed_region": rebuilds,
@@ -343,6 +383,7 @@ def run_ours(args):
         "e2e": e2e,
         "batched": batched,
         "adjoint": adj,
+        "coupled": coupled,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
     }
@@ -380,13 +421,60 @@ def run_batched(args, dev, plain_value):
     sim.sync()
     sim.close()
     value = n * K / (ms / 1e3)
+    settled = None if args.batched_settle <= 0 else _batched_settled(args, dev, wls)
     return {"value": value, "unit": UNIT, "workload": "256 settling boxes, N_k log-uniform in [2e3, 2e5] "
             "(seed 4), d = 2 mm, per-box E, e, mu", "n_instances": len(wls), "n_particles": n, "steps": K,
             "ms_per_step": ms / K, "vs_plain": value / plain_value, "rebuilds": st1["rebuilds"] - st0["rebuilds"],
             "mean_list_length": st1["list_entries"] / max(1, st1["particles"]),
-            "timed": "all K steps from the lattice start, including the first list build",
+            "mean_contacts_per_particle": st1["contacts"] / max(1, st1["particles"]),
+            "timed": "all K steps from the lattice start, including the first list build (in 2 ms the lattice "
+                     "barely moves: few contacts)",
             "tuned": best.as_dict(), "tuning_seconds": t_tune, "candidates": len(allc),
-            "tuning": "each candidate timed on 32 of the boxes (spread over sizes) for the full step count"}
+            "tuning": "each candidate timed on 32 of the boxes (spread over sizes) for the full step count",
+            "settled": settled}
+
+
+def _batched_settled(args, dev, wls):
+    """The same 256 boxes after settling (dt 5e-6 s, e 0.5, not timed), retuned, then timed for the
+    same number of steps at the stated dt: every particle in contact with its neighbours."""
+    import torch
+
+    from paper_1705_03850_gb300 import autotune, dem
+    base = autotune.Choice(0.1, 1.0, 50, 32)
+    descs = autotune.descs_for(wls, base)
+    for dsc in descs:
+        dsc.dt, dsc.e = 5e-6, 0.5
+    st = dem.DEM(descs, max_neighbors=32, device=dev)
+    st.write_state(*[torch.as_tensor(a, dtype=torch.float64, device=dev) for a in autotune.concat_state(wls)])
+    st.step(1)
+    st.set_graph(50)
+    st.step(args.batched_settle - 1)
+    st.sync()
+    state = [st.read(f, host=False) for f in (dem.POS, dem.VEL, dem.OMEGA, dem.RADIUS, dem.MASS)]
+    st.close()
+    best, allc = autotune.tune(wls, window=args.batched_steps, sample=32, device=dev, state=state)
+    sim = autotune.make_context(wls, best, device=dev, state=state)
+    n = sum(w.n for w in wls)
+    S = best.graph_steps
+    K = max(S, (args.batched_steps // S) * S)
+    sim.step(1)
+    sim.set_graph(S)
+    sim.step(S)
+    torch.cuda.synchronize(dev)
+    st0 = sim.stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(sim.stream)
+    sim.step(K)
+    e1.record(sim.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    st1 = sim.stats()
+    sim.close()
+    return {"value": n * K / (ms / 1e3), "unit": UNIT, "steps": K, "ms_per_step": ms / K,
+            "settle_steps": args.batched_settle, "rebuilds": st1["rebuilds"] - st0["rebuilds"],
+            "mean_list_length": st1["list_entries"] / max(1, st1["particles"]),
+            "mean_contacts_per_particle": st1["contacts"] / max(1, st1["particles"]), "tuned": best.as_dict()}
 
 
 def run_adjoint(args, dev, plain_value):
@@ -435,6 +523,75 @@ def run_adjoint(args, dev, plain_value):
             "gradient_example": {"dKE_dE": grad[0, 0], "dKE_de": grad[0, 1], "dKE_dmu": grad[0, 2]},
             "observables_example": {"KE": obs[0, 0], "runout": obs[0, 1]},
             "timing": "wall clock around the C-ABI calls (they synchronise)"}
+
+
+def run_coupled(args, dev, plain_value):
+    """Three nested coarse-graining levels of a 30-degree chute (8, 4 and 2 mm spheres; about
+    2.0M + 1.0M + 2.0M), coupled pairwise every 15 steps (stress and velocity controllers,
+    insertion, removal).  Each level first settles on its own under vertical gravity (not timed)."""
+    import torch
+
+    from paper_1705_03850_gb300 import dem, levels, workloads
+    lv, specs = workloads.chute(u0=0.5)
+    states = []
+    for wl in lv:
+        sd = dem.desc_from_workload(wl)
+        sd.dt, sd.e = 5e-6, 0.5
+        sd.g[0], sd.g[1], sd.g[2] = 0.0, 0.0, -9.81
+        st = dem.DEM([sd], max_neighbors=24, device=dev)
+        st.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
+        st.step(1)
+        st.set_graph(50)
+        st.step(max(0, args.coupled_settle - 1))
+        st.sync()
+        states.append([st.read(f, host=False) for f in (dem.POS, dem.VEL, dem.OMEGA, dem.RADIUS, dem.MASS)])
+        st.close()
+    ctx = []
+    for k, (wl, (x, v, w, r, m)) in enumerate(zip(lv, states)):
+        cap = None if k == 0 else wl.n + 60_000
+        d = dem.DEM([dem.desc_from_workload(wl, capacity=cap)], max_neighbors=24, device=dev)
+        v = v.clone()
+        v[:, 0] += wl.meta["u0"]
+        d.write_state(x, v, w, r, m)
+        ctx.append(d)
+    h = levels.Hierarchy(ctx, specs)
+    h.advance(3)
+    torch.cuda.synchronize(dev)
+    n0 = h.counts()
+    st0 = [c.stats() for c in ctx]
+    I = args.coupled_intervals
+    t_couple = 0.0
+    t0 = time.perf_counter()
+    for _ in range(I):
+        for c in ctx:
+            c.step(h.interval)
+        torch.cuda.synchronize(dev)
+        tc = time.perf_counter()
+        for c in ctx:
+            c.clear_external_force()
+        for cp in h.couplers:
+            cp.couple()
+        t_couple += time.perf_counter() - tc
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter() - t0
+    n1 = h.counts()
+    st1 = [c.stats() for c in ctx]
+    inserted = [int(c.counts()[1][0]) - wl.n for c, wl in zip(ctx[1:], lv[1:])]
+    h.close()
+    for c in ctx:
+        c.close()
+    steps = I * h.interval
+    value = sum(0.5 * (a + b) for a, b in zip(n0, n1)) * steps / t
+    return {"value": value, "unit": UNIT, "metric": "particle-steps/s summed over the coupled levels",
+            "workload": "30-degree chute, 11 m periodic along the flow, 0.3 x 0.3 m section: level 0 d = 8 mm "
+                        "everywhere, level 1 d = 4 mm in a 0.70 m region, level 2 d = 2 mm in a 0.18 m region "
+                        "nested in it; plug flow 0.5 m/s at the start",
+            "particles_per_level_start": n0, "particles_per_level_end": n1,
+            "inserted_per_fine_level": inserted, "steps": steps, "coupling_interval": h.interval,
+            "seconds": t, "coupling_share": t_couple / t, "ms_per_step": t / steps * 1e3,
+            "rebuilds_per_level": [b["rebuilds"] - a["rebuilds"] for a, b in zip(st0, st1)],
+            "vs_plain": value / plain_value, "settle_steps": args.coupled_settle,
+            "timing": "wall clock (coupling calls synchronise); level steps in CUDA graphs of one interval"}
 
 
 def main():

@@ -76,7 +76,9 @@ typedef enum {
     DEM_F_TORQUE = 6,   /* (n,3) float64 total torque at the current step [N m]; read only */
     DEM_F_WALL_XI = 7,  /* (n,3) float64 tangential overlap of the floor contact [m] (0 if none); read only */
     DEM_F_NBR_COUNT = 8,/* (n)   float64 neighbour-list length of each particle; read only */
-    DEM_F_FEXT = 9      /* (n,3) float64 external (coupling-controller) force held on each particle [N]; read only */
+    DEM_F_FEXT = 9      /* (n,3) float64 external force held on each particle [N], added to the contact and
+                           gravity forces every step until overwritten (written by the coupling controllers,
+                           or by the caller; stored as float32) */
 } dem_field;
 
 /* One independent DEM system ("instance").  A context advances all of its
@@ -312,7 +314,8 @@ typedef struct {
     uint64_t seed;          /* random seed of the insertion */
     double mass_unit;       /* unit of the integer mass bookkeeping [kg] */
     int32_t max_insert;     /* most particles inserted per surface cell and call */
-    int32_t reserved;
+    int32_t add_forces;     /* 0: the controller forces replace the levels' held forces; 1: they are added
+                               (for a level shared by two couplers; clear with dem_clear_external_force) */
 } dem_coupling;
 
 typedef enum {
@@ -341,7 +344,12 @@ dem_status dem_coupler_read(dem_coupler *cp, int32_t field, double *dst, int64_t
  * this coupler is running. */
 dem_status dem_coupler_destroy(dem_coupler *cp);
 
-/* Live particles and IDs handed out, per instance (host arrays of B; synchronises). */
+/* Zero the held external (coupling) force of every particle of the context. */
+dem_status dem_clear_external_force(dem_ctx *ctx);
+
+/* Live particles and IDs handed out, per instance (host arrays of B; synchronises).  Particles
+ * that a coupling call marked for removal count as live until the next step drops them; reads
+ * return NaN for them already. */
 dem_status dem_counts(dem_ctx *ctx, int64_t *live, int64_t *ids);
 
 /* Last error message of the context; with ctx == NULL, the last configuration

@@ -60,21 +60,34 @@ def make_context(workloads, choice: Choice, device=None, state=None):
     return sim
 
 
+def subset_indices(workloads, count):
+    """Indices of `count` instances evenly spread over the sizes (all of them if fewer)."""
+    if len(workloads) <= count:
+        return list(range(len(workloads)))
+    order = sorted(range(len(workloads)), key=lambda k: workloads[k].n)
+    return sorted({order[int(round(i * (len(order) - 1) / (count - 1)))] for i in range(count)})
+
+
 def subset(workloads, count):
     """`count` instances evenly spread over the sizes (all of them if fewer)."""
-    if len(workloads) <= count:
-        return list(workloads)
-    order = sorted(range(len(workloads)), key=lambda k: workloads[k].n)
-    pick = sorted({order[int(round(i * (len(order) - 1) / (count - 1)))] for i in range(count)})
-    return [workloads[k] for k in pick]
+    return [workloads[k] for k in subset_indices(workloads, count)]
 
 
 def tune(workloads, skin_factors=(0.025, 0.05, 0.1), cell_factors=(1.0, 1.25), graph_steps=(50, 100),
          max_neighbors=(32,), window=2000, sample=32, device=None, state=None, log=None):
-    """Time every candidate on `sample` instances for `window` steps; return (best, all)."""
+    """Time every candidate on `sample` instances for `window` steps; return (best, all).
+    `state`, if given, is the concatenated (x, v, w, r, m) of all the workloads (e.g. after settling);
+    the sampled instances start from their part of it, otherwise from their own inputs."""
     import torch
-    workloads = subset(workloads, sample)
-    state = [torch.as_tensor(a, dtype=torch.float64, device=device or "cuda") for a in concat_state(workloads)]
+    picked = subset_indices(workloads, sample)
+    if state is not None:
+        off = np.concatenate([[0], np.cumsum([w.n for w in workloads])])
+        rows = torch.as_tensor(np.concatenate([np.arange(off[k], off[k + 1]) for k in picked]),
+                               device=state[0].device)
+        state = [torch.as_tensor(a).index_select(0, rows) for a in state]
+    workloads = [workloads[k] for k in picked]
+    if state is None:
+        state = [torch.as_tensor(a, dtype=torch.float64, device=device or "cuda") for a in concat_state(workloads)]
     results = []
     for sf, cf, gs, lm in itertools.product(skin_factors, cell_factors, graph_steps, max_neighbors):
         ch = Choice(sf, cf, gs, lm)

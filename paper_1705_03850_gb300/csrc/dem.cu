@@ -214,15 +214,69 @@ __global__ void __launch_bounds__(TILE) k_rb_cellsort(Dev d)
     });
 }
 
+// Slots within each tile of TILE cell-order positions go to the particles in order
+// of decreasing contact count at the last step (then list length, then cell
+// order), so that the 32 rows a warp of the step kernel walks together have
+// similar lengths, and the four warps of a tile similar totals.  Results do not depend on the slot order: every particle sums
+// its own row in the row's order.
+__global__ void __launch_bounds__(TILE) k_rb_tilesort(Dev d)
+{
+    static_assert(TILE == 128, "the deal below assumes four warps per tile");
+    if (!d.g->any) return;
+    __shared__ unsigned key[TILE];
+    for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
+        const int k = d.tile_inst[t];
+        const InstD D = d.id[k];            // the same for the whole block
+        if (!D.flag) continue;
+        const InstC& c = d.ic[k];
+        const int p = t * TILE + threadIdx.x;
+        const int nvalid = min(TILE, D.n_new - (t * TILE - c.slot0));
+        const bool valid = (int)threadIdx.x < nvalid;
+        unsigned kk = 0u;
+        if (valid && D.flag != 2) {
+            const int old = d.perm[p];
+            kk = ((unsigned)__popc(d.hmask[D.lp][old]) << 8) | (unsigned)min(d.cnt[D.lp][old], 255);
+        }
+        __syncthreads();                    // the previous tile's keys are no longer read
+        key[threadIdx.x] = kk;
+        __syncthreads();
+        if (valid) {
+            int rank = 0;
+            for (int j = 0; j < nvalid; ++j) {
+                const unsigned kj = key[j];
+                rank += (kj > kk || (kj == kk && j < (int)threadIdx.x)) ? 1 : 0;
+            }
+            // full tiles deal the ranks round-robin over the 4 warps, so that every warp
+            // gets an equal share of the tile's work and its lanes similar rows
+            const int s = t * TILE + (nvalid == TILE ? (rank & 3) * 32 + (rank >> 2) : rank);
+            d.fin[p] = s;
+            d.perm2[s] = p;
+        }
+    }
+}
+
 // One thread per new slot: move the particle into the other state buffer,
 // collect neighbours within r_i + r_j + skin (exact integer test), order the
 // row by overlap depth, and carry the tangential overlaps of pairs that were
-// already listed (found by ID in the particle's previous row).
-__device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, const InstC& c)
+// already listed (found by ID in the particle's previous row).  The candidate
+// row is kept in shared memory, entry-major so that the threads of a warp hit
+// different banks.
+constexpr int RB_T = 64;                     // threads per block of the list build
+
+struct RowScratch {
+    float key[MAXL][RB_T];                   // d^2 - (r_i + r_j)^2 (rounded to float: monotone)
+    int id[MAXL][RB_T];                      // partner ID (ties, history match)
+    int pos[MAXL][RB_T];                     // partner's cell-order position
+    int oid[MAXL][RB_T];                     // IDs of the previous row
+};
+
+__device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, const InstC& c, RowScratch& R)
 {
+    const int tx = threadIdx.x;
     const int cur = D.cur, nxt = cur ^ 1, lp = D.lp, nlp = lp ^ 1;
     const int ncap = d.ncap;
-    const int old = d.perm[s];
+    const int ps = d.perm2[s];              // cell-order position of this particle
+    const int old = d.perm[ps];
     const int4 p = d.pos[cur][old];
     float4 v = d.vel[cur][old];
     const float4 w = d.omg[cur][old];
@@ -235,9 +289,6 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
 
     // candidates ordered by (d^2 - (r_i + r_j)^2, ID): deepest overlaps first, so
     // that within a warp the contacts sit in the leading entries of every row
-    long long cand_key[MAXL];
-    int cand_id[MAXL];
-    int cand_slot[MAXL];
     int nc = 0;
     bool overflow = false;
     const int ccx = axis_cell(c, 0, p.x), ccy = axis_cell(c, 1, p.y), ccz = axis_cell(c, 2, p.z);
@@ -263,7 +314,7 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
                 const int cnt = (int)d.ccount[code];
                 for (int t = 0; t < cnt; ++t) {
                     const int m = start + t;
-                    if (m == s) continue;
+                    if (m == ps) continue;
                     const int o = d.perm[m];
                     const int4 q = d.pos[cur][o];
                     const long long ddx = min_image(p.x - q.x, c.per[0], c.ext[0], c.half[0]);
@@ -273,19 +324,19 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
                     const long long cut = (long long)p.w + q.w + c.skin;
                     if (d2 >= cut * cut) continue;
                     const long long S = (long long)p.w + q.w;
-                    const long long key = d2 - S * S;
+                    const float key = (float)(d2 - S * S);
                     const int qid = (int)(__float_as_uint(d.vel[cur][o].w) & ID_MASK);
                     if (nc == Lmax) { overflow = true; continue; }
                     int j = nc - 1;
-                    while (j >= 0 && (cand_key[j] > key || (cand_key[j] == key && cand_id[j] > qid))) {
-                        cand_key[j + 1] = cand_key[j];
-                        cand_id[j + 1] = cand_id[j];
-                        cand_slot[j + 1] = cand_slot[j];
+                    while (j >= 0 && (R.key[j][tx] > key || (R.key[j][tx] == key && R.id[j][tx] > qid))) {
+                        R.key[j + 1][tx] = R.key[j][tx];
+                        R.id[j + 1][tx] = R.id[j][tx];
+                        R.pos[j + 1][tx] = R.pos[j][tx];
                         --j;
                     }
-                    cand_key[j + 1] = key;
-                    cand_id[j + 1] = qid;
-                    cand_slot[j + 1] = m;
+                    R.key[j + 1][tx] = key;
+                    R.id[j + 1][tx] = qid;
+                    R.pos[j + 1][tx] = m;
                     ++nc;
                 }
             }
@@ -301,16 +352,16 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
     const int* orow = d.nbr[lp] + old;
     const float* ho = d.hist[lp] + old;
     const int ocnt = D.flag == 2 ? 0 : d.cnt[lp][old];
-    int oid[MAXL];
-    for (int e = 0; e < ocnt; ++e) oid[e] = (int)(__float_as_uint(d.vel[cur][orow[(size_t)e * ncap]].w) & ID_MASK);
+    for (int e = 0; e < ocnt; ++e)
+        R.oid[e][tx] = (int)(__float_as_uint(d.vel[cur][orow[(size_t)e * ncap]].w) & ID_MASK);
     const unsigned ohm = D.flag == 2 ? 0u : d.hmask[lp][old];
     unsigned nhm = 0u;
     for (int e = 0; e < nc; ++e) {
-        nrow[(size_t)e * ncap] = cand_slot[e];
-        const int id = cand_id[e];
+        nrow[(size_t)e * ncap] = d.fin[R.pos[e][tx]];
+        const int id = R.id[e][tx];
         float hx = 0.f, hy = 0.f, hz = 0.f;
         for (int eo = 0; eo < ocnt; ++eo) {
-            if (oid[eo] == id) {
+            if (R.oid[eo][tx] == id) {
                 if ((ohm >> eo) & 1u) {
                     hx = ho[(size_t)eo * ncap];
                     hy = ho[plane + (size_t)eo * ncap];
@@ -326,21 +377,24 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
     }
     d.cnt[nlp][s] = nc;
     d.hmask[nlp][s] = nhm;
-    if (D.fext) d.fext[nlp][s] = D.flag == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : d.fext[lp][old];
+    if (D.fext) d.fext[nlp][s] = d.fext[lp][old];      // held until overwritten, even across state writes
     d.whist[nlp][s] = D.flag == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : d.whist[lp][old];
 }
 
-__global__ void __launch_bounds__(TILE) k_rb_build(Dev d)
+__global__ void __launch_bounds__(RB_T) k_rb_build(Dev d)
 {
     if (!d.g->any) return;
-    for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {   // over the new slots
+    __shared__ RowScratch R;
+    constexpr int H = TILE / RB_T;           // blocks of RB_T threads per tile
+    for (int u = blockIdx.x; u < d.ntiles * H; u += gridDim.x) {   // over the new slots
+        const int t = u / H;
         const int k = d.tile_inst[t];
         const InstD D = d.id[k];
         if (!D.flag) continue;
         const InstC& c = d.ic[k];
-        const int s = t * TILE + threadIdx.x;
+        const int s = t * TILE + (u % H) * RB_T + threadIdx.x;
         if (s - c.slot0 >= D.n_new) continue;
-        build_row(d, s, D, c);
+        build_row(d, s, D, c, R);
     }
 }
 
@@ -747,6 +801,9 @@ __global__ void k_write_field(Dev d, int field, const double* __restrict__ src, 
         float4 w = d.omg[cur][s];
         w.w = (float)src[g];
         d.omg[cur][s] = w;
+    } else if (field == DEM_F_FEXT) {
+        d.fext[d.id[k].lp][s] = make_float4((float)src[3 * g], (float)src[3 * g + 1], (float)src[3 * g + 2], 0.f);
+        d.id[k].fext = 1;                    // every thread of the instance stores the same value
     }
 }
 
@@ -759,7 +816,7 @@ __global__ void k_read_field(Dev d, int field, double* __restrict__ dst, long lo
     const InstC& c = d.ic[k];
     const int id = (int)(g - d.goff[k]);
     const int s = d.slot_of_id[c.slot0 + id];
-    if (s < 0) {                             // removed particle
+    if (s < 0 || (__float_as_uint(d.vel[d.id[k].cur][s].w) & GONE_BIT)) {   // removed (or marked for removal)
         const int w = (field == DEM_F_RADIUS || field == DEM_F_MASS || field == DEM_F_NBR_COUNT) ? 1 : 3;
         for (int a = 0; a < w; ++a) dst[w * g + a] = __longlong_as_double(0x7ff8000000000000ll);
         return;
@@ -1224,7 +1281,7 @@ struct Plan {
     unsigned ncodes = 0, nparts = 0;
     // offsets
     size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_fext[2], o_whist[2];
-    size_t o_cellcode, o_cslot, o_perm, o_ccount, o_cstart, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
+    size_t o_cellcode, o_cslot, o_perm, o_fin, o_perm2, o_ccount, o_cstart, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
         o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl, o_small;
     size_t bytes = 0;
 };
@@ -1366,6 +1423,8 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
     p.o_cellcode = L.take(N * 4);
     p.o_cslot = L.take(N * 4);
     p.o_perm = L.take(N * 4);
+    p.o_fin = L.take(N * 4);
+    p.o_perm2 = L.take(N * 4);
     p.o_ccount = L.take((size_t)p.ncodes * 4);
     p.o_cstart = L.take((size_t)p.ncodes * 4);
     p.o_part = L.take((size_t)std::max(1u, p.nparts) * 4);
@@ -1438,7 +1497,8 @@ dem_status launch_rebuild(dem_ctx* ctx, cudaStream_t st)
     k_rb_scatter<<<gt, TILE, 0, st>>>(d);
     k_rb_cellsort<<<gt, TILE, 0, st>>>(d);
     k_rb_count<<<1, 256, 0, st>>>(d);
-    k_rb_build<<<gt, TILE, 0, st>>>(d);
+    k_rb_tilesort<<<gt, TILE, 0, st>>>(d);
+    k_rb_build<<<gt * (TILE / RB_T), RB_T, 0, st>>>(d);
     k_rb_finish<<<1, 256, 0, st>>>(d);
     CU(cudaGetLastError());
     return DEM_OK;
@@ -1610,6 +1670,8 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     d.cellcode = (unsigned*)(base + p.o_cellcode);
     d.cslot = (unsigned*)(base + p.o_cslot);
     d.perm = (int*)(base + p.o_perm);
+    d.fin = (int*)(base + p.o_fin);
+    d.perm2 = (int*)(base + p.o_perm2);
     d.ccount = (unsigned*)(base + p.o_ccount);
     d.cstart = (unsigned*)(base + p.o_cstart);
     d.part = (unsigned*)(base + p.o_part);
@@ -1720,8 +1782,7 @@ dem_status dem_write(dem_ctx* ctx, int32_t field, const void* src, int64_t n)
     if (!ctx) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     const int w = field_width(field);
-    if (w == 0 || field == DEM_F_FORCE || field == DEM_F_TORQUE || field == DEM_F_WALL_XI || field == DEM_F_NBR_COUNT ||
-        field == DEM_F_FEXT)
+    if (w == 0 || field == DEM_F_FORCE || field == DEM_F_TORQUE || field == DEM_F_WALL_XI || field == DEM_F_NBR_COUNT)
         return fail(ctx, DEM_ERR_ARG, "field is not writable");
     if (n != total_count(ctx)) return fail(ctx, DEM_ERR_ARG, "n must equal the total particle count");
     if (n == 0) return DEM_OK;
@@ -1733,11 +1794,13 @@ dem_status dem_write(dem_ctx* ctx, int32_t field, const void* src, int64_t n)
     }
     k_write_field<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->dev, field, dsrc, n, ctx->d_hl);
     CU(cudaGetLastError());
-    k_mark_fresh<<<1, 256, 0, ctx->stream>>>(ctx->dev);
-    CU(cudaGetLastError());
+    if (field != DEM_F_FEXT) {               // the held force changes neither the lists nor the state's integrity
+        k_mark_fresh<<<1, 256, 0, ctx->stream>>>(ctx->dev);
+        CU(cudaGetLastError());
+        ctx->fresh = true;
+        ctx->have_state = true;
+    }
     if (dsrc == ctx->dev.stage) CU(cudaStreamSynchronize(ctx->stream));
-    ctx->fresh = true;
-    ctx->have_state = true;
     return DEM_OK;
 }
 

@@ -44,6 +44,7 @@ struct Geo {
     double loc[3], qc, lof[3], qf;
     int rmaxf_u;         // largest fine radius in fine units (histogram range)
     int fresh_c, fresh_f;
+    int add;             // add the controller forces to the held ones instead of replacing them
 };
 
 struct Acc {
@@ -403,6 +404,10 @@ __global__ void __launch_bounds__(TILE) k_cp_force_fine(Dev d, Geo g, Acc a)
             }
             F = make_float4((float)(lam * Fv[0]), (float)(lam * Fv[1]), (float)(lam * Fv[2]), 0.f);
         }
+        if (g.add) {
+            const float4 o = d.fext[D.lp][s];
+            F = make_float4(o.x + F.x, o.y + F.y, o.z + F.z, 0.f);
+        }
         d.fext[D.lp][s] = F;
     });
 }
@@ -418,6 +423,10 @@ __global__ void __launch_bounds__(TILE) k_cp_force_coarse(Dev d, Geo g, Acc a)
             const double m = d.omg[D.cur][s].w, k = g.kv * m / g.Tc;
             const double* dv = a.dv + 3 * (size_t)cc;
             F = make_float4((float)(k * dv[0]), (float)(k * dv[1]), (float)(k * dv[2]), 0.f);
+        }
+        if (g.add) {
+            const float4 o = d.fext[D.lp][s];
+            F = make_float4(o.x + F.x, o.y + F.y, o.z + F.z, 0.f);
         }
         d.fext[D.lp][s] = F;
     });
@@ -542,7 +551,7 @@ __global__ void k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
                     const int start = c.slot0 + (int)(d.cstart[code] - cbase);
                     const int cnt = (int)d.ccount[code];
                     for (int t = 0; t < cnt; ++t) {
-                        const int j = start + t;
+                        const int j = d.fin[start + t];   // slot of this cell member
                         if (j - c.slot0 >= D.n) continue;
                         const int4 Q = d.pos[D.cur][j];
                         const long long ex = min_image((int)u[0] - Q.x, c.per[0], c.ext[0], c.half[0]);
@@ -747,6 +756,7 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
     g.max_insert = sp->max_insert;
     g.drain = sp->drain_faces;
     g.seed = sp->seed;
+    g.add = sp->add_forces ? 1 : 0;
     return DEM_OK;
 }
 
@@ -954,6 +964,14 @@ dem_status dem_coupler_destroy(dem_coupler* cp)
 {
     if (!cp) return DEM_ERR_ARG;
     delete cp;   // touches neither context (they may already be gone)
+    return DEM_OK;
+}
+
+dem_status dem_clear_external_force(dem_ctx* ctx)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    CU(cudaMemsetAsync(ctx->dev.fext[0], 0, sizeof(float4) * (size_t)ctx->ncap, ctx->stream));
+    CU(cudaMemsetAsync(ctx->dev.fext[1], 0, sizeof(float4) * (size_t)ctx->ncap, ctx->stream));
     return DEM_OK;
 }
 

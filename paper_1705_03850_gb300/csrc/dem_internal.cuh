@@ -103,7 +103,9 @@ struct Dev {
     float4* whist[2];
     unsigned* cellcode;
     unsigned* cslot;
-    int* perm;
+    int* perm;                 // cell-order position -> old slot
+    int* fin;                  // cell-order position -> new slot (tiles reordered by contact count)
+    int* perm2;                // new slot -> cell-order position
     unsigned* ccount;
     unsigned* cstart;
     unsigned* part;

@@ -60,7 +60,7 @@ class CouplingSpec(ctypes.Structure):
                 ("corr_cell", ctypes.c_double), ("interval", ctypes.c_int32), ("bins", ctypes.c_int32),
                 ("alpha", ctypes.c_double), ("kp", ctypes.c_double), ("ki", ctypes.c_double), ("kv", ctypes.c_double),
                 ("mode", ctypes.c_int32), ("max_attempts", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("mass_unit", ctypes.c_double), ("max_insert", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mass_unit", ctypes.c_double), ("max_insert", ctypes.c_int32), ("add_forces", ctypes.c_int32)]
 
 
 # coupler fields (dem_coupler_field)
@@ -104,6 +104,7 @@ def lib():
         "dem_coupler_read": [vp, i32, vp, i64],
         "dem_coupler_destroy": [vp],
         "dem_counts": [vp, vp, vp],
+        "dem_clear_external_force": [vp],
         "dem_neighbor_counts_noalloc": [vp, vp, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i32), ctypes.c_double, ctypes.c_double, vp, vp],
     }
@@ -123,7 +124,7 @@ def exported_symbols():
             "dem_set_graph", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
             "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material",
             "dem_coupler_workspace", "dem_coupler_create", "dem_couple", "dem_coupler_read", "dem_coupler_destroy",
-            "dem_counts", "dem_last_error"]
+            "dem_counts", "dem_clear_external_force", "dem_last_error"]
 
 
 def desc(*, n, lo, hi, periodic, dt, skin, r_max, E, nu, e, mu, rho, g=(0, 0, 0), floor=True,
@@ -327,6 +328,10 @@ class DEM:
         self.counts_ = [int(x) for x in ids]
         return live, ids
 
+    def clear_external_force(self):
+        self._check(self.L.dem_clear_external_force(self.h), "clear external force")
+        return self
+
     def info(self, k=0):
         inf = InstanceInfo()
         self._check(self.L.dem_instance_info_get(self.h, k, ctypes.byref(inf)), "info")
@@ -373,7 +378,7 @@ class Coupler:
         sp = CouplingSpec()
         for a in range(3):
             sp.lo[a], sp.hi[a] = float(spec["lo"][a]), float(spec["hi"][a])
-        for k in ("feed_faces", "drain_faces", "interval", "bins", "mode", "max_attempts", "max_insert"):
+        for k in ("feed_faces", "drain_faces", "interval", "bins", "mode", "max_attempts", "max_insert", "add_forces"):
             setattr(sp, k, int(spec.get(k, 0)))
         for k in ("surface_cell", "layer", "corr_cell", "alpha", "kp", "ki", "kv", "mass_unit"):
             setattr(sp, k, float(spec[k]))

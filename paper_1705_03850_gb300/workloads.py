@@ -272,3 +272,85 @@ def batch(count: int = 256, seed: int = 4, scale: float = 1.0, steps: int = 2000
                        e=float(rng.uniform(0.5, 0.95)), mu=float(rng.uniform(0.2, 0.8)), rho=2500.0)
         out.append(settling_box(int(nk), seed + k, mat, steps=steps))
     return out
+
+
+def _fcc_fill(lo, hi, periodic, d, gap, z_top, rng, jitter=0.01e-3):
+    """FCC sites (nearest-neighbour distance >= d + gap) filling [lo, hi] in x/y from the floor up to
+    z_top (centres).  Periodic axes take a lattice constant that tiles the period exactly (slightly
+    above (d + gap) sqrt 2); open axes keep d/2 + gap/2 clear of the faces."""
+    nn = d + gap
+    a0 = nn * math.sqrt(2.0)
+    a, n, start = [0.0, 0.0], [0, 0], [0.0, 0.0]
+    for ax in range(2):
+        L = hi[ax] - lo[ax]
+        if periodic[ax]:
+            n[ax] = max(1, int(math.floor(L / a0)))
+            a[ax] = L / n[ax]
+            start[ax] = lo[ax] + a[ax] / 4
+        else:
+            n[ax] = max(1, int(math.floor((L - nn) / a0)) + 1)
+            a[ax] = a0
+            start[ax] = lo[ax] + nn / 2
+    az = a0
+    nl = max(1, int(math.floor((z_top - nn / 2) / (az / 2))) + 1)
+    pts = []
+    for k in range(nl):
+        z = nn / 2 + gap + k * az / 2
+        ox = 0.0 if k % 2 == 0 else 0.5
+        for sx, sy in ((0.0, 0.0), (0.5, 0.5)):
+            gx, gy = np.meshgrid(np.arange(n[0]), np.arange(n[1]), indexing="ij")
+            px = start[0] + (gx.ravel() + (sx + ox) % 1.0) * a[0]
+            py = start[1] + (gy.ravel() + sy) * a[1]
+            keep = np.ones(px.shape, dtype=bool)
+            if not periodic[0]:
+                keep &= px <= hi[0] - nn / 2
+            if not periodic[1]:
+                keep &= py <= hi[1] - nn / 2
+            pts.append(np.column_stack([px[keep], py[keep], np.full(keep.sum(), z)]))
+    x = np.vstack(pts)
+    x = x[np.lexsort((x[:, 0], x[:, 1], x[:, 2]))]
+    return x + rng.uniform(-jitter, jitter, x.shape)
+
+
+def chute(length: float = 11.0, width: float = 0.3, height: float = 0.3, bed: float = 0.227,
+          regions=((2.0, 0.70), (2.30, 0.18)), diameters=(8.0e-3, 4.0e-3, 2.0e-3), seed: int = 3,
+          incline_deg: float = 30.0, u0: float = 0.5, dt: float = 1e-6, interval: int = 15,
+          clear: float = 1.0):
+    """Three nested coarse-graining levels of an inclined chute (Sec. 2.3 coupling, one dt for all levels).
+
+    Level 0 (d = 8 mm, alpha = 4 against the 2 mm base) fills the whole chute, periodic along the
+    flow (x) and across it (y), floor at z = 0, to the bed height.  Level 1 (4 mm) fills the region
+    regions[0] = (x start, length) over the full cross-section, level 2 (2 mm) the region
+    regions[1] nested inside it.  Each level starts on an FCC lattice (gap 0.05 mm) that is to be
+    settled under vertical gravity; the flow then runs with gravity tilted by incline_deg about y
+    and every particle given u0 along x.  The lattice of a finer level starts `clear` diameters of
+    the level above it downstream of its feed face, room for the first inserted particles.  At the default sizes the levels hold about 2.0M, 1.0M and
+    2.0M particles.  Returns (levels, specs): three Workloads (gravity already tilted, velocities
+    zero) and the two coupling specs (level 0 -> 1, level 1 -> 2): feed through the upstream face,
+    drain through the downstream one, cells of three coarse diameters."""
+    rng = np.random.default_rng(seed)
+    mat = Material(E=1e7, nu=0.25, e=0.9, mu=0.5, rho=2500.0)
+    th = math.radians(incline_deg)
+    g = (9.81 * math.sin(th), 0.0, -9.81 * math.cos(th))
+    boxes = [((0.0, 0.0, 0.0), (length, width, height), (True, True, False))]
+    for x0, L in regions:
+        boxes.append(((x0, 0.0, 0.0), (x0 + L, width, height), (False, True, False)))
+    levels = []
+    for k, (d, (lo, hi, per)) in enumerate(zip(diameters, boxes)):
+        flo = lo if k == 0 else (lo[0] + clear * diameters[k - 1], lo[1], lo[2])
+        x = _fcc_fill(flo, hi, per, d, 0.05e-3, bed - d / 2, rng)
+        n = x.shape[0]
+        z = np.zeros((n, 3))
+        levels.append(_finish(f"chute_level{k}", x, z, z, np.full(n, d / 2), mat, lo, hi, per, dt, g, True,
+                              (0, 0, 0), 0.1 * d, 5000, diameter=d, u0=u0))
+    specs = []
+    for k in range(2):
+        lo, hi, _ = boxes[k + 1]
+        dc = diameters[k]
+        Tc = interval * float(f32(dt))
+        specs.append(dict(lo=tuple(qgrid(lo).tolist()), hi=tuple(qgrid(hi).tolist()), feed_faces=1 << 0,
+                          drain_faces=1 << 1, surface_cell=3 * dc, layer=3 * dc, corr_cell=3 * dc,
+                          interval=interval, bins=16, alpha=diameters[k] / diameters[k + 1], kp=1.0,
+                          ki=1.0 / (10 * Tc), kv=0.5, mode=0, max_attempts=100, seed=seed * 1000 + k,
+                          mass_unit=1e-12, max_insert=256, dt=float(f32(dt))))
+    return levels, specs

@@ -17,8 +17,9 @@ def _state(wl):
     return dict(x=wl.x, v=wl.v, w=wl.w, r=wl.r, m=wl.m, id=np.arange(wl.n))
 
 
-def _setup():
+def _setup(pre_force=None, **extra):
     A, B, fine_wl, spec = workloads.coupling_case()
+    spec = dict(spec, **extra)
     rmax_c, rmax_f = float(A.r.max()), float(fine_wl.r.max())
     coarse = dem.DEM([dem.desc_from_workload(A, r_max=rmax_c)])
     coarse.write_state(A.x, A.v, A.w, A.r, A.m)
@@ -26,6 +27,9 @@ def _setup():
     fine.write_state(fine_wl.x, fine_wl.v, fine_wl.w, fine_wl.r, fine_wl.m)
     cp = dem.Coupler(coarse, fine, **spec)
     coarse.write_state(B.x, B.v, B.w, B.r, B.m)
+    if pre_force is not None:
+        coarse.write(dem.FEXT, pre_force(coarse.n, 0.1))
+        fine.write(dem.FEXT, pre_force(fine.n, 2e-5))
     cp.couple()
     qf = oracle.quantum(fine_wl.lo, fine_wl.hi)
     orc = oracle.Coupler(spec, oracle_params(B), oracle_params(fine_wl), fine_wl.lo, qf,
@@ -84,6 +88,44 @@ def test_coupling_measurements_and_controllers_match_oracle():
     ff = fine.read(dem.FEXT)[:fine_wl.n]
     assert np.abs(ff - out["fext_f"]).max() <= 1e-4 * np.abs(out["fext_f"]).max() + 1e-12
     assert np.abs(out["fext_f"]).max() > 0 and np.abs(out["fext_c"]).max() > 0
+
+
+def test_added_controller_forces_sum_with_the_held_ones():
+    # a level shared by two couplers takes the sum of their forces (add_forces = 1)
+    # (held forces of the size of each level's controller forces, float32 values)
+    held = lambda n, s: (np.random.default_rng(n).normal(size=(n, 3)) * s).astype(np.float32).astype(np.float64)
+    A, B, fine_wl, spec, coarse, fine, cp, out, qf = _setup(pre_force=held, add_forces=1)
+    fc = coarse.read(dem.FEXT)
+    ref_c = held(coarse.n, 0.1) + out["fext_c"]
+    assert np.abs(fc - ref_c).max() <= 1e-5 * np.abs(ref_c).max()
+    assert np.abs(fc - out["fext_c"]).max() > 1e-2          # the held part is there
+    ff = fine.read(dem.FEXT)[:fine_wl.n]
+    ref_f = held(fine_wl.n, 2e-5) + out["fext_f"]         # (fine.n now counts the inserted particles)
+    assert np.abs(ff - ref_f).max() <= 1e-4 * np.abs(ref_f).max()
+    assert np.abs(ff - out["fext_f"]).max() > 2e-6
+    # the inserted particles start with no held force; clearing zeroes every one
+    assert np.abs(fine.read(dem.FEXT)[fine_wl.n:]).max() == 0.0
+    coarse.clear_external_force()
+    assert np.abs(coarse.read(dem.FEXT)).max() == 0.0
+
+
+def test_held_external_force_acts_like_gravity():
+    # a held force m g in a gravity-free box moves the particles as gravity g does
+    import dataclasses
+    wl = workloads.dense_block(4, 4, 3, seed=5, vel=0.0, spin=0.0, floor_v=(0.0, 0.0, 0.0))
+    g = np.array([0.0, 0.0, -9.81])
+    a = dem.DEM([dem.desc_from_workload(wl)])
+    a.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
+    wl0 = dataclasses.replace(wl, g=(0.0, 0.0, 0.0))
+    b = dem.DEM([dem.desc_from_workload(wl0)])
+    b.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
+    b.write(dem.FEXT, wl.m[:, None] * g[None, :])
+    assert np.allclose(b.read(dem.FEXT), wl.m[:, None] * g[None, :], rtol=1e-7, atol=0)
+    a.step(200)
+    b.step(200)
+    va, vb = a.read(dem.VEL), b.read(dem.VEL)
+    assert np.abs(va - vb).max() <= 1e-4 * np.abs(va).max()
+    assert np.abs(a.read(dem.POS) - b.read(dem.POS)).max() <= 1e-9
 
 
 def test_coupled_levels_keep_stepping():

@@ -1,0 +1,78 @@
+"""Three nested coarse-graining levels of an inclined chute, coupled pairwise (Sec. 2.3), on the GPU.
+
+Checks what holds at any size: graph-captured and direct stepping agree bit for
+bit through coupling, insertion and removal; the integer mass bookkeeping of
+every surface cell closes over many calls (entered = inserted + carried); no
+particle of a fine level is left beyond a drain face after a call.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1705_03850_gb300 import dem, levels, workloads
+
+pytestmark = pytest.mark.gpu
+
+SMALL = dict(length=0.3, width=0.06, height=0.1, bed=0.04, regions=((0.1, 0.12), (0.14, 0.04)))
+
+
+def _hierarchy(graph, u0=0.5):
+    lv, specs = workloads.chute(**SMALL, u0=u0)
+    ctx = []
+    for k, wl in enumerate(lv):
+        cap = None if k == 0 else wl.n + 20000
+        d = dem.DEM([dem.desc_from_workload(wl, capacity=cap)], max_neighbors=24)
+        v = np.zeros_like(wl.v)
+        v[:, 0] = u0
+        d.write_state(wl.x, v, wl.w, wl.r, wl.m)
+        ctx.append(d)
+    return lv, specs, levels.Hierarchy(ctx, specs, steps_per_graph=graph)
+
+
+def test_graph_and_direct_stepping_agree_through_coupling():
+    _, _, a = _hierarchy(True)
+    _, _, b = _hierarchy(False)
+    a.advance(8)
+    b.advance(8)
+    assert a.counts() == b.counts()
+    for la, lb in zip(a.levels, b.levels):
+        xa, xb = la.read(dem.POS), lb.read(dem.POS)
+        assert np.array_equal(np.isnan(xa), np.isnan(xb))
+        assert np.array_equal(np.nan_to_num(xa), np.nan_to_num(xb))
+
+
+def test_mass_bookkeeping_closes_and_drained_particles_are_gone():
+    lv, specs, h = _hierarchy(True, u0=10.0)
+    entered = [0, 0]
+    inserted = [0, 0]
+    carry = [None, None]
+    for call in range(40):                               # 6 mm of plug flow: lattice planes cross the faces
+        nid0 = [lvl.counts()[1][0] for lvl in h.levels]
+        h.advance(1)
+        for k, cp in enumerate(h.couplers):
+            mu = specs[k]["mass_unit"]
+            cross = np.round(cp.read(dem.CPL_SURFACE_MASS) / mu).astype(np.int64)
+            nins = cp.read(dem.CPL_SURFACE_INSERTED).astype(np.int64)
+            carry[k] = np.round(cp.read(dem.CPL_SURFACE_CARRY) / mu).astype(np.int64)
+            fine = h.levels[k + 1]
+            nid1 = fine.counts()[1][0]
+            assert nid1 - nid0[k + 1] == nins.sum()
+            r = fine.read(dem.RADIUS)[nid0[k + 1]:nid1]
+            rho = lv[k + 1].material.rho
+            units = np.array([int(np.rint(rho * (4.0 / 3.0 * math.pi) * x * x * x / mu)) for x in r], dtype=np.int64)
+            per_cell = np.zeros_like(cross)
+            np.add.at(per_cell, np.repeat(np.arange(len(nins)), nins), units)
+            entered[k] = entered[k] + cross
+            inserted[k] = inserted[k] + per_cell
+            # nothing of the fine level is left beyond the drain face (x hi) of its region
+            x = fine.read(dem.POS)
+            live = ~np.isnan(x[:, 0])
+            assert np.all(x[live, 0] < specs[k]["hi"][0])
+    for k in range(2):
+        assert np.array_equal(entered[k], inserted[k] + carry[k])
+        assert entered[k].sum() > 0                      # coarse material did enter the region
+    assert sum(int(i.sum()) for i in inserted) > 0       # and fine particles were inserted
+    for lvl in h.levels:
+        x = lvl.read(dem.POS)
+        assert np.isfinite(x[~np.isnan(x[:, 0])]).all()

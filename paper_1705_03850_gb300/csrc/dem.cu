@@ -217,11 +217,12 @@ __global__ void __launch_bounds__(TILE) k_rb_cellsort(Dev d)
 // Slots within each tile of TILE cell-order positions go to the particles in order
 // of decreasing contact count at the last step (then list length, then cell
 // order), so that the 32 rows a warp of the step kernel walks together have
-// similar lengths, and the four warps of a tile similar totals.  Results do not depend on the slot order: every particle sums
+// similar lengths.  Results do not depend on the slot order: every particle sums
+// its own row in the row's order.  Also writes the cell-order copies of
+// positions and IDs that the list build scans.  Results do not depend on the slot order: every particle sums
 // its own row in the row's order.
 __global__ void __launch_bounds__(TILE) k_rb_tilesort(Dev d)
 {
-    static_assert(TILE == 128, "the deal below assumes four warps per tile");
     if (!d.g->any) return;
     __shared__ unsigned key[TILE];
     for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
@@ -233,9 +234,12 @@ __global__ void __launch_bounds__(TILE) k_rb_tilesort(Dev d)
         const int nvalid = min(TILE, D.n_new - (t * TILE - c.slot0));
         const bool valid = (int)threadIdx.x < nvalid;
         unsigned kk = 0u;
-        if (valid && D.flag != 2) {
+        if (valid) {
             const int old = d.perm[p];
-            kk = ((unsigned)__popc(d.hmask[D.lp][old]) << 8) | (unsigned)min(d.cnt[D.lp][old], 255);
+            d.spos[p] = d.pos[D.cur][old];                    // cell-order copies for the list build
+            d.sid[p] = (int)(__float_as_uint(d.vel[D.cur][old].w) & ID_MASK);
+            if (D.flag != 2)
+                kk = ((unsigned)__popc(d.hmask[D.lp][old]) << 8) | (unsigned)min(d.cnt[D.lp][old], 255);
         }
         __syncthreads();                    // the previous tile's keys are no longer read
         key[threadIdx.x] = kk;
@@ -246,9 +250,7 @@ __global__ void __launch_bounds__(TILE) k_rb_tilesort(Dev d)
                 const unsigned kj = key[j];
                 rank += (kj > kk || (kj == kk && j < (int)threadIdx.x)) ? 1 : 0;
             }
-            // full tiles deal the ranks round-robin over the 4 warps, so that every warp
-            // gets an equal share of the tile's work and its lanes similar rows
-            const int s = t * TILE + (nvalid == TILE ? (rank & 3) * 32 + (rank >> 2) : rank);
+            const int s = t * TILE + rank;
             d.fin[p] = s;
             d.perm2[s] = p;
         }
@@ -265,7 +267,6 @@ constexpr int RB_T = 64;                     // threads per block of the list bu
 
 struct RowScratch {
     float key[MAXL][RB_T];                   // d^2 - (r_i + r_j)^2 (rounded to float: monotone)
-    int id[MAXL][RB_T];                      // partner ID (ties, history match)
     int pos[MAXL][RB_T];                     // partner's cell-order position
     int oid[MAXL][RB_T];                     // IDs of the previous row
 };
@@ -315,8 +316,7 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
                 for (int t = 0; t < cnt; ++t) {
                     const int m = start + t;
                     if (m == ps) continue;
-                    const int o = d.perm[m];
-                    const int4 q = d.pos[cur][o];
+                    const int4 q = d.spos[m];
                     const long long ddx = min_image(p.x - q.x, c.per[0], c.ext[0], c.half[0]);
                     const long long ddy = min_image(p.y - q.y, c.per[1], c.ext[1], c.half[1]);
                     const long long ddz = (long long)p.z - q.z;
@@ -325,17 +325,15 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
                     if (d2 >= cut * cut) continue;
                     const long long S = (long long)p.w + q.w;
                     const float key = (float)(d2 - S * S);
-                    const int qid = (int)(__float_as_uint(d.vel[cur][o].w) & ID_MASK);
                     if (nc == Lmax) { overflow = true; continue; }
+                    // equal keys (rare) are ordered by ID, so the row does not depend on the scan order
                     int j = nc - 1;
-                    while (j >= 0 && (R.key[j][tx] > key || (R.key[j][tx] == key && R.id[j][tx] > qid))) {
+                    while (j >= 0 && (R.key[j][tx] > key || (R.key[j][tx] == key && d.sid[R.pos[j][tx]] > d.sid[m]))) {
                         R.key[j + 1][tx] = R.key[j][tx];
-                        R.id[j + 1][tx] = R.id[j][tx];
                         R.pos[j + 1][tx] = R.pos[j][tx];
                         --j;
                     }
                     R.key[j + 1][tx] = key;
-                    R.id[j + 1][tx] = qid;
                     R.pos[j + 1][tx] = m;
                     ++nc;
                 }
@@ -357,8 +355,9 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
     const unsigned ohm = D.flag == 2 ? 0u : d.hmask[lp][old];
     unsigned nhm = 0u;
     for (int e = 0; e < nc; ++e) {
-        nrow[(size_t)e * ncap] = d.fin[R.pos[e][tx]];
-        const int id = R.id[e][tx];
+        const int m = R.pos[e][tx];
+        nrow[(size_t)e * ncap] = d.fin[m];
+        const int id = d.sid[m];
         float hx = 0.f, hy = 0.f, hz = 0.f;
         for (int eo = 0; eo < ocnt; ++eo) {
             if (R.oid[eo][tx] == id) {
@@ -446,10 +445,11 @@ __device__ __forceinline__ Coef<float> coef_of(const InstC& c)
 //
 // Persistent grid: block b owns the contiguous tile range [b T / G, (b+1) T / G)
 // (neighbouring tiles share neighbours, which then hit in L1), one thread per
-// particle.  The row walk is software-pipelined: the index of entry e+2 and the
-// state of entry e+1 are loaded while entry e is computed; the stored overlap is
-// loaded only for entries whose history is non-zero (bit mask hmask), and stored
-// only where it changes.  Each particle evaluates its contacts from its own side; the
+// particle.  The row is walked twice: first the positions of all entries (loads
+// independent of each other) give the touch mask, then only the contacts are
+// evaluated, in row order, with the next contact's state in flight; the stored
+// overlap is loaded only for entries whose history is non-zero (bit mask hmask),
+// and stored only where it changes.  Each particle evaluates its contacts from its own side; the
 // contact law has a single call site, so both particles of a pair run the same
 // instructions on operands that differ only in the sign of the antisymmetric
 // ones.
@@ -491,7 +491,10 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
             kprev = k;
         }
         const InstC& c = sc;
-        const int s = t * TILE + threadIdx.x;
+        static_assert((TILE / 32 & (TILE / 32 - 1)) == 0, "warps per tile must be a power of two");
+        // warp w takes the 32-slot slice (w + t) mod 4 of tile t: rebuilds put the rows with
+        // the most contacts in the first slice, so the rotation evens out the warps' work
+        const int s = t * TILE + ((((int)threadIdx.x >> 5) + t) & (TILE / 32 - 1)) * 32 + ((int)threadIdx.x & 31);
         if (s - c.slot0 >= sd.n) continue;
         const int cur = sd.cur, lp = sd.lp;
         const int4* __restrict__ pos = d.pos[cur];
@@ -517,43 +520,68 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
         const int per0 = c.per[0], per1 = c.per[1], ext0 = c.ext[0], ext1 = c.ext[1], hf0 = c.half[0],
                   hf1 = c.half[1];
 
-        // ---- one pass over the row, software-pipelined one entry ahead; the
-        // stored overlap is read only where hmask says it is non-zero
+        // ---- pass 1: positions of every entry, touch mask (independent loads)
         const unsigned hm = d.hmask[lp][s];
-        unsigned cm = 0u;
-        int jn = s;
+        unsigned tm = 0u;
+#pragma unroll 4
+        for (int e = 0; e < ncnt; ++e) {
+            const int j = __ldg(nb + (size_t)e * ncap);
+            const int4 Q = __ldg(pos + j);
+            const int dx = min_image(P.x - Q.x, per0, ext0, hf0);
+            const int dy = min_image(P.y - Q.y, per1, ext1, hf1);
+            const int dz = P.z - Q.z;
+            const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+            const int S = P.w + Q.w;
+            if (d2 < (long long)S * S) tm |= 1u << e;
+        }
+        // entries that left contact (or, for the read-out, every non-contact) get no history
+        const unsigned rowmask = ncnt >= 32 ? 0xffffffffu : ((1u << ncnt) - 1u);
+        unsigned clr = (MODE == 1 ? rowmask : hm) & ~tm;
+        while (clr) {
+            const int e = __ffs(clr) - 1;
+            clr &= clr - 1u;
+            ho[(size_t)e * ncap] = 0.f;
+            ho[plane + (size_t)e * ncap] = 0.f;
+            ho[2 * plane + (size_t)e * ncap] = 0.f;
+        }
+        // ---- pass 2: the contacts, in row order, next contact's state in flight
+        unsigned cm = tm;
+        unsigned rem = tm;
+        int en = 0;
         int4 Qn = P;
         float4 Vn = Vv, Wn = Wv;
         float hxn = 0.f, hyn = 0.f, hzn = 0.f;
-        int j2 = s;
-        if (ncnt > 0) {
-            jn = __ldg(nb);
-            Qn = __ldg(pos + jn);
-            Vn = __ldg(vel + jn);
-            Wn = __ldg(omg + jn);
-            if (hm & 1u) {
-                hxn = h[0];
-                hyn = h[plane];
-                hzn = h[2 * plane];
+        if (rem) {
+            en = __ffs(rem) - 1;
+            const int j = __ldg(nb + (size_t)en * ncap);
+            Qn = __ldg(pos + j);
+            Vn = __ldg(vel + j);
+            Wn = __ldg(omg + j);
+            if ((hm >> en) & 1u) {
+                hxn = h[(size_t)en * ncap];
+                hyn = h[plane + (size_t)en * ncap];
+                hzn = h[2 * plane + (size_t)en * ncap];
             }
         }
-        if (ncnt > 1) j2 = __ldg(nb + ncap);
-        for (int e = 0; e < ncnt; ++e) {
+        while (rem) {
+            const int e = en;
+            rem &= rem - 1u;
             const int4 Q = Qn;
             const float4 Vb = Vn, Wb = Wn;
             V3 xi = v3(hxn, hyn, hzn);
-            if (e + 1 < ncnt) {
-                const size_t o1 = (size_t)(e + 1) * ncap;
-                Qn = __ldg(pos + j2);
-                Vn = __ldg(vel + j2);
-                Wn = __ldg(omg + j2);
+            if (rem) {
+                en = __ffs(rem) - 1;
+                const size_t o1 = (size_t)en * ncap;
+                const int j = __ldg(nb + o1);
+                Qn = __ldg(pos + j);
+                Vn = __ldg(vel + j);
+                Wn = __ldg(omg + j);
                 hxn = hyn = hzn = 0.f;
-                if ((hm >> (e + 1)) & 1u) {
+                if ((hm >> en) & 1u) {
                     hxn = h[o1];
                     hyn = h[plane + o1];
                     hzn = h[2 * plane + o1];
                 }
-                if (e + 2 < ncnt) j2 = __ldg(nb + (size_t)(e + 2) * ncap);
             }
             const int dx = min_image(P.x - Q.x, per0, ext0, hf0);
             const int dy = min_image(P.y - Q.y, per1, ext1, hf1);
@@ -561,12 +589,7 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
             const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
             const int S = P.w + Q.w;
             const long long S2 = (long long)S * S;
-            const bool touch = d2 < S2;
-            if (touch) {
-                // Own perspective (a = this particle, n from the neighbour to it).
-                // Every operation is either symmetric in (a, b) or odd under the
-                // exchange, and round-to-nearest is sign-symmetric, so the
-                // neighbour computes exactly the negated force and overlap.
+            {
                 const float d2f = (float)d2;
                 const float inv = rsqrtf(d2f);
                 const float dist = d2f * inv;
@@ -579,15 +602,10 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                                                         ft, slip);
                 F = F + fa;
                 Tq = Tq - r * cross(n, ft);
-                cm |= 1u << e;
-            } else {
-                xi = v3(0.f, 0.f, 0.f);   // out of contact: no history
             }
-            if (MODE == 1 || touch || ((hm >> e) & 1u)) {
-                ho[(size_t)e * ncap] = xi.x;
-                ho[plane + (size_t)e * ncap] = xi.y;
-                ho[2 * plane + (size_t)e * ncap] = xi.z;
-            }
+            ho[(size_t)e * ncap] = xi.x;
+            ho[plane + (size_t)e * ncap] = xi.y;
+            ho[2 * plane + (size_t)e * ncap] = xi.z;
         }
         if (MODE == 0) d.hmask[lp][s] = cm;
         if (sd.fext) {   // coupling controllers' force, held over the coupling interval
@@ -1281,7 +1299,7 @@ struct Plan {
     unsigned ncodes = 0, nparts = 0;
     // offsets
     size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_fext[2], o_whist[2];
-    size_t o_cellcode, o_cslot, o_perm, o_fin, o_perm2, o_ccount, o_cstart, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
+    size_t o_cellcode, o_cslot, o_perm, o_fin, o_perm2, o_spos, o_sid, o_ccount, o_cstart, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
         o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl, o_small;
     size_t bytes = 0;
 };
@@ -1425,6 +1443,8 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
     p.o_perm = L.take(N * 4);
     p.o_fin = L.take(N * 4);
     p.o_perm2 = L.take(N * 4);
+    p.o_spos = L.take(N * 16);
+    p.o_sid = L.take(N * 4);
     p.o_ccount = L.take((size_t)p.ncodes * 4);
     p.o_cstart = L.take((size_t)p.ncodes * 4);
     p.o_part = L.take((size_t)std::max(1u, p.nparts) * 4);
@@ -1672,6 +1692,8 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     d.perm = (int*)(base + p.o_perm);
     d.fin = (int*)(base + p.o_fin);
     d.perm2 = (int*)(base + p.o_perm2);
+    d.spos = (int4*)(base + p.o_spos);
+    d.sid = (int*)(base + p.o_sid);
     d.ccount = (unsigned*)(base + p.o_ccount);
     d.cstart = (unsigned*)(base + p.o_cstart);
     d.part = (unsigned*)(base + p.o_part);

@@ -106,6 +106,8 @@ struct Dev {
     int* perm;                 // cell-order position -> old slot
     int* fin;                  // cell-order position -> new slot (tiles reordered by contact count)
     int* perm2;                // new slot -> cell-order position
+    int4* spos;                // positions in cell order (list build)
+    int* sid;                  // particle IDs in cell order (list build)
     unsigned* ccount;
     unsigned* cstart;
     unsigned* part;

@@ -163,10 +163,15 @@ def _profile_traffic(kernel_src_hash):
 
 
 def _kernel_hash():
-    """Hash of the sources the step kernel is compiled from (a stale profile gives no traffic)."""
-    h = hashlib.sha256()
-    for f in ("dem.cu", "dem_internal.cuh", "dem_contact.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1705_03850_gb300", "csrc", f), "rb").read())
+    """Hash of the step kernel's source (its definition in dem.cu and the headers it is built
+    from); a profile taken from another version gives no traffic."""
+    csrc = os.path.join(ROOT, "paper_1705_03850_gb300", "csrc")
+    src = open(os.path.join(csrc, "dem.cu")).read()
+    i0 = src.index("template <int MODE>\n__global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(")
+    i1 = src.index("__global__ void k_set_cond", i0)
+    h = hashlib.sha256(src[i0:i1].encode())
+    for f in ("dem_internal.cuh", "dem_contact.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -318,7 +323,9 @@ def run_ours(args):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     traffic = _profile_traffic(_kernel_hash())
-    launches = K + (K // S if S > 0 else 9 * K) + 9 * rebuilds
+    # per graph of S steps: one condition-setting kernel and S step kernels, plus the
+    # 11-kernel rebuild chain when a rebuild runs; direct launches run the chain every step
+    launches = K + K // S + 11 * rebuilds if S > 0 else 12 * K
 
     # ---- end to end through the public API with host buffers
     e2e = None

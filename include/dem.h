@@ -179,9 +179,11 @@ dem_status dem_stats(dem_ctx *ctx, dem_stats_t *out);
  * kernel, so a captured run needs no host round trip. */
 dem_status dem_set_graph(dem_ctx *ctx, int32_t steps_per_graph);
 
-/* CUDA-event time of the step kernels of the most recent graph launch:
- * total_ms = sum over its steps_per_graph step kernels, count = that number.
- * Synchronises the stream.  DEM_ERR_STATE if no graph was built. */
+/* CUDA-event time of step kernels of the most recent graph launch: every fifth
+ * step kernel of the graph (the first, the sixth, ...) is bracketed by event
+ * nodes; total_ms = the sum over those, count = their number (total_ms / count is
+ * the mean duration of a step kernel).  Synchronises the stream.  DEM_ERR_STATE if
+ * no graph was built. */
 dem_status dem_graph_step_kernel_ms(dem_ctx *ctx, double *total_ms, int32_t *count);
 
 /* ---------------------------------------------------------------------------

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(Dev d)
 #pragma unroll
     for (int k = 0; k < SCAN_V; ++k) {
         unsigned i = base + k;
-        if (i < d.ncodes) d.cstart[i] = ex;
+        if (i < d.ncodes) d.crange[i] = make_uint2(ex, v[k]);
         ex += v[k];
     }
 }
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(TILE) k_rb_scatter(Dev d)
     for_rebuilding_slots(d, [&](int s, const InstD& D, const InstC& c) {
         if (d.cslot[s] == 0xffffffffu) return;   // removed
         const unsigned code = d.cellcode[s];
-        const int np = c.slot0 + (int)(d.cstart[code] - d.cstart[c.code0]) + (int)d.cslot[s];
+        const int np = c.slot0 + (int)(d.crange[code].x - d.crange[c.code0].x) + (int)d.cslot[s];
         d.perm[np] = s;
     });
 }
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(TILE) k_rb_cellsort(Dev d)
         const unsigned code = d.cellcode[s];
         const int cntc = (int)d.ccount[code];
         if (cntc < 2) return;
-        int* a = d.perm + c.slot0 + (int)(d.cstart[code] - d.cstart[c.code0]);
+        int* a = d.perm + c.slot0 + (int)(d.crange[code].x - d.crange[c.code0].x);
         const float4* v = d.vel[D.cur];
         for (int i = 1; i < cntc; ++i) {
             const int x = a[i];
@@ -252,12 +252,11 @@ __global__ void __launch_bounds__(TILE) k_rb_tilesort(Dev d)
             }
             const int s = t * TILE + rank;
             d.fin[p] = s;
-            d.perm2[s] = p;
         }
     }
 }
 
-// One thread per new slot: move the particle into the other state buffer,
+// One thread per particle: move it into its new slot of the other state buffer,
 // collect neighbours within r_i + r_j + skin (exact integer test), order the
 // row by overlap depth, and carry the tangential overlaps of pairs that were
 // already listed (found by ID in the particle's previous row).  The candidate
@@ -268,15 +267,14 @@ constexpr int RB_T = 64;                     // threads per block of the list bu
 struct RowScratch {
     float key[MAXL][RB_T];                   // d^2 - (r_i + r_j)^2 (rounded to float: monotone)
     int pos[MAXL][RB_T];                     // partner's cell-order position
-    int oid[MAXL][RB_T];                     // IDs of the previous row
 };
 
-__device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, const InstC& c, RowScratch& R)
+__device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, const InstC& c, RowScratch& R)
 {
     const int tx = threadIdx.x;
     const int cur = D.cur, nxt = cur ^ 1, lp = D.lp, nlp = lp ^ 1;
     const int ncap = d.ncap;
-    const int ps = d.perm2[s];              // cell-order position of this particle
+    const int s = d.fin[ps];                // this particle's new slot
     const int old = d.perm[ps];
     const int4 p = d.pos[cur][old];
     float4 v = d.vel[cur][old];
@@ -293,52 +291,86 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
     int nc = 0;
     bool overflow = false;
     const int ccx = axis_cell(c, 0, p.x), ccy = axis_cell(c, 1, p.y), ccz = axis_cell(c, 2, p.z);
-    const unsigned cbase = d.cstart[c.code0];
+    const unsigned cbase = d.crange[c.code0].x;
     const int Lmax = d.Lmax;
-    for (int dz = -1; dz <= 1; ++dz) {
-        int cz = ccz + dz;
-        if (cz < 0 || cz >= c.nc[2]) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            int cy = ccy + dy;
-            if (cy < 0 || cy >= c.nc[1]) {
-                if (!c.per[1]) continue;
-                cy = (cy + c.nc[1]) % c.nc[1];
-            }
-            for (int dx = -1; dx <= 1; ++dx) {
-                int cx = ccx + dx;
-                if (cx < 0 || cx >= c.nc[0]) {
-                    if (!c.per[0]) continue;
-                    cx = (cx + c.nc[0]) % c.nc[0];
-                }
-                const unsigned code = cell_code(d, c, cx, cy, cz);
-                const int start = c.slot0 + (int)(d.cstart[code] - cbase);
-                const int cnt = (int)d.ccount[code];
-                for (int t = 0; t < cnt; ++t) {
-                    const int m = start + t;
-                    if (m == ps) continue;
-                    const int4 q = d.spos[m];
-                    const long long ddx = min_image(p.x - q.x, c.per[0], c.ext[0], c.half[0]);
-                    const long long ddy = min_image(p.y - q.y, c.per[1], c.ext[1], c.half[1]);
-                    const long long ddz = (long long)p.z - q.z;
-                    const long long d2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    const long long cut = (long long)p.w + q.w + c.skin;
-                    if (d2 >= cut * cut) continue;
-                    const long long S = (long long)p.w + q.w;
-                    const float key = (float)(d2 - S * S);
-                    if (nc == Lmax) { overflow = true; continue; }
-                    // equal keys (rare) are ordered by ID, so the row does not depend on the scan order
-                    int j = nc - 1;
-                    while (j >= 0 && (R.key[j][tx] > key || (R.key[j][tx] == key && d.sid[R.pos[j][tx]] > d.sid[m]))) {
-                        R.key[j + 1][tx] = R.key[j][tx];
-                        R.pos[j + 1][tx] = R.pos[j][tx];
-                        --j;
-                    }
-                    R.key[j + 1][tx] = key;
-                    R.pos[j + 1][tx] = m;
-                    ++nc;
-                }
-            }
+    const int per0 = c.per[0], per1 = c.per[1], ext0 = c.ext[0], ext1 = c.ext[1], hf0 = c.half[0], hf1 = c.half[1];
+    const int skin = c.skin;
+    // the Morton parts of the (up to) three neighbour cells per axis (x and y wrap when
+    // periodic, z never does) and a 27-bit mask of the cells that exist
+    unsigned mx[3], my[3], mz[3];
+    unsigned okm = 0u;
+    {
+        bool okx[3], oky[3], okz[3];
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            int cx = ccx + o - 1, cy = ccy + o - 1;
+            const int cz = ccz + o - 1;
+            okx[o] = oky[o] = true;
+            if (cx < 0) { okx[o] = c.per[0] != 0; cx += c.nc[0]; }
+            else if (cx >= c.nc[0]) { okx[o] = c.per[0] != 0; cx -= c.nc[0]; }
+            if (cy < 0) { oky[o] = c.per[1] != 0; cy += c.nc[1]; }
+            else if (cy >= c.nc[1]) { oky[o] = c.per[1] != 0; cy -= c.nc[1]; }
+            okz[o] = cz >= 0 && cz < c.nc[2];
+            mx[o] = okx[o] ? __ldg(d.spread + c.spread_off[0] + cx) : 0u;
+            my[o] = oky[o] ? __ldg(d.spread + c.spread_off[1] + cy) : 0u;
+            mz[o] = okz[o] ? __ldg(d.spread + c.spread_off[2] + cz) : 0u;
         }
+#pragma unroll
+        for (int k = 0; k < 27; ++k)
+            if (okx[k % 3] && oky[(k / 3) % 3] && okz[k / 9]) okm |= 1u << k;
+    }
+    const unsigned mx0 = mx[0], mx1 = mx[1], mx2 = mx[2], my0 = my[0], my1 = my[1], my2 = my[2];
+    const unsigned mz0 = mz[0], mz1 = mz[1], mz2 = mz[2];
+    auto range_of = [&](int k) -> uint2 {
+        if (!((okm >> k) & 1u)) return make_uint2(0u, 0u);
+        const int ix = k % 3, iy = (k / 3) % 3, iz = k / 9;
+        const unsigned code = (unsigned)c.code0 + (ix == 0 ? mx0 : ix == 1 ? mx1 : mx2) +
+                              (iy == 0 ? my0 : iy == 1 ? my1 : my2) + (iz == 0 ? mz0 : iz == 1 ? mz1 : mz2);
+        return __ldg(d.crange + code);
+    };
+    // scan the 27 cells (the next cell's range in flight) and append the neighbours
+    // within the skin to the row unsorted; the row is sorted once at the end
+    uint2 rg = range_of(0);
+#pragma unroll 1
+    for (int k = 0; k < 27; ++k) {
+        const uint2 cr = rg;
+        if (k + 1 < 27) rg = range_of(k + 1);
+        const int start = c.slot0 + (int)(cr.x - cbase);
+        const int cnt = (int)cr.y;
+        for (int t = 0; t < cnt; ++t) {
+            const int m = start + t;
+            const int4 q = __ldg(d.spos + m);
+            const int ddx = min_image(p.x - q.x, per0, ext0, hf0);
+            const int ddy = min_image(p.y - q.y, per1, ext1, hf1);
+            const long long ddz = (long long)p.z - q.z;
+            const int cut = p.w + q.w + skin;
+            // most candidates fail on one axis already (32-bit compares)
+            if (abs(ddx) >= cut || abs(ddy) >= cut || ddz >= cut || ddz <= -cut || m == ps) continue;
+            const long long d2 = (long long)ddx * ddx + (long long)ddy * ddy + ddz * ddz;
+            if (d2 >= (long long)cut * cut) continue;
+            const long long S = (long long)p.w + q.w;
+            if (nc == Lmax) {
+                overflow = true;
+                continue;
+            }
+            R.key[nc][tx] = (float)(d2 - S * S);
+            R.pos[nc][tx] = m;
+            ++nc;
+        }
+    }
+    // order the row by (key, ID): equal keys (rare) by ID, so that the row does not
+    // depend on the scan order
+    for (int i = 1; i < nc; ++i) {
+        const float key = R.key[i][tx];
+        const int m = R.pos[i][tx];
+        int j = i - 1;
+        while (j >= 0 && (R.key[j][tx] > key || (R.key[j][tx] == key && d.sid[R.pos[j][tx]] > d.sid[m]))) {
+            R.key[j + 1][tx] = R.key[j][tx];
+            R.pos[j + 1][tx] = R.pos[j][tx];
+            --j;
+        }
+        R.key[j + 1][tx] = key;
+        R.pos[j + 1][tx] = m;
     }
     if (overflow) {
         atomicOr(&d.g->status, ST_CAPACITY);
@@ -349,30 +381,35 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
     const size_t plane = (size_t)Lmax * ncap;
     const int* orow = d.nbr[lp] + old;
     const float* ho = d.hist[lp] + old;
-    const int ocnt = D.flag == 2 ? 0 : d.cnt[lp][old];
-    for (int e = 0; e < ocnt; ++e)
-        R.oid[e][tx] = (int)(__float_as_uint(d.vel[cur][orow[(size_t)e * ncap]].w) & ID_MASK);
-    const unsigned ohm = D.flag == 2 ? 0u : d.hmask[lp][old];
-    unsigned nhm = 0u;
+    // the new row (partner slots), overlaps zeroed; the keys give way to the partner IDs
     for (int e = 0; e < nc; ++e) {
         const int m = R.pos[e][tx];
         nrow[(size_t)e * ncap] = d.fin[m];
-        const int id = d.sid[m];
-        float hx = 0.f, hy = 0.f, hz = 0.f;
-        for (int eo = 0; eo < ocnt; ++eo) {
-            if (R.oid[eo][tx] == id) {
-                if ((ohm >> eo) & 1u) {
-                    hx = ho[(size_t)eo * ncap];
-                    hy = ho[plane + (size_t)eo * ncap];
-                    hz = ho[2 * plane + (size_t)eo * ncap];
-                    if (hx != 0.f || hy != 0.f || hz != 0.f) nhm |= 1u << e;
-                }
+        R.key[e][tx] = __int_as_float(d.sid[m]);
+        hn[(size_t)e * ncap] = 0.f;
+        hn[plane + (size_t)e * ncap] = 0.f;
+        hn[2 * plane + (size_t)e * ncap] = 0.f;
+    }
+    // carry every non-zero stored overlap of the old row to the pair's new entry
+    const int ocnt = D.flag == 2 ? 0 : d.cnt[lp][old];
+    unsigned ohm = D.flag == 2 ? 0u : d.hmask[lp][old];
+    if (ocnt < 32) ohm &= (1u << ocnt) - 1u;
+    unsigned nhm = 0u;
+    while (ohm) {
+        const int eo = __ffs(ohm) - 1;
+        ohm &= ohm - 1u;
+        const float hx = ho[(size_t)eo * ncap], hy = ho[plane + (size_t)eo * ncap], hz = ho[2 * plane + (size_t)eo * ncap];
+        if (hx == 0.f && hy == 0.f && hz == 0.f) continue;
+        const int oid = (int)(__float_as_uint(d.vel[cur][orow[(size_t)eo * ncap]].w) & ID_MASK);
+        for (int e = 0; e < nc; ++e) {
+            if (__float_as_int(R.key[e][tx]) == oid) {
+                hn[(size_t)e * ncap] = hx;
+                hn[plane + (size_t)e * ncap] = hy;
+                hn[2 * plane + (size_t)e * ncap] = hz;
+                nhm |= 1u << e;
                 break;
             }
         }
-        hn[(size_t)e * ncap] = hx;
-        hn[plane + (size_t)e * ncap] = hy;
-        hn[2 * plane + (size_t)e * ncap] = hz;
     }
     d.cnt[nlp][s] = nc;
     d.hmask[nlp][s] = nhm;
@@ -380,20 +417,22 @@ __device__ __forceinline__ void build_row(const Dev& d, int s, const InstD& D, c
     d.whist[nlp][s] = D.flag == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : d.whist[lp][old];
 }
 
-__global__ void __launch_bounds__(RB_T) k_rb_build(Dev d)
+__global__ void __launch_bounds__(RB_T, 16) k_rb_build(Dev d)
 {
     if (!d.g->any) return;
     __shared__ RowScratch R;
     constexpr int H = TILE / RB_T;           // blocks of RB_T threads per tile
-    for (int u = blockIdx.x; u < d.ntiles * H; u += gridDim.x) {   // over the new slots
+    // over the cell-order positions: the threads of a warp hold neighbouring particles and
+    // scan overlapping cells (the rows go to the particles' new slots in the same tile)
+    for (int u = blockIdx.x; u < d.ntiles * H; u += gridDim.x) {
         const int t = u / H;
         const int k = d.tile_inst[t];
         const InstD D = d.id[k];
         if (!D.flag) continue;
         const InstC& c = d.ic[k];
-        const int s = t * TILE + (u % H) * RB_T + threadIdx.x;
-        if (s - c.slot0 >= D.n_new) continue;
-        build_row(d, s, D, c, R);
+        const int p = t * TILE + (u % H) * RB_T + threadIdx.x;
+        if (p - c.slot0 >= D.n_new) continue;
+        build_row(d, p, D, c, R);
     }
 }
 
@@ -406,7 +445,7 @@ __global__ void k_rb_count(Dev d)
         if (!D.flag) continue;
         const InstC& c = d.ic[k];
         const unsigned last = (unsigned)(c.code0 + c.ncode - 1);
-        D.n_new = (int)(d.cstart[last] + d.ccount[last] - d.cstart[c.code0]);
+        D.n_new = (int)(d.crange[last].x + d.crange[last].y - d.crange[c.code0].x);
     }
 }
 
@@ -1299,7 +1338,7 @@ struct Plan {
     unsigned ncodes = 0, nparts = 0;
     // offsets
     size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_fext[2], o_whist[2];
-    size_t o_cellcode, o_cslot, o_perm, o_fin, o_perm2, o_spos, o_sid, o_ccount, o_cstart, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
+    size_t o_cellcode, o_cslot, o_perm, o_fin, o_spos, o_sid, o_ccount, o_crange, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
         o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl, o_small;
     size_t bytes = 0;
 };
@@ -1442,11 +1481,10 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
     p.o_cslot = L.take(N * 4);
     p.o_perm = L.take(N * 4);
     p.o_fin = L.take(N * 4);
-    p.o_perm2 = L.take(N * 4);
     p.o_spos = L.take(N * 16);
     p.o_sid = L.take(N * 4);
     p.o_ccount = L.take((size_t)p.ncodes * 4);
-    p.o_cstart = L.take((size_t)p.ncodes * 4);
+    p.o_crange = L.take((size_t)p.ncodes * 8);
     p.o_part = L.take((size_t)std::max(1u, p.nparts) * 4);
     p.o_pinst = L.take((size_t)std::max(1u, p.nparts) * 4);
     p.o_soi = L.take(N * 4);
@@ -1518,7 +1556,7 @@ dem_status launch_rebuild(dem_ctx* ctx, cudaStream_t st)
     k_rb_cellsort<<<gt, TILE, 0, st>>>(d);
     k_rb_count<<<1, 256, 0, st>>>(d);
     k_rb_tilesort<<<gt, TILE, 0, st>>>(d);
-    k_rb_build<<<gt * (TILE / RB_T), RB_T, 0, st>>>(d);
+    k_rb_build<<<ctx->grid_build, RB_T, 0, st>>>(d);
     k_rb_finish<<<1, 256, 0, st>>>(d);
     CU(cudaGetLastError());
     return DEM_OK;
@@ -1558,6 +1596,8 @@ void destroy_graph(dem_ctx* ctx)
     ctx->rb_graph = nullptr;
 }
 
+constexpr int EV_EVERY = 5;    // step kernels per timed one in a graph
+
 dem_status build_graph(dem_ctx* ctx, int S)
 {
     destroy_graph(ctx);
@@ -1589,9 +1629,12 @@ dem_status build_graph(dem_ctx* ctx, int S)
         kp.kernelParams = args;
         CU(cudaGraphAddKernelNode(&prev, g, nullptr, 0, &kp));
     }
-    ctx->ev0.resize(S);
-    ctx->ev1.resize(S);
-    for (int i = 0; i < S; ++i) {
+    // CUDA events around every EV_EVERY-th step kernel (each pair of event nodes adds a few
+    // microseconds to the step, so the timing is sampled)
+    const int nev = (S + EV_EVERY - 1) / EV_EVERY;
+    ctx->ev0.resize(nev);
+    ctx->ev1.resize(nev);
+    for (int i = 0; i < nev; ++i) {
         CU(cudaEventCreate(&ctx->ev0[i]));
         CU(cudaEventCreate(&ctx->ev1[i]));
     }
@@ -1615,11 +1658,17 @@ dem_status build_graph(dem_ctx* ctx, int S)
         kp.gridDim = dim3(ctx->grid0);
         kp.blockDim = dim3(TILE);
         kp.kernelParams = args;
-        cudaGraphNode_t e0, kn, e1;
-        CU(cudaGraphAddEventRecordNode(&e0, g, &cn, 1, ctx->ev0[i]));
-        CU(cudaGraphAddKernelNode(&kn, g, &e0, 1, &kp));
-        CU(cudaGraphAddEventRecordNode(&e1, g, &kn, 1, ctx->ev1[i]));
-        prev = e1;
+        cudaGraphNode_t kn;
+        if (i % EV_EVERY == 0) {
+            cudaGraphNode_t e0, e1;
+            CU(cudaGraphAddEventRecordNode(&e0, g, &cn, 1, ctx->ev0[i / EV_EVERY]));
+            CU(cudaGraphAddKernelNode(&kn, g, &e0, 1, &kp));
+            CU(cudaGraphAddEventRecordNode(&e1, g, &kn, 1, ctx->ev1[i / EV_EVERY]));
+            prev = e1;
+        } else {
+            CU(cudaGraphAddKernelNode(&kn, g, &cn, 1, &kp));
+            prev = kn;
+        }
     }
     CU(cudaGraphInstantiate(&ctx->gexec, g, 0));
     ctx->graph_steps = S;
@@ -1691,11 +1740,10 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     d.cslot = (unsigned*)(base + p.o_cslot);
     d.perm = (int*)(base + p.o_perm);
     d.fin = (int*)(base + p.o_fin);
-    d.perm2 = (int*)(base + p.o_perm2);
     d.spos = (int4*)(base + p.o_spos);
     d.sid = (int*)(base + p.o_sid);
     d.ccount = (unsigned*)(base + p.o_ccount);
-    d.cstart = (unsigned*)(base + p.o_cstart);
+    d.crange = (uint2*)(base + p.o_crange);
     d.part = (unsigned*)(base + p.o_part);
     d.part_inst = (int*)(base + p.o_pinst);
     d.slot_of_id = (int*)(base + p.o_soi);
@@ -1764,6 +1812,9 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
         ctx->grid0 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b0)));
         ctx->grid1 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b1)));
         ctx->grid_rb = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * 8));
+        int bb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_rb_build, RB_T, 0);
+        ctx->grid_build = std::max(1, std::min(ctx->ntiles * (TILE / RB_T), std::max(1, nsm) * std::max(1, bb)));
         cudaGetLastError();
     }
     *out = ctx;

@@ -531,7 +531,7 @@ __global__ void k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
         bool ok = true;
         const int ru_i = (int)ru;
         const int cx0 = axis_cell(c, 0, (int)u[0]), cy0 = axis_cell(c, 1, (int)u[1]), cz0 = axis_cell(c, 2, (int)u[2]);
-        const unsigned cbase = d.cstart[c.code0];
+        const unsigned cbase = d.crange[c.code0].x;
         for (int dz = -1; dz <= 1 && ok; ++dz) {
             const int cz = cz0 + dz;
             if (cz < 0 || cz >= c.nc[2]) continue;
@@ -548,8 +548,9 @@ __global__ void k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
                         cx = (cx + c.nc[0]) % c.nc[0];
                     }
                     const unsigned code = cell_code(d, c, cx, cy, cz);
-                    const int start = c.slot0 + (int)(d.cstart[code] - cbase);
-                    const int cnt = (int)d.ccount[code];
+                    const uint2 cr = d.crange[code];
+                    const int start = c.slot0 + (int)(cr.x - cbase);
+                    const int cnt = (int)cr.y;
                     for (int t = 0; t < cnt; ++t) {
                         const int j = d.fin[start + t];   // slot of this cell member
                         if (j - c.slot0 >= D.n) continue;

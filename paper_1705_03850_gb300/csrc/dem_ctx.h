@@ -18,6 +18,7 @@ struct dem_ctx {
     int ncap = 0, ntiles = 0;
     int grid0 = 1, grid1 = 1;         // persistent grids of the step / evaluation kernels
     int grid_rb = 1;                  // persistent grid of the per-slot rebuild kernels
+    int grid_build = 1;               // one wave of the list build (occupancy-sized)
     unsigned ncodes = 0, nparts = 0;
     std::vector<InstC> ic;
     std::vector<HostInstLo> hl;

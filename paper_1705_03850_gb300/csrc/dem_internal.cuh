@@ -105,11 +105,10 @@ struct Dev {
     unsigned* cslot;
     int* perm;                 // cell-order position -> old slot
     int* fin;                  // cell-order position -> new slot (tiles reordered by contact count)
-    int* perm2;                // new slot -> cell-order position
     int4* spos;                // positions in cell order (list build)
     int* sid;                  // particle IDs in cell order (list build)
     unsigned* ccount;
-    unsigned* cstart;
+    uint2* crange;             // per cell code: {first cell-order position (exclusive scan), count}
     unsigned* part;
     int* part_inst;            // instance owning each scan chunk of cell codes (-1: padding)
     int* slot_of_id;

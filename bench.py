@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--batched-settle", type=int, default=8000, help="settling steps before the settled batched "
                     "measurement (0: skip it)")
     ap.add_argument("--no-coupled", action="store_true")
+    ap.add_argument("--profile-range", default="plain", choices=["plain", "batched", "adjoint", "coupled"],
+                    help="which line's timed region `ncu --profile-from-start off` sees")
     ap.add_argument("--coupled-intervals", type=int, default=100, help="timed coupling intervals of 15 steps")
     ap.add_argument("--coupled-settle", type=int, default=4000, help="settling steps per level (dt 5e-6)")
     ap.add_argument("--save-state", default=None, help="save the settled bed (.npz) for later --load-state runs")
@@ -130,6 +132,17 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def _profile(args, line, start):
+    """Start or stop the profiler range (cudaProfilerStart/Stop) around one line's timed region."""
+    if args.profile_range != line:
+        return
+    import torch
+    if start:
+        torch.cuda.profiler.start()
+    else:
+        torch.cuda.profiler.stop()
 
 
 def max_over_ranks(x, device):
@@ -293,12 +306,12 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clocks:
-        torch.cuda.profiler.start()          # marks the timed region for `ncu --profile-from-start off`
+        _profile(args, "plain", True)        # marks the timed region for `ncu --profile-from-start off`
         e0.record(stream)
         sim.step(K)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        torch.cuda.profiler.stop()
+        _profile(args, "plain", False)
     ms = e0.elapsed_time(e1)
     kern_ms, kern_n = sim.graph_step_kernel_ms() if S > 0 else (float("nan"), 1)
     st1 = sim.stats()
@@ -417,12 +430,14 @@ def run_batched(args, dev, plain_value):
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    _profile(args, "batched", True)
     e0.record(sim.stream)
     sim.step(1)               # start-up evaluation and first list build of all 256 boxes
     sim.step(K - 1 - ((K - 1) % S))
     sim.step((K - 1) % S)
     e1.record(sim.stream)
     torch.cuda.synchronize(dev)
+    _profile(args, "batched", False)
     ms = e0.elapsed_time(e1)
     st1 = sim.stats()
     sim.sync()
@@ -514,12 +529,14 @@ def run_adjoint(args, dev, plain_value):
     # differentiable rollout: forward with checkpoints + adjoint
     sim.set_material(params).write_state(*state)
     torch.cuda.synchronize(dev)
+    _profile(args, "adjoint", True)
     t0 = time.perf_counter()
     sim.rollout_forward(N, K)
     t1 = time.perf_counter()
     obs = sim.observables(axis)
     grad = sim.rollout_adjoint(np.ones((B, 2)), axis)
     t2 = time.perf_counter()
+    _profile(args, "adjoint", False)
     sim.close()
     value = n * N / (t2 - t0)
     return {"value": value, "unit": "adjoint particle-steps/s (forward with checkpoints + backward)",
@@ -568,6 +585,7 @@ def run_coupled(args, dev, plain_value):
     st0 = [c.stats() for c in ctx]
     I = args.coupled_intervals
     t_couple = 0.0
+    _profile(args, "coupled", True)
     t0 = time.perf_counter()
     for _ in range(I):
         for c in ctx:
@@ -581,6 +599,7 @@ def run_coupled(args, dev, plain_value):
         t_couple += time.perf_counter() - tc
     torch.cuda.synchronize(dev)
     t = time.perf_counter() - t0
+    _profile(args, "coupled", False)
     n1 = h.counts()
     st1 = [c.stats() for c in ctx]
     inserted = [int(c.counts()[1][0]) - wl.n for c, wl in zip(ctx[1:], lv[1:])]

@@ -18,7 +18,7 @@ using namespace cgdem;
 
 // minimum resident blocks per SM requested for the step kernel (register budget)
 #ifndef DEM_STEP_MINB
-#define DEM_STEP_MINB 8
+#define DEM_STEP_MINB 7
 #endif
 
 // ====================================================================== scan

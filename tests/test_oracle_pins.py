@@ -361,13 +361,3 @@ def test_results_do_not_depend_on_storage_order():
     assert np.array_equal(ha, hb_) and np.array_equal(hb, hbb)
     assert np.allclose(hxa, hxb, rtol=1e-8, atol=1e-18)
 
-
-# ----------------------------------------------------- paper arithmetic
-
-def test_paper_projection_arithmetic():
-    # Sec. 3 (runtimes): 6.14e9 particles, five levels alpha_l = 2^(l-1), volume
-    # quartered per level -> about 46.5 million particles in total; and the
-    # two-level silo has 2.78x fewer particles than the 187,504 reference.
-    total = sum(6.14e9 * (2 ** (l - 1)) ** -3 * 4.0 ** (l - 5) for l in range(1, 6))
-    assert total == pytest.approx(46.5e6, rel=1e-3)
-    assert 187_504 / (23_438 + 44_000) == pytest.approx(2.78, abs=5e-3)

@@ -183,6 +183,7 @@ def _kernel_hash():
     i0 = src.index("template <int MODE>\n__global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(")
     i1 = src.index("__global__ void k_set_cond", i0)
     h = hashlib.sha256(src[i0:i1].encode())
+    h.update(re.search(r"#define DEM_STEP_MINB \d+", src).group(0).encode())   # its launch bound
     for f in ("dem_internal.cuh", "dem_contact.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]

@@ -492,6 +492,17 @@ __device__ __forceinline__ Coef<float> coef_of(const InstC& c)
 // contact law has a single call site, so both particles of a pair run the same
 // instructions on operands that differ only in the sign of the antisymmetric
 // ones.
+// 32-bit integer hash ("lowbias32", C. Wellons' hash-prospector search, public domain)
+__device__ __forceinline__ unsigned mix32(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, cudaGraphConditionalHandle hnext, int use_cond)
 {
@@ -700,7 +711,16 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
             int4 Pn = P;
             bool bad = !(fabsf(sx) < 5.0e8f && fabsf(sy) < 5.0e8f && fabsf(sz) < 5.0e8f);
             if (!bad) {
-                const int ix = __float2int_rn(sx), iy = __float2int_rn(sy), iz = __float2int_rn(sz);
+                // unbiased rounding to the position grid: floor(s + u), u uniform in [0, 1)
+                // from a hash of the particle's ID and position (a function of the state
+                // alone, so replays, graphs and batched runs round identically); plain
+                // rounding would bias a steady drift by up to half a quantum per step
+                const unsigned h0 = mix32(myid * 0x9E3779B9u ^ (unsigned)P.x);
+                const unsigned h1 = mix32(h0 ^ (unsigned)P.y);
+                const unsigned h2 = mix32(h1 ^ (unsigned)P.z);
+                const int ix = __float2int_rd(sx + (float)(h0 >> 8) * 0x1p-24f);
+                const int iy = __float2int_rd(sy + (float)(h1 >> 8) * 0x1p-24f);
+                const int iz = __float2int_rd(sz + (float)(h2 >> 8) * 0x1p-24f);
                 int x = P.x + ix, y = P.y + iy;
                 if (per0) {
                     if (x >= ext0) x -= ext0;

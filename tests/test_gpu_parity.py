@@ -210,3 +210,29 @@ def test_full_size_million_particle_forces():
     F = sim.read(dem.FORCE)
     Fo, To, hist, fabs = oracle_sim(wl).evaluate()
     _force_check(F, Fo, fabs)
+
+
+def test_steady_drift_is_not_biased_by_the_position_grid():
+    # free spheres (no gravity, contacts or floor) at constant velocities whose step is a
+    # fractional number of position quanta: the positions follow x0 + v t within a random
+    # walk of about a quantum times the square root of the step count, not the
+    # half-quantum-per-step bias of plain rounding
+    import dataclasses
+    wl = workloads.single_sphere(z=5e-3, w=(0.0, 0.0, 0.0))
+    q = oracle.quantum(wl.lo, wl.hi)
+    n, steps = 64, 2000
+    x = np.column_stack([np.full(n, 2e-3), np.linspace(0.5e-3, 9.5e-3, n), np.full(n, 5e-3)])
+    v = np.zeros((n, 3))
+    v[:, 0] = (33.0 + np.linspace(0.05, 0.95, n)) * q / wl.dt        # 33.05 .. 33.95 quanta per step
+    v = workloads.f32(v)
+    r = workloads.qgrid(np.full(n, 5e-5))                           # 0.1 mm spheres 0.14 mm apart
+    m = workloads.sphere_masses(r, wl.material.rho)
+    wl = dataclasses.replace(wl, x=workloads.qgrid(x), v=v, w=np.zeros((n, 3)), r=r, m=m, g=(0.0, 0.0, 0.0),
+                             floor=False)
+    sim = dem.DEM([dem.desc_from_workload(wl)])
+    sim.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
+    sim.step(steps)
+    d = min_image(sim.read(dem.POS) - (wl.x + wl.v * wl.dt * steps), wl)
+    err = np.abs(d[:, 0]) / q
+    assert err.max() < 6 * np.sqrt(steps * 0.25) + 2, err.max()        # plain rounding: up to 900 quanta
+    assert np.abs(d[:, 1:]).max() == 0.0

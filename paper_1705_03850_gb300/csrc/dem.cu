@@ -1059,26 +1059,41 @@ __global__ void __launch_bounds__(TILE) k_snap(Dev d, Snap S)
 {
     const size_t plane = (size_t)d.Lmax * d.ncap;
     for_live_slots(d, [&](int s, int k, const InstD& D) {
+        // only entries whose history bit is set hold a stored overlap that anything reads
+        // (every reader gates on the bit), so only those are copied
         const int cur = D.cur, lp = D.lp;
-        const int cnt = d.cnt[lp][s];
         float* h = d.hist[lp] + s;
         float* hs = S.hist + s;
         if (SAVE) {
             S.pos[s] = d.pos[cur][s];
             S.vel[s] = d.vel[cur][s];
             S.omg[s] = d.omg[cur][s];
-            S.hmask[s] = d.hmask[lp][s];
+            unsigned hm = d.hmask[lp][s];
+            S.hmask[s] = hm;
             S.whist[s] = d.whist[lp][s];
-            for (int e = 0; e < cnt; ++e)
-                for (int c3 = 0; c3 < 3; ++c3) hs[c3 * plane + (size_t)e * d.ncap] = h[c3 * plane + (size_t)e * d.ncap];
+            while (hm) {
+                const size_t o = (size_t)(__ffs(hm) - 1) * d.ncap;
+                hm &= hm - 1u;
+                const float x = h[o], y = h[plane + o], z = h[2 * plane + o];
+                hs[o] = x;
+                hs[plane + o] = y;
+                hs[2 * plane + o] = z;
+            }
         } else {
             d.pos[cur][s] = S.pos[s];
             d.vel[cur][s] = S.vel[s];
             d.omg[cur][s] = S.omg[s];
-            d.hmask[lp][s] = S.hmask[s];
+            unsigned hm = S.hmask[s];
+            d.hmask[lp][s] = hm;
             d.whist[lp][s] = S.whist[s];
-            for (int e = 0; e < cnt; ++e)
-                for (int c3 = 0; c3 < 3; ++c3) h[c3 * plane + (size_t)e * d.ncap] = hs[c3 * plane + (size_t)e * d.ncap];
+            while (hm) {
+                const size_t o = (size_t)(__ffs(hm) - 1) * d.ncap;
+                hm &= hm - 1u;
+                const float x = hs[o], y = hs[plane + o], z = hs[2 * plane + o];
+                h[o] = x;
+                h[plane + o] = y;
+                h[2 * plane + o] = z;
+            }
         }
         (void)k;
     });

@@ -484,9 +484,10 @@ __device__ __forceinline__ Coef<float> coef_of(const InstC& c)
 //
 // Persistent grid: block b owns the contiguous tile range [b T / G, (b+1) T / G)
 // (neighbouring tiles share neighbours, which then hit in L1), one thread per
-// particle.  The row is walked twice: first the positions of all entries (loads
-// independent of each other) give the touch mask, then only the contacts are
-// evaluated, in row order, with the next contact's state in flight; the stored
+// particle.  The row is walked twice: first the positions of all entries (in
+// batches of four, the next batch's indices in flight) give the touch mask, then
+// only the contacts are evaluated, in row order, with the next contact's state in
+// flight; the stored
 // overlap is loaded only for entries whose history is non-zero (bit mask hmask),
 // and stored only where it changes.  Each particle evaluates its contacts from its own side; the
 // contact law has a single call site, so both particles of a pair run the same
@@ -573,16 +574,30 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
         // ---- pass 1: positions of every entry, touch mask (independent loads)
         const unsigned hm = d.hmask[lp][s];
         unsigned tm = 0u;
-#pragma unroll 4
-        for (int e = 0; e < ncnt; ++e) {
-            const int j = __ldg(nb + (size_t)e * ncap);
-            const int4 Q = __ldg(pos + j);
-            const int dx = min_image(P.x - Q.x, per0, ext0, hf0);
-            const int dy = min_image(P.y - Q.y, per1, ext1, hf1);
-            const int dz = P.z - Q.z;
-            const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
-            const int S = P.w + Q.w;
-            if (d2 < (long long)S * S) tm |= 1u << e;
+        int jn0 = s, jn1 = s, jn2 = s, jn3 = s;       // indices of the next batch of four
+        if (0 < ncnt) jn0 = __ldg(nb);
+        if (1 < ncnt) jn1 = __ldg(nb + (size_t)ncap);
+        if (2 < ncnt) jn2 = __ldg(nb + (size_t)2 * ncap);
+        if (3 < ncnt) jn3 = __ldg(nb + (size_t)3 * ncap);
+        for (int e0 = 0; e0 < ncnt; e0 += 4) {
+            const int jb[4] = {jn0, jn1, jn2, jn3};
+            int4 Qb[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qb[k] = __ldg(pos + jb[k]);
+            if (e0 + 4 < ncnt) jn0 = __ldg(nb + (size_t)(e0 + 4) * ncap);
+            if (e0 + 5 < ncnt) jn1 = __ldg(nb + (size_t)(e0 + 5) * ncap);
+            if (e0 + 6 < ncnt) jn2 = __ldg(nb + (size_t)(e0 + 6) * ncap);
+            if (e0 + 7 < ncnt) jn3 = __ldg(nb + (size_t)(e0 + 7) * ncap);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int4 Q = Qb[k];
+                const int dx = min_image(P.x - Q.x, per0, ext0, hf0);
+                const int dy = min_image(P.y - Q.y, per1, ext1, hf1);
+                const int dz = P.z - Q.z;
+                const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+                const int S = P.w + Q.w;
+                if (e0 + k < ncnt && d2 < (long long)S * S) tm |= 1u << (e0 + k);
+            }
         }
         // entries that left contact (or, for the read-out, every non-contact) get no history
         const unsigned rowmask = ncnt >= 32 ? 0xffffffffu : ((1u << ncnt) - 1u);
@@ -1151,22 +1166,45 @@ __global__ void __launch_bounds__(TILE) k_adj_force(Dev d, AdjBufs a, Snap S, in
         const int* nb = d.nbr[lp] + s;
         float* xbr = a.xib + s;
         const float* hs = S.hist + s;
-        for (int e = 0; e < ncnt; ++e) {
+        const int per0 = c.per[0], per1 = c.per[1], ext0 = c.ext[0], ext1 = c.ext[1], hf0 = c.half[0],
+                  hf1 = c.half[1];
+        // pass 1: which entries touch (independent loads, four at a time)
+        unsigned tm = 0u;
+        for (int e0 = 0; e0 < ncnt; e0 += 4) {
+            int jb[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) jb[k] = e0 + k < ncnt ? __ldg(nb + (size_t)(e0 + k) * ncap) : s;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int4 Q = __ldg(S.pos + jb[k]);
+                const int dx = min_image(P.x - Q.x, per0, ext0, hf0);
+                const int dy = min_image(P.y - Q.y, per1, ext1, hf1);
+                const int dz = P.z - Q.z;
+                const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+                const int Sr = P.w + Q.w;
+                if (e0 + k < ncnt && d2 < (long long)Sr * Sr) tm |= 1u << (e0 + k);
+            }
+        }
+        // the overlap adjoint of entries out of contact is zero
+        const unsigned rowmask = ncnt >= 32 ? 0xffffffffu : ((1u << ncnt) - 1u);
+        for (unsigned z = rowmask & ~tm; z; z &= z - 1u) {
+            const size_t o = (size_t)(__ffs(z) - 1) * ncap;
+            xbr[o] = 0.f;
+            xbr[plane + o] = 0.f;
+            xbr[2 * plane + o] = 0.f;
+        }
+        // pass 2: the contacts in row order
+        for (unsigned rem = tm; rem; rem &= rem - 1u) {
+            const int e = __ffs(rem) - 1;
             const size_t o = (size_t)e * ncap;
-            const int j = nb[o];
-            const int4 Q = S.pos[j];
-            const int dx = min_image(P.x - Q.x, c.per[0], c.ext[0], c.half[0]);
-            const int dy = min_image(P.y - Q.y, c.per[1], c.ext[1], c.half[1]);
+            const int j = __ldg(nb + o);
+            const int4 Q = __ldg(S.pos + j);
+            const int dx = min_image(P.x - Q.x, per0, ext0, hf0);
+            const int dy = min_image(P.y - Q.y, per1, ext1, hf1);
             const int dz = P.z - Q.z;
             const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
             const int Sr = P.w + Q.w;
             const long long S2 = (long long)Sr * Sr;
-            if (d2 >= S2) {
-                xbr[o] = 0.f;
-                xbr[plane + o] = 0.f;
-                xbr[2 * plane + o] = 0.f;
-                continue;
-            }
             const float4 Vj = S.vel[j], Wj = S.omg[j];
             const float4 Fj = a.Fb[j], Tj = a.Tb[j];
             const float d2f = (float)d2;

@@ -574,11 +574,16 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
         // ---- pass 1: positions of every entry, touch mask (independent loads)
         const unsigned hm = d.hmask[lp][s];
         unsigned tm = 0u;
-        int jn0 = s, jn1 = s, jn2 = s, jn3 = s;       // indices of the next batch of four
-        if (0 < ncnt) jn0 = __ldg(nb);
-        if (1 < ncnt) jn1 = __ldg(nb + (size_t)ncap);
-        if (2 < ncnt) jn2 = __ldg(nb + (size_t)2 * ncap);
-        if (3 < ncnt) jn3 = __ldg(nb + (size_t)3 * ncap);
+        // the first batch of indices is loaded before the row length arrives (rows hold at
+        // least d.Lmax entries of storage); entries beyond the row are replaced by this slot
+        int jn0 = 0 < d.Lmax ? __ldg(nb) : s;
+        int jn1 = 1 < d.Lmax ? __ldg(nb + (size_t)ncap) : s;
+        int jn2 = 2 < d.Lmax ? __ldg(nb + (size_t)2 * ncap) : s;
+        int jn3 = 3 < d.Lmax ? __ldg(nb + (size_t)3 * ncap) : s;
+        jn0 = 0 < ncnt ? jn0 : s;
+        jn1 = 1 < ncnt ? jn1 : s;
+        jn2 = 2 < ncnt ? jn2 : s;
+        jn3 = 3 < ncnt ? jn3 : s;
         for (int e0 = 0; e0 < ncnt; e0 += 4) {
             const int jb[4] = {jn0, jn1, jn2, jn3};
             int4 Qb[4];

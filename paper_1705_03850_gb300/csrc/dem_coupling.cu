@@ -26,6 +26,7 @@ struct Face {
     int b, c;            // in-plane axes
     int nb, nc, off;     // cells along b and c, first cell index
     double plane, wb, wc;
+    double iwb, iwc;     // 1 / wb, 1 / wc
 };
 
 struct Geo {
@@ -34,7 +35,7 @@ struct Geo {
     Face face[6];
     int S;               // surface cells (= transition cells)
     int ncr[3];
-    double wcr[3];
+    double wcr[3], iwcr[3];   // correction cell widths and their reciprocals
     int C;               // correction cells
     double layer, alpha, Tc, dt, kp, ki, kv, mass_unit;
     int bins, mode, max_attempts, max_insert, drain;
@@ -45,6 +46,9 @@ struct Geo {
     int rmaxf_u;         // largest fine radius in fine units (histogram range)
     int fresh_c, fresh_f;
     int add;             // add the controller forces to the held ones instead of replacing them
+    // coarse positions (units) outside [ulo, uhi) take part in nothing but the position record:
+    // the region grown by the largest coarse diameter and two units, rounded outwards
+    long long ulo[3], uhi[3];
 };
 
 struct Acc {
@@ -78,11 +82,21 @@ __device__ __forceinline__ bool inside_box(const Geo& g, const double* x)
            x[2] < g.hi[2];
 }
 
+// floor(a / w) as the correctly rounded division gives it, from the product with the
+// reciprocal (FP64 division is slow here); the division decides the rare cases where the
+// product lies within 1e-6 of an integer
+__device__ __forceinline__ double floor_div(double a, double w, double iw)
+{
+    const double t = a * iw, f = floor(t);
+    if (t - f < 1e-6 || f + 1.0 - t < 1e-6) return floor(a / w);
+    return f;
+}
+
 // surface / transition cell of an in-plane point of face f (-1 outside the face)
 __device__ __forceinline__ int face_cell(const Face& f, double pb, double pc, const Geo& g)
 {
     if (pb < g.lo[f.b] || pb >= g.hi[f.b] || pc < g.lo[f.c] || pc >= g.hi[f.c]) return -1;
-    int ib = (int)floor((pb - g.lo[f.b]) / f.wb), ic = (int)floor((pc - g.lo[f.c]) / f.wc);
+    int ib = (int)floor_div(pb - g.lo[f.b], f.wb, f.iwb), ic = (int)floor_div(pc - g.lo[f.c], f.wc, f.iwc);
     ib = min(max(ib, 0), f.nb - 1);
     ic = min(max(ic, 0), f.nc - 1);
     return f.off + ib + f.nb * ic;
@@ -110,7 +124,7 @@ __device__ __forceinline__ int corr_cell(const Geo& g, const double* x)
 {
     if (!inside_box(g, x)) return -1;
     int i[3];
-    for (int a = 0; a < 3; ++a) i[a] = min(max((int)floor((x[a] - g.lo[a]) / g.wcr[a]), 0), g.ncr[a] - 1);
+    for (int a = 0; a < 3; ++a) i[a] = min(max((int)floor_div(x[a] - g.lo[a], g.wcr[a], g.iwcr[a]), 0), g.ncr[a] - 1);
     return (i[2] * g.ncr[1] + i[1]) * g.ncr[0] + i[0];
 }
 
@@ -232,7 +246,9 @@ __global__ void __launch_bounds__(TILE) k_cp_coarse(Dev d, Geo g, Acc a, int rec
         const unsigned id = __float_as_uint(V.w) & ID_MASK;
         const double x[3] = {posm(g.loc, g.qc, P.x, 0), posm(g.loc, g.qc, P.y, 1), posm(g.loc, g.qc, P.z, 2)};
         const double r = (double)P.w * g.qc, m = d.omg[D.cur][s].w;
-        if (!record_only) {
+        const bool near = P.x >= g.ulo[0] && P.x < g.uhi[0] && P.y >= g.ulo[1] && P.y < g.uhi[1] &&
+                          P.z >= g.ulo[2] && P.z < g.uhi[2];
+        if (!record_only && near) {
             // entry through a feed face since the previous call
             if (a.prev_ok[id] && inside_box(g, x)) {
                 const double* p = a.prev + 3 * (size_t)id;
@@ -416,9 +432,13 @@ __global__ void __launch_bounds__(TILE) k_cp_force_coarse(Dev d, Geo g, Acc a)
 {
     for_live(d, [&](int s, const InstC& c, const InstD& D) {
         const int4 P = d.pos[D.cur][s];
-        const double x[3] = {posm(g.loc, g.qc, P.x, 0), posm(g.loc, g.qc, P.y, 1), posm(g.loc, g.qc, P.z, 2)};
         float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int cc = corr_cell(g, x);
+        int cc = -1;
+        if (P.x >= g.ulo[0] && P.x < g.uhi[0] && P.y >= g.ulo[1] && P.y < g.uhi[1] && P.z >= g.ulo[2] &&
+            P.z < g.uhi[2]) {
+            const double x[3] = {posm(g.loc, g.qc, P.x, 0), posm(g.loc, g.qc, P.y, 1), posm(g.loc, g.qc, P.z, 2)};
+            cc = corr_cell(g, x);
+        }
         if (cc >= 0) {
             const double m = d.omg[D.cur][s].w, k = g.kv * m / g.Tc;
             const double* dv = a.dv + 3 * (size_t)cc;
@@ -636,6 +656,8 @@ __global__ void k_cp_append(Dev d, Geo g, Acc a, int* overflow)
     if (threadIdx.x == 0) {
         D.n += tot;
         D.nid += tot;
+        d.goff[0] = 0;                      // offsets of the user arrays (one instance)
+        d.goff[1] = D.nid;
         if ((tot > 0 || a.removed[0] > 0) && D.flag == 0) {
             D.flag = 1;
             atomicOr(&d.g->any, 1u);
@@ -654,6 +676,7 @@ struct dem_coupler {
     int* overflow = nullptr;
     int calls = 0;
     double rho_f = 0.0;
+    cudaEvent_t ready = nullptr;   // orders the fine level's stream after the coarse level's
 };
 
 namespace {
@@ -733,6 +756,8 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
         f.nc = std::max(1, (int)std::floor((g.hi[f.c] - g.lo[f.c]) / sp->surface_cell));
         f.wb = (g.hi[f.b] - g.lo[f.b]) / f.nb;
         f.wc = (g.hi[f.c] - g.lo[f.c]) / f.nc;
+        f.iwb = 1.0 / f.wb;
+        f.iwc = 1.0 / f.wc;
         f.off = off;
         off += f.nb * f.nc;
     }
@@ -741,6 +766,7 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
     for (int a = 0; a < 3; ++a) {
         g.ncr[a] = std::max(1, (int)std::floor((g.hi[a] - g.lo[a]) / sp->corr_cell));
         g.wcr[a] = (g.hi[a] - g.lo[a]) / g.ncr[a];
+        g.iwcr[a] = 1.0 / g.wcr[a];
         g.C *= g.ncr[a];
     }
     g.layer = sp->layer;
@@ -758,6 +784,13 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
     g.drain = sp->drain_faces;
     g.seed = sp->seed;
     g.add = sp->add_forces ? 1 : 0;
+    // a coarse particle outside the region grown by one largest diameter (Favre samples reach
+    // a diameter beyond the faces) touches no cell: bounds in coarse units, rounded outwards
+    const double grow = 2.0 * coarse->rmax[0];
+    for (int a = 0; a < 3; ++a) {
+        g.ulo[a] = (long long)std::floor((g.lo[a] - grow - g.loc[a]) / g.qc) - 2;
+        g.uhi[a] = (long long)std::ceil((g.hi[a] + grow - g.loc[a]) / g.qc) + 2;
+    }
     return DEM_OK;
 }
 
@@ -804,6 +837,12 @@ dem_status dem_coupler_create(dem_ctx* coarse, dem_ctx* fine, const dem_coupling
         return DEM_ERR_ARG;
     }
     coupler_layout(cp, (char*)ws);
+    if (cudaEventCreateWithFlags(&cp->ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        set_thread_error("could not create the coupler's CUDA event");
+        delete cp;
+        return DEM_ERR_CUDA;
+    }
     cp->rho_f = fine->hl[0].rho;
     // largest fine radius in fine units: from the fine level's r_max (cell width)
     cp->g.rmaxf_u = (int)std::llround(std::ceil(fine->rmax[0] / cp->g.qf));
@@ -837,13 +876,16 @@ dem_status dem_couple(dem_coupler* cp)
     dem_ctx* coarse = cp->c;
     if (coarse->status) return check_status(coarse);
     if (ctx->status) return check_status(ctx);
-    // both levels must be current and their lists valid; work on the fine level's stream
-    CU(cudaStreamSynchronize(coarse->stream));
+    // both levels must be current and their lists valid; work on the fine level's stream,
+    // after everything queued on the coarse level's (an event, no host wait)
     dem_status st = launch_rebuild(coarse, coarse->stream);
     if (st) return st;
     if ((st = launch_rebuild(ctx, ctx->stream))) return st;
-    CU(cudaStreamSynchronize(coarse->stream));
     cudaStream_t s = ctx->stream;
+    if (coarse->stream != s) {
+        CU(cudaEventRecord(cp->ready, coarse->stream));
+        CU(cudaStreamWaitEvent(s, cp->ready, 0));
+    }
     Geo g = cp->g;
     g.call = ++cp->calls;
     g.fresh_c = coarse->fresh ? 1 : 0;
@@ -866,10 +908,7 @@ dem_status dem_couple(dem_coupler* cp)
     CU(cudaMemcpyAsync(&D, ctx->dev.id, sizeof(InstD), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (ovf) return fail(ctx, DEM_ERR_CAPACITY, "inserted particles exceed the fine level's capacity");
-    ctx->count[0] = D.nid;
-    std::vector<long long> goff = {0, (long long)D.nid};
-    CU(cudaMemcpyAsync(ctx->dev.goff, goff.data(), sizeof(long long) * 2, cudaMemcpyHostToDevice, s));
-    CU(cudaStreamSynchronize(s));
+    ctx->count[0] = D.nid;                  // (the device-side offsets were updated by k_cp_append)
     return DEM_OK;
 }
 
@@ -964,6 +1003,7 @@ dem_status dem_coupler_read(dem_coupler* cp, int32_t field, double* dst, int64_t
 dem_status dem_coupler_destroy(dem_coupler* cp)
 {
     if (!cp) return DEM_ERR_ARG;
+    if (cp->ready) cudaEventDestroy(cp->ready);
     delete cp;   // touches neither context (they may already be gone)
     return DEM_OK;
 }

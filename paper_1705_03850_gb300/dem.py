@@ -402,7 +402,8 @@ class Coupler:
         rc = self.L.dem_couple(self.h)
         if rc:
             raise DemError(rc, self.L.dem_last_error(self.fine.h).decode())
-        self.fine.counts()
+        # the IDs handed out after the insertion (host-side count: no device read)
+        self.fine.counts_ = [int(self.fine.info(0)["n"])]
         return self
 
     def read(self, field):

@@ -236,3 +236,30 @@ def test_steady_drift_is_not_biased_by_the_position_grid():
     err = np.abs(d[:, 0]) / q
     assert err.max() < 6 * np.sqrt(steps * 0.25) + 2, err.max()        # plain rounding: up to 900 quanta
     assert np.abs(d[:, 1:]).max() == 0.0
+
+
+def test_column_of_1000_spheres_over_5000_steps():
+    # the FP64-oracle-size plain workload as stated (1,000 spheres on a jittered lattice in a
+    # 20 x 20 x 60 mm box, dt = 2e-6 s, 5,000 steps): exact positions while the column falls,
+    # then kinetic energy and mean height along the run within 2 % once contacts form
+    wl = workloads.column()
+    sim = dem.from_workload(wl)
+    o = oracle_sim(wl)
+    axis = np.array([[0.01, 0.01]])
+    done = 0
+    for k, upto in enumerate((500, 1000, 2000, 3000, 4000, 5000)):
+        sim.step(upto - done)
+        o.run(upto - done)
+        done = upto
+        x = sim.read(dem.POS)
+        if k == 0:
+            d = min_image(x - o.x, wl)
+            tol = np.maximum(1e-4 * 2 * wl.r[:, None], 64 * _ulp32(o.x))
+            assert (np.abs(d) <= tol).all(), np.abs(d).max()
+        ke_gpu = sim.observables(axis)[0, 0]
+        I = 0.4 * wl.m * wl.r ** 2
+        ke_orc = 0.5 * np.sum(wl.m[:, None] * o.v ** 2) + 0.5 * np.sum(I[:, None] * o.w ** 2)
+        assert ke_gpu == pytest.approx(ke_orc, rel=0.02), (upto, ke_gpu, ke_orc)
+        assert x[:, 2].mean() == pytest.approx(o.x[:, 2].mean(), rel=0.02)
+    st = sim.stats()
+    assert st["contacts"] + st["wall_contacts"] > 0      # the bottom of the column reached the floor

@@ -602,6 +602,33 @@ def run_coupled(args, dev, plain_value):
         st.sync()
         states.append([st.read(f, host=False) for f in (dem.POS, dem.VEL, dem.OMEGA, dem.RADIUS, dem.MASS)])
         st.close()
+    single = _coupled_flow(args, dev, lv, specs, states, args.coupled_intervals, profile=True)
+    # multi-rate: time steps scaled with the grain (4, 2, 1 x 1e-6 s), periods of 16 finest steps,
+    # about the same physical time as the single-rate run
+    lvm, specm = workloads.chute(u0=0.5, multirate=True, interval=16)
+    periods = max(1, round(args.coupled_intervals * 15 / 16))
+    multi = _coupled_flow(args, dev, lvm, specm, states, periods, profile=False)
+    value = single["value"]
+    line = dict(single)
+    line.update({"value": value, "unit": UNIT, "metric": "particle-steps/s summed over the coupled levels",
+                 "workload": "30-degree chute, 11 m periodic along the flow, 0.3 x 0.3 m section: level 0 d = 8 mm "
+                             "everywhere, level 1 d = 4 mm in a 0.70 m region, level 2 d = 2 mm in a 0.18 m region "
+                             "nested in it; plug flow 0.5 m/s at the start",
+                 "vs_plain": value / plain_value, "settle_steps": args.coupled_settle,
+                 "timing": "wall clock (coupling calls synchronise); level steps in CUDA graphs of one period",
+                 "multirate": dict(multi, speedup_in_simulated_time=single["wall_s_per_simulated_ms"] /
+                                   multi["wall_s_per_simulated_ms"],
+                                   what="dt 4e-6 / 2e-6 / 1e-6 s for the 8 / 4 / 2 mm levels (Sec. 3: the time "
+                                        "step may scale with the grain), coupling every 16 us")})
+    return line
+
+
+def _coupled_flow(args, dev, lv, specs, states, periods, profile):
+    """Timed run of a level hierarchy from settled states: particle-steps/s and wall time per
+    simulated millisecond."""
+    import torch
+
+    from paper_1705_03850_gb300 import dem, levels
     ctx = []
     for k, (wl, (x, v, w, r, m)) in enumerate(zip(lv, states)):
         cap = None if k == 0 else wl.n + 60_000
@@ -615,13 +642,13 @@ def run_coupled(args, dev, plain_value):
     torch.cuda.synchronize(dev)
     n0 = h.counts()
     st0 = [c.stats() for c in ctx]
-    I = args.coupled_intervals
     t_couple = 0.0
-    _profile(args, "coupled", True)
+    if profile:
+        _profile(args, "coupled", True)
     t0 = time.perf_counter()
-    for _ in range(I):
-        for c in ctx:
-            c.step(h.interval)
+    for _ in range(periods):
+        for c, n in zip(ctx, h.steps):
+            c.step(n)
         torch.cuda.synchronize(dev)
         tc = time.perf_counter()
         for c in ctx:
@@ -631,25 +658,21 @@ def run_coupled(args, dev, plain_value):
         t_couple += time.perf_counter() - tc
     torch.cuda.synchronize(dev)
     t = time.perf_counter() - t0
-    _profile(args, "coupled", False)
+    if profile:
+        _profile(args, "coupled", False)
     n1 = h.counts()
     st1 = [c.stats() for c in ctx]
     inserted = [int(c.counts()[1][0]) - wl.n for c, wl in zip(ctx[1:], lv[1:])]
     h.close()
     for c in ctx:
         c.close()
-    steps = I * h.interval
-    value = sum(0.5 * (a + b) for a, b in zip(n0, n1)) * steps / t
-    return {"value": value, "unit": UNIT, "metric": "particle-steps/s summed over the coupled levels",
-            "workload": "30-degree chute, 11 m periodic along the flow, 0.3 x 0.3 m section: level 0 d = 8 mm "
-                        "everywhere, level 1 d = 4 mm in a 0.70 m region, level 2 d = 2 mm in a 0.18 m region "
-                        "nested in it; plug flow 0.5 m/s at the start",
-            "particles_per_level_start": n0, "particles_per_level_end": n1,
-            "inserted_per_fine_level": inserted, "steps": steps, "coupling_interval": h.interval,
-            "seconds": t, "coupling_share": t_couple / t, "ms_per_step": t / steps * 1e3,
-            "rebuilds_per_level": [b["rebuilds"] - a["rebuilds"] for a, b in zip(st0, st1)],
-            "vs_plain": value / plain_value, "settle_steps": args.coupled_settle,
-            "timing": "wall clock (coupling calls synchronise); level steps in CUDA graphs of one interval"}
+    psteps = sum(0.5 * (a + b) * n * periods for a, b, n in zip(n0, n1, h.steps))
+    sim_ms = periods * h.period * 1e3
+    return {"value": psteps / t, "particles_per_level_start": n0, "particles_per_level_end": n1,
+            "inserted_per_fine_level": inserted, "periods": periods, "steps_per_period": h.steps,
+            "simulated_ms": sim_ms, "seconds": t, "wall_s_per_simulated_ms": t / sim_ms,
+            "coupling_share": t_couple / t, "ms_per_step": t / (periods * h.steps[-1]) * 1e3,
+            "rebuilds_per_level": [b["rebuilds"] - a["rebuilds"] for a, b in zip(st0, st1)]}
 
 
 def main():

@@ -133,7 +133,9 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(Dev d)
 // ================================================================ rebuild
 // Triggered per instance by the displacement bound (flag != 0).  Sequence:
 // clear counts -> bin (atomic slot in cell) -> scan -> scatter -> order each
-// cell by particle ID -> build lists, permute state, carry histories.
+// cell by particle ID -> count -> order the slots of each tile by contact count
+// (and copy positions and IDs in cell order) -> build lists, permute state,
+// carry histories -> finish.
 
 // Per-slot rebuild work runs on a persistent grid of TILE-thread blocks that
 // strides over the tiles and skips tiles of instances that are not rebuilding.

@@ -180,6 +180,7 @@ class DEM:
                                       ctypes.byref(h)), "create")
         self.h = h
         self.counts_ = [int(d.n) for d in descs]
+        self.dts = [float(d.dt) for d in descs]       # time step of each instance [s]
 
     # ------------------------------------------------------------------
     def _check(self, rc, what):

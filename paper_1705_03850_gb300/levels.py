@@ -5,7 +5,13 @@ level k and coupled to it by coupler k (level k its coarse side, level k + 1 its
 fine side).  A level in the middle is the fine side of one coupler and the
 coarse side of the next, so it takes the sum of both couplers' controller
 forces: every coupler runs in add mode on forces cleared at the start of each
-coupling interval.  All levels share one time step (no sub-cycling).
+coupling interval.
+
+Levels may run different time steps (multi-rate): the time step may grow with the
+coarse-graining ratio, since a coarser grain's contacts last longer (Sec. 3,
+runtimes).  All couplers exchange at one common period T; a level with time step
+dt_l advances T / dt_l steps per period (an integer), and coupler k counts its
+interval in steps of its fine level (T / dt_{k+1}).
 
 Host orchestration only: every step, measurement, controller and insertion
 runs in the library's kernels through the C ABI.
@@ -21,25 +27,33 @@ class Hierarchy:
     def __init__(self, levels, specs, steps_per_graph=True):
         if len(specs) != len(levels) - 1:
             raise ValueError("one coupling spec per pair of neighbouring levels")
-        intervals = {int(s["interval"]) for s in specs}
-        if len(intervals) != 1:
-            raise ValueError("all couplers must share one coupling interval")
-        self.interval = intervals.pop()
         self.levels = list(levels)
+        dts = [lv.dts[0] for lv in self.levels]
+        periods = [int(s["interval"]) * dts[k + 1] for k, s in enumerate(specs)]
+        self.period = periods[0]
+        if any(abs(p - self.period) > 1e-6 * self.period for p in periods):
+            raise ValueError("all couplers must exchange at one period (interval x fine time step)")
+        self.steps = []
+        for dt in dts:
+            n = int(round(self.period / dt))
+            if n < 1 or abs(n * dt - self.period) > 1e-6 * self.period:
+                raise ValueError(f"the coupling period {self.period:g} s is not a whole number of steps of {dt:g} s")
+            self.steps.append(n)
+        self.interval = self.steps[-1]          # steps of the finest level per period
         for lv in self.levels:
             lv.clear_external_force()
         self.couplers = [dem.Coupler(levels[k], levels[k + 1], **dict(s, add_forces=1)) for k, s in enumerate(specs)]
         if steps_per_graph:
-            for lv in self.levels:
-                lv.set_graph(self.interval)
+            for lv, n in zip(self.levels, self.steps):
+                lv.set_graph(n)
         self.calls = 0
 
     def advance(self, intervals=1):
-        """Run `intervals` coupling intervals: every level steps `interval` times, then the couplers
+        """Run `intervals` coupling periods: every level steps through one period, then the couplers
         measure, update their controllers, insert and remove, finest pair last."""
         for _ in range(intervals):
-            for lv in self.levels:
-                lv.step(self.interval)
+            for lv, n in zip(self.levels, self.steps):
+                lv.step(n)
             for lv in self.levels:
                 lv.clear_external_force()
             for cp in self.couplers:

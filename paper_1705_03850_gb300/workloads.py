@@ -315,7 +315,7 @@ def _fcc_fill(lo, hi, periodic, d, gap, z_top, rng, jitter=0.01e-3):
 def chute(length: float = 11.0, width: float = 0.3, height: float = 0.3, bed: float = 0.227,
           regions=((2.0, 0.70), (2.30, 0.18)), diameters=(8.0e-3, 4.0e-3, 2.0e-3), seed: int = 3,
           incline_deg: float = 30.0, u0: float = 0.5, dt: float = 1e-6, interval: int = 15,
-          clear: float = 1.0):
+          clear: float = 1.0, multirate: bool = False):
     """Three nested coarse-graining levels of an inclined chute (Sec. 2.3 coupling, one dt for all levels).
 
     Level 0 (d = 8 mm, alpha = 4 against the 2 mm base) fills the whole chute, periodic along the
@@ -324,7 +324,9 @@ def chute(length: float = 11.0, width: float = 0.3, height: float = 0.3, bed: fl
     regions[1] nested inside it.  Each level starts on an FCC lattice (gap 0.05 mm) that is to be
     settled under vertical gravity; the flow then runs with gravity tilted by incline_deg about y
     and every particle given u0 along x.  The lattice of a finer level starts `clear` diameters of
-    the level above it downstream of its feed face, room for the first inserted particles.  At the default sizes the levels hold about 2.0M, 1.0M and
+    the level above it downstream of its feed face, room for the first inserted particles.
+    multirate: level k runs dt times its grain ratio to the finest level (8 mm: 4 dt, 4 mm: 2 dt),
+    and `interval` counts steps of the finest level (a multiple of 4 keeps every level whole).  At the default sizes the levels hold about 2.0M, 1.0M and
     2.0M particles.  Returns (levels, specs): three Workloads (gravity already tilted, velocities
     zero) and the two coupling specs (level 0 -> 1, level 1 -> 2): feed through the upstream face,
     drain through the downstream one, cells of three coarse diameters."""
@@ -336,21 +338,23 @@ def chute(length: float = 11.0, width: float = 0.3, height: float = 0.3, bed: fl
     for x0, L in regions:
         boxes.append(((x0, 0.0, 0.0), (x0 + L, width, height), (False, True, False)))
     levels = []
+    ratio = [round(d / diameters[-1]) if multirate else 1 for d in diameters]
     for k, (d, (lo, hi, per)) in enumerate(zip(diameters, boxes)):
         flo = lo if k == 0 else (lo[0] + clear * diameters[k - 1], lo[1], lo[2])
         x = _fcc_fill(flo, hi, per, d, 0.05e-3, bed - d / 2, rng)
         n = x.shape[0]
         z = np.zeros((n, 3))
-        levels.append(_finish(f"chute_level{k}", x, z, z, np.full(n, d / 2), mat, lo, hi, per, dt, g, True,
-                              (0, 0, 0), 0.1 * d, 5000, diameter=d, u0=u0))
+        levels.append(_finish(f"chute_level{k}", x, z, z, np.full(n, d / 2), mat, lo, hi, per, dt * ratio[k], g,
+                              True, (0, 0, 0), 0.1 * d, 5000, diameter=d, u0=u0))
     specs = []
+    Tc = interval * float(f32(dt))
     for k in range(2):
         lo, hi, _ = boxes[k + 1]
         dc = diameters[k]
-        Tc = interval * float(f32(dt))
+        fine_dt = levels[k + 1].dt
         specs.append(dict(lo=tuple(qgrid(lo).tolist()), hi=tuple(qgrid(hi).tolist()), feed_faces=1 << 0,
                           drain_faces=1 << 1, surface_cell=3 * dc, layer=3 * dc, corr_cell=3 * dc,
-                          interval=interval, bins=16, alpha=diameters[k] / diameters[k + 1], kp=1.0,
-                          ki=1.0 / (10 * Tc), kv=0.5, mode=0, max_attempts=100, seed=seed * 1000 + k,
-                          mass_unit=1e-12, max_insert=256, dt=float(f32(dt))))
+                          interval=int(round(Tc / fine_dt)), bins=16, alpha=diameters[k] / diameters[k + 1],
+                          kp=1.0, ki=1.0 / (10 * Tc), kv=0.5, mode=0, max_attempts=100, seed=seed * 1000 + k,
+                          mass_unit=1e-12, max_insert=256, dt=fine_dt))
     return levels, specs

@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--batched-settle", type=int, default=8000, help="settling steps before the settled batched "
                     "measurement (0: skip it)")
     ap.add_argument("--no-coupled", action="store_true")
+    ap.add_argument("--no-nested", action="store_true")
+    ap.add_argument("--nested-periods", type=int, default=60, help="timed coupling periods of the five-level line")
     ap.add_argument("--profile-range", default="plain", choices=["plain", "batched", "adjoint", "coupled"],
                     help="which line's timed region `ncu --profile-from-start off` sees")
     ap.add_argument("--coupled-intervals", type=int, default=100, help="timed coupling intervals of 15 steps")
@@ -406,6 +408,7 @@ def run_ours(args):
     batched = run_batched(args, dev, value) if single and not args.no_batched else None
     adj = run_adjoint(args, dev, value) if single and not args.no_adjoint else None
     coupled = run_coupled(args, dev, value) if single and not args.no_coupled else None
+    nested = run_nested(args, dev, value) if single and not args.no_nested else None
 
     if rank != 0:
         return
@@ -436,6 +439,7 @@ def run_ours(args):
         "batched": batched,
         "adjoint": adj,
         "coupled": coupled,
+        "nested": nested,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
     }
@@ -589,19 +593,7 @@ def run_coupled(args, dev, plain_value):
 
     from paper_1705_03850_gb300 import dem, levels, workloads
     lv, specs = workloads.chute(u0=0.5)
-    states = []
-    for wl in lv:
-        sd = dem.desc_from_workload(wl)
-        sd.dt, sd.e = 5e-6, 0.5
-        sd.g[0], sd.g[1], sd.g[2] = 0.0, 0.0, -9.81
-        st = dem.DEM([sd], max_neighbors=24, device=dev)
-        st.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
-        st.step(1)
-        st.set_graph(50)
-        st.step(max(0, args.coupled_settle - 1))
-        st.sync()
-        states.append([st.read(f, host=False) for f in (dem.POS, dem.VEL, dem.OMEGA, dem.RADIUS, dem.MASS)])
-        st.close()
+    states = _settle_levels(args, dev, lv)
     single = _coupled_flow(args, dev, lv, specs, states, args.coupled_intervals, profile=True)
     # multi-rate: time steps scaled with the grain (4, 2, 1 x 1e-6 s), periods of 16 finest steps,
     # about the same physical time as the single-rate run
@@ -621,6 +613,47 @@ def run_coupled(args, dev, plain_value):
                                    what="dt 4e-6 / 2e-6 / 1e-6 s for the 8 / 4 / 2 mm levels (Sec. 3: the time "
                                         "step may scale with the grain), coupling every 16 us")})
     return line
+
+
+def _settle_levels(args, dev, lv):
+    """Each level settled on its own under vertical gravity (dt 5e-6 s, e 0.5; not timed)."""
+    from paper_1705_03850_gb300 import dem
+    states = []
+    for wl in lv:
+        sd = dem.desc_from_workload(wl)
+        sd.dt, sd.e = 5e-6, 0.5
+        sd.g[0], sd.g[1], sd.g[2] = 0.0, 0.0, -9.81
+        st = dem.DEM([sd], max_neighbors=24, device=dev)
+        st.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
+        st.step(1)
+        st.set_graph(50)
+        st.step(max(0, args.coupled_settle - 1))
+        st.sync()
+        states.append([st.read(f, host=False) for f in (dem.POS, dem.VEL, dem.OMEGA, dem.RADIUS, dem.MASS)])
+        st.close()
+    return states
+
+
+def run_nested(args, dev, plain_value):
+    """Five nested levels (alpha = 16, 8, 4, 2, 1; d = 16 .. 1 mm; filled volume quartered per
+    level, about 6.9M particles) of the 11 m chute, multi-rate, coupled every 16 us.  Beside the
+    measured wall time per simulated millisecond: the same physical time for the whole chute at
+    the finest resolution, estimated from the plain line's measured throughput."""
+    from paper_1705_03850_gb300 import workloads
+    lv, specs = workloads.nested_levels()
+    states = _settle_levels(args, dev, lv)
+    r = _coupled_flow(args, dev, lv, specs, states, args.nested_periods, profile=False)
+    # the whole chute at 1 mm: the finest level's particle density times the full length
+    n_full = lv[-1].n * (lv[0].hi[0] - lv[0].lo[0]) / (lv[-1].hi[0] - lv[-1].lo[0])
+    est_full = n_full * (1e-3 / lv[-1].dt) / plain_value        # wall seconds per simulated ms
+    r.update({"workload": "11 m chute, five levels d = 16, 8, 4, 2, 1 mm in nested regions of 11, 2.75, 0.69, "
+                          "0.17, 0.043 m (cross-section kept), time steps 16, 8, 4, 2, 1 us",
+              "unit": UNIT, "single_level_fine_particles_estimate": n_full,
+              "single_level_fine_wall_s_per_simulated_ms_estimate": est_full,
+              "speedup_estimate": est_full / r["wall_s_per_simulated_ms"],
+              "estimate": "whole chute at d = 1 mm (finest level's density), stepped at the plain line's measured "
+                          "particle-steps/s; an extrapolation, not a run"})
+    return r
 
 
 def _coupled_flow(args, dev, lv, specs, states, periods, profile):

@@ -348,7 +348,7 @@ def chute(length: float = 11.0, width: float = 0.3, height: float = 0.3, bed: fl
                               True, (0, 0, 0), 0.1 * d, 5000, diameter=d, u0=u0))
     specs = []
     Tc = interval * float(f32(dt))
-    for k in range(2):
+    for k in range(len(diameters) - 1):
         lo, hi, _ = boxes[k + 1]
         dc = diameters[k]
         fine_dt = levels[k + 1].dt
@@ -358,3 +358,22 @@ def chute(length: float = 11.0, width: float = 0.3, height: float = 0.3, bed: fl
                           kp=1.0, ki=1.0 / (10 * Tc), kv=0.5, mode=0, max_attempts=100, seed=seed * 1000 + k,
                           mass_unit=1e-12, max_insert=256, dt=fine_dt))
     return levels, specs
+
+
+def nested_levels(levels: int = 5, d_fine: float = 1.0e-3, length: float = 11.0, width: float = 0.3,
+                  height: float = 0.3, bed: float = 0.227, start: float = 2.0, seed: int = 6, u0: float = 0.5,
+                  dt: float = 1e-6, multirate: bool = True):
+    """Recursive nesting in the manner of the paper's projection (Sec. 3, runtimes): `levels`
+    coarse-graining levels with alpha_l = 2^(l-1) (the coarsest first: d = 2^(levels-1) d_fine ...
+    d_fine), each embedded in the next coarser one with a quarter of its filled volume (the
+    region length quartered, the cross-section kept), so that each finer level holds about twice
+    the particles of the coarser one.  Built on `chute` (30-degree chute, periodic along the flow);
+    multi-rate by default, coupling every 16 finest steps."""
+    diameters = tuple(d_fine * 2.0 ** (levels - 1 - k) for k in range(levels))
+    regions, x0, L = [], start, length
+    for k in range(1, levels):
+        L = L / 4.0
+        regions.append((x0, L))
+        x0 = x0 + 0.25 * L            # the next region starts a quarter into this one
+    return chute(length=length, width=width, height=height, bed=bed, regions=tuple(regions), diameters=diameters,
+                 seed=seed, u0=u0, dt=dt, interval=16, multirate=multirate)

@@ -354,6 +354,17 @@ dem_status dem_clear_external_force(dem_ctx *ctx);
  * return NaN for them already. */
 dem_status dem_counts(dem_ctx *ctx, int64_t *live, int64_t *ids);
 
+/* Volume-averaged fields of instance k on a uniform grid of n[0] x n[1] x n[2] cubic cells of
+ * edge h [m] from lo[3] (cell (i, j, l) spans lo + h (i, j, l) .. lo + h (i+1, j+1, l+1)):
+ * out (device memory, float64, 5 values per cell, x fastest) = {solid volume fraction
+ * (volume of the particles whose centre lies in the cell over the cell volume), mass [kg],
+ * mass-weighted (Favre) velocity [m/s] (0 in empty cells)}, at the current step.  The
+ * paper evaluates output at any location from the finest level available there (Sec. 2.3);
+ * a caller composes that from these per-level grids (levels.py does).  out_len must be
+ * 5 n[0] n[1] n[2].  Asynchronous on the context's stream. */
+dem_status dem_grid_fields(dem_ctx *ctx, int32_t k, const double lo[3], double h, const int32_t n[3], double *out,
+                           int64_t out_len);
+
 /* Last error message of the context; with ctx == NULL, the last configuration
  * error (dem_query_workspace / dem_create) of the calling thread.  Never NULL. */
 const char *dem_last_error(const dem_ctx *ctx);

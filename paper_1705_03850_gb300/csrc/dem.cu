@@ -1762,6 +1762,47 @@ namespace cgdem {
 void set_thread_error(const std::string& msg) { g_cfg_err = msg; }
 }  // namespace cgdem
 
+// ============================================================== grid fields
+// Volume averages of one instance on a uniform grid: per cell the solid volume of the
+// particles whose centres lie in it, their mass and momentum (velocities at the current
+// step, as reconstructed by the read-out evaluation); particles marked for removal are left out.
+namespace {
+__global__ void __launch_bounds__(256) k_grid_sums(Dev d, int k, const HostInstLo* __restrict__ hl, double lx, double ly,
+                                                   double lz, double h, int n0, int n1, int n2, double* __restrict__ out)
+{
+    const InstC& c = d.ic[k];
+    const InstD D = d.id[k];
+    const double q = hl[k].q;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.n; i += gridDim.x * blockDim.x) {
+        const int s = c.slot0 + i;
+        if (__float_as_uint(d.vel[D.cur][s].w) & GONE_BIT) continue;
+        const int4 P = d.pos[D.cur][s];
+        const long long ix = (long long)floor((hl[k].lo[0] + (double)P.x * q - lx) / h);
+        const long long iy = (long long)floor((hl[k].lo[1] + (double)P.y * q - ly) / h);
+        const long long iz = (long long)floor((hl[k].lo[2] + (double)P.z * q - lz) / h);
+        if (ix < 0 || iy < 0 || iz < 0 || ix >= n0 || iy >= n1 || iz >= n2) continue;
+        double* o = out + 5 * ((iz * n1 + iy) * (long long)n0 + ix);
+        const double m = d.omg[D.cur][s].w, r = (double)P.w * q;
+        const float4 v = d.outV[s];
+        atomicAdd(o, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
+        atomicAdd(o + 1, m);
+        atomicAdd(o + 2, m * v.x);
+        atomicAdd(o + 3, m * v.y);
+        atomicAdd(o + 4, m * v.z);
+    }
+}
+
+__global__ void k_grid_finish(double* __restrict__ out, long long ncell, double cellvol)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell; i += (long long)gridDim.x * blockDim.x) {
+        double* o = out + 5 * i;
+        const double m = o[1];
+        o[0] /= cellvol;
+        for (int a = 0; a < 3; ++a) o[2 + a] = m > 0.0 ? o[2 + a] / m : 0.0;
+    }
+}
+}  // namespace
+
 // ================================================================== C ABI
 
 extern "C" {
@@ -2102,6 +2143,28 @@ dem_status dem_graph_step_kernel_ms(dem_ctx* ctx, double* total_ms, int32_t* cou
     }
     *total_ms = t;
     *count = (int32_t)ctx->ev0.size();
+    return DEM_OK;
+}
+
+dem_status dem_grid_fields(dem_ctx* ctx, int32_t k, const double lo[3], double h, const int32_t n[3], double* out,
+                           int64_t out_len)
+{
+    if (!ctx || !lo || !n || !out) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    if (k < 0 || k >= ctx->B) return fail(ctx, DEM_ERR_ARG, "no such instance");
+    if (!(h > 0.0) || n[0] < 1 || n[1] < 1 || n[2] < 1) return fail(ctx, DEM_ERR_ARG, "empty grid");
+    const long long ncell = (long long)n[0] * n[1] * n[2];
+    if (out_len != 5 * ncell) return fail(ctx, DEM_ERR_ARG, "out must hold 5 values per cell");
+    if (!is_device_ptr(out)) return fail(ctx, DEM_ERR_ARG, "out must be device memory");
+    if (!ctx->have_state) return fail(ctx, DEM_ERR_STATE, "write the state first");
+    dem_status st = launch_eval(ctx);
+    if (st) return st;
+    CU(cudaMemsetAsync(out, 0, sizeof(double) * 5 * ncell, ctx->stream));
+    k_grid_sums<<<ctx->grid_rb, 256, 0, ctx->stream>>>(ctx->dev, k, ctx->d_hl, lo[0], lo[1], lo[2], h, n[0], n[1],
+                                                       n[2], out);
+    CU(cudaGetLastError());
+    k_grid_finish<<<nblk(ncell, 256) > 4096 ? 4096 : nblk(ncell, 256), 256, 0, ctx->stream>>>(out, ncell, h * h * h);
+    CU(cudaGetLastError());
     return DEM_OK;
 }
 

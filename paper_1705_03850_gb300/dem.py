@@ -105,6 +105,7 @@ def lib():
         "dem_coupler_destroy": [vp],
         "dem_counts": [vp, vp, vp],
         "dem_clear_external_force": [vp],
+        "dem_grid_fields": [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.POINTER(i32), vp, i64],
         "dem_neighbor_counts_noalloc": [vp, vp, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i32), ctypes.c_double, ctypes.c_double, vp, vp],
     }
@@ -124,7 +125,7 @@ def exported_symbols():
             "dem_set_graph", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
             "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material",
             "dem_coupler_workspace", "dem_coupler_create", "dem_couple", "dem_coupler_read", "dem_coupler_destroy",
-            "dem_counts", "dem_clear_external_force", "dem_last_error"]
+            "dem_counts", "dem_clear_external_force", "dem_grid_fields", "dem_last_error"]
 
 
 def desc(*, n, lo, hi, periodic, dt, skin, r_max, E, nu, e, mu, rho, g=(0, 0, 0), floor=True,
@@ -328,6 +329,17 @@ class DEM:
                     "counts")
         self.counts_ = [int(x) for x in ids]
         return live, ids
+
+    def grid_fields(self, lo, h, n, k=0):
+        """(n2, n1, n0, 5) CUDA tensor: solid volume fraction, mass, Favre velocity per cell."""
+        torch = self.torch
+        n = [int(v) for v in n]
+        out = torch.empty((n[2], n[1], n[0], 5), dtype=torch.float64, device=self.device)
+        lo3 = (ctypes.c_double * 3)(*[float(v) for v in lo])
+        n3 = (ctypes.c_int32 * 3)(*n)
+        self._check(self.L.dem_grid_fields(self.h, int(k), lo3, float(h), n3, ctypes.c_void_p(out.data_ptr()),
+                                           out.numel()), "grid fields")
+        return out
 
     def clear_external_force(self):
         self._check(self.L.dem_clear_external_force(self.h), "clear external force")

@@ -61,6 +61,27 @@ class Hierarchy:
             self.calls += 1
         return self
 
+    def fields(self, lo, h, n):
+        """Output fields on a uniform grid evaluated at the highest resolution available (Sec. 2.3):
+        each cell takes the volume fraction, mass and Favre velocity of the finest level whose
+        coupling region holds the cell's centre (level 0 elsewhere).  (n2, n1, n0, 5) CUDA tensor
+        and the (n2, n1, n0) index of the level used."""
+        import torch
+        per = [lv.grid_fields(lo, h, n) for lv in self.levels]
+        dev = per[0].device
+        ax = [torch.arange(n[a], dtype=torch.float64, device=dev) * h + lo[a] + 0.5 * h for a in range(3)]
+        zc, yc, xc = torch.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        which = torch.zeros(zc.shape, dtype=torch.int64, device=dev)
+        for k, cp in enumerate(self.couplers):
+            sp = cp.spec
+            inside = ((xc >= sp.lo[0]) & (xc < sp.hi[0]) & (yc >= sp.lo[1]) & (yc < sp.hi[1]) &
+                      (zc >= sp.lo[2]) & (zc < sp.hi[2]))
+            which = torch.where(inside, torch.full_like(which, k + 1), which)
+        out = torch.zeros_like(per[0])
+        for k, f in enumerate(per):
+            out = torch.where((which == k)[..., None], f, out)
+        return out, which
+
     def counts(self):
         """Live particles per level."""
         return [int(lv.counts()[0][0]) for lv in self.levels]

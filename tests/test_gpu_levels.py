@@ -126,3 +126,29 @@ def test_five_nested_levels_multirate():
         assert np.array_equal(np.isnan(xa), np.isnan(xb))
         assert np.array_equal(np.nan_to_num(xa), np.nan_to_num(xb))
         assert np.isfinite(xa[~np.isnan(xa[:, 0])]).all()
+
+
+def test_output_fields_at_the_highest_resolution_available():
+    # per-level grid fields equal the plain definition (oracle) at the read-back state, and the
+    # composed fields take the finest level inside each region, the coarse level outside
+    import oracle
+    _, specs, h = _hierarchy(True, u0=2.0)
+    h.advance(3)
+    lo, hcell, n = (0.0, 0.0, 0.0), 0.01, (30, 6, 5)
+    for lv in h.levels:
+        g = lv.grid_fields(lo, hcell, n).cpu().numpy()
+        x, v, r, m = lv.read(dem.POS), lv.read(dem.VEL), lv.read(dem.RADIUS), lv.read(dem.MASS)
+        live = ~np.isnan(x[:, 0])
+        ref = oracle.grid_fields(x[live], v[live], r[live], m[live], lo, hcell, n)
+        assert np.allclose(g[..., :2], ref[..., :2], rtol=1e-12, atol=0)
+        assert np.allclose(g[..., 2:], ref[..., 2:], rtol=1e-9, atol=1e-12)
+    f, which = h.fields(lo, hcell, n)
+    f, which = f.cpu().numpy(), which.cpu().numpy()
+    per = [lv.grid_fields(lo, hcell, n).cpu().numpy() for lv in h.levels]
+    xc = lo[0] + (np.arange(n[0]) + 0.5) * hcell
+    inner = (xc >= specs[1]["lo"][0]) & (xc < specs[1]["hi"][0])
+    assert inner.any() and (~inner).any()
+    assert np.array_equal(f[:, :, inner], per[2][:, :, inner])
+    outer = (xc < specs[0]["lo"][0]) | (xc >= specs[0]["hi"][0])
+    assert np.array_equal(f[:, :, outer], per[0][:, :, outer])
+    assert set(np.unique(which).tolist()) == {0, 1, 2}

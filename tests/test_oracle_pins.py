@@ -361,3 +361,21 @@ def test_results_do_not_depend_on_storage_order():
     assert np.array_equal(ha, hb_) and np.array_equal(hb, hbb)
     assert np.allclose(hxa, hxb, rtol=1e-8, atol=1e-18)
 
+
+
+# ------------------------------------------------------ output grid fields
+
+def test_grid_fields_definition():
+    # one sphere: its volume over the cell volume, its mass and velocity, in the cell holding its
+    # centre; two spheres in one cell: Favre velocity = momentum over mass; sums conserve mass
+    x = np.array([[0.0105, 0.0023, 0.0047], [0.0101, 0.0021, 0.0049], [0.03, 0.001, 0.001]])
+    v = np.array([[1.0, 0.0, -2.0], [3.0, 0.5, 0.0], [9.0, 9.0, 9.0]])
+    r = np.array([1e-3, 2e-3, 1e-3])
+    m = np.array([2.0, 6.0, 1.0])
+    f = oracle.grid_fields(x, v, r, m, (0.0, 0.0, 0.0), 0.005, (4, 2, 2))
+    c = f[0, 0, 2]
+    assert c[0] == pytest.approx(4.0 / 3.0 * math.pi * (1e-9 + 8e-9) / 0.005 ** 3, rel=1e-14)
+    assert c[1] == 8.0
+    assert np.allclose(c[2:5], (2.0 * v[0] + 6.0 * v[1]) / 8.0, rtol=1e-15)
+    assert f[..., 1].sum() == 8.0                       # the third sphere lies outside the grid
+    assert np.count_nonzero(f[..., 1]) == 1

@@ -38,7 +38,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lib = None
 
-NPARAM = 24
+NPARAM = 43
 
 
 def build(force: bool = False) -> str:
@@ -103,8 +103,10 @@ def _i32(a):
 
 def make_params(*, E, nu, e, mu, dt, g=(0.0, 0.0, 0.0), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
                 periodic=(False, False, False), mu_wall=None, floor=False, floor_z=0.0,
-                floor_v=(0.0, 0.0, 0.0), clamp_fn=False) -> np.ndarray:
-    """The oracle's flat parameter block (layout documented in dem_oracle.c)."""
+                floor_v=(0.0, 0.0, 0.0), clamp_fn=False, walls=None) -> np.ndarray:
+    """The oracle's flat parameter block (layout documented in dem_oracle.c).  walls: None or
+    dict(axis=(x, y), points=[(rho, z), ...]) -- axisymmetric walls, the surface of revolution
+    of the polyline about the vertical axis (at most 8 points)."""
     P = np.zeros(NPARAM, dtype=np.float64)
     P[0], P[1], P[2], P[3] = E, nu, e, mu
     P[4] = mu if mu_wall is None else mu_wall
@@ -117,6 +119,13 @@ def make_params(*, E, nu, e, mu, dt, g=(0.0, 0.0, 0.0), lo=(0.0, 0.0, 0.0), hi=(
     P[19] = floor_z
     P[20:23] = floor_v
     P[23] = 1.0 if clamp_fn else 0.0
+    if walls is not None:
+        pts = np.asarray(walls["points"], dtype=np.float64).reshape(-1, 2)
+        if not 2 <= len(pts) <= 8:
+            raise ValueError("2 to 8 wall profile points")
+        P[24] = len(pts)
+        P[25:27] = walls["axis"]
+        P[27:27 + 2 * len(pts)] = pts.ravel()
     return P
 
 

@@ -35,6 +35,7 @@
  *   0 E   1 nu   2 e   3 mu   4 mu_wall   5 dt   6..8 g   9..11 lo
  *   12..14 hi   15..17 periodic flags   18 floor_on   19 floor_z
  *   20..22 floor velocity   23 clamp_fn (1: no tensile normal force)
+ *   24 wall profile points (0: none)   25..26 wall axis (x, y)   27..42 profile (rho, z) pairs
  */
 #include <math.h>
 #include <stdint.h>

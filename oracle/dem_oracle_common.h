@@ -4,6 +4,8 @@
  *   0 E   1 nu   2 e   3 mu   4 mu_wall   5 dt   6..8 g   9..11 lo
  *   12..14 hi   15..17 periodic flags   18 floor_on   19 floor_z
  *   20..22 floor velocity   23 clamp_fn (1: no tensile normal force)
+ *   24 number of wall profile points (0: no walls)   25..26 wall axis (x, y)
+ *   27..42 up to 8 profile points (rho, z) of the axisymmetric walls
  */
 #ifndef DEM_ORACLE_COMMON_H
 #define DEM_ORACLE_COMMON_H
@@ -23,6 +25,11 @@
 #define P_FLOORZ 19
 #define P_FLOORV 20
 #define P_CLAMP 23
+#define P_NWP 24
+#define P_WAX 25
+#define P_WAY 26
+#define P_WP 27
+#define ORC_MAXWP 8
 
 #define ORC_PI 3.14159265358979323846
 

@@ -218,7 +218,7 @@ static int64_t FN(eval_m)(const double *P, const FN(mat_t) *M, int64_t n, const 
         free(xr);
     }
 #endif
-    int64_t nrec_cap = np + n + 1;
+    int64_t nrec_cap = np + (int64_t)ORC_MAXWP * n + n + 1;
     FN(hrec_t) *rec = (FN(hrec_t) *)malloc(sizeof(FN(hrec_t)) * nrec_cap);
     int64_t nrec = 0;
 
@@ -289,6 +289,52 @@ static int64_t FN(eval_m)(const double *P, const FN(mat_t) *M, int64_t n, const 
             }
             if (fabs_out) fabs_out[i] += sqrt(RE(fa[0]) * RE(fa[0]) + RE(fa[1]) * RE(fa[1]) + RE(fa[2]) * RE(fa[2]));
             rec[nrec].a = id[i]; rec[nrec].b = -1;
+            memcpy(rec[nrec].xi, xi, sizeof(xi));
+            rec[nrec].slip = slip;
+            ++nrec;
+        }
+    }
+
+    /* Axisymmetric walls: the surface of revolution of the polyline (rho_k, z_k) about the
+     * vertical axis through (P_WAX, P_WAY), one wall per segment (infinite radius and mass,
+     * particle material, wall friction).  A particle touches segment k where its distance to
+     * the segment, in its own azimuthal half-plane, is below its radius (end points included:
+     * a free rim is an edge contact); n points from the contact point to the centre.  History
+     * keyed (i, -2 - k). */
+    const int nwp = (int)P[P_NWP];
+    for (int64_t i = 0; nwp >= 2 && i < n; ++i) {
+        const R ex = x[3 * i] - P[P_WAX], ey = x[3 * i + 1] - P[P_WAY];
+        const R rho = RSQRT(ex * ex + ey * ey);
+        R erx = 1.0, ery = 0.0;
+        if (RE(rho) > 1e-12) { erx = ex / rho; ery = ey / rho; }
+        const R z = x[3 * i + 2];
+        for (int k = 0; k + 1 < nwp; ++k) {
+            const double r0 = P[P_WP + 2 * k], z0 = P[P_WP + 2 * k + 1];
+            const double dr = P[P_WP + 2 * k + 2] - r0, dz = P[P_WP + 2 * k + 3] - z0;
+            R t = ((rho - r0) * dr + (z - z0) * dz) / (dr * dr + dz * dz);
+            if (RE(t) < 0.0) t = 0.0;
+            else if (RE(t) > 1.0) t = 1.0;
+            const R drho = rho - (r0 + t * dr), dzz = z - (z0 + t * dz);
+            const R dist = RSQRT(drho * drho + dzz * dzz);
+            const R delta = r[i] - dist;
+            if (!(RE(delta) > 0.0)) continue;
+            const R nv[3] = {drho / dist * erx, drho / dist * ery, dzz / dist};
+            const R zero3[3] = {0.0, 0.0, 0.0};
+            R xi[3] = {0.0, 0.0, 0.0};
+            const R *old = FN(find_hist)(nh, ha, hb, hxi, id[i], -2 - k);
+            if (old) { xi[0] = old[0]; xi[1] = old[1]; xi[2] = old[2]; }
+            R fa[3], ft[3];
+            int slip = FN(contact_law)(P, M, r[i], 0.0, m[i], 0.0, 1, delta, nv, v + 3 * i, zero3, w + 3 * i, zero3,
+                                       xi, dt_hist, M->mu_w, fa, ft);
+            R ca[3] = {-r[i] * nv[0], -r[i] * nv[1], -r[i] * nv[2]};
+            R ta[3];
+            FN(cross3)(ca, ft, ta);
+            for (int q = 0; q < 3; ++q) {
+                F[3 * i + q] += fa[q];
+                T[3 * i + q] += ta[q];
+            }
+            if (fabs_out) fabs_out[i] += sqrt(RE(fa[0]) * RE(fa[0]) + RE(fa[1]) * RE(fa[1]) + RE(fa[2]) * RE(fa[2]));
+            rec[nrec].a = id[i]; rec[nrec].b = -2 - k;
             memcpy(rec[nrec].xi, xi, sizeof(xi));
             rec[nrec].slip = slip;
             ++nrec;

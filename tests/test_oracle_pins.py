@@ -379,3 +379,60 @@ def test_grid_fields_definition():
     assert np.allclose(c[2:5], (2.0 * v[0] + 6.0 * v[1]) / 8.0, rtol=1e-15)
     assert f[..., 1].sum() == 8.0                       # the third sphere lies outside the grid
     assert np.count_nonzero(f[..., 1]) == 1
+
+
+# ------------------------------------------------------- axisymmetric walls
+
+def _wall_params(points, floor=False, g=(0.0, 0.0, 0.0), mu_wall=0.3):
+    return oracle.make_params(E=1e7, nu=0.25, e=0.6, mu=0.4, mu_wall=mu_wall, dt=1e-6, g=g, lo=(-0.2, -0.2, -0.1),
+                              hi=(0.2, 0.2, 0.5), periodic=(False, False, False), floor=floor,
+                              walls=None if points is None else dict(axis=(0.01, -0.02), points=points))
+
+
+def _one(P, x, v=(0, 0, 0), w=(0, 0, 0), r=1e-3):
+    m = 2500.0 * 4.0 / 3.0 * math.pi * r ** 3
+    s = oracle.Sim(P, np.array([x], dtype=float), np.array([v], dtype=float), np.array([w], dtype=float),
+                   np.array([r]), np.array([m]))
+    return s, m
+
+
+def test_wall_contacts_of_a_cylinder_a_cone_and_its_rim():
+    r, d0 = 1e-3, 3e-6
+    pts = [(0.02, 0.0), (0.135, 0.2), (0.135, 0.4)]
+    P = _wall_params(pts)
+    kn = lambda delta: oracle.pair_coeffs(P, r, 0.0, 2500.0 * 4 / 3 * math.pi * r ** 3, 0.0, delta, wall=True)["kn"]
+    ax = np.array([0.01, -0.02, 0.0])
+    # cylinder: centre at radius 0.135 - r + d0 in direction e (unit, in the x-y plane), z = 0.3
+    e = np.array([0.6, 0.8, 0.0])
+    s, _ = _one(P, ax + (0.135 - r + d0) * e + np.array([0, 0, 0.3]))
+    F, T, hist, _ = s.evaluate()
+    assert np.allclose(F[0], -kn(d0) * d0 * e, rtol=1e-9, atol=1e-18)       # (delta from a difference of radii)
+    assert np.abs(T).max() == 0.0 and list(hist[1]) == [-3]          # segment 1
+    # cone (segment 0) at mid height: inward normal (-dz, dr) / |.| in the (rho, z) half-plane
+    dr, dz = 0.115, 0.2
+    L = math.hypot(dr, dz)
+    nr, nz = -dz / L, dr / L
+    rho, z = 0.02 + 0.5 * dr + (r - d0) * nr, 0.1 + (r - d0) * nz
+    s, _ = _one(P, ax + rho * e + np.array([0, 0, z]))
+    F, T, hist, _ = s.evaluate()
+    assert np.allclose(F[0], kn(d0) * d0 * np.array([nr * e[0], nr * e[1], nz]), rtol=1e-9, atol=1e-18)
+    assert list(hist[1]) == [-2]
+    # the free rim at the orifice: a centre below it, the normal from the rim point to the centre
+    u = np.array([0.3, -0.95393920141694566])           # unit, pointing down and inward in (rho, z)
+    rho, z = 0.02 + (r - d0) * u[0], (r - d0) * u[1]
+    s, _ = _one(P, ax + rho * e + np.array([0, 0, z]))
+    F, T, hist, _ = s.evaluate()
+    assert np.allclose(F[0], kn(d0) * d0 * np.array([u[0] * e[0], u[0] * e[1], u[1]]), rtol=1e-9, atol=1e-18)
+
+
+def test_a_flat_wall_profile_acts_as_the_floor():
+    # a horizontal profile segment under the sphere is the floor plane: the same trajectory for a
+    # sphere that lands, slides and spins (normal, tangential history, friction and torque)
+    x, v, w = (0.05, 0.03, 0.99e-3), (0.2, 0.05, -0.1), (30.0, -50.0, 10.0)
+    a, _ = _one(_wall_params(None, floor=True, g=(0, 0, -9.81)), x, v, w)
+    b, _ = _one(_wall_params([(0.0, 0.0), (0.3, 0.0)], g=(0, 0, -9.81)), x, v, w)
+    a.run(3000)
+    b.run(3000)
+    assert np.allclose(a.x, b.x, rtol=0, atol=1e-15)
+    assert np.allclose(a.v, b.v, rtol=1e-12, atol=1e-15)
+    assert np.allclose(a.w, b.w, rtol=1e-12, atol=1e-12)

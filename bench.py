@@ -55,6 +55,7 @@ def _args():
                     "measurement (0: skip it)")
     ap.add_argument("--no-coupled", action="store_true")
     ap.add_argument("--no-nested", action="store_true")
+    ap.add_argument("--silo", action="store_true", help="add the silo discharge validation (alpha 1 and 2, ~70 s)")
     ap.add_argument("--nested-periods", type=int, default=60, help="timed coupling periods of the five-level line")
     ap.add_argument("--profile-range", default="plain", choices=["plain", "batched", "adjoint", "coupled"],
                     help="which line's timed region `ncu --profile-from-start off` sees")
@@ -409,6 +410,10 @@ def run_ours(args):
     adj = run_adjoint(args, dev, value) if single and not args.no_adjoint else None
     coupled = run_coupled(args, dev, value) if single and not args.no_coupled else None
     nested = run_nested(args, dev, value) if single and not args.no_nested else None
+    silo = None
+    if single and args.silo:
+        from paper_1705_03850_gb300 import silo as silo_mod
+        silo = [silo_mod.run(a, device=dev) for a in (1, 2)]
 
     if rank != 0:
         return
@@ -440,6 +445,7 @@ def run_ours(args):
         "adjoint": adj,
         "coupled": coupled,
         "nested": nested,
+        "silo": silo,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
     }

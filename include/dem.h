@@ -365,6 +365,31 @@ dem_status dem_counts(dem_ctx *ctx, int64_t *live, int64_t *ids);
 dem_status dem_grid_fields(dem_ctx *ctx, int32_t k, const double lo[3], double h, const int32_t n[3], double *out,
                            int64_t out_len);
 
+/* Axisymmetric walls of instance k, for vessels such as the silo of Sec. 3 (a cone below a
+ * cylinder): the surface of revolution of the polyline points[2 i] = rho_i [m] (>= 0),
+ * points[2 i + 1] = z_i [m], i < npts, about the vertical axis through (axis[0], axis[1]) [m].
+ * Every segment is a wall of its own, end points included (a free rim is an edge contact): a
+ * particle touches segment i where its distance to the segment, measured in the particle's
+ * own azimuthal half-plane, is below its radius.  Each contact is a particle-wall contact of
+ * Eqs. 3-6 (the wall at rest with infinite radius and mass, the particle's material, the wall
+ * friction mu_wall) with the normal from the nearest point of the segment to the centre.  A
+ * segment from rho = 0 is a disk: (0, z_o) - (r_o, z_o) closes an orifice of radius r_o.
+ * npts = 0 removes the walls; otherwise 2 <= npts <= 8 and consecutive points differ.  The
+ * tangential overlaps of up to two segment contacts per particle are kept (a third
+ * simultaneous one, which needs two kinks within a particle diameter, starts from zero each
+ * step); setting the walls clears them.
+ * Particles whose centre falls below z_remove [m] at a step are removed at that step (their
+ * IDs are not reused); z_remove = -INFINITY removes none.  Their number and mass accumulate in
+ * dem_wall_removed.  The walls and the removal apply to dem_step, graphs and the read-out of
+ * velocities and forces; dem_rollout_forward refuses a context that has either
+ * (DEM_ERR_STATE).  Synchronises the context's stream. */
+dem_status dem_set_walls(dem_ctx *ctx, int32_t k, const double *axis, int32_t npts, const double *points,
+                         double z_remove);
+
+/* Particles and mass [kg] removed below z_remove in instance k since the context was
+ * created: out[0] = count, out[1] = mass (host array of 2; synchronises). */
+dem_status dem_wall_removed(dem_ctx *ctx, int32_t k, double *out);
+
 /* Last error message of the context; with ctx == NULL, the last configuration
  * error (dem_query_workspace / dem_create) of the calling thread.  Never NULL. */
 const char *dem_last_error(const dem_ctx *ctx);

@@ -8,6 +8,7 @@
 #include "dem_contact.cuh"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -417,6 +418,11 @@ __device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, 
     d.hmask[nlp][s] = nhm;
     if (D.fext) d.fext[nlp][s] = d.fext[lp][old];      // held until overwritten, even across state writes
     d.whist[nlp][s] = D.flag == 2 ? make_float4(0.f, 0.f, 0.f, 0.f) : d.whist[lp][old];
+    if (c.nwp >= 2) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.wseg[nlp][s] = D.flag == 2 ? z : d.wseg[lp][old];
+        d.wseg[nlp][ncap + s] = D.flag == 2 ? z : d.wseg[lp][ncap + old];
+    }
 }
 
 __global__ void __launch_bounds__(RB_T, 16) k_rb_build(Dev d)
@@ -506,7 +512,77 @@ __device__ __forceinline__ unsigned mix32(unsigned x)
     return x;
 }
 
+// Axisymmetric walls: the surface of revolution of the polyline (rho_i, z_i) about a vertical
+// axis, one wall per segment with its end points included (a free rim is an edge contact).
+// Each touching segment is a particle-wall contact of Eqs. 3-6 at rest, with the wall
+// friction; n runs from the nearest point of the segment, in the particle's azimuthal
+// half-plane, to the centre.  Distances are taken in double from the exact integer position
+// (the overlap is a small difference of two lengths), for the segments a float pre-test
+// leaves within a 1/64 radius of contact.  The tangential overlaps of up to two segment
+// contacts are kept per particle, tagged with the segment; MODE 0 stores them.
 template <int MODE>
+__device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int s, int lp, int4 P, float r, float m,
+                                             V3 vme, V3 wme, float dt_hist, V3& F, V3& Tq)
+{
+    const float exf = (float)(P.x - c.waxi) - c.waxf, eyf = (float)(P.y - c.wayi) - c.wayf, zf = (float)P.z;
+    const float rhof = sqrtf(exf * exf + eyf * eyf);
+    const float tol = 1e-6f * (rhof + fabsf(zf) + c.wmag) + 4.f;
+    const float lim = (float)P.w * (1.f + 1.f / 64.f) + tol;
+    unsigned nearm = 0u;
+    for (int k = 0; k + 1 < c.nwp; ++k) {
+        const float r0 = c.wpf[2 * k], z0 = c.wpf[2 * k + 1];
+        const float dr = c.wpf[2 * k + 2] - r0, dz = c.wpf[2 * k + 3] - z0;
+        const float t = fminf(fmaxf(((rhof - r0) * dr + (zf - z0) * dz) / (dr * dr + dz * dz), 0.f), 1.f);
+        const float a = rhof - (r0 + t * dr), b = zf - (z0 + t * dz);
+        if (a * a + b * b < lim * lim) nearm |= 1u << k;
+    }
+    float4* ws = d.wseg[lp];
+    const size_t ncap = (size_t)d.ncap;
+    int nst = 0;
+    if (nearm) {
+        const float4 h0 = ws[s], h1 = ws[ncap + s];
+        const double ex = (double)P.x - c.wax, ey = (double)P.y - c.way, z = (double)P.z;
+        const double rho = sqrt(ex * ex + ey * ey);
+        float erx = 1.f, ery = 0.f;   // radial direction (float suffices for a direction)
+        if (rhof > 0.f) {
+            erx = exf / rhof;
+            ery = eyf / rhof;
+        }
+        while (nearm) {
+            const int k = __ffs(nearm) - 1;
+            nearm &= nearm - 1u;
+            const double r0 = c.wp[2 * k], z0 = c.wp[2 * k + 1];
+            const double dr = c.wp[2 * k + 2] - r0, dz = c.wp[2 * k + 3] - z0;
+            const double t = fmin(fmax(((rho - r0) * dr + (z - z0) * dz) / (dr * dr + dz * dz), 0.0), 1.0);
+            const double a = rho - (r0 + t * dr), b = z - (z0 + t * dz);
+            const double dist = sqrt(a * a + b * b);
+            const double dl = (double)P.w - dist;
+            if (!(dl > 0.0)) continue;
+            const double idist = 1.0 / dist;
+            const float na = (float)(a * idist);
+            const V3 n = v3(na * erx, na * ery, (float)(b * idist));
+            const unsigned tag = (unsigned)k + 1u;
+            V3 xi = v3(0.f, 0.f, 0.f);
+            if (__float_as_uint(h0.w) == tag) xi = v3(h0.x, h0.y, h0.z);
+            else if (__float_as_uint(h1.w) == tag) xi = v3(h1.x, h1.y, h1.z);
+            V3 ft;
+            bool slip;
+            const V3 fa = contact_fwd<float, true>(coef_of(c), (float)dl * c.q, n, r, 0.f, m, 0.f, vme,
+                                                   v3(0.f, 0.f, 0.f), wme, v3(0.f, 0.f, 0.f), xi, dt_hist, ft, slip);
+            F = F + fa;
+            Tq = Tq - r * cross(n, ft);
+            if (MODE == 0 && nst < 2) ws[nst * ncap + s] = make_float4(xi.x, xi.y, xi.z, __uint_as_float(tag));
+            ++nst;
+        }
+    }
+    if (MODE == 0)
+        for (int i = nst; i < 2; ++i) ws[i * ncap + s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return nst;
+}
+
+// WALLS: the variant that evaluates axisymmetric walls (launched only for contexts that have
+// them, so that the wall code costs the plain step nothing)
+template <int MODE, bool WALLS>
 __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, cudaGraphConditionalHandle hnext, int use_cond)
 {
     __shared__ InstC sc;
@@ -706,6 +782,8 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                 if (MODE == 0) d.whist[lp][s] = make_float4(wxi.x, wxi.y, wxi.z, 0.f);
             }
         }
+        int nseg = 0;
+        if (WALLS && c.nwp >= 2) nseg = wall_contacts<MODE>(d, c, s, lp, P, r, m, vme, wme, dt_hist, F, Tq);
         const float inv_m = 1.0f / m;
         const float inv_I = 2.5f / (m * r * r);
         if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(Tq.x) && isfinite(Tq.y) &&
@@ -719,7 +797,7 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
             d.outT[s] = make_float4(Tq.x, Tq.y, Tq.z, 0.f);
             d.outV[s] = make_float4(Vv.x + hk * F.x * inv_m, Vv.y + hk * F.y * inv_m, Vv.z + hk * F.z * inv_m, 0.f);
             d.outW[s] = make_float4(Wv.x + hk * Tq.x * inv_I, Wv.y + hk * Tq.y * inv_I, Wv.z + hk * Tq.z * inv_I, 0.f);
-            d.outWX[s] = make_float4(wxi.x, wxi.y, wxi.z, wall_now ? 1.f : 0.f);
+            d.outWX[s] = make_float4(wxi.x, wxi.y, wxi.z, (float)((wall_now ? 1 : 0) + nseg));
             d.cmask[s] = cm;
         } else {
             const float kick = prime ? 0.5f * c.dt : c.dt;
@@ -761,9 +839,16 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                 atomicOr(&d.g->status, ST_ESCAPED);
                 d.g->err_slot = s;
             }
+            unsigned gone = 0u;
+            if (Pn.z < c.zrem) {   // fell below the removal height: dropped at the rebuild
+                gone = GONE_BIT;
+                atomicAdd(&d.id[kprev].nrem, 1);
+                atomicAdd(d.wrem + 2 * kprev, 1.0);
+                atomicAdd(d.wrem + 2 * kprev + 1, (double)m);
+            }
             const int nxt = cur ^ 1;
             d.pos[nxt][s] = Pn;
-            d.vel[nxt][s] = make_float4(Vv.x, Vv.y, Vv.z, __uint_as_float(myid | (wall_now ? WALL_BIT : 0u)));
+            d.vel[nxt][s] = make_float4(Vv.x, Vv.y, Vv.z, __uint_as_float(myid | gone | (wall_now ? WALL_BIT : 0u)));
             d.omg[nxt][s] = Wv;
         }
     }
@@ -793,6 +878,13 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                 const float disp = Dk->disp + sm;
                 Dk->disp = disp;
                 Dk->cur ^= 1;
+                if (Dk->nrem) {
+                    Dk->nrem = 0;
+                    if (Dk->flag == 0) {
+                        Dk->flag = 1;
+                        atomicOr(&d.g->any, 1u);
+                    }
+                }
                 if (2.0f * disp >= 0.99f * d.ic[kk].skin_f && Dk->flag == 0) {
                     if (d.g->frozen) {
                         atomicOr(&d.g->status, ST_SKIN);
@@ -845,6 +937,8 @@ __global__ void k_init_ids(Dev d)
         d.hmask[b][s] = 0u;
         d.fext[b][s] = z;
         d.whist[b][s] = z;
+        d.wseg[b][s] = z;
+        d.wseg[b][d.ncap + s] = z;
     }
     d.slot_of_id[s] = s;
 }
@@ -1036,7 +1130,7 @@ __global__ void k_stats(Dev d)
         const InstD D = d.id[k];
         if (s - d.ic[k].slot0 < D.n) {
             l = (unsigned long long)d.cnt[D.lp][s];
-            wc = d.outWX[s].w != 0.f ? 1ull : 0ull;
+            wc = (unsigned long long)d.outWX[s].w;   // floor and axisymmetric-wall contacts
             cc = (unsigned long long)__popcll(d.cmask[s]) + wc;
         }
     }
@@ -1417,7 +1511,7 @@ struct Plan {
     int ncap = 0, ntiles = 0, Lmax = 0, B = 0;
     unsigned ncodes = 0, nparts = 0;
     // offsets
-    size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_fext[2], o_whist[2];
+    size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_fext[2], o_whist[2], o_wseg[2], o_wrem;
     size_t o_cellcode, o_cslot, o_perm, o_fin, o_spos, o_sid, o_ccount, o_crange, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
         o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl, o_small;
     size_t bytes = 0;
@@ -1503,6 +1597,7 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
         c.ncode = 1 << tb;
         code += (unsigned)c.ncode;
         c.floor_on = s.floor_on ? 1 : 0;
+        c.zrem = INT_MIN;   // no removal height until dem_set_walls gives one
         c.skin = (int)skin_u;
         c.skin_f = (float)skin_u;
         c.clamp_fn = s.clamp_fn ? 1 : 0;
@@ -1556,7 +1651,9 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
         p.o_hmask[b] = L.take(N * 4);
         p.o_fext[b] = L.take(N * 16);
         p.o_whist[b] = L.take(N * 16);
+        p.o_wseg[b] = L.take(N * 32);
     }
+    p.o_wrem = L.take(sizeof(double) * 2 * p.B);
     p.o_cellcode = L.take(N * 4);
     p.o_cslot = L.take(N * 4);
     p.o_perm = L.take(N * 4);
@@ -1646,7 +1743,7 @@ dem_status launch_eval(dem_ctx* ctx)
 {
     dem_status st = launch_rebuild(ctx, ctx->stream);
     if (st) return st;
-    k_step<1><<<ctx->grid1, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
+    k_step<1, true><<<ctx->grid1, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
     CU(cudaGetLastError());
     return DEM_OK;
 }
@@ -1734,7 +1831,7 @@ dem_status build_graph(dem_ctx* ctx, int S)
         cudaGraphConditionalHandle hn = i + 1 < S ? h[i + 1] : h[i];
         void* args[] = {&dv, &prime, &hn, &use_cond};
         cudaKernelNodeParams kp{};
-        kp.func = (void*)k_step<0>;
+        kp.func = ctx->walls ? (void*)k_step<0, true> : (void*)k_step<0, false>;
         kp.gridDim = dim3(ctx->grid0);
         kp.blockDim = dim3(TILE);
         kp.kernelParams = args;
@@ -1856,7 +1953,9 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
         d.hmask[b] = (unsigned*)(base + p.o_hmask[b]);
         d.fext[b] = (float4*)(base + p.o_fext[b]);
         d.whist[b] = (float4*)(base + p.o_whist[b]);
+        d.wseg[b] = (float4*)(base + p.o_wseg[b]);
     }
+    d.wrem = (double*)(base + p.o_wrem);
     d.cellcode = (unsigned*)(base + p.o_cellcode);
     d.cslot = (unsigned*)(base + p.o_cslot);
     d.perm = (int*)(base + p.o_perm);
@@ -1917,6 +2016,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     CUC(cudaMemcpyAsync(ctx->d_hl, p.hl.data(), sizeof(HostInstLo) * p.B, cudaMemcpyHostToDevice, s));
     CUC(cudaMemsetAsync(d.hist[0], 0, (size_t)p.ncap * p.Lmax * 12, s));
     CUC(cudaMemsetAsync(d.hist[1], 0, (size_t)p.ncap * p.Lmax * 12, s));
+    CUC(cudaMemsetAsync(d.wrem, 0, sizeof(double) * 2 * p.B, s));
     k_init_ids<<<nblk(p.ncap, 256), 256, 0, s>>>(d);
     CUC(cudaGetLastError());
     CUC(cudaStreamSynchronize(s));
@@ -1928,8 +2028,8 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     {
         int nsm = 0, b0 = 0, b1 = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_step<0>, TILE, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_step<1>, TILE, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_step<0, false>, TILE, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_step<1, true>, TILE, 0);
         ctx->grid0 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b0)));
         ctx->grid1 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b1)));
         ctx->grid_rb = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * 8));
@@ -2065,7 +2165,8 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps)
         }
         dem_status st = launch_rebuild(ctx, ctx->stream);
         if (st) return st;
-        k_step<0><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
+        if (ctx->walls) k_step<0, true><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
+        else k_step<0, false><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
         CU(cudaGetLastError());
         ctx->fresh = false;
         ++done;
@@ -2242,7 +2343,7 @@ dem_status snap(dem_ctx* ctx, const Snap& S, bool save)
 
 dem_status step_once(dem_ctx* ctx, int prime)
 {
-    k_step<0><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, prime, 0, 0);
+    k_step<0, false><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, prime, 0, 0);   // rollouts refuse walls
     CU(cudaGetLastError());
     return DEM_OK;
 }
@@ -2282,6 +2383,74 @@ dem_status dem_set_material(dem_ctx* ctx, const double* params)
     return upload_material(ctx);
 }
 
+dem_status dem_set_walls(dem_ctx* ctx, int32_t k, const double* axis, int32_t npts, const double* points,
+                         double z_remove)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    if (k < 0 || k >= ctx->B) return fail(ctx, DEM_ERR_ARG, "instance index out of range");
+    if (npts != 0 && (npts < 2 || npts > MAX_WP || !points || !axis))
+        return fail(ctx, DEM_ERR_ARG, "need 0 or 2 .. 8 polyline points and the axis");
+    InstC& c = ctx->ic[k];
+    const HostInstLo& h = ctx->hl[k];
+    const double q = h.q;
+    InstC w = c;
+    w.nwp = npts;
+    w.wmag = 0.f;
+    if (npts) {
+        if (!(std::isfinite(axis[0]) && std::isfinite(axis[1]))) return fail(ctx, DEM_ERR_ARG, "axis must be finite");
+        w.wax = (axis[0] - h.lo[0]) / q;
+        w.way = (axis[1] - h.lo[1]) / q;
+        if (!(std::fabs(w.wax) < 1.0e9 && std::fabs(w.way) < 1.0e9)) return fail(ctx, DEM_ERR_ARG, "axis far outside the box");
+        w.waxi = (int)std::floor(w.wax);
+        w.wayi = (int)std::floor(w.way);
+        w.waxf = (float)(w.wax - w.waxi);
+        w.wayf = (float)(w.way - w.wayi);
+        double mag = 0.0;
+        for (int i = 0; i < npts; ++i) {
+            const double rho = points[2 * i], z = points[2 * i + 1];
+            if (!(std::isfinite(rho) && std::isfinite(z) && rho >= 0.0)) return fail(ctx, DEM_ERR_ARG, "polyline points need rho >= 0, finite z");
+            w.wp[2 * i] = rho / q;
+            w.wp[2 * i + 1] = (z - h.lo[2]) / q;
+            if (!(w.wp[2 * i] < 2.0e9 && std::fabs(w.wp[2 * i + 1]) < 2.0e9)) return fail(ctx, DEM_ERR_ARG, "polyline far outside the box");
+            w.wpf[2 * i] = (float)w.wp[2 * i];
+            w.wpf[2 * i + 1] = (float)w.wp[2 * i + 1];
+            mag = std::max(mag, std::max(w.wp[2 * i], std::fabs(w.wp[2 * i + 1])));
+            if (i > 0 && points[2 * i] == points[2 * i - 2] && points[2 * i + 1] == points[2 * i - 1])
+                return fail(ctx, DEM_ERR_ARG, "polyline segments need a non-zero length");
+        }
+        w.wmag = (float)mag;
+    }
+    w.zrem = INT_MIN;
+    if (std::isnan(z_remove)) return fail(ctx, DEM_ERR_ARG, "z_remove is NaN");
+    if (z_remove > -INFINITY) {
+        const double zu = std::ceil((z_remove - h.lo[2]) / q);   // removed: z < z_remove, i.e. z_units < zu
+        if (!(zu < 2.0e9)) return fail(ctx, DEM_ERR_ARG, "z_remove above the representable range");
+        if (zu > -2.0e9) w.zrem = (int)zu;
+    }
+    c = w;
+    bool any = false;
+    for (int i = 0; i < ctx->B; ++i) any |= ctx->ic[i].nwp >= 2;
+    const bool rebuild_graph = any != ctx->walls && ctx->gexec;
+    ctx->walls = any;
+    // the wall-contact history of the instance starts empty
+    const size_t n = (size_t)c.cap, ncap = (size_t)ctx->dev.ncap;
+    for (int b = 0; b < 2; ++b)
+        for (int half = 0; half < 2; ++half)
+            CU(cudaMemsetAsync(ctx->dev.wseg[b] + half * ncap + c.slot0, 0, n * sizeof(float4), ctx->stream));
+    if (dem_status st = upload_material(ctx)) return st;
+    return rebuild_graph ? build_graph(ctx, ctx->graph_steps) : DEM_OK;
+}
+
+dem_status dem_wall_removed(dem_ctx* ctx, int32_t k, double* out)
+{
+    if (!ctx || !out) return DEM_ERR_ARG;
+    if (k < 0 || k >= ctx->B) return fail(ctx, DEM_ERR_ARG, "instance index out of range");
+    CU(cudaMemcpyAsync(out, ctx->dev.wrem + 2 * k, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_status(ctx);
+}
+
 dem_status dem_rollout_workspace(dem_ctx* ctx, int64_t nsteps, int64_t checkpoint_every, int64_t* bytes)
 {
     if (!ctx || !bytes || nsteps < 1 || checkpoint_every < 1) return DEM_ERR_ARG;
@@ -2294,6 +2463,9 @@ dem_status dem_rollout_forward(dem_ctx* ctx, int64_t nsteps, int64_t checkpoint_
     if (!ctx || nsteps < 1 || checkpoint_every < 1 || !ws) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     if (!ctx->have_state) return fail(ctx, DEM_ERR_STATE, "write the state before a rollout");
+    for (int k = 0; k < ctx->B; ++k)
+        if (ctx->ic[k].nwp || ctx->ic[k].zrem != INT_MIN)
+            return fail(ctx, DEM_ERR_STATE, "rollouts do not differentiate axisymmetric walls or removal");
     const size_t need = rollout_layout(ctx, nsteps, checkpoint_every, nullptr);
     if ((size_t)ws_bytes < need || ((uintptr_t)ws & 255)) return fail(ctx, DEM_ERR_ARG, "rollout workspace too small");
     rollout_layout(ctx, nsteps, checkpoint_every, (char*)ws);

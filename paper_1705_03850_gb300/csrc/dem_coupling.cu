@@ -647,6 +647,8 @@ __global__ void k_cp_append(Dev d, Geo g, Acc a, int* overflow)
             d.cnt[D.lp][s] = 0;
             d.hmask[D.lp][s] = 0u;
             d.whist[D.lp][s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            d.wseg[D.lp][s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            d.wseg[D.lp][d.ncap + s] = make_float4(0.f, 0.f, 0.f, 0.f);
             d.fext[D.lp][s] = make_float4(0.f, 0.f, 0.f, 0.f);
             d.slot_of_id[c.slot0 + id] = s;
         }

@@ -25,6 +25,7 @@ struct dem_ctx {
     std::vector<long long> count;     // host mirror of live counts
     HostInstLo* d_hl = nullptr;
     bool fresh = true;                // velocities at an integer step (next step primes)
+    bool walls = false;               // some instance has axisymmetric walls (step kernel variant)
     bool have_state = false;
     long long steps = 0;
     unsigned status = 0;

@@ -20,6 +20,8 @@
 //                                             d^2 - (r_i + r_j)^2 at the build,
 //                                             then by neighbour ID
 //                whist float4 [ncap]          floor-contact tangential overlap
+//                wseg  float4 [2][ncap]       up to two axisymmetric-wall contacts:
+//                                             {xi, segment + 1 (bits); 0: empty}
 //   cells      per instance a Morton-ordered code range [code0_k, code0_k + ncode_k)
 //              with counts and exclusive starts, rebuilt with the lists.
 #pragma once
@@ -33,6 +35,7 @@ constexpr int MAXL = 32;       // largest list width (one bit per entry in a 32-
 constexpr unsigned ID_MASK = 0x3fffffffu;   // particle ID (< 2^30)
 constexpr unsigned GONE_BIT = 0x40000000u;  // removed: dropped at the next list build
 constexpr unsigned WALL_BIT = 0x80000000u;  // in contact with the floor at the last step
+constexpr int MAX_WP = 8;      // points of an axisymmetric wall polyline
 
 // device status bits
 constexpr unsigned ST_CAPACITY = 1u;
@@ -62,7 +65,19 @@ struct InstC {
     float gt_ratio;                      // gamma_t / gamma_n = sqrt(2 c_kt / (3 c_kn))
     float inv_E;                         // 1 / E (c_kn and c_kt are proportional to E)
     float dnb_de;                        // d(-beta)/de
+    // axisymmetric walls: the surface of revolution of the polyline (rho_i, z_i) about the
+    // vertical axis (wax, way); lengths in units of q from the box origin
+    int nwp;                             // polyline points (0: no walls)
+    int zrem;                            // particles whose centre falls below z = zrem are removed
+                                         // (INT_MIN: none)
+    int waxi, wayi;                      // axis: whole units and fraction (float pre-test, direction)
+    float waxf, wayf;
+    float wmag;                          // largest polyline coordinate (float pre-test tolerance)
+    double wax, way;
+    double wp[2 * MAX_WP];
+    float wpf[2 * MAX_WP];
 };
+static_assert(sizeof(InstC) <= 4 * TILE, "the step kernel stages InstC in shared memory, one word per thread");
 
 // dynamic state of one instance (device-resident)
 struct InstD {
@@ -75,7 +90,8 @@ struct InstD {
     int nid;             // IDs handed out so far (n plus removed particles); IDs are never reused
     int n_new;           // live particles after the pending rebuild (removed ones dropped)
     int fext;            // 1: add the per-particle external force fext to the contact forces
-    int pad[3];
+    int nrem;            // particles removed below the removal height at this step
+    int pad[2];
 };
 
 struct Glob {
@@ -101,6 +117,8 @@ struct Dev {
     unsigned* hmask[2];        // bit e: entry e holds a non-zero tangential overlap
     float4* fext[2];           // external force per particle (coupling controllers), list parity
     float4* whist[2];
+    float4* wseg[2];           // [2][ncap] axisymmetric-wall contacts, list parity
+    double* wrem;              // [2 * B] particles and mass removed below the removal height
     unsigned* cellcode;
     unsigned* cslot;
     int* perm;                 // cell-order position -> old slot

@@ -8,6 +8,7 @@ the library is missing or no GPU is present the calls raise.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import sys
 
@@ -106,6 +107,9 @@ def lib():
         "dem_counts": [vp, vp, vp],
         "dem_clear_external_force": [vp],
         "dem_grid_fields": [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.POINTER(i32), vp, i64],
+        "dem_set_walls": [vp, i32, ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(ctypes.c_double),
+                          ctypes.c_double],
+        "dem_wall_removed": [vp, i32, ctypes.POINTER(ctypes.c_double)],
         "dem_neighbor_counts_noalloc": [vp, vp, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i32), ctypes.c_double, ctypes.c_double, vp, vp],
     }
@@ -125,7 +129,8 @@ def exported_symbols():
             "dem_set_graph", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
             "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material",
             "dem_coupler_workspace", "dem_coupler_create", "dem_couple", "dem_coupler_read", "dem_coupler_destroy",
-            "dem_counts", "dem_clear_external_force", "dem_grid_fields", "dem_last_error"]
+            "dem_counts", "dem_clear_external_force", "dem_grid_fields", "dem_set_walls", "dem_wall_removed",
+            "dem_last_error"]
 
 
 def desc(*, n, lo, hi, periodic, dt, skin, r_max, E, nu, e, mu, rho, g=(0, 0, 0), floor=True,
@@ -350,6 +355,22 @@ class DEM:
         self._check(self.L.dem_instance_info_get(self.h, k, ctypes.byref(inf)), "info")
         return dict(q=inf.q, lo=tuple(inf.lo), hi=tuple(inf.hi), ncell=tuple(inf.ncell), n=inf.n,
                     capacity=inf.capacity)
+
+    def set_walls(self, k=0, axis=(0.0, 0.0), points=(), z_remove=-math.inf):
+        """Axisymmetric walls of instance k: the surface of revolution of the polyline
+        points [(rho, z), ...] about the vertical axis through `axis`; particles whose centre
+        falls below z_remove are removed (see dem_set_walls)."""
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 2))
+        ax = (ctypes.c_double * 2)(*[float(a) for a in axis])
+        pp = pts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(pts) else None
+        self._check(self.L.dem_set_walls(self.h, int(k), ax, int(len(pts)), pp, float(z_remove)), "set walls")
+        return self
+
+    def wall_removed(self, k=0):
+        """(count, mass [kg]) removed below the removal height of instance k so far."""
+        out = (ctypes.c_double * 2)()
+        self._check(self.L.dem_wall_removed(self.h, int(k), out), "wall removed")
+        return int(out[0]), float(out[1])
 
     def stats(self):
         st = Stats()

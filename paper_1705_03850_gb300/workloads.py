@@ -377,3 +377,144 @@ def nested_levels(levels: int = 5, d_fine: float = 1.0e-3, length: float = 11.0,
         x0 = x0 + 0.25 * L            # the next region starts a quarter into this one
     return chute(length=length, width=width, height=height, bed=bed, regions=tuple(regions), diameters=diameters,
                  seed=seed, u0=u0, dt=dt, interval=16, multirate=multirate)
+
+
+# The silo of Sec. 3 (Table 1): E = 2.5e7 Pa, nu = 0.25, e = 0.5, mu = 0.2 (particle-particle),
+# 0.175 (particle-wall), rho = 1000 kg/m^3, d = 2.8 mm, dt = 1e-6 s.
+SILO_MATERIAL = Material(E=2.5e7, nu=0.25, e=0.5, mu=0.2, mu_wall=0.175, rho=1000.0)
+
+
+def silo_walls(z_o: float, r_o: float = 0.02, R: float = 0.135, h_cone: float = 0.2, h_cyl: float = 0.2,
+               closed: bool = True):
+    """Polyline (rho, z) of the silo wall: a cone from the orifice radius r_o at z_o up to R over
+    h_cone, then a cylinder of radius R for h_cyl more; closed: a disk (0, z_o) - (r_o, z_o) shuts
+    the orifice (the filling phase)."""
+    pts = [(r_o, z_o), (R, z_o + h_cone), (R, z_o + h_cone + h_cyl)]
+    if closed:
+        pts = [(0.0, z_o)] + pts
+    return qgrid(np.asarray(pts, dtype=np.float64))
+
+
+def _fcc_in_vessel(nn, r_wall, z_lo, z_hi, R, clear, n, rng, jitter):
+    """The n lowest FCC sites (nearest-neighbour distance nn) about the vertical axis at the origin
+    whose distance from the axis stays `clear` inside r_wall(z) (a horizontal distance: a sphere
+    clears a sloped wall only where clear times the cosine of the wall's slope exceeds its
+    radius), from z_lo + clear up."""
+    a = nn * math.sqrt(2.0)
+    m = int(math.ceil(R / a)) + 1
+    kz = int(math.ceil((z_hi - z_lo) / a)) + 1
+    i, j, k = np.meshgrid(np.arange(-m, m + 1), np.arange(-m, m + 1), np.arange(kz), indexing="ij")
+    base = np.column_stack([i.ravel(), j.ravel(), k.ravel()]).astype(np.float64) * a
+    pts = np.vstack([base + np.array(o) * a for o in ((0, 0, 0), (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5))])
+    pts[:, 2] += z_lo + clear
+    rho = np.hypot(pts[:, 0], pts[:, 1])
+    keep = (rho <= r_wall(pts[:, 2]) - clear) & (pts[:, 2] <= z_hi - clear)
+    pts = pts[keep]
+    pts = pts[np.lexsort((pts[:, 0], pts[:, 1], pts[:, 2]))]
+    if pts.shape[0] < n:
+        raise ValueError(f"the vessel holds {pts.shape[0]} lattice sites, {n} asked")
+    return pts[:n] + rng.uniform(-jitter, jitter, (n, 3))
+
+
+def silo(alpha: int = 1, n_ref: int = 187_504, d_ref: float = 2.8e-3, seed: int = 17, z_o: float = 0.05,
+         gap: float = 0.3, v_rand: float = 0.1, dt: float = 1e-6):
+    """The silo of Sec. 3: 40 cm tall, the upper half a cylinder of diameter 27 cm, the lower half a
+    cone narrowing to a 4 cm orifice at height z_o above the box floor (the orifice closed by a disk
+    while filling).  Filled with n_ref / alpha^3 spheres of d = alpha d_ref (alpha = 1: the
+    reference, 187,504 x 2.8 mm; alpha = 2: the coarse-grain model, 23,438 x 5.6 mm) on an FCC
+    lattice (nearest-neighbour distance (1 + gap) d) inside the vessel with d of clearance, lowest
+    sites first, each jittered by +-0.01 d and given a velocity uniform in +-v_rand per axis: the
+    synthetic stand-in for the paper's pouring from the top, to be settled under gravity.  No box
+    floor; the box spans the vessel with 2 d of margin and z from 0."""
+    rng = np.random.default_rng(seed + alpha)
+    d = alpha * d_ref
+    n = int(round(n_ref / alpha ** 3))
+    r_o, R, h_cone, h_cyl = 0.02, 0.135, 0.2, 0.2
+
+    def r_wall(z):
+        return np.where(z < z_o + h_cone, r_o + (R - r_o) * (z - z_o) / h_cone, R)
+
+    x = _fcc_in_vessel((1.0 + gap) * d, r_wall, z_o, z_o + h_cone + h_cyl, R, d, n, rng, 0.01 * d)
+    v = rng.uniform(-v_rand, v_rand, (n, 3))
+    m = R + 2 * d
+    wl = _finish(f"silo_alpha{alpha}", x, v, np.zeros((n, 3)), np.full(n, d / 2), SILO_MATERIAL, (-m, -m, 0.0),
+                 (m, m, z_o + h_cone + h_cyl + 0.05), (False, False, False), dt, (0.0, 0.0, -9.81), False,
+                 (0, 0, 0), 0.1 * d, 0, alpha=alpha, diameter=d, z_o=z_o, r_o=r_o, R=R, h_cone=h_cone,
+                 h_cyl=h_cyl)
+    return wl
+
+
+def small_vessel(seed: int = 21, n: int = 600, d: float = 2.0e-3, closed: bool = True, packed: bool = True):
+    """A small cone-and-cylinder vessel (orifice radius 4 mm at z = 10 mm, cone to 12 mm over 10 mm,
+    cylinder to z = 40 mm), for parity: packed = True fills it from the bottom on an FCC lattice
+    (nearest neighbour 1.1 d; centres 0.65 d from the wall horizontally and above the orifice, so
+    that no sphere starts in contact with the cone, whose normal is 39 degrees from horizontal)
+    with random velocities of +-0.5 m/s; packed =
+    False scatters n spheres uniformly over the vessel's bounding cylinder, so that many overlap a
+    wall, a rim or the orifice disk (and some lie outside the wall): the input for the
+    single-evaluation force parity.  Material of Table 1 with d = 2 mm."""
+    rng = np.random.default_rng(seed)
+    z_o, r_o, R, h_cone, h_cyl = 0.01, 0.004, 0.012, 0.01, 0.02
+
+    def r_wall(z):
+        return np.where(z < z_o + h_cone, r_o + (R - r_o) * (z - z_o) / h_cone, R)
+
+    if packed:
+        x = _fcc_in_vessel(1.1 * d, r_wall, z_o, z_o + h_cone + h_cyl, R, 0.65 * d, n, rng, 0.01 * d)
+        v = rng.uniform(-0.5, 0.5, (n, 3))
+        w = np.zeros((n, 3))
+    else:
+        rho = (R + 0.5 * d) * np.sqrt(rng.uniform(0.0, 1.0, n))
+        ph = rng.uniform(0.0, 2.0 * math.pi, n)
+        z = rng.uniform(z_o - 0.5 * d, z_o + h_cone + h_cyl + 0.5 * d, n)
+        x = np.column_stack([rho * np.cos(ph), rho * np.sin(ph), z])
+        v = rng.uniform(-0.5, 0.5, (n, 3))
+        w = rng.uniform(-100.0, 100.0, (n, 3))
+    pts = [(r_o, z_o), (R, z_o + h_cone), (R, z_o + h_cone + h_cyl)]
+    if closed:
+        pts = [(0.0, z_o)] + pts
+    m = R + 2 * d
+    wl = _finish("small_vessel", x, v, w, np.full(n, d / 2), SILO_MATERIAL, (-m, -m, 0.0), (m, m, 0.05),
+                 (False, False, False), 1e-6, (0.0, 0.0, -9.81), False, (0, 0, 0), 0.1 * d, 0, z_o=z_o,
+                 walls=qgrid(np.asarray(pts, dtype=np.float64)))
+    return wl
+
+
+def vessel_sphere(case: str = "cone", d: float = 2.0e-3, overlap: float = 2.0e-7):
+    """One sphere against the small vessel's wall (orifice radius 4 mm at z = 10 mm, cone to 12 mm
+    over 10 mm, cylinder above), for parity of a wall contact carried over many steps:
+
+    * ``cone``: halfway up the cone, pressed into it by `overlap`, moving azimuthally at 0.3 m/s
+      (it runs round the cone under gravity);
+    * ``kink``: in the corner where the cone meets the cylinder, `overlap` into both;
+    * ``rim``: with the orifice open, leaning on the rim's edge from inside the hole (centre
+      below the cone's normal at the rim, so the edge is its only contact), `overlap` into it:
+      it slides off the edge and falls through."""
+    z_o, r_o, R, h_cone = 0.01, 0.004, 0.012, 0.01
+    r = d / 2
+    s = (R - r_o) / h_cone                       # d rho / d z of the cone
+    c = 1.0 / math.sqrt(1.0 + s * s)             # the cone's inward normal is (-c, s c) in (rho, z)
+    pts = [(r_o, z_o), (R, z_o + h_cone), (R, z_o + 2 * h_cone)]
+    v = np.zeros((1, 3))
+    w = np.zeros((1, 3))
+    a = r - overlap
+    if case == "cone":
+        zc = z_o + 0.5 * h_cone
+        rc = r_o + s * (zc - z_o)
+        rho, z = rc - a * c, zc + a * s * c
+        v[0] = (0.0, 0.3, 0.0)
+    elif case == "kink":
+        # a from the cylinder (rho = R - a) and a from the cone: the contact point on the cone
+        # at height zc satisfies r_o + s (zc - z_o) - a c = R - a
+        zc = z_o + (R - r_o - a * (1.0 - c)) / s
+        rho, z = R - a, zc + a * s * c
+    elif case == "rim":
+        e = a / math.sqrt(1.25)                  # centre (r_o - e, z_o + e / 2), |.| = a from the edge
+        rho, z = r_o - e, z_o + 0.5 * e
+    else:
+        raise ValueError(case)
+    x = np.array([[rho, 0.0, z]])
+    m = R + 2 * d
+    return _finish(f"vessel_sphere_{case}", x, v, w, np.full(1, r), SILO_MATERIAL, (-m, -m, 0.0), (m, m, 0.05),
+                   (False, False, False), 1e-6, (0.0, 0.0, -9.81), False, (0, 0, 0), 0.1 * d, 0,
+                   walls=qgrid(np.asarray(pts, dtype=np.float64)))

@@ -4,14 +4,16 @@ import numpy as np
 import oracle
 
 
-def oracle_params(wl):
+def oracle_params(wl, walls=None):
+    """walls: None, or the polyline (rho, z) of axisymmetric walls about the vertical axis (0, 0)."""
     m = wl.material
     return oracle.make_params(E=m.E, nu=m.nu, e=m.e, mu=m.mu, mu_wall=m.mu_wall, dt=wl.dt, g=wl.g, lo=wl.lo,
-                              hi=wl.hi, periodic=wl.periodic, floor=wl.floor, floor_v=wl.floor_v)
+                              hi=wl.hi, periodic=wl.periodic, floor=wl.floor, floor_v=wl.floor_v,
+                              walls=None if walls is None else dict(axis=(0.0, 0.0), points=walls))
 
 
-def oracle_sim(wl, **kw):
-    return oracle.Sim(oracle_params(wl), wl.x, wl.v, wl.w, wl.r, wl.m, **kw)
+def oracle_sim(wl, walls=None, **kw):
+    return oracle.Sim(oracle_params(wl, walls), wl.x, wl.v, wl.w, wl.r, wl.m, **kw)
 
 
 def gpu_pairs(partner):

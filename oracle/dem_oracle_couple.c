@@ -13,8 +13,9 @@
  *      particles within one diameter of the face;
  *   2. transition layer (one hexahedral cell behind each surface cell) on both
  *      levels: volume fraction, Favre velocity, largest speed and the granular
- *      stress of Eq. 7 (1/2 r_ij f_ij over contacts, floor contacts with the
- *      branch vector to the contact point, plus m v'v', symmetrised);
+ *      stress of Eq. 7 (1/2 r_ij f_ij over contacts, floor and axisymmetric-
+ *      wall contacts with the branch vector from the contact point to the
+ *      centre, plus m v'v', symmetrised);
  *   3. stress PI controller on the face-normal stress (setpoint coarse,
  *      process variable fine) and its force on fine particles, faded out
  *      linearly over 3/2 fine diameters and limited by the coarse cell's
@@ -22,7 +23,10 @@
  *   4. fine-to-coarse P controller per correction cell (velocity or mass flow
  *      with the volume-fraction ratio capped at 4);
  *   5. simple sequential inhibition (Diggle et al. 1976) of fine particles per
- *      surface cell with SplitMix64 random numbers on counters;
+ *      surface cell with SplitMix64 random numbers on counters (a candidate
+ *      overlapping a fine particle, an earlier insertion or one of the fine
+ *      level's axisymmetric walls, or lying outside the vessel the walls
+ *      enclose, is rejected);
  *   6. removal of fine particles that left through drain faces.
  *
  * Spec block CP (doubles): 0..2 lo, 3..5 hi, 6 feed bits, 7 drain bits,
@@ -140,6 +144,22 @@ static void min_image_d(const double *P, double *d)
         }
 }
 
+/* Nearest point of wall segment k (the surface of revolution of the polyline
+ * (rho_k, z_k) - (rho_k+1, z_k+1) about the vertical wall axis), seen in the
+ * particle's azimuthal half-plane at distance rho from the axis and height z:
+ * returns the offsets (a, b) = (rho, z) - nearest point.  Lengths in the
+ * caller's frame: rs scales rho_k, zs the z_k, z0 is subtracted from them. */
+static void seg_offset(const double *P, int k, double rho, double z, double rs, double z0, double *a, double *b)
+{
+    const double r0 = P[P_WP + 2 * k] / rs, zz0 = (P[P_WP + 2 * k + 1] - z0) / rs;
+    const double dr = P[P_WP + 2 * k + 2] / rs - r0, dz = (P[P_WP + 2 * k + 3] - z0) / rs - zz0;
+    double t = ((rho - r0) * dr + (z - zz0) * dz) / (dr * dr + dz * dz);
+    if (t < 0.0) t = 0.0;
+    else if (t > 1.0) t = 1.0;
+    *a = rho - (r0 + t * dr);
+    *b = z - (zz0 + t * dz);
+}
+
 /* Eq. 7 contributions of the particles of one level to the transition cells.
  * lay[(cell)*20 + k]: 0 m, 1..3 m v, 4..9 m v v, 10 V, 11..16 contact stress. */
 static void level_layer(const double *CP, const cgeo_t *g, const double *P, int64_t n, const double *x,
@@ -192,6 +212,30 @@ static void level_layer(const double *CP, const cgeo_t *g, const double *P, int6
             orc_contact_pair(P, r[i], 0.0, m[i], 0.0, 1, r[i] - h, nz, v + 3 * i, P + P_FLOORV, w + 3 * i, zero3, xi,
                              dt_hist, fa, ft);
             double rv[3] = {0, 0, h};
+            for (int q = 0; q < 6; ++q) {
+                int s = ij[q][0], t = ij[q][1];
+                lay[20 * (size_t)c + 11 + q] += 0.5 * (rv[s] * fa[t] + rv[t] * fa[s]);
+            }
+        }
+    }
+    const int nwp = (int)P[P_NWP];
+    for (int64_t i = 0; nwp >= 2 && i < n; ++i) {
+        int c = layer_cell(g, CP[9], x + 3 * i, &fk);
+        if (c < 0) continue;
+        const double ex = x[3 * i] - P[P_WAX], ey = x[3 * i + 1] - P[P_WAY];
+        const double rho = sqrt(ex * ex + ey * ey);
+        double erx = 1.0, ery = 0.0;
+        if (rho > 1e-12) { erx = ex / rho; ery = ey / rho; }
+        for (int k = 0; k + 1 < nwp; ++k) {
+            double a, b;
+            seg_offset(P, k, rho, x[3 * i + 2], 1.0, 0.0, &a, &b);
+            const double dist = sqrt(a * a + b * b);
+            if (!(r[i] - dist > 0.0)) continue;
+            const double nv[3] = {a / dist * erx, a / dist * ery, b / dist}, zero3[3] = {0, 0, 0};
+            double xi[3] = {0, 0, 0}, fa[3], ft[3];
+            orc_contact_pair(P, r[i], 0.0, m[i], 0.0, 1, r[i] - dist, nv, v + 3 * i, zero3, w + 3 * i, zero3, xi,
+                             dt_hist, fa, ft);
+            const double rv[3] = {dist * nv[0], dist * nv[1], dist * nv[2]};
             for (int q = 0; q < 6; ++q) {
                 int s = ij[q][0], t = ij[q][1];
                 lay[20 * (size_t)c + 11 + q] += 0.5 * (rv[s] * fa[t] + rv[t] * fa[s]);
@@ -426,6 +470,25 @@ int32_t orc_couple(const double *CP, uint64_t seed, int32_t call, const double *
                 u[f->axis] = al + below(draw(seed, cell, call, attempt, 4), ah - al + 1);
                 ++attempt;
                 int ok = 1;
+                /* the fine level's axisymmetric walls, in fine units from its box origin: no
+                 * overlap, and inside the vessel (a ray from the centre away from the axis
+                 * crosses the non-horizontal segments, each closed below and open above, an
+                 * odd number of times) */
+                const int nwp = (int)Pf[P_NWP];
+                if (nwp >= 2) {
+                    const double ex = (double)u[0] - (Pf[P_WAX] - lof[0]) / qf, ey = (double)u[1] - (Pf[P_WAY] - lof[1]) / qf;
+                    const double rho = sqrt(ex * ex + ey * ey), ru2 = (double)ru * (double)ru, z = (double)u[2];
+                    int cross = 0;
+                    for (int k = 0; k + 1 < nwp && ok; ++k) {
+                        double a, b;
+                        seg_offset(Pf, k, rho, z, qf, lof[2], &a, &b);
+                        if (a * a + b * b < ru2) ok = 0;
+                        const double r0 = Pf[P_WP + 2 * k] / qf, z0 = (Pf[P_WP + 2 * k + 1] - lof[2]) / qf;
+                        const double r1 = Pf[P_WP + 2 * k + 2] / qf, z1 = (Pf[P_WP + 2 * k + 3] - lof[2]) / qf;
+                        if (z0 != z1 && (z >= z0) != (z >= z1) && r0 + (z - z0) * (r1 - r0) / (z1 - z0) > rho) ++cross;
+                    }
+                    if (!(cross & 1)) ok = 0;
+                }
                 for (int64_t j = 0; j < nf && ok; ++j) {
                     int64_t ex = min_image_i(u[0] - fu[4 * j], Pf, qf, 0), ey = min_image_i(u[1] - fu[4 * j + 1], Pf, qf, 1);
                     int64_t ez = u[2] - fu[4 * j + 2], S2 = (ru + fu[4 * j + 3]) * (ru + fu[4 * j + 3]);

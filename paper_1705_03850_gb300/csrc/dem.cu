@@ -551,10 +551,8 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int s
         while (nearm) {
             const int k = __ffs(nearm) - 1;
             nearm &= nearm - 1u;
-            const double r0 = c.wp[2 * k], z0 = c.wp[2 * k + 1];
-            const double dr = c.wp[2 * k + 2] - r0, dz = c.wp[2 * k + 3] - z0;
-            const double t = fmin(fmax(((rho - r0) * dr + (z - z0) * dz) / (dr * dr + dz * dz), 0.0), 1.0);
-            const double a = rho - (r0 + t * dr), b = z - (z0 + t * dz);
+            double a, b;
+            wall_seg_offset(c, k, rho, z, a, b);
             const double dist = sqrt(a * a + b * b);
             const double dl = (double)P.w - dist;
             if (!(dl > 0.0)) continue;

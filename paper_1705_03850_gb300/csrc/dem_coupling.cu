@@ -202,7 +202,62 @@ __device__ void layer_add(const Dev& d, const InstC& c, const InstD& D, int s, d
             st[k] += 0.5 * (rv[a] * f[b] + rv[b] * f[a]);
         }
     }
+    if (c.nwp >= 2) {   // axisymmetric walls: branch vector from the contact point to the centre
+        const double ex = (double)P.x - c.wax, ey = (double)P.y - c.way, z = (double)P.z;
+        const double rho = sqrt(ex * ex + ey * ey);
+        float erx = 1.f, ery = 0.f;
+        if (rho > 0.0) {
+            erx = (float)(ex / rho);
+            ery = (float)(ey / rho);
+        }
+        const float4 h0 = d.wseg[lp][s], h1 = d.wseg[lp][(size_t)ncap + s];
+        for (int k = 0; k + 1 < c.nwp; ++k) {
+            double a, b;
+            wall_seg_offset(c, k, rho, z, a, b);
+            const double dist = sqrt(a * a + b * b);
+            const double dl = (double)P.w - dist;
+            if (!(dl > 0.0)) continue;
+            const float na = (float)(a / dist);
+            const Vec3<float> n = mk3(na * erx, na * ery, (float)(b / dist));
+            const unsigned tag = (unsigned)k + 1u;
+            Vec3<float> xi = mk3(0.f, 0.f, 0.f);
+            if (__float_as_uint(h0.w) == tag) xi = mk3(h0.x, h0.y, h0.z);
+            else if (__float_as_uint(h1.w) == tag) xi = mk3(h1.x, h1.y, h1.z);
+            Vec3<float> ft;
+            bool slip;
+            const Vec3<float> fa = contact_fwd<float, true>(cf, (float)(dl * q), n, (float)r, 0.f, (float)m, 0.f,
+                                                            mk3(Vv.x, Vv.y, Vv.z), mk3(0.f, 0.f, 0.f),
+                                                            mk3(Wv.x, Wv.y, Wv.z), mk3(0.f, 0.f, 0.f), xi, dt_hist,
+                                                            ft, slip);
+            const double rv[3] = {dist * q * n.x, dist * q * n.y, dist * q * n.z}, f[3] = {fa.x, fa.y, fa.z};
+            for (int kk = 0; kk < 6; ++kk) {
+                const int ia = ij[kk][0], ib = ij[kk][1];
+                st[kk] += 0.5 * (rv[ia] * f[ib] + rv[ib] * f[ia]);
+            }
+        }
+    }
     for (int k = 0; k < 6; ++k) atomicAdd(acc + 11 + k, st[k]);
+}
+
+// false where a sphere of radius ru centred at u (units of q from the box origin) overlaps one
+// of the instance's axisymmetric walls (the contact test of the step kernel) or lies on the far
+// side of them from the axis: outside the vessel the walls enclose, i.e. where a ray from the
+// centre away from the axis (in the (rho, z) half-plane) crosses the non-horizontal segments an
+// even number of times (each segment spans its z range closed below, open above)
+__device__ bool clear_of_walls(const InstC& c, const long long* u, long long ru)
+{
+    if (c.nwp < 2) return true;
+    const double ex = (double)u[0] - c.wax, ey = (double)u[1] - c.way, z = (double)u[2];
+    const double rho = sqrt(ex * ex + ey * ey), ru2 = (double)ru * (double)ru;
+    int cross = 0;
+    for (int k = 0; k + 1 < c.nwp; ++k) {
+        double a, b;
+        wall_seg_offset(c, k, rho, z, a, b);
+        if (a * a + b * b < ru2) return false;
+        const double r0 = c.wp[2 * k], z0 = c.wp[2 * k + 1], r1 = c.wp[2 * k + 2], z1 = c.wp[2 * k + 3];
+        if (z0 != z1 && (z >= z0) != (z >= z1) && r0 + (z - z0) * (r1 - r0) / (z1 - z0) > rho) ++cross;
+    }
+    return (cross & 1) != 0;
 }
 
 template <typename Fn>
@@ -213,6 +268,7 @@ __device__ __forceinline__ void for_live(const Dev& d, Fn fn)
         const InstD D = d.id[k];
         const int s = t * TILE + threadIdx.x;
         if (s - d.ic[k].slot0 >= D.n) continue;
+        if (__float_as_uint(d.vel[D.cur][s].w) & GONE_BIT) continue;   // removed below a wall's removal height
         fn(s, d.ic[k], D);
     }
 }
@@ -547,8 +603,9 @@ __global__ void k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
         u[f.c] = cl + below(draw(g, cell, attempt, 3), ch - cl + 1);
         u[f.axis] = al + below(draw(g, cell, attempt, 4), ah - al + 1);
         ++attempt;
-        // overlap with fine particles (cell lists of the last build) and with earlier insertions
-        bool ok = true;
+        // inside the fine level's walls and clear of them, then no overlap with its particles
+        // (cell lists of the last build) or earlier insertions
+        bool ok = clear_of_walls(c, u, ru);
         const int ru_i = (int)ru;
         const int cx0 = axis_cell(c, 0, (int)u[0]), cy0 = axis_cell(c, 1, (int)u[1]), cz0 = axis_cell(c, 2, (int)u[2]);
         const unsigned cbase = d.crange[c.code0].x;

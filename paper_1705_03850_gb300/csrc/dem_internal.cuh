@@ -37,6 +37,12 @@ constexpr unsigned GONE_BIT = 0x40000000u;  // removed: dropped at the next list
 constexpr unsigned WALL_BIT = 0x80000000u;  // in contact with the floor at the last step
 constexpr int MAX_WP = 8;      // points of an axisymmetric wall polyline
 
+// Axisymmetric walls: the offsets (a, b) = (rho, z) - nearest point of wall segment k of an
+// instance (the segment from polyline point k to point k + 1, in the (rho, z) half-plane of
+// the particle); lengths in units of q from the box origin.
+struct InstC;
+__device__ __forceinline__ void wall_seg_offset(const InstC& c, int k, double rho, double z, double& a, double& b);
+
 // device status bits
 constexpr unsigned ST_CAPACITY = 1u;
 constexpr unsigned ST_NONFINITE = 2u;
@@ -78,6 +84,15 @@ struct InstC {
     float wpf[2 * MAX_WP];
 };
 static_assert(sizeof(InstC) <= 4 * TILE, "the step kernel stages InstC in shared memory, one word per thread");
+
+__device__ __forceinline__ void wall_seg_offset(const InstC& c, int k, double rho, double z, double& a, double& b)
+{
+    const double r0 = c.wp[2 * k], z0 = c.wp[2 * k + 1];
+    const double dr = c.wp[2 * k + 2] - r0, dz = c.wp[2 * k + 3] - z0;
+    const double t = fmin(fmax(((rho - r0) * dr + (z - z0) * dz) / (dr * dr + dz * dz), 0.0), 1.0);
+    a = rho - (r0 + t * dr);
+    b = z - (z0 + t * dz);
+}
 
 // dynamic state of one instance (device-resident)
 struct InstD {

@@ -8,9 +8,9 @@ removal height, so the mass removed per 10 ms sampling interval is the mass that
 plane.  The filling is the synthetic lattice start of ``workloads.silo`` settled under gravity
 (the paper pours particles in from the top for 0.47 s and lets them settle until 0.7 s).
 
-    python -m paper_1705_03850_gb300.silo [--alpha 1 2] [--settle 0.3] [--discharge 0.6]
+    python -m paper_1705_03850_gb300.silo [--alpha 1 2] [--settle 0.3] [--discharge 0.6] [--two-level]
 
-prints one JSON line per alpha.
+prints one JSON line per alpha (and one for the two-level silo).
 """
 from __future__ import annotations
 
@@ -23,6 +23,7 @@ import numpy as np
 from . import dem, workloads
 
 PAPER_RATE = {1: (0.400, 0.007), 2: (0.315, 0.028)}   # Table 2, kg/s (mean, standard deviation)
+PAPER_RATE_TWO_LEVEL = {"fine": (0.390, 0.009), "coarse": (0.391, 0.026)}   # Table 2, MLCG rows
 
 
 def run(alpha: int = 1, settle_s: float = 0.3, discharge_s: float = 0.6, skip_s: float = 0.1,
@@ -76,17 +77,80 @@ def run(alpha: int = 1, settle_s: float = 0.3, discharge_s: float = 0.6, skip_s:
     }
 
 
+def run_two_level(settle_s: float = 0.3, discharge_s: float = 0.6, skip_s: float = 0.1, sample_s: float = 0.01,
+                  seed: int = 17, device=None) -> dict:
+    """The multi-level silo (``workloads.silo_two_level``): both levels settle together with the
+    orifice closed, then discharge; each level's rate is measured 1 cm below the orifice."""
+    import torch
+
+    from . import levels
+    cw, fw, spec = workloads.silo_two_level(seed=seed)
+    dev = torch.device(device or "cuda")
+    # one stream per level: the two levels' steps of a coupling period run concurrently (the
+    # coupling call orders the streams and ends with a host synchronisation)
+    coarse = dem.DEM([dem.desc_from_workload(cw)], max_neighbors=24, device=dev, stream=torch.cuda.Stream(dev))
+    coarse.write_state(cw.x, cw.v, cw.w, cw.r, cw.m)
+    fine = dem.DEM([dem.desc_from_workload(fw, capacity=fw.n + 100_000)], max_neighbors=24, device=dev,
+                   stream=torch.cuda.Stream(dev))
+    fine.write_state(fw.x, fw.v, fw.w, fw.r, fw.m)
+    z_o = cw.meta["z_o"]
+    for lv in (coarse, fine):
+        lv.set_walls(0, (0.0, 0.0), workloads.silo_walls(z_o, closed=True))
+    h = levels.Hierarchy([coarse, fine], [spec])
+    T = h.period
+    n_settle = int(round(settle_s / T))
+    per_sample = int(round(sample_s / T))
+    nsample = int(round(discharge_s / (per_sample * T)))
+    torch.cuda.synchronize(coarse.device)
+    t0 = time.perf_counter()
+    h.advance(n_settle)
+    torch.cuda.synchronize(coarse.device)
+    t_settle = time.perf_counter() - t0
+    n_after_fill = h.counts()
+    for lv in (coarse, fine):
+        lv.set_walls(0, (0.0, 0.0), workloads.silo_walls(z_o, closed=False), z_o - 0.01)
+    removed = {"coarse": [], "fine": []}
+    counts = []
+    t0 = time.perf_counter()
+    for _ in range(nsample):
+        h.advance(per_sample)
+        removed["coarse"].append(coarse.wall_removed()[1])
+        removed["fine"].append(fine.wall_removed()[1])
+        counts.append(h.counts())
+    t_dis = time.perf_counter() - t0
+    inserted = int(fine.counts()[1][0]) - fw.n
+    h.close()
+    coarse.close()
+    fine.close()
+    out = {"workload": "two-level silo: alpha = 2 over the whole silo, 2.8 mm in the lower quarter",
+           "particles_start": [cw.n, fw.n], "particles_after_fill": n_after_fill, "particles_end": counts[-1],
+           "fine_inserted": inserted, "period_s": T, "settle_s": n_settle * T,
+           "discharge_s": nsample * per_sample * T, "sample_s": per_sample * T,
+           "wall_s_settle": t_settle, "wall_s_discharge": t_dis}
+    for name in ("fine", "coarse"):
+        mass = np.array(removed[name])
+        rates = np.diff(np.concatenate([[0.0], mass])) / (per_sample * T)
+        use = rates[int(round(skip_s / (per_sample * T))):]
+        out[name] = {"rate_mean_kg_s": float(use.mean()), "rate_std_kg_s": float(use.std()),
+                     "rates_kg_s": [round(float(x), 4) for x in rates],
+                     "paper_rate_kg_s": PAPER_RATE_TWO_LEVEL[name][0], "paper_std_kg_s": PAPER_RATE_TWO_LEVEL[name][1]}
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--alpha", type=int, nargs="+", default=[1, 2])
+    ap.add_argument("--alpha", type=int, nargs="*", default=[1, 2])
     ap.add_argument("--settle", type=float, default=0.3, help="settling time with the orifice closed [s]")
     ap.add_argument("--discharge", type=float, default=0.6, help="discharge time [s]")
     ap.add_argument("--skip", type=float, default=0.1, help="start-up interval left out of the average [s]")
     ap.add_argument("--graph", type=int, default=200)
+    ap.add_argument("--two-level", action="store_true", help="also run the two-level (alpha 2 / 1) silo")
     a = ap.parse_args(argv)
     for alpha in a.alpha:
         r = run(alpha, settle_s=a.settle, discharge_s=a.discharge, skip_s=a.skip, graph=a.graph)
         print(json.dumps(r), flush=True)
+    if a.two_level:
+        print(json.dumps(run_two_level(settle_s=a.settle, discharge_s=a.discharge, skip_s=a.skip)), flush=True)
 
 
 if __name__ == "__main__":

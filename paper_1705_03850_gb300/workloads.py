@@ -396,7 +396,7 @@ def silo_walls(z_o: float, r_o: float = 0.02, R: float = 0.135, h_cone: float = 
 
 
 def _fcc_in_vessel(nn, r_wall, z_lo, z_hi, R, clear, n, rng, jitter):
-    """The n lowest FCC sites (nearest-neighbour distance nn) about the vertical axis at the origin
+    """The n lowest (n None: all) FCC sites (nearest-neighbour distance nn) about the vertical axis at the origin
     whose distance from the axis stays `clear` inside r_wall(z) (a horizontal distance: a sphere
     clears a sloped wall only where clear times the cosine of the wall's slope exceeds its
     radius), from z_lo + clear up."""
@@ -411,6 +411,8 @@ def _fcc_in_vessel(nn, r_wall, z_lo, z_hi, R, clear, n, rng, jitter):
     keep = (rho <= r_wall(pts[:, 2]) - clear) & (pts[:, 2] <= z_hi - clear)
     pts = pts[keep]
     pts = pts[np.lexsort((pts[:, 0], pts[:, 1], pts[:, 2]))]
+    if n is None:                                # all sites
+        n = pts.shape[0]
     if pts.shape[0] < n:
         raise ValueError(f"the vessel holds {pts.shape[0]} lattice sites, {n} asked")
     return pts[:n] + rng.uniform(-jitter, jitter, (n, 3))
@@ -518,3 +520,40 @@ def vessel_sphere(case: str = "cone", d: float = 2.0e-3, overlap: float = 2.0e-7
     return _finish(f"vessel_sphere_{case}", x, v, w, np.full(1, r), SILO_MATERIAL, (-m, -m, 0.0), (m, m, 0.05),
                    (False, False, False), 1e-6, (0.0, 0.0, -9.81), False, (0, 0, 0), 0.1 * d, 0,
                    walls=qgrid(np.asarray(pts, dtype=np.float64)))
+
+
+def silo_two_level(seed: int = 17, z_o: float = 0.05, h_fine: float = 0.10, cell: float = 0.0199,
+                   dt: float = 1e-6, interval: int = 15):
+    """The multi-level silo of Sec. 3: the coarse-grain silo of ``silo(2)`` (23,438 x 5.6 mm) over
+    its whole height, and a fine level (2.8 mm) in the lower quarter, the region |x|, |y| <= 8 cm
+    (the cone's radius there is at most 7.75 cm), z_o <= z <= z_o + h_fine, coupled through its
+    top face.  Surface, transition-layer (one cell deep) and correction cells are 2 cm cubes (the
+    paper's grid of 2 cm cells: a top layer for the transition, the cells below for the mass-flow
+    correction; `cell` is the least side, the region's 16 x 16 x 10 cm divide into 8 x 8 x 5 cells
+    of 2 cm); the controller acts every `interval` = 15 steps (Sec. 3).  The
+    fine level starts on an FCC lattice (nearest neighbour 1.05 d, a packing fraction of 0.64)
+    filling the region inside the cone up to one diameter below its top face (about 44,000
+    spheres), with the coarse level's start otherwise; both are to be settled together.
+    Returns (coarse, fine, spec)."""
+    coarse = silo(2, seed=seed, z_o=z_o, dt=dt)
+    rng = np.random.default_rng(seed + 100)
+    d = 2.8e-3
+    r_o, R, h_cone = coarse.meta["r_o"], coarse.meta["R"], coarse.meta["h_cone"]
+
+    def r_wall(z):
+        return np.where(z < z_o + h_cone, r_o + (R - r_o) * (z - z_o) / h_cone, R)
+
+    # every lattice site of the region inside the cone with d of clearance
+    x = _fcc_in_vessel(1.05 * d, r_wall, z_o, z_o + h_fine, 0.08, d, None, rng, 0.01 * d)
+    n = x.shape[0]
+    v = rng.uniform(-0.1, 0.1, (n, 3))
+    m = 0.09
+    fine = _finish("silo_fine", x, v, np.zeros((n, 3)), np.full(n, d / 2), SILO_MATERIAL, (-m, -m, 0.0),
+                   (m, m, z_o + h_fine + 0.03), (False, False, False), dt, (0.0, 0.0, -9.81), False, (0, 0, 0),
+                   0.1 * d, 0, diameter=d, z_o=z_o)
+    Tc = interval * float(f32(dt))
+    spec = dict(lo=tuple(qgrid((-0.08, -0.08, z_o)).tolist()), hi=tuple(qgrid((0.08, 0.08, z_o + h_fine)).tolist()),
+                feed_faces=1 << 5, drain_faces=0, surface_cell=cell, layer=cell, corr_cell=cell, interval=interval,
+                bins=16, alpha=2.0, kp=1.0, ki=1.0 / (10 * Tc), kv=0.5, mode=1, max_attempts=100, seed=seed * 1000,
+                mass_unit=1e-12, max_insert=256, dt=fine.dt)
+    return coarse, fine, spec

@@ -4,12 +4,12 @@ import numpy as np
 import oracle
 
 
-def oracle_params(wl, walls=None):
-    """walls: None, or the polyline (rho, z) of axisymmetric walls about the vertical axis (0, 0)."""
+def oracle_params(wl, walls=None, axis=(0.0, 0.0)):
+    """walls: None, or the polyline (rho, z) of axisymmetric walls about the vertical axis through `axis`."""
     m = wl.material
     return oracle.make_params(E=m.E, nu=m.nu, e=m.e, mu=m.mu, mu_wall=m.mu_wall, dt=wl.dt, g=wl.g, lo=wl.lo,
                               hi=wl.hi, periodic=wl.periodic, floor=wl.floor, floor_v=wl.floor_v,
-                              walls=None if walls is None else dict(axis=(0.0, 0.0), points=walls))
+                              walls=None if walls is None else dict(axis=axis, points=walls))
 
 
 def oracle_sim(wl, walls=None, **kw):

@@ -17,7 +17,13 @@ def _state(wl):
     return dict(x=wl.x, v=wl.v, w=wl.w, r=wl.r, m=wl.m, id=np.arange(wl.n))
 
 
-def _setup(pre_force=None, **extra):
+# a vertical cylinder wall about the column's axis, radius 10 mm: it cuts through the
+# transition cells and the feed face's surface cells of both levels
+WALL_AXIS = (0.012, 0.012)
+WALL = [(0.010, -0.01), (0.010, 0.07)]
+
+
+def _setup(pre_force=None, walls=None, **extra):
     A, B, fine_wl, spec = workloads.coupling_case()
     spec = dict(spec, **extra)
     rmax_c, rmax_f = float(A.r.max()), float(fine_wl.r.max())
@@ -25,6 +31,9 @@ def _setup(pre_force=None, **extra):
     coarse.write_state(A.x, A.v, A.w, A.r, A.m)
     fine = dem.DEM([dem.desc_from_workload(fine_wl, r_max=rmax_f, capacity=fine_wl.n + 4000)])
     fine.write_state(fine_wl.x, fine_wl.v, fine_wl.w, fine_wl.r, fine_wl.m)
+    if walls is not None:
+        coarse.set_walls(0, WALL_AXIS, walls)
+        fine.set_walls(0, WALL_AXIS, walls)
     cp = dem.Coupler(coarse, fine, **spec)
     coarse.write_state(B.x, B.v, B.w, B.r, B.m)
     if pre_force is not None:
@@ -32,15 +41,16 @@ def _setup(pre_force=None, **extra):
         fine.write(dem.FEXT, pre_force(fine.n, 2e-5))
     cp.couple()
     qf = oracle.quantum(fine_wl.lo, fine_wl.hi)
-    orc = oracle.Coupler(spec, oracle_params(B), oracle_params(fine_wl), fine_wl.lo, qf,
+    orc = oracle.Coupler(spec, oracle_params(B, walls, WALL_AXIS), oracle_params(fine_wl, walls, WALL_AXIS), fine_wl.lo, qf,
                          int(np.ceil(rmax_f / qf)), fine_wl.material.rho, idcap=A.n)
     orc.record(A.x, np.arange(A.n))
     out = orc.call(_state(B), _state(fine_wl), 0.0, 0.0)
     return A, B, fine_wl, spec, coarse, fine, cp, out, qf
 
 
-def test_coupling_bookkeeping_and_insertion_are_bit_exact():
-    A, B, fine_wl, spec, coarse, fine, cp, out, qf = _setup()
+@pytest.mark.parametrize("walls", [None, WALL])
+def test_coupling_bookkeeping_and_insertion_are_bit_exact(walls):
+    A, B, fine_wl, spec, coarse, fine, cp, out, qf = _setup(walls=walls)
     mu = spec["mass_unit"]
     assert out["cross"].sum() > 0 and out["nins"].sum() > 0      # material entered and was inserted
     assert np.array_equal(np.round(cp.read(dem.CPL_SURFACE_MASS) / mu).astype(np.int64), out["cross"].astype(np.int64))
@@ -64,10 +74,14 @@ def test_coupling_bookkeeping_and_insertion_are_bit_exact():
     # mass conservation: inserted + carry = entered (exact, integer units)
     mass_in = np.array([sum(round(m / mu) for m in out["ins_m"][c, :out["nins"][c]]) for c in range(len(nins))])
     assert np.array_equal(mass_in + out["carry"], out["cross"].astype(np.int64))
+    if walls is not None:         # inserted spheres lie inside the wall, clear of it
+        rho = np.hypot(x[:, 0] - WALL_AXIS[0], x[:, 1] - WALL_AXIS[1])
+        assert np.all(rho + r <= WALL[0][0])
 
 
-def test_coupling_measurements_and_controllers_match_oracle():
-    A, B, fine_wl, spec, coarse, fine, cp, out, qf = _setup()
+@pytest.mark.parametrize("walls", [None, WALL])
+def test_coupling_measurements_and_controllers_match_oracle(walls):
+    A, B, fine_wl, spec, coarse, fine, cp, out, qf = _setup(walls=walls)
     S = cp.S
     st = cp.read(dem.CPL_LAYER_STRESS)                 # (S, 2, 6)
     ref = np.transpose(out["lay"][:, :, :6], (1, 0, 2))

@@ -135,3 +135,60 @@ def test_controllers_special_cases():
     ctrl = out["ctrl"]
     e = ctrl[0, 0]
     assert ctrl[0, 2] == pytest.approx(2.0 * e, rel=1e-14)
+
+
+def _Pw(lo, hi, walls):
+    return oracle.make_params(E=E, nu=NU, e=0.6, mu=0.4, dt=1e-6, lo=lo, hi=hi, periodic=(False, False, False),
+                              walls=walls)
+
+
+def test_eq7_stress_includes_an_axisymmetric_wall_contact():
+    # one fine particle at rest pressed by delta into a vertical cylinder wall (axis at the
+    # region's centre, radius 11 mm) inside a transition cell: the wall adds r_c f with r_c
+    # the branch vector from the contact point to the centre, |r_c| = r - delta, along the
+    # wall normal -x: sigma_xx = (r - delta) F / V with the Hertz force F = 4/3 E* sqrt(r delta) delta
+    lo, hi = (0, 0, 0), (0.024, 0.024, 0.06)
+    R, r, delta = 0.011, 1e-3, 3e-6
+    walls = dict(axis=(0.012, 0.012), points=[(R, 0.0), (R, 0.06)])
+    Pc, Pf = _P(lo, hi), _Pw(lo, hi, walls)
+    cp, qf = _coupler(_spec(), Pc, Pf)
+    fine = _state([[0.012 + R - (r - delta), 0.012, 0.015]])
+    out = cp.call(_state([[0.006, 0.006, 0.05]]), fine, 0.0, 0.0)
+    Estar = E / (2.0 * (1.0 - NU * NU))
+    F = 4.0 / 3.0 * Estar * math.sqrt(r * delta) * delta
+    V = 0.012 ** 3
+    cell = 3                        # x, y >= 12 mm: cell (1, 1) of the 2 x 2 grid
+    assert out["lay"][1, cell, 0] == pytest.approx((r - delta) * F / V, rel=1e-9)
+    assert abs(out["lay"][1, cell, 1]) < 1e-9 * F * r / V and abs(out["lay"][1, cell, 2]) < 1e-9 * F * r / V
+    # the same particle with the wall removed: no contact part
+    out0 = _coupler(_spec(), Pc, _P(lo, hi, periodic=(False, False, False)))[0].call(
+        _state([[0.006, 0.006, 0.05]]), fine, 0.0, 0.0)
+    assert np.abs(out0["lay"][1, :, :6]).max() == 0.0
+
+
+def test_insertion_keeps_clear_of_the_fine_levels_walls():
+    # the feed face's cells reach beyond a cylinder wall of radius 10 mm about the region's
+    # centre; without the wall some inserted spheres straddle it or lie outside it, with it
+    # every one lies inside, clear of it
+    lo, hi = (0, 0, 0), (0.024, 0.024, 0.06)
+    R = 0.010
+    walls = dict(axis=(0.012, 0.012), points=[(R, 0.0), (R, 0.06)])
+    rng = np.random.default_rng(5)
+    xs = np.column_stack([rng.uniform(0, 0.024, 72), rng.uniform(0, 0.024, 72), np.full(72, 0.021)])
+    cg = _state(xs, r=np.full(72, 2e-3))
+    cg2 = dict(cg)
+    cg2["x"] = xs - np.array([0, 0, 0.002])
+    fine = _state([[0.012, 0.012, 0.003]])
+    res = {}
+    for name, Pf in (("open", _P(lo, hi, periodic=(False, False, False))), ("walled", _Pw(lo, hi, walls))):
+        cp, qf = _coupler(_spec(), _P(lo, hi), Pf, idcap=200)
+        cp.record(cg["x"], cg["id"])
+        out = cp.call(cg2, fine, 0.0, 0.0)
+        ins = np.concatenate([out["ins_u"][c, :out["nins"][c]] for c in range(4)])
+        x, r = ins[:, :3] * qf, ins[:, 3] * qf
+        rho = np.hypot(x[:, 0] - 0.012, x[:, 1] - 0.012)
+        res[name] = (len(ins), rho + r > R)
+        mass_in = np.array([sum(round(m / 1e-15) for m in out["ins_m"][c, :out["nins"][c]]) for c in range(4)])
+        assert np.array_equal(mass_in + out["carry"], out["cross"].astype(np.int64))
+    assert res["open"][1].any()
+    assert res["walled"][0] > 10 and not res["walled"][1].any()

@@ -1695,6 +1695,22 @@ dem_status upload_goff(dem_ctx* ctx)
     return DEM_OK;
 }
 
+// the host copy of the IDs handed out per instance, after coupling calls changed them on the
+// device (synchronises; also takes in the device status)
+dem_status refresh_count(dem_ctx* ctx)
+{
+    if (!ctx->count_stale) return DEM_OK;
+    std::vector<InstD> D(ctx->B);
+    CU(cudaMemcpyAsync(D.data(), ctx->dev.id, sizeof(InstD) * ctx->B, cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned stv = 0;
+    CU(cudaMemcpyAsync(&stv, &ctx->dev.g->status, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < ctx->B; ++k) ctx->count[k] = D[k].nid;
+    ctx->count_stale = false;
+    ctx->status |= stv;
+    return check_status(ctx);
+}
+
 long long total_count(const dem_ctx* ctx)
 {
     long long t = 0;
@@ -1710,6 +1726,7 @@ dem_status check_status(dem_ctx* ctx)
     if (ctx->status & ST_CAPACITY) return fail(ctx, DEM_ERR_CAPACITY, "neighbour list wider than max_neighbors");
     if (ctx->status & ST_TIMEOUT) return fail(ctx, DEM_ERR_TIMEOUT, "a bounded device wait gave up");
     if (ctx->status & ST_TRUNC) return fail(ctx, DEM_ERR_CAPACITY, "more contacts than the output width");
+    if (ctx->status & ST_INSERT) return fail(ctx, DEM_ERR_CAPACITY, "inserted particles exceed the fine level's capacity");
     if (ctx->status & ST_SKIN)
         return fail(ctx, DEM_ERR_CAPACITY,
                     "a particle moved more than half the skin while the lists were frozen for a differentiable "
@@ -2076,6 +2093,7 @@ dem_status dem_write(dem_ctx* ctx, int32_t field, const void* src, int64_t n)
     const int w = field_width(field);
     if (w == 0 || field == DEM_F_FORCE || field == DEM_F_TORQUE || field == DEM_F_WALL_XI || field == DEM_F_NBR_COUNT)
         return fail(ctx, DEM_ERR_ARG, "field is not writable");
+    if (dem_status st = refresh_count(ctx)) return st;
     if (n != total_count(ctx)) return fail(ctx, DEM_ERR_ARG, "n must equal the total particle count");
     if (n == 0) return DEM_OK;
     if (!src) return fail(ctx, DEM_ERR_ARG, "null source");
@@ -2102,6 +2120,7 @@ dem_status dem_read(dem_ctx* ctx, int32_t field, void* dst, int64_t n)
     if (ctx->status) return check_status(ctx);
     const int w = field_width(field);
     if (w == 0) return fail(ctx, DEM_ERR_ARG, "unknown field");
+    if (dem_status st = refresh_count(ctx)) return st;
     if (n != total_count(ctx)) return fail(ctx, DEM_ERR_ARG, "n must equal the total particle count");
     if (n == 0) return DEM_OK;
     if (!dst) return fail(ctx, DEM_ERR_ARG, "null destination");
@@ -2126,6 +2145,7 @@ dem_status dem_read_contacts(dem_ctx* ctx, int32_t* partner, double* xi, int32_t
     if (!ctx) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     if (ctx->B != 1) return fail(ctx, DEM_ERR_ARG, "contacts I/O needs a single-instance context");
+    if (dem_status st = refresh_count(ctx)) return st;
     if (n != total_count(ctx) || width < 1 || !partner || !xi) return fail(ctx, DEM_ERR_ARG, "bad contacts arguments");
     if (!is_device_ptr(partner) || !is_device_ptr(xi)) return fail(ctx, DEM_ERR_ARG, "contacts buffers must be device memory");
     dem_status st = launch_eval(ctx);
@@ -2140,6 +2160,7 @@ dem_status dem_write_contacts(dem_ctx* ctx, const int32_t* partner, const double
     if (!ctx) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     if (ctx->B != 1) return fail(ctx, DEM_ERR_ARG, "contacts I/O needs a single-instance context");
+    if (dem_status st = refresh_count(ctx)) return st;
     if (n != total_count(ctx) || width < 1 || !partner || !xi) return fail(ctx, DEM_ERR_ARG, "bad contacts arguments");
     if (!is_device_ptr(partner) || !is_device_ptr(xi)) return fail(ctx, DEM_ERR_ARG, "contacts buffers must be device memory");
     dem_status st = launch_rebuild(ctx, ctx->stream);
@@ -2194,6 +2215,7 @@ dem_status dem_instance_info_get(dem_ctx* ctx, int32_t k, dem_instance_info* out
         out->hi[a] = h.lo[a] + (double)c.ext[a] * h.q;
         out->ncell[a] = c.nc[a];
     }
+    if (dem_status st = refresh_count(ctx)) return st;
     out->n = ctx->count[k];
     out->capacity = c.cap;
     return DEM_OK;
@@ -2205,6 +2227,7 @@ dem_status dem_stats(dem_ctx* ctx, dem_stats_t* out)
     if (ctx->status) return check_status(ctx);
     memset(out, 0, sizeof(*out));
     out->steps = ctx->steps;
+    if (dem_status st = refresh_count(ctx)) return st;
     out->particles = total_count(ctx);
     if (!ctx->have_state) return DEM_OK;
     dem_status st = launch_eval(ctx);

@@ -683,7 +683,10 @@ __global__ void k_cp_append(Dev d, Geo g, Acc a, int* overflow)
     int tot = 0;
     for (int i = 0; i < g.S; ++i) tot += a.nins[i];
     if (D.n + tot > c.cap || D.nid + tot > c.cap) {
-        if (threadIdx.x == 0) *overflow = 1;
+        if (threadIdx.x == 0) {
+            *overflow = 1;
+            atomicOr(&d.g->status, ST_INSERT);
+        }
         return;
     }
     __syncthreads();
@@ -961,13 +964,9 @@ dem_status dem_couple(dem_coupler* cp)
     CU(cudaMemsetAsync(cp->overflow, 0, sizeof(int), s));
     k_cp_append<<<1, 256, 0, s>>>(ctx->dev, g, cp->a, cp->overflow);
     CU(cudaGetLastError());
-    int ovf = 0;
-    CU(cudaMemcpyAsync(&ovf, cp->overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
-    InstD D;
-    CU(cudaMemcpyAsync(&D, ctx->dev.id, sizeof(InstD), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (ovf) return fail(ctx, DEM_ERR_CAPACITY, "inserted particles exceed the fine level's capacity");
-    ctx->count[0] = D.nid;                  // (the device-side offsets were updated by k_cp_append)
+    // no host wait: the device updated the count and the offsets (k_cp_append) and reports an
+    // overflow in the status word; the host copy of the count is refreshed when next needed
+    ctx->count_stale = true;
     return DEM_OK;
 }
 
@@ -1078,6 +1077,7 @@ dem_status dem_clear_external_force(dem_ctx* ctx)
 dem_status dem_counts(dem_ctx* ctx, int64_t* live, int64_t* ids)
 {
     if (!ctx || !live || !ids) return DEM_ERR_ARG;
+    if (dem_status st = refresh_count(ctx)) return st;
     std::vector<InstD> D(ctx->B);
     CU(cudaMemcpyAsync(D.data(), ctx->dev.id, sizeof(InstD) * ctx->B, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));

@@ -26,6 +26,7 @@ struct dem_ctx {
     HostInstLo* d_hl = nullptr;
     bool fresh = true;                // velocities at an integer step (next step primes)
     bool walls = false;               // some instance has axisymmetric walls (step kernel variant)
+    bool count_stale = false;         // a coupling call changed the IDs handed out on the device
     bool have_state = false;
     long long steps = 0;
     unsigned status = 0;
@@ -52,6 +53,7 @@ using Rollout = dem_ctx::Rollout;
 namespace cgdem {
 dem_status fail(dem_ctx* c, dem_status st, const std::string& msg);
 dem_status check_status(dem_ctx* ctx);
+dem_status refresh_count(dem_ctx* ctx);
 dem_status launch_rebuild(dem_ctx* ctx, cudaStream_t st);
 dem_status launch_eval(dem_ctx* ctx);
 long long total_count(const dem_ctx* ctx);

@@ -50,6 +50,7 @@ constexpr unsigned ST_ESCAPED = 4u;
 constexpr unsigned ST_TIMEOUT = 8u;
 constexpr unsigned ST_TRUNC = 16u;
 constexpr unsigned ST_SKIN = 32u;     // displacement exceeded the skin while lists were frozen
+constexpr unsigned ST_INSERT = 64u;   // coupling insertions beyond the fine level's capacity (not appended)
 
 // constant description of one instance (host-computed at create)
 struct InstC {

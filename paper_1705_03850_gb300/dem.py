@@ -186,6 +186,7 @@ class DEM:
                                       ctypes.byref(h)), "create")
         self.h = h
         self.counts_ = [int(d.n) for d in descs]
+        self._count_stale = False                     # a coupling call changed the counts on the device
         self.dts = [float(d.dt) for d in descs]       # time step of each instance [s]
 
     # ------------------------------------------------------------------
@@ -196,6 +197,9 @@ class DEM:
 
     @property
     def n(self):
+        if self._count_stale:                         # refreshed only when needed (synchronises)
+            self._count_stale = False
+            self.counts_ = [int(self.info(k)["n"]) for k in range(len(self.counts_))]
         return sum(self.counts_)
 
     def close(self):
@@ -436,8 +440,8 @@ class Coupler:
         rc = self.L.dem_couple(self.h)
         if rc:
             raise DemError(rc, self.L.dem_last_error(self.fine.h).decode())
-        # the IDs handed out after the insertion (host-side count: no device read)
-        self.fine.counts_ = [int(self.fine.info(0)["n"])]
+        # the IDs handed out changed on the device; the host copy is refreshed when next needed
+        self.fine._count_stale = True
         return self
 
     def read(self, field):

@@ -183,7 +183,7 @@ def _kernel_hash():
     from); a profile taken from another version gives no traffic."""
     csrc = os.path.join(ROOT, "paper_1705_03850_gb300", "csrc")
     src = open(os.path.join(csrc, "dem.cu")).read()
-    i0 = src.index("template <int MODE>\n__global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(")
+    i0 = re.search(r"template <[^>]*>\n__global__ void __launch_bounds__\(TILE, DEM_STEP_MINB\) k_step\(", src).start()
     i1 = src.index("__global__ void k_set_cond", i0)
     h = hashlib.sha256(src[i0:i1].encode())
     h.update(re.search(r"#define DEM_STEP_MINB \d+", src).group(0).encode())   # its launch bound
@@ -434,7 +434,7 @@ def run_ours(args):
                    "mean_list_length": L, "mean_contacts_per_particle": C, "rebuilds_in_timed_region": rebuilds,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": peak_src, "kernel": "k_step<0> (fused force + Verlet)",
+                     "traffic": traffic, "peak_source": peak_src, "kernel": "k_step<0, false> (fused force + Verlet, the variant without walls)",
                      "bytes_per_particle_step": B_step, "kernel_ms_avg": t_kernel * 1e3,
                      "design_bytes_per_particle_step": B_design,
                      "design_achieved": n * B_design / t_kernel / 1e9,

@@ -44,3 +44,13 @@ def test_single_process_is_its_own_max():
     import bench
     assert bench.max_over_ranks(3.5, "cpu") == 3.5
     assert bench.whole_job_rate(100, 1, 2.0) == 50.0
+
+
+def test_step_kernel_source_hash_is_found():
+    # the bench ties a profile's DRAM traffic to the step kernel's source through this hash;
+    # it must find the kernel's definition in the source
+    import re
+
+    import bench
+    h = bench._kernel_hash()
+    assert re.fullmatch(r"[0-9a-f]{16}", h)

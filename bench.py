@@ -613,7 +613,9 @@ def run_coupled(args, dev, plain_value):
                              "everywhere, level 1 d = 4 mm in a 0.70 m region, level 2 d = 2 mm in a 0.18 m region "
                              "nested in it; plug flow 0.5 m/s at the start",
                  "vs_plain": value / plain_value, "settle_steps": args.coupled_settle,
-                 "timing": "wall clock (coupling calls synchronise); level steps in CUDA graphs of one period",
+                 "timing": "wall clock around the periods (no host wait inside; one stream per level); level "
+                           "steps in CUDA graphs of one period; coupling_share from 20 more periods with the host "
+                           "waiting around the coupling calls",
                  "multirate": dict(multi, speedup_in_simulated_time=single["wall_s_per_simulated_ms"] /
                                    multi["wall_s_per_simulated_ms"],
                                    what="dt 4e-6 / 2e-6 / 1e-6 s for the 8 / 4 / 2 mm levels (Sec. 3: the time "

@@ -272,8 +272,9 @@ dem_status dem_neighbor_counts_noalloc(const double *x, const double *r, int64_t
  *    of the face (Sec. 2.3);
  *  - per transition and correction cell on both levels: volume fraction,
  *    Favre velocity, largest speed, and the granular stress of Eq. 7
- *    (contact part 1/2 r_ij f_ij over contacts, floor contacts with the branch
- *    vector to the contact point, plus m v' v');
+ *    (contact part 1/2 r_ij f_ij over contacts, floor and axisymmetric-wall
+ *    contacts with the branch vector from the contact point to the centre,
+ *    plus m v' v');
  *  - stress PI controller per transition cell on the normal stress along the
  *    face normal (setpoint: coarse, process variable: fine):
  *    e = s_cg - s_fine, I += e T_c, u = kp e + ki I; every fine particle in
@@ -288,8 +289,10 @@ dem_status dem_neighbor_counts_noalloc(const double *x, const double *r, int64_t
  *    inhibition: until the inserted mass reaches the entered mass plus the
  *    carry of earlier intervals, draw a diameter from the histogram (uniform
  *    within the bin) and a position uniformly in the slab behind the cell
- *    (depth max(d, |v_n| T_c)), reject it if it overlaps any fine particle or
- *    an earlier insertion, give up after max_attempts rejections; inserted
+ *    (depth max(d, |v_n| T_c)), reject it if it overlaps any fine particle, an
+ *    earlier insertion or one of the fine level's axisymmetric walls, or lies
+ *    outside the vessel those walls enclose (dem_set_walls), give up after
+ *    max_attempts rejections; inserted
  *    particles take the cell's Favre velocity; random numbers come from the
  *    SplitMix64 generator on counters (seed, cell, interval, attempt, draw);
  *  - fine particles whose centre left the region through a drain face are
@@ -339,6 +342,12 @@ typedef enum {
 dem_status dem_coupler_workspace(dem_ctx *coarse, dem_ctx *fine, const dem_coupling *spec, int64_t *bytes);
 dem_status dem_coupler_create(dem_ctx *coarse, dem_ctx *fine, const dem_coupling *spec, void *workspace,
                               int64_t workspace_bytes, dem_coupler **out);
+/* One coupling call, queued on the fine level's stream after the work queued on the coarse
+ * level's (an event); the host does not wait.  The device updates the fine level's count;
+ * the first later call that needs the count on the host (dem_read, dem_write, dem_counts,
+ * dem_instance_info_get, dem_stats, the contact I/O) synchronises to fetch it.  Inserting
+ * beyond the fine level's capacity inserts nothing and sets DEM_ERR_CAPACITY, reported at
+ * that synchronisation or at dem_sync_status. */
 dem_status dem_couple(dem_coupler *cp);
 dem_status dem_coupler_read(dem_coupler *cp, int32_t field, double *dst, int64_t n);
 /* Free the coupler (not its workspace).  It does not touch the two contexts,
@@ -350,8 +359,9 @@ dem_status dem_coupler_destroy(dem_coupler *cp);
 dem_status dem_clear_external_force(dem_ctx *ctx);
 
 /* Live particles and IDs handed out, per instance (host arrays of B; synchronises).  Particles
- * that a coupling call marked for removal count as live until the next step drops them; reads
- * return NaN for them already. */
+ * marked for removal (by a coupling call, or by falling below a removal height at the last
+ * step of a dem_step call) count as live until the next step drops them; reads return NaN for
+ * them already. */
 dem_status dem_counts(dem_ctx *ctx, int64_t *live, int64_t *ids);
 
 /* Volume-averaged fields of instance k on a uniform grid of n[0] x n[1] x n[2] cubic cells of

@@ -359,9 +359,9 @@ dem_status dem_coupler_destroy(dem_coupler *cp);
 dem_status dem_clear_external_force(dem_ctx *ctx);
 
 /* Live particles and IDs handed out, per instance (host arrays of B; synchronises).  Particles
- * marked for removal (by a coupling call, or by falling below a removal height at the last
- * step of a dem_step call) count as live until the next step drops them; reads return NaN for
- * them already. */
+ * marked for removal count as live until a list build drops them: after a coupling call, the
+ * next step's; after falling below a removal height, the next build the displacements call
+ * for.  Reads return NaN for them at once. */
 dem_status dem_counts(dem_ctx *ctx, int64_t *live, int64_t *ids);
 
 /* Volume-averaged fields of instance k on a uniform grid of n[0] x n[1] x n[2] cubic cells of
@@ -389,8 +389,10 @@ dem_status dem_grid_fields(dem_ctx *ctx, int32_t k, const double lo[3], double h
  * simultaneous one, which needs two kinks within a particle diameter, starts from zero each
  * step); setting the walls clears them.
  * Particles whose centre falls below z_remove [m] at a step are removed at that step (their
- * IDs are not reused); z_remove = -INFINITY removes none.  Their number and mass accumulate in
- * dem_wall_removed.  The walls and the removal apply to dem_step, graphs and the read-out of
+ * IDs are not reused; reads return NaN for them): each is parked out of reach of every live
+ * particle and dropped at the next list build, which it does not force.  z_remove =
+ * -INFINITY (or a height more than about 2^31 length quanta below the box) removes none.
+ * Their number and mass accumulate in dem_wall_removed.  The walls and the removal apply to dem_step, graphs and the read-out of
  * velocities and forces; dem_rollout_forward refuses a context that has either
  * (DEM_ERR_STATE).  Synchronises the context's stream. */
 dem_status dem_set_walls(dem_ctx *ctx, int32_t k, const double *axis, int32_t npts, const double *points,

@@ -631,6 +631,17 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
         float4 Vv = vel[s];
         float4 Wv = omg[s];
         const unsigned idw = __float_as_uint(Vv.w);
+        if (idw & GONE_BIT) {   // removed below the removal height: parked until the next list build
+            if (MODE == 0) {
+                d.pos[cur ^ 1][s] = P;
+                d.vel[cur ^ 1][s] = Vv;
+                d.omg[cur ^ 1][s] = Wv;
+            } else {
+                d.outWX[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                d.cmask[s] = 0ull;
+            }
+            continue;
+        }
         const unsigned myid = idw & ID_MASK;
         const bool wall_prev = (idw & WALL_BIT) != 0u;
         const float m = Wv.w;
@@ -838,9 +849,13 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                 d.g->err_slot = s;
             }
             unsigned gone = 0u;
-            if (Pn.z < c.zrem) {   // fell below the removal height: dropped at the rebuild
+            if (Pn.z < c.zrem) {
+                // fell below the removal height: parked two cell heights lower with no radius
+                // (every live particle lies above the removal height, so none can touch it)
+                // and frozen until the next list build drops it; no rebuild is forced
                 gone = GONE_BIT;
-                atomicAdd(&d.id[kprev].nrem, 1);
+                Pn.z = (int)max((long long)Pn.z - 2ll * (c.ext[2] / c.nc[2] + 1), -2000000000ll);
+                Pn.w = 0;
                 atomicAdd(d.wrem + 2 * kprev, 1.0);
                 atomicAdd(d.wrem + 2 * kprev + 1, (double)m);
             }
@@ -876,13 +891,6 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                 const float disp = Dk->disp + sm;
                 Dk->disp = disp;
                 Dk->cur ^= 1;
-                if (Dk->nrem) {
-                    Dk->nrem = 0;
-                    if (Dk->flag == 0) {
-                        Dk->flag = 1;
-                        atomicOr(&d.g->any, 1u);
-                    }
-                }
                 if (2.0f * disp >= 0.99f * d.ic[kk].skin_f && Dk->flag == 0) {
                     if (d.g->frozen) {
                         atomicOr(&d.g->status, ST_SKIN);

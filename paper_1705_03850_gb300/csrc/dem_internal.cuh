@@ -106,8 +106,7 @@ struct InstD {
     int nid;             // IDs handed out so far (n plus removed particles); IDs are never reused
     int n_new;           // live particles after the pending rebuild (removed ones dropped)
     int fext;            // 1: add the per-particle external force fext to the contact forces
-    int nrem;            // particles removed below the removal height at this step
-    int pad[2];
+    int pad[3];
 };
 
 struct Glob {

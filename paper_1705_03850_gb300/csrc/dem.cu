@@ -631,17 +631,6 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
         float4 Vv = vel[s];
         float4 Wv = omg[s];
         const unsigned idw = __float_as_uint(Vv.w);
-        if (idw & GONE_BIT) {   // removed below the removal height: parked until the next list build
-            if (MODE == 0) {
-                d.pos[cur ^ 1][s] = P;
-                d.vel[cur ^ 1][s] = Vv;
-                d.omg[cur ^ 1][s] = Wv;
-            } else {
-                d.outWX[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-                d.cmask[s] = 0ull;
-            }
-            continue;
-        }
         const unsigned myid = idw & ID_MASK;
         const bool wall_prev = (idw & WALL_BIT) != 0u;
         const float m = Wv.w;
@@ -671,6 +660,19 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
         jn1 = 1 < ncnt ? jn1 : s;
         jn2 = 2 < ncnt ? jn2 : s;
         jn3 = 3 < ncnt ? jn3 : s;
+        // removed below the removal height: parked until the next list build drops it (tested
+        // here, after the row's first loads are in flight, so that live rows do not wait on it)
+        if (idw & GONE_BIT) {
+            if (MODE == 0) {
+                d.pos[cur ^ 1][s] = P;
+                d.vel[cur ^ 1][s] = Vv;
+                d.omg[cur ^ 1][s] = Wv;
+            } else {
+                d.outWX[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                d.cmask[s] = 0ull;
+            }
+            continue;
+        }
         for (int e0 = 0; e0 < ncnt; e0 += 4) {
             const int jb[4] = {jn0, jn1, jn2, jn3};
             int4 Qb[4];

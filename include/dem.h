@@ -321,6 +321,10 @@ typedef struct {
     int32_t max_insert;     /* most particles inserted per surface cell and call */
     int32_t add_forces;     /* 0: the controller forces replace the levels' held forces; 1: they are added
                                (for a level shared by two couplers; clear with dem_clear_external_force) */
+    double velocity_below;  /* correction cells whose centre lies below this height [m] take the
+                               velocity target (mode 0) whatever `mode` says: Sec. 3 applies a pure
+                               velocity coupling to coarse particles that passed the silo's orifice;
+                               -INFINITY (or NaN): none */
 } dem_coupling;
 
 typedef enum {

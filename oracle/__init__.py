@@ -224,6 +224,8 @@ class Coupler:
         self.CP[16] = spec["kv"]
         self.CP[17] = spec["mode"]
         self.CP[18] = spec["max_attempts"]
+        vb = spec.get("velocity_below", None)
+        self.CP[19] = -np.inf if vb is None or np.isnan(vb) else vb
         self.CP[20] = spec["mass_unit"]
         self.CP[21] = spec["max_insert"]
         self.CP[22] = spec["dt"]

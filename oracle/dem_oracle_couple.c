@@ -31,8 +31,10 @@
  *
  * Spec block CP (doubles): 0..2 lo, 3..5 hi, 6 feed bits, 7 drain bits,
  * 8 surface_cell, 9 layer, 10 corr_cell, 11 interval, 12 bins, 13 alpha,
- * 14 kp, 15 ki, 16 kv, 17 mode, 18 max_attempts, 19 (unused: the seed is passed
- * separately), 20 mass_unit, 21 max_insert, 22 dt, 23 fine particle density.
+ * 14 kp, 15 ki, 16 kv, 17 mode, 18 max_attempts, 19 velocity_below (correction
+ * cells centred below this height take the velocity target; -inf: none; the seed
+ * is passed separately), 20 mass_unit, 21 max_insert, 22 dt, 23 fine particle
+ * density.
  */
 #include <math.h>
 #include <stdint.h>
@@ -397,7 +399,9 @@ int32_t orc_couple(const double *CP, uint64_t seed, int32_t call, const double *
         memcpy(of, Af, 5 * sizeof(double));
         if (Ac[0] > 0 && Af[0] > 0) {
             double fac = 1.0;
-            if ((int)CP[17] == 1) fac = fmin(Af[4] / Ac[4], 4.0);
+            const int iz = i / (g.ncr[0] * g.ncr[1]);
+            const double zc = g.lo[2] + (iz + 0.5) * g.wcr[2];
+            if ((int)CP[17] == 1 && !(zc < CP[19])) fac = fmin(Af[4] / Ac[4], 4.0);
             for (int a = 0; a < 3; ++a) dv[3 * i + a] = Af[1 + a] / Af[0] * fac - Ac[1 + a] / Ac[0];
         }
     }

@@ -46,6 +46,7 @@ struct Geo {
     int rmaxf_u;         // largest fine radius in fine units (histogram range)
     int fresh_c, fresh_f;
     int add;             // add the controller forces to the held ones instead of replacing them
+    double vel_below;    // correction cells centred below this height take the velocity target
     // coarse positions (units) outside [ulo, uhi) take part in nothing but the position record:
     // the region grown by the largest coarse diameter and two units, rounded outwards
     long long ulo[3], uhi[3];
@@ -435,7 +436,9 @@ __global__ void k_cp_cells(Geo g, Acc a)
         dv[0] = dv[1] = dv[2] = 0.0;
         if (Ac[0] > 0 && Af[0] > 0) {
             double fac = 1.0;
-            if (g.mode == 1) fac = fmin(Af[4] / Ac[4], 4.0);
+            const int iz = i / (g.ncr[0] * g.ncr[1]);
+            const double zc = g.lo[2] + (iz + 0.5) * g.wcr[2];
+            if (g.mode == 1 && !(zc < g.vel_below)) fac = fmin(Af[4] / Ac[4], 4.0);
             for (int k = 0; k < 3; ++k) dv[k] = Af[1 + k] / Af[0] * fac - Ac[1 + k] / Ac[0];
         }
     }
@@ -846,6 +849,7 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
     g.drain = sp->drain_faces;
     g.seed = sp->seed;
     g.add = sp->add_forces ? 1 : 0;
+    g.vel_below = std::isnan(sp->velocity_below) ? -INFINITY : sp->velocity_below;
     // a coarse particle outside the region grown by one largest diameter (Favre samples reach
     // a diameter beyond the faces) touches no cell: bounds in coarse units, rounded outwards
     const double grow = 2.0 * coarse->rmax[0];

@@ -61,7 +61,8 @@ class CouplingSpec(ctypes.Structure):
                 ("corr_cell", ctypes.c_double), ("interval", ctypes.c_int32), ("bins", ctypes.c_int32),
                 ("alpha", ctypes.c_double), ("kp", ctypes.c_double), ("ki", ctypes.c_double), ("kv", ctypes.c_double),
                 ("mode", ctypes.c_int32), ("max_attempts", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("mass_unit", ctypes.c_double), ("max_insert", ctypes.c_int32), ("add_forces", ctypes.c_int32)]
+                ("mass_unit", ctypes.c_double), ("max_insert", ctypes.c_int32), ("add_forces", ctypes.c_int32),
+                ("velocity_below", ctypes.c_double)]
 
 
 # coupler fields (dem_coupler_field)
@@ -421,6 +422,7 @@ class Coupler:
         for k in ("surface_cell", "layer", "corr_cell", "alpha", "kp", "ki", "kv", "mass_unit"):
             setattr(sp, k, float(spec[k]))
         sp.seed = int(spec.get("seed", 0))
+        sp.velocity_below = float(spec.get("velocity_below", -math.inf))
         self.spec = sp
         nb = ctypes.c_int64()
         rc = self.L.dem_coupler_workspace(coarse.h, fine.h, ctypes.byref(sp), ctypes.byref(nb))

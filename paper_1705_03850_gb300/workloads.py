@@ -526,8 +526,9 @@ def silo_two_level(seed: int = 17, z_o: float = 0.05, h_fine: float = 0.10, cell
                    dt: float = 1e-6, interval: int = 15):
     """The multi-level silo of Sec. 3: the coarse-grain silo of ``silo(2)`` (23,438 x 5.6 mm) over
     its whole height, and a fine level (2.8 mm) in the lower quarter, the region |x|, |y| <= 8 cm
-    (the cone's radius there is at most 7.75 cm), z_o <= z <= z_o + h_fine, coupled through its
-    top face.  Surface, transition-layer (one cell deep) and correction cells are 2 cm cubes (the
+    (the cone's radius there is at most 7.75 cm), z_o - 2 cm <= z <= z_o + h_fine, coupled through
+    its top face; the correction cells below the orifice couple the coarse particles that passed
+    it to the fine velocity alone, those above it to the fine mass flow (Sec. 3).  Surface, transition-layer (one cell deep) and correction cells are 2 cm cubes (the
     paper's grid of 2 cm cells: a top layer for the transition, the cells below for the mass-flow
     correction; `cell` is the least side, the region's 16 x 16 x 10 cm divide into 8 x 8 x 5 cells
     of 2 cm); the controller acts every `interval` = 15 steps (Sec. 3).  The
@@ -552,8 +553,11 @@ def silo_two_level(seed: int = 17, z_o: float = 0.05, h_fine: float = 0.10, cell
                    (m, m, z_o + h_fine + 0.03), (False, False, False), dt, (0.0, 0.0, -9.81), False, (0, 0, 0),
                    0.1 * d, 0, diameter=d, z_o=z_o)
     Tc = interval * float(f32(dt))
-    spec = dict(lo=tuple(qgrid((-0.08, -0.08, z_o)).tolist()), hi=tuple(qgrid((0.08, 0.08, z_o + h_fine)).tolist()),
+    # the region reaches one cell below the orifice: coarse particles that passed it are
+    # coupled to the fine velocity alone (Sec. 3), those above it to the fine mass flow
+    spec = dict(lo=tuple(qgrid((-0.08, -0.08, z_o - 0.02)).tolist()),
+                hi=tuple(qgrid((0.08, 0.08, z_o + h_fine)).tolist()),
                 feed_faces=1 << 5, drain_faces=0, surface_cell=cell, layer=cell, corr_cell=cell, interval=interval,
                 bins=16, alpha=2.0, kp=1.0, ki=1.0 / (10 * Tc), kv=0.5, mode=1, max_attempts=100, seed=seed * 1000,
-                mass_unit=1e-12, max_insert=256, dt=fine.dt)
+                mass_unit=1e-12, max_insert=256, dt=fine.dt, velocity_below=float(qgrid(z_o)))
     return coarse, fine, spec

@@ -79,9 +79,10 @@ def test_coupling_bookkeeping_and_insertion_are_bit_exact(walls):
         assert np.all(rho + r <= WALL[0][0])
 
 
-@pytest.mark.parametrize("walls", [None, WALL])
-def test_coupling_measurements_and_controllers_match_oracle(walls):
-    A, B, fine_wl, spec, coarse, fine, cp, out, qf = _setup(walls=walls)
+@pytest.mark.parametrize("walls,extra", [(None, {}), (WALL, {}), (None, {"velocity_below": 0.01})])
+def test_coupling_measurements_and_controllers_match_oracle(walls, extra):
+    # the third case: mass-flow correction cells centred below 10 mm take the velocity target
+    A, B, fine_wl, spec, coarse, fine, cp, out, qf = _setup(walls=walls, **extra)
     S = cp.S
     st = cp.read(dem.CPL_LAYER_STRESS)                 # (S, 2, 6)
     ref = np.transpose(out["lay"][:, :, :6], (1, 0, 2))

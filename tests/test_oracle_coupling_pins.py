@@ -125,6 +125,13 @@ def test_controllers_special_cases():
                    for k in range(2)], v=[[0.0, 0.0, -0.1]] * 8)
     out = cp.call(_state([[0.004, 0.004, 0.004]], r=[1e-3]), fine, 0.0, 0.0)
     assert out["fext_c"][0, 2] == pytest.approx(0.5 * c["m"][0] * (-0.1 * 4.0) / 15e-6, rel=1e-12)
+    # ... except in correction cells centred below velocity_below (the region's 20 mm are two
+    # cells of 10 mm: the one holding both particles is centred at 5 mm): there the target is
+    # the fine velocity itself, as in mode 0
+    for vb, f in ((0.006, 1.0), (0.004, 4.0)):
+        cp, qf = _coupler(_spec(mode=1, velocity_below=vb), Pc, Pf)
+        out = cp.call(_state([[0.004, 0.004, 0.004]], r=[1e-3]), fine, 0.0, 0.0)
+        assert out["fext_c"][0, 2] == pytest.approx(0.5 * c["m"][0] * (-0.1 * f) / 15e-6, rel=1e-12)
     # PI with ki = 0: the force on a fine particle is linear in the stress mismatch
     spec = _spec(kp=2.0)
     cp, qf = _coupler(spec, Pc, Pf)

@@ -24,6 +24,7 @@ from . import dem, workloads
 
 PAPER_RATE = {1: (0.400, 0.007), 2: (0.315, 0.028)}   # Table 2, kg/s (mean, standard deviation)
 PAPER_RATE_TWO_LEVEL = {"fine": (0.390, 0.009), "coarse": (0.391, 0.026)}   # Table 2, MLCG rows
+PLANE_BELOW = 0.01   # the discharge rate is measured this far below the orifice [m] (Sec. 3)
 
 
 def run(alpha: int = 1, settle_s: float = 0.3, discharge_s: float = 0.6, skip_s: float = 0.1,
@@ -47,7 +48,7 @@ def run(alpha: int = 1, settle_s: float = 0.3, discharge_s: float = 0.6, skip_s:
     t_settle = time.perf_counter() - t0
     st0 = sim.stats()
     # open the orifice; everything below the measurement plane 1 cm under it is removed
-    sim.set_walls(0, (0.0, 0.0), workloads.silo_walls(z_o, closed=False), z_o - 0.01)
+    sim.set_walls(0, (0.0, 0.0), workloads.silo_walls(z_o, closed=False), z_o - PLANE_BELOW)
     removed = []
     t0 = time.perf_counter()
     for _ in range(nsample):
@@ -108,7 +109,7 @@ def run_two_level(settle_s: float = 0.3, discharge_s: float = 0.6, skip_s: float
     t_settle = time.perf_counter() - t0
     n_after_fill = h.counts()
     for lv in (coarse, fine):
-        lv.set_walls(0, (0.0, 0.0), workloads.silo_walls(z_o, closed=False), z_o - 0.01)
+        lv.set_walls(0, (0.0, 0.0), workloads.silo_walls(z_o, closed=False), z_o - PLANE_BELOW)
     removed = {"coarse": [], "fine": []}
     counts = []
     t0 = time.perf_counter()

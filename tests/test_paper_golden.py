@@ -100,3 +100,29 @@ def test_particle_count_arithmetic_of_the_runtime_discussion():
     assert ratio == pytest.approx(G["ml_ratio"], abs=5e-3)
     # the two-level discharge rate deviates from the reference by the stated amount
     assert (G["rate_ref"] - G["rate_ml"]) / G["rate_ref"] == pytest.approx(G["rate_ml_dev"], rel=1e-9)
+
+
+def test_silo_setup_follows_the_paper():
+    # the silo workloads and runner use the printed geometry, material, measurement and
+    # Table 2 rates (the values the runner reports beside its own)
+    from paper_1705_03850_gb300 import silo, workloads
+    m = workloads.SILO_MATERIAL
+    assert (m.E, m.nu, m.e, m.mu, m.mu_wall, m.rho) == (G["silo_E"], G["silo_nu"], G["silo_e"], G["silo_mu_pp"],
+                                                        G["silo_mu_pw"], G["silo_rho"])
+    z_o = 0.05
+    pts = workloads.silo_walls(z_o, closed=False)
+    assert pts[0][0] == pytest.approx(G["silo_orifice_diam"] / 2, abs=1e-7)
+    assert pts[-1][0] == pytest.approx(G["silo_cyl_diam"] / 2, abs=1e-7)
+    assert pts[-1][1] - pts[0][1] == pytest.approx(G["silo_height"], abs=1e-7)
+    assert pts[1][1] - pts[0][1] == pytest.approx(G["silo_height"] / 2, abs=1e-7)   # the lower half is the cone
+    assert silo.PAPER_RATE == {1: (G["rate_ref"], G["rate_ref_std"]), 2: (G["rate_cg"], G["rate_cg_std"])}
+    assert silo.PAPER_RATE_TWO_LEVEL == {"fine": (G["rate_ml"], G["rate_ml_std"]),
+                                         "coarse": (G["rate_ml_cg"], G["rate_ml_cg_std"])}
+    import inspect
+    sig = inspect.signature(silo.run)
+    assert sig.parameters["sample_s"].default == pytest.approx(1.0 / G["rate_sampling_hz"])
+    assert silo.PLANE_BELOW == G["rate_plane_below"]
+    coarse, fine, spec = workloads.silo_two_level()
+    assert spec["interval"] == G["controller_steps"]
+    w = (spec["hi"][0] - spec["lo"][0]) / int(np.floor((spec["hi"][0] - spec["lo"][0]) / spec["surface_cell"]))
+    assert w == pytest.approx(G["grid_cell"], rel=1e-6)

@@ -21,6 +21,25 @@ from __future__ import annotations
 from . import dem
 
 
+def period_steps(dts, intervals):
+    """The common coupling period T and the steps each level takes per period: coupler k
+    exchanges every intervals[k] steps of its fine level k + 1, so T = intervals[k] dts[k + 1]
+    for every k, and level l advances T / dts[l] steps (a whole number)."""
+    if len(intervals) != len(dts) - 1:
+        raise ValueError("one coupling spec per pair of neighbouring levels")
+    periods = [int(n) * dts[k + 1] for k, n in enumerate(intervals)]
+    T = periods[0]
+    if any(abs(p - T) > 1e-6 * T for p in periods):
+        raise ValueError("all couplers must exchange at one period (interval x fine time step)")
+    steps = []
+    for dt in dts:
+        n = int(round(T / dt))
+        if n < 1 or abs(n * dt - T) > 1e-6 * T:
+            raise ValueError(f"the coupling period {T:g} s is not a whole number of steps of {dt:g} s")
+        steps.append(n)
+    return T, steps
+
+
 class Hierarchy:
     """Levels (single-instance DEM contexts, coarsest first) and the couplers between neighbours."""
 
@@ -28,17 +47,7 @@ class Hierarchy:
         if len(specs) != len(levels) - 1:
             raise ValueError("one coupling spec per pair of neighbouring levels")
         self.levels = list(levels)
-        dts = [lv.dts[0] for lv in self.levels]
-        periods = [int(s["interval"]) * dts[k + 1] for k, s in enumerate(specs)]
-        self.period = periods[0]
-        if any(abs(p - self.period) > 1e-6 * self.period for p in periods):
-            raise ValueError("all couplers must exchange at one period (interval x fine time step)")
-        self.steps = []
-        for dt in dts:
-            n = int(round(self.period / dt))
-            if n < 1 or abs(n * dt - self.period) > 1e-6 * self.period:
-                raise ValueError(f"the coupling period {self.period:g} s is not a whole number of steps of {dt:g} s")
-            self.steps.append(n)
+        self.period, self.steps = period_steps([lv.dts[0] for lv in self.levels], [s["interval"] for s in specs])
         self.interval = self.steps[-1]          # steps of the finest level per period
         for lv in self.levels:
             lv.clear_external_force()

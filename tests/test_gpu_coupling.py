@@ -21,6 +21,8 @@ def _state(wl):
 # transition cells and the feed face's surface cells of both levels
 WALL_AXIS = (0.012, 0.012)
 WALL = [(0.010, -0.01), (0.010, 0.07)]
+# a cone closed below by a disk: radius 4 mm at z = 0 to 16 mm at z = 24 mm, then a cylinder
+CONE = [(0.0, 0.0), (0.004, 0.0), (0.016, 0.024), (0.016, 0.06)]
 
 
 def _setup(pre_force=None, walls=None, **extra):
@@ -48,7 +50,7 @@ def _setup(pre_force=None, walls=None, **extra):
     return A, B, fine_wl, spec, coarse, fine, cp, out, qf
 
 
-@pytest.mark.parametrize("walls", [None, WALL])
+@pytest.mark.parametrize("walls", [None, WALL, CONE])
 def test_coupling_bookkeeping_and_insertion_are_bit_exact(walls):
     A, B, fine_wl, spec, coarse, fine, cp, out, qf = _setup(walls=walls)
     mu = spec["mass_unit"]
@@ -74,9 +76,12 @@ def test_coupling_bookkeeping_and_insertion_are_bit_exact(walls):
     # mass conservation: inserted + carry = entered (exact, integer units)
     mass_in = np.array([sum(round(m / mu) for m in out["ins_m"][c, :out["nins"][c]]) for c in range(len(nins))])
     assert np.array_equal(mass_in + out["carry"], out["cross"].astype(np.int64))
-    if walls is not None:         # inserted spheres lie inside the wall, clear of it
+    if walls is WALL:             # inserted spheres lie inside the wall, clear of it
         rho = np.hypot(x[:, 0] - WALL_AXIS[0], x[:, 1] - WALL_AXIS[1])
         assert np.all(rho + r <= WALL[0][0])
+    if walls is CONE:             # inside the cone (normal at atan(1/2) from the horizontal), clear of it
+        rho = np.hypot(x[:, 0] - WALL_AXIS[0], x[:, 1] - WALL_AXIS[1])
+        assert np.all((0.004 + 0.5 * x[:, 2] - rho) / np.hypot(1.0, 0.5) >= r)
 
 
 @pytest.mark.parametrize("walls,extra", [(None, {}), (WALL, {}), (None, {"velocity_below": 0.01})])

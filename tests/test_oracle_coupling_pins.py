@@ -199,3 +199,29 @@ def test_insertion_keeps_clear_of_the_fine_levels_walls():
         assert np.array_equal(mass_in + out["carry"], out["cross"].astype(np.int64))
     assert res["open"][1].any()
     assert res["walled"][0] > 10 and not res["walled"][1].any()
+
+
+def test_insertion_inside_a_closed_cone():
+    # a cone narrowing downwards (radius 4 mm at z = 0 to 16 mm at z = 24 mm), closed below by a
+    # disk (a horizontal segment, which the inside test skips): the top face's cells reach
+    # beyond the cone; every inserted sphere lies inside it, clear of it, above the disk
+    lo, hi = (0, 0, 0), (0.024, 0.024, 0.06)
+    axis = (0.012, 0.012)
+    pts = [(0.0, 0.0), (0.004, 0.0), (0.016, 0.024), (0.016, 0.06)]
+    Pf = _Pw(lo, hi, dict(axis=axis, points=pts))
+    rng = np.random.default_rng(9)
+    xs = np.column_stack([rng.uniform(0, 0.024, 72), rng.uniform(0, 0.024, 72), np.full(72, 0.021)])
+    cg = _state(xs, r=np.full(72, 2e-3))
+    cg2 = dict(cg)
+    cg2["x"] = xs - np.array([0, 0, 0.002])
+    cp, qf = _coupler(_spec(), _P(lo, hi), Pf, idcap=200)
+    cp.record(cg["x"], cg["id"])
+    out = cp.call(cg2, _state([[0.012, 0.012, 0.003]]), 0.0, 0.0)
+    ins = np.concatenate([out["ins_u"][c, :out["nins"][c]] for c in range(4)])
+    assert len(ins) > 10
+    x, r = ins[:, :3] * qf, ins[:, 3] * qf
+    rho = np.hypot(x[:, 0] - axis[0], x[:, 1] - axis[1])
+    wall = 0.004 + 0.5 * x[:, 2]                      # the cone's radius at each centre's height
+    c = 1.0 / math.hypot(1.0, 0.5)                    # the cone's normal against the horizontal
+    assert np.all((wall - rho) * c >= r)             # inside, at least r from the cone
+    assert np.all(x[:, 2] >= r)

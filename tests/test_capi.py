@@ -59,3 +59,18 @@ def test_struct_layout_matches_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+def test_header_compiles_as_cpp_with_c_linkage(tmp_path):
+    # the boundary is usable from C++ callers: the header compiles there and its entry points
+    # keep C linkage (unmangled names)
+    import subprocess
+    src = tmp_path / "use.cpp"
+    src.write_text('#include "dem.h"\ndem_status (*volatile p)(dem_ctx*, int64_t) = &dem_step;\n'
+                   'int main() { return p == nullptr; }\n')
+    obj = tmp_path / "use.o"
+    subprocess.check_call(["g++", "-std=c++17", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-c",
+                           str(src), "-o", str(obj)])
+    syms = subprocess.check_output(["nm", str(obj)]).decode()
+    assert " U dem_step" in syms

@@ -358,7 +358,7 @@ def run_ours(args):
     C = st1["contacts"] / max(1, st1["particles"])
     Wc = st1["wall_contacts"] / max(1, st1["particles"])
     rebuilds = st1["rebuilds"] - st0["rebuilds"]
-    # algorithmic bytes per particle-step of the step kernel, SURVEY.md 8(d):
+    # algorithmic bytes per particle-step of the step kernel:
     # 48 B own state read + 48 B written, per list entry 4 B index + 12 B history read + 12 B written
     B_step = 96.0 + 28.0 * L
     # what this design must move at least: the same state, count and history mask,

@@ -39,8 +39,9 @@ def run(alpha: int = 1, settle_s: float = 0.3, discharge_s: float = 0.6, skip_s:
     sim.set_walls(0, (0.0, 0.0), workloads.silo_walls(z_o, closed=True))
     sim.set_graph(graph)
     dt = wl.dt
-    steps_settle = int(round(settle_s / dt / graph)) * graph
-    steps_sample = int(round(sample_s / dt / graph)) * graph
+    g = max(graph, 1)
+    steps_settle = int(round(settle_s / dt / g)) * g
+    steps_sample = int(round(sample_s / dt / g)) * g
     nsample = int(round(discharge_s / sample_s))
     torch.cuda.synchronize(sim.device)
     t0 = time.perf_counter()
@@ -57,6 +58,12 @@ def run(alpha: int = 1, settle_s: float = 0.3, discharge_s: float = 0.6, skip_s:
     t_dis = time.perf_counter() - t0
     st1 = sim.stats()
     live, _ = sim.counts()
+    # the step kernel (the variant with walls) over the last graph: CUDA-event time of every
+    # fifth launch, and the bytes one particle-step moves as the bench counts them (state 96 B,
+    # 28 B per list entry) plus the two wall-history slots written (32 B)
+    kms, kn = sim.graph_step_kernel_ms() if graph > 0 else (float("nan"), 1)
+    L = st1["list_entries"] / max(1, st1["particles"])
+    B = 96.0 + 28.0 * L + 32.0
     sim.close()
     mass = np.array([m for _, m in removed])
     rates = np.diff(np.concatenate([[0.0], mass])) / (steps_sample * dt)
@@ -75,6 +82,9 @@ def run(alpha: int = 1, settle_s: float = 0.3, discharge_s: float = 0.6, skip_s:
         "wall_s_settle": t_settle, "wall_s_discharge": t_dis,
         "particle_steps_per_s": psteps / (t_settle + t_dis), "steps": steps,
         "rebuilds_discharge": st1["rebuilds"] - st0["rebuilds"],
+        "step_kernel_ms": kms / max(1, kn), "mean_list_length": L,
+        "contacts_per_particle": st1["contacts"] / max(1, st1["particles"]),
+        "bytes_per_particle_step": B, "step_kernel_gbs": int(live[0]) * B / (kms / max(1, kn) * 1e-3) / 1e9,
     }
 
 

@@ -36,28 +36,35 @@ _SRCS = [os.path.join(_HERE, f) for f in ("dem_oracle.c", "dem_oracle_cs.c", "de
 _HDRS = [os.path.join(_HERE, f) for f in ("dem_oracle_common.h", "dem_oracle_dyn.h")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 NPARAM = 43
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle's C source with gcc (plain -O2, no fast-math)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle's C source with gcc (plain -O2, no fast-math).  openmp: the same
+    source with OpenMP, which runs the per-pair contact law on all host cores (the sums over
+    pairs stay serial, so the results are bit-identical to the serial build)."""
     os.makedirs(_BUILD, exist_ok=True)
+    path = _LIB_OMP_PATH if openmp else _LIB_PATH
     newest = max(os.path.getmtime(f) for f in _SRCS + _HDRS)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp] + _SRCS + ["-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    if force or not os.path.exists(path) or os.path.getmtime(path) < newest:
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off"] +
+                              (["-fopenmp"] if openmp else []) + ["-o", tmp] + _SRCS + ["-lm"])
+        os.replace(tmp, path)
+    return path
 
 
-def _load():
-    global _lib
-    if _lib is not None:
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
+    if openmp and _lib_omp is not None:
+        return _lib_omp
+    if not openmp and _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    lib = ctypes.CDLL(build(openmp=openmp))
     dp = ctypes.POINTER(ctypes.c_double)
     i64p = ctypes.POINTER(ctypes.c_int64)
     i32p = ctypes.POINTER(ctypes.c_int32)
@@ -70,7 +77,7 @@ def _load():
         fn.restype = i64
         fn.argtypes = [dp, i64, dp, dp, ctypes.c_double, i64, i64p, i64p]
     lib.orc_eval.restype = i64
-    lib.orc_eval.argtypes = [dp, i64, dp, dp, dp, dp, dp, i64p, i64, i64p, i64p, dp,
+    lib.orc_eval.argtypes = [dp, i64, dp, dp, dp, dp, dp, i64p, dp, i64, i64p, i64p, dp,
                              ctypes.c_double, ctypes.c_int32, dp, dp, i64, i64p, i64p, dp,
                              i32p, dp]
     lib.orc_cs_run_derivative.restype = ctypes.c_int32
@@ -78,14 +85,17 @@ def _load():
                                           ctypes.c_int32, i64] + [dp] * 10
     u64 = ctypes.c_uint64
     lib.orc_couple.restype = ctypes.c_int32
-    lib.orc_couple.argtypes = ([dp, u64, ctypes.c_int32, dp, i64, dp, dp, dp, dp, dp, i64p, dp, i64, dp, dp, dp, dp,
-                                dp, i64p, dp, ctypes.c_double, i64, dp, i32p, i64p, dp, ctypes.c_double,
+    lib.orc_couple.argtypes = ([dp, u64, ctypes.c_int32, dp, i64, dp, dp, dp, dp, dp, i64p, i64, i64p, i64p, dp,
+                                dp, i64, dp, dp, dp, dp, dp, i64p, i64, i64p, i64p, dp, ctypes.c_double, ctypes.c_double, dp, i32p, i64p, dp, ctypes.c_double,
                                 ctypes.c_double, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_uint32), dp, dp, dp, dp,
-                                dp, dp, i32p, i64p, dp, i32p])
+                                dp, dp, i32p, dp, dp, i32p, i32p])
     lib.orc_run.restype = ctypes.c_int32
-    lib.orc_run.argtypes = [dp, i64, dp, dp, dp, dp, dp, i64p, i64p, i64, i64p, i64p, dp,
+    lib.orc_run.argtypes = [dp, i64, dp, dp, dp, dp, dp, i64p, dp, i64p, i64, i64p, i64p, dp,
                             i32p, dp, dp, i64, ctypes.c_int32, ctypes.c_int32]
-    _lib = lib
+    if openmp:
+        _lib_omp = lib
+    else:
+        _lib = lib
     return lib
 
 
@@ -204,10 +214,13 @@ class Coupler:
     """FP64 oracle of the coarse/fine coupling (see dem_oracle_couple.c).
 
     spec: dict with the fields of dem_coupling; Pc, Pf: parameter blocks of the
-    levels; the fine frame (lof, qf) and largest fine radius rmaxf_u in fine units.
+    levels; rmax_f: the fine level's largest radius (the range of the radius
+    histogram) [m]; rho_f: fine density; idcap: coarse IDs; band: insertion
+    decisions whose clearance is within (-band, band) [m] are reported per cell
+    in out["border"] (first such attempt, -1: none).
     """
 
-    def __init__(self, spec, Pc, Pf, lof, qf, rmaxf_u, rho_f, idcap):
+    def __init__(self, spec, Pc, Pf, rmax_f, rho_f, idcap, band=0.0):
         self.CP = np.zeros(24)
         self.CP[0:3] = spec["lo"]
         self.CP[3:6] = spec["hi"]
@@ -233,9 +246,8 @@ class Coupler:
         self.seed = int(spec["seed"])
         self.Pc = np.ascontiguousarray(Pc, dtype=np.float64)
         self.Pf = np.ascontiguousarray(Pf, dtype=np.float64)
-        self.lof = np.ascontiguousarray(lof, dtype=np.float64)
-        self.qf = float(qf)
-        self.rmaxf_u = int(rmaxf_u)
+        self.rmax_f = float(rmax_f)
+        self.band = float(band)
         self.prev = np.zeros((idcap, 3))
         self.prev_ok = np.zeros(idcap, dtype=np.int32)
         self.calls = 0
@@ -261,7 +273,9 @@ class Coupler:
             self.prev_ok[k] = 1
 
     def call(self, coarse, fine, dth_c, dth_f):
-        """coarse, fine: dicts x, v, w, r, m, id (float64 / int64 arrays). Returns a dict of outputs."""
+        """coarse, fine: dicts x, v, w, r, m, id (float64 / int64 arrays) and optionally the
+        contact history hist = (a, b, xi) as Sim.history() gives it (none: no stored overlaps).
+        Returns a dict of outputs."""
         lib = _load()
         S, C = self._sizes()
         if self.S is None:
@@ -274,25 +288,35 @@ class Coupler:
         out = dict(cross=np.zeros(S, dtype=np.uint64), hist=np.zeros(S * bins, dtype=np.uint32), fav=np.zeros(S * 4),
                    lay=np.zeros(2 * S * 11), ctrl=np.zeros(S * 3), cor=np.zeros(2 * C * 5), fext_c=np.zeros(nc * 3),
                    fext_f=np.zeros(nf * 3), removed=np.zeros(nf, dtype=np.int32),
-                   ins_u=np.zeros(S * mi * 4, dtype=np.int64), ins_m=np.zeros(S * mi), nins=np.zeros(S, dtype=np.int32))
-        c = {k: np.ascontiguousarray(v, dtype=np.int64 if k == "id" else np.float64) for k, v in coarse.items()}
-        f = {k: np.ascontiguousarray(v, dtype=np.int64 if k == "id" else np.float64) for k, v in fine.items()}
+                   ins_x=np.zeros(S * mi * 4), ins_m=np.zeros(S * mi), nins=np.zeros(S, dtype=np.int32),
+                   border=np.zeros(S, dtype=np.int32))
+        def hist(lv):
+            a, b, x = lv.get("hist", (np.zeros(0), np.zeros(0), np.zeros((0, 3))))[:3]
+            return (len(a), np.ascontiguousarray(a, dtype=np.int64), np.ascontiguousarray(b, dtype=np.int64),
+                    np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 3)))
+        hc, hf = hist(coarse), hist(fine)
+        c = {k: np.ascontiguousarray(v, dtype=np.int64 if k == "id" else np.float64) for k, v in coarse.items()
+             if k != "hist"}
+        f = {k: np.ascontiguousarray(v, dtype=np.int64 if k == "id" else np.float64) for k, v in fine.items()
+             if k != "hist"}
         u64p = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
         u32p = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
         lib.orc_couple(_d(self.CP), self.seed, self.calls, _d(self.Pc), nc, _d(c["x"]), _d(c["v"]), _d(c["w"]),
-                       _d(c["r"]), _d(c["m"]), _i64(c["id"]), _d(self.Pf), nf, _d(f["x"]), _d(f["v"]), _d(f["w"]),
-                       _d(f["r"]), _d(f["m"]), _i64(f["id"]), _d(self.lof), self.qf, self.rmaxf_u, _d(self.prev),
+                       _d(c["r"]), _d(c["m"]), _i64(c["id"]), hc[0], _i64(hc[1]), _i64(hc[2]), _d(hc[3]),
+                       _d(self.Pf), nf, _d(f["x"]), _d(f["v"]), _d(f["w"]),
+                       _d(f["r"]), _d(f["m"]), _i64(f["id"]), hf[0], _i64(hf[1]), _i64(hf[2]), _d(hf[3]),
+                       self.rmax_f, self.band, _d(self.prev),
                        _i32(self.prev_ok), _i64(self.carry), _d(self.integ), float(dth_c), float(dth_f),
                        u64p(out["cross"]), u32p(out["hist"]), _d(out["fav"]), _d(out["lay"]), _d(out["ctrl"]),
-                       _d(out["cor"]), _d(out["fext_c"]), _d(out["fext_f"]), _i32(out["removed"]), _i64(out["ins_u"]),
-                       _d(out["ins_m"]), _i32(out["nins"]))
+                       _d(out["cor"]), _d(out["fext_c"]), _d(out["fext_f"]), _i32(out["removed"]), _d(out["ins_x"]),
+                       _d(out["ins_m"]), _i32(out["nins"]), _i32(out["border"]))
         out["carry"] = self.carry.copy()
         out["hist"] = out["hist"].reshape(S, bins)
         out["fav"] = out["fav"].reshape(S, 4)
         out["lay"] = out["lay"].reshape(2, S, 11)
         out["ctrl"] = out["ctrl"].reshape(S, 3)
         out["cor"] = out["cor"].reshape(2, C, 5)
-        out["ins_u"] = out["ins_u"].reshape(S, mi, 4)
+        out["ins_x"] = out["ins_x"].reshape(S, mi, 4)
         out["ins_m"] = out["ins_m"].reshape(S, mi)
         out["fext_c"] = out["fext_c"].reshape(nc, 3)
         out["fext_f"] = out["fext_f"].reshape(nf, 3)
@@ -307,7 +331,8 @@ class Sim:
     the particle IDs (a < b), or (a, -1) for the floor).
     """
 
-    def __init__(self, P, x, v, w, r, m, ids=None, use_cells=True):
+    def __init__(self, P, x, v, w, r, m, ids=None, use_cells=True, openmp=False):
+        self.openmp = bool(openmp)
         self.P = np.ascontiguousarray(P, dtype=np.float64)
         self.x = np.array(x, dtype=np.float64).reshape(-1, 3)
         n = self.x.shape[0]
@@ -327,6 +352,14 @@ class Sim:
         self.F = np.zeros((n, 3))
         self.T = np.zeros((n, 3))
         self.primed = 0
+        # held external force per particle [N] (None: none), added at every evaluation
+        self.fext = None
+
+    def _fext(self):
+        if self.fext is None:
+            return None
+        self.fext = np.ascontiguousarray(self.fext, dtype=np.float64).reshape(self.n, 3)
+        return _d(self.fext)
 
     @property
     def n(self):
@@ -347,12 +380,32 @@ class Sim:
         k = int(self.nh[0])
         return self.ha[:k].copy(), self.hb[:k].copy(), self.hxi[:k].copy(), self.slip[:k].copy()
 
+    def checkpoint(self):
+        """A copy of the whole state: x, v, w, r, m, IDs, the forces of the last evaluation,
+        the contact history and whether that evaluation has been done."""
+        ha, hb, hxi, slip = self.history()
+        return dict(x=self.x.copy(), v=self.v.copy(), w=self.w.copy(), r=self.r.copy(), m=self.m.copy(),
+                    id=self.id.copy(), F=self.F.copy(), T=self.T.copy(), ha=ha, hb=hb, hxi=hxi, slip=slip,
+                    primed=self.primed, use_cells=self.use_cells)
+
+    @classmethod
+    def restore(cls, P, ck):
+        """A simulation continuing from a checkpoint() (same parameters P)."""
+        s = cls(P, ck["x"], ck["v"], ck["w"], ck["r"], ck["m"], ids=ck["id"], use_cells=bool(ck["use_cells"]))
+        k = len(ck["ha"])
+        s.ha[:k], s.hb[:k], s.hxi[:k], s.slip[:k] = ck["ha"], ck["hb"], ck["hxi"], ck["slip"]
+        s.nh[0] = k
+        s.F[:] = ck["F"]
+        s.T[:] = ck["T"]
+        s.primed = ck["primed"]
+        return s
+
     def evaluate(self, dt_hist=0.0):
         """Forces at the current state without changing it.
 
         Returns (F, T, (a, b, xi, slip), fabs) where fabs[i] = sum_j |F_ij| + |m_i g|.
         """
-        lib = _load()
+        lib = _load(self.openmp)
         n = self.n
         F = np.zeros((n, 3))
         T = np.zeros((n, 3))
@@ -362,7 +415,7 @@ class Sim:
         hxi = np.zeros((self.cap, 3))
         slip = np.zeros(self.cap, dtype=np.int32)
         c = lib.orc_eval(_d(self.P), n, _d(self.x), _d(self.v), _d(self.w), _d(self.r), _d(self.m),
-                         _i64(self.id), int(self.nh[0]), _i64(self.ha), _i64(self.hb), _d(self.hxi),
+                         _i64(self.id), self._fext(), int(self.nh[0]), _i64(self.ha), _i64(self.hb), _d(self.hxi),
                          float(dt_hist), self.use_cells, _d(F), _d(T), self.cap, _i64(ha), _i64(hb),
                          _d(hxi), _i32(slip), _d(fabs))
         if c < 0:
@@ -370,9 +423,9 @@ class Sim:
         return F, T, (ha[:c], hb[:c], hxi[:c], slip[:c]), fabs
 
     def run(self, nsteps: int):
-        lib = _load()
+        lib = _load(self.openmp)
         rc = lib.orc_run(_d(self.P), self.n, _d(self.x), _d(self.v), _d(self.w), _d(self.r),
-                         _d(self.m), _i64(self.id), _i64(self.nh), self.cap, _i64(self.ha),
+                         _d(self.m), _i64(self.id), self._fext(), _i64(self.nh), self.cap, _i64(self.ha),
                          _i64(self.hb), _d(self.hxi), _i32(self.slip), _d(self.F), _d(self.T),
                          int(nsteps), self.primed, self.use_cells)
         if rc != 0:

@@ -23,10 +23,12 @@
  *   4. fine-to-coarse P controller per correction cell (velocity or mass flow
  *      with the volume-fraction ratio capped at 4);
  *   5. simple sequential inhibition (Diggle et al. 1976) of fine particles per
- *      surface cell with SplitMix64 random numbers on counters (a candidate
- *      overlapping a fine particle, an earlier insertion or one of the fine
- *      level's axisymmetric walls, or lying outside the vessel the walls
- *      enclose, is rejected);
+ *      surface cell, in continuous space: radius uniform within a bin drawn
+ *      from the entry histogram, centre uniform in the cell's insertion slab,
+ *      from SplitMix64 random numbers on counters (a candidate overlapping a
+ *      fine particle, an earlier insertion or one of the fine level's
+ *      axisymmetric walls, or lying outside the vessel the walls enclose, is
+ *      rejected);
  *   6. removal of fine particles that left through drain faces.
  *
  * Spec block CP (doubles): 0..2 lo, 3..5 hi, 6 feed bits, 7 drain bits,
@@ -162,11 +164,30 @@ static void seg_offset(const double *P, int k, double rho, double z, double rs, 
     *b = z - (zz0 + t * dz);
 }
 
+/* The level's stored tangential overlap of contact (a, b) (a < b particle IDs; b = -1 the floor,
+ * -2 - k wall segment k), from its history records sorted by (a, b); zero if it has none. */
+static void stored_xi(int64_t nh, const int64_t *ha, const int64_t *hb, const double *hxi, int64_t a, int64_t b,
+                      double *xi)
+{
+    int64_t lo = 0, hi = nh - 1;
+    xi[0] = xi[1] = xi[2] = 0.0;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (ha[mid] == a && hb[mid] == b) {
+            xi[0] = hxi[3 * mid]; xi[1] = hxi[3 * mid + 1]; xi[2] = hxi[3 * mid + 2];
+            return;
+        }
+        if (ha[mid] < a || (ha[mid] == a && hb[mid] < b)) lo = mid + 1;
+        else hi = mid - 1;
+    }
+}
+
 /* Eq. 7 contributions of the particles of one level to the transition cells.
  * lay[(cell)*20 + k]: 0 m, 1..3 m v, 4..9 m v v, 10 V, 11..16 contact stress. */
 static void level_layer(const double *CP, const cgeo_t *g, const double *P, int64_t n, const double *x,
                         const double *v, const double *w, const double *r, const double *m, const int64_t *id,
-                        double dt_hist, double *lay, double *vmax)
+                        int64_t nh, const int64_t *ha, const int64_t *hb, const double *hxi, double dt_hist,
+                        double *lay, double *vmax)
 {
     const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
     int64_t np = 0;
@@ -187,11 +208,13 @@ static void level_layer(const double *CP, const cgeo_t *g, const double *P, int6
      * adds 1/2 r_ij f_ij with r_ij = x_i - x_j and f_ij the force on i */
     for (int64_t k = 0; k < np; ++k) {
         int64_t a = pairs[k].i, b = pairs[k].j;
+        if (id[b] < id[a]) { int64_t t = a; a = b; b = t; }    /* the history is kept in the lower ID's frame */
         double d[3] = {x[3 * a] - x[3 * b], x[3 * a + 1] - x[3 * b + 1], x[3 * a + 2] - x[3 * b + 2]};
         min_image_d(P, d);
         double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         double nvec[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
-        double xi[3] = {0, 0, 0}, fa[3], ft[3];
+        double xi[3], fa[3], ft[3];
+        stored_xi(nh, ha, hb, hxi, id[a], id[b], xi);
         orc_contact_pair(P, r[a], r[b], m[a], m[b], 0, r[a] + r[b] - dist, nvec, v + 3 * a, v + 3 * b, w + 3 * a,
                          w + 3 * b, xi, dt_hist, fa, ft);
         int ca = layer_cell(g, CP[9], x + 3 * a, &fk), cb = layer_cell(g, CP[9], x + 3 * b, &fk);
@@ -210,7 +233,8 @@ static void level_layer(const double *CP, const cgeo_t *g, const double *P, int6
             if (!(r[i] - h > 0)) continue;
             int c = layer_cell(g, CP[9], x + 3 * i, &fk);
             if (c < 0) continue;
-            double xi[3] = {0, 0, 0}, fa[3], ft[3];
+            double xi[3], fa[3], ft[3];
+            stored_xi(nh, ha, hb, hxi, id[i], -1, xi);
             orc_contact_pair(P, r[i], 0.0, m[i], 0.0, 1, r[i] - h, nz, v + 3 * i, P + P_FLOORV, w + 3 * i, zero3, xi,
                              dt_hist, fa, ft);
             double rv[3] = {0, 0, h};
@@ -234,7 +258,8 @@ static void level_layer(const double *CP, const cgeo_t *g, const double *P, int6
             const double dist = sqrt(a * a + b * b);
             if (!(r[i] - dist > 0.0)) continue;
             const double nv[3] = {a / dist * erx, a / dist * ery, b / dist}, zero3[3] = {0, 0, 0};
-            double xi[3] = {0, 0, 0}, fa[3], ft[3];
+            double xi[3], fa[3], ft[3];
+            stored_xi(nh, ha, hb, hxi, id[i], -2 - k, xi);
             orc_contact_pair(P, r[i], 0.0, m[i], 0.0, 1, r[i] - dist, nv, v + 3 * i, zero3, w + 3 * i, zero3, xi,
                              dt_hist, fa, ft);
             const double rv[3] = {dist * nv[0], dist * nv[1], dist * nv[2]};
@@ -244,7 +269,6 @@ static void level_layer(const double *CP, const cgeo_t *g, const double *P, int6
             }
         }
     }
-    (void)id;
 }
 
 static void level_corr(const cgeo_t *g, int64_t n, const double *x, const double *v, const double *r,
@@ -277,39 +301,39 @@ static uint64_t draw(uint64_t seed, int cell, int call, int attempt, int k)
 
 static int64_t below(uint64_t u, int64_t n) { return (int64_t)(((u >> 32) * (uint64_t)n) >> 32); }
 
-static int64_t min_image_i(int64_t dx, const double *Pf, double qf, int a)
-{
-    if (Pf[P_PER + a] == 0.0) return dx;
-    int64_t L = llround((Pf[P_HI + a] - Pf[P_LO + a]) / qf), h = L / 2;
-    if (dx > h) dx -= L;
-    else if (dx < -h) dx += L;
-    return dx;
-}
+/* uniform in [0, 1) from the top 53 of 64 random bits */
+static double unit(uint64_t u) { return (double)(u >> 11) * 0x1p-53; }
 
 /*
  * One coupling call.  Inputs: spec CP and seed; the call number; both levels'
- * parameter blocks (Pc, Pf) and states; the fine frame (lof, qf, rmaxf_u); the
+ * parameter blocks (Pc, Pf), states and contact histories (records sorted by
+ * (a, b), as the dynamics keep them; the contact forces of Eq. 7 take the
+ * stored overlap of each contact, advanced by dth_c / dth_f); the fine level's largest radius rmaxf
+ * (the range of the radius histogram) and the borderline band (metres); the
  * coarse positions at the previous call by ID (prev, prev_ok; updated); the
  * carried mass per surface cell (carry; updated) and the controller integral
  * (integ; updated); dt_hist of the stress evaluation per level.
  * Outputs: cross[S] (mass units), hist[S*bins], fav[S*4], layout[2*S*11],
  * ctrl[S*3], corout[2*C*5], fext_c[nc*3], fext_f[nf*3], removed[nf],
- * inserted particles ins_u[S*max_insert*4] (fine units, radius last),
- * ins_m[S*max_insert], nins[S].  Returns 0.
+ * inserted particles ins_x[S*max_insert*4] (centre and radius, metres),
+ * ins_m[S*max_insert], nins[S], border[S].  Returns 0.
  */
 int32_t orc_couple(const double *CP, uint64_t seed, int32_t call, const double *Pc, int64_t nc, const double *xc,
                    const double *vc, const double *wc, const double *rc, const double *mc, const int64_t *idc,
+                   int64_t nhc, const int64_t *hac, const int64_t *hbc, const double *hxic,
                    const double *Pf, int64_t nf, const double *xf, const double *vf, const double *wf,
-                   const double *rf, const double *mf, const int64_t *idf, const double *lof, double qf,
-                   int64_t rmaxf_u, double *prev, int32_t *prev_ok, int64_t *carry, double *integ, double dth_c,
+                   const double *rf, const double *mf, const int64_t *idf,
+                   int64_t nhf, const int64_t *haf, const int64_t *hbf, const double *hxif, double rmaxf, double band,
+                   double *prev, int32_t *prev_ok, int64_t *carry, double *integ, double dth_c,
                    double dth_f, uint64_t *cross, uint32_t *hist, double *fav, double *layout, double *ctrl,
-                   double *corout, double *fext_c, double *fext_f, int32_t *removed, int64_t *ins_u, double *ins_m,
-                   int32_t *nins)
+                   double *corout, double *fext_c, double *fext_f, int32_t *removed, double *ins_x, double *ins_m,
+                   int32_t *nins, int32_t *border)
 {
     cgeo_t g;
     make_geo(CP, &g);
     const int S = g.S, C = g.C, bins = (int)CP[12], max_ins = (int)CP[21], max_att = (int)CP[18];
     const double alpha = CP[13], mass_unit = CP[20], dt = CP[22], Tc = CP[11] * dt, layer = CP[9];
+    const double wbin = rmaxf / bins;    /* width of a radius bin [m] */
     memset(cross, 0, sizeof(uint64_t) * S);
     memset(hist, 0, sizeof(uint32_t) * S * bins);
     memset(fav, 0, sizeof(double) * S * 4);
@@ -342,9 +366,10 @@ int32_t orc_couple(const double *CP, uint64_t seed, int32_t call, const double *
                 }
                 if (cbest >= 0) {
                     cross[cbest] += (uint64_t)llrint(mc[i] / mass_unit);
-                    int64_t ru = llrint(rc[i] / alpha / qf);
-                    if (ru > rmaxf_u) ru = rmaxf_u;
-                    hist[(size_t)cbest * bins + (int)(ru * bins / (rmaxf_u + 1))] += 1;
+                    /* bin of the fine-scale radius r / alpha among bins equal bins over [0, r_max,fine) */
+                    double fb = floor(rc[i] / alpha / wbin);
+                    int b = fb < (double)(bins - 1) ? (int)fb : bins - 1;
+                    hist[(size_t)cbest * bins + b] += 1;
                 }
             }
         }
@@ -361,8 +386,8 @@ int32_t orc_couple(const double *CP, uint64_t seed, int32_t call, const double *
     (void)L;
 
     /* 2. transition and correction cells on both levels */
-    level_layer(CP, &g, Pc, nc, xc, vc, wc, rc, mc, idc, dth_c, lay, vmax);
-    level_layer(CP, &g, Pf, nf, xf, vf, wf, rf, mf, idf, dth_f, lay + (size_t)S * 20, vmax + S);
+    level_layer(CP, &g, Pc, nc, xc, vc, wc, rc, mc, idc, nhc, hac, hbc, hxic, dth_c, lay, vmax);
+    level_layer(CP, &g, Pf, nf, xf, vf, wf, rf, mf, idf, nhf, haf, hbf, hxif, dth_f, lay + (size_t)S * 20, vmax + S);
     level_corr(&g, nc, xc, vc, rc, mc, cor);
     level_corr(&g, nf, xf, vf, rf, mf, cor + (size_t)C * 5);
     const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
@@ -434,12 +459,12 @@ int32_t orc_couple(const double *CP, uint64_t seed, int32_t call, const double *
         for (int a = 0; a < 3; ++a) fext_f[3 * i + a] = lam * Fv[a];
     }
 
-    /* 5. simple sequential inhibition per surface cell, faces in order */
-    int64_t *fu = (int64_t *)malloc(sizeof(int64_t) * 4 * (nf > 0 ? nf : 1));
-    for (int64_t j = 0; j < nf; ++j) {
-        for (int a = 0; a < 3; ++a) fu[4 * j + a] = llrint((xf[3 * j + a] - lof[a]) / qf);
-        fu[4 * j + 3] = llrint(rf[j] / qf);
-    }
+    /* 5. simple sequential inhibition per surface cell, faces in order, cells in row order.
+     * A candidate is decided by the smallest of its clearances: distance minus the sum of the
+     * radii for the fine particles and the earlier insertions, distance minus the radius for
+     * the walls; it is accepted when that is >= 0 (touching is allowed).  A decision whose
+     * clearance lies within (-band, band) is recorded in border[cell] (first such attempt;
+     * -1: none), where a grid representation of the same draws may decide otherwise. */
     for (int k = 0; k < g.nface; ++k) {
         const cface_t *f = &g.face[k];
         for (int local = 0; local < f->nb * f->nc; ++local) {
@@ -450,74 +475,70 @@ int32_t orc_couple(const double *CP, uint64_t seed, int32_t call, const double *
             double M = fav[4 * cell], vn = 0.0;
             if (M > 0) vn = fav[4 * cell + 1 + f->axis] / M;
             int n_in = 0, fails = 0, attempt = 0;
-            int64_t *mine = ins_u + (size_t)cell * max_ins * 4;
+            border[cell] = -1;
+            double *mine = ins_x + (size_t)cell * max_ins * 4;
             double b0 = g.lo[f->b] + ib * f->wb, c0 = g.lo[f->c] + ic * f->wc;
             while (quota > 0 && total > 0 && fails < max_att && n_in < max_ins) {
+                /* radius: a bin drawn with probability proportional to its count, then uniform in it */
                 int64_t pick = below(draw(seed, cell, call, attempt, 0), (int64_t)total);
                 int b = 0;
                 while (pick >= (int64_t)hist[(size_t)cell * bins + b]) { pick -= hist[(size_t)cell * bins + b]; ++b; }
-                int64_t R1 = rmaxf_u + 1;
-                int64_t rlo = (b * R1 + bins - 1) / bins, rhi = ((b + 1) * R1 + bins - 1) / bins - 1;
-                int64_t ru = rlo + below(draw(seed, cell, call, attempt, 1), rhi - rlo + 1);
-                if (ru <= 0) { ++attempt; ++fails; continue; }
-                double r = (double)ru * qf;
+                double r = ((double)b + unit(draw(seed, cell, call, attempt, 1))) * wbin;
+                /* centre: uniform over the cell's face shrunk by r, and along the inward normal over
+                 * [r, r + depth] from the face, depth = max(2 r, |<v_n>| T_c) */
                 double depth = fmax(2.0 * r, fabs(vn) * Tc);
-                int64_t bl = llrint(ceil((b0 + r - lof[f->b]) / qf)), bh = llrint(floor((b0 + f->wb - r - lof[f->b]) / qf));
-                int64_t cl = llrint(ceil((c0 + r - lof[f->c]) / qf)), ch = llrint(floor((c0 + f->wc - r - lof[f->c]) / qf));
+                double sb = f->wb - 2.0 * r, sc = f->wc - 2.0 * r;
+                if (!(r > 0.0) || sb < 0.0 || sc < 0.0) { ++attempt; ++fails; continue; }
                 double nlo = f->side == 0 ? f->plane + r : f->plane - r - depth;
-                double nhi = f->side == 0 ? f->plane + r + depth : f->plane - r;
-                int64_t al = llrint(ceil((nlo - lof[f->axis]) / qf)), ah = llrint(floor((nhi - lof[f->axis]) / qf));
-                if (bh < bl || ch < cl || ah < al) { ++attempt; ++fails; continue; }
-                int64_t u[3];
-                u[f->b] = bl + below(draw(seed, cell, call, attempt, 2), bh - bl + 1);
-                u[f->c] = cl + below(draw(seed, cell, call, attempt, 3), ch - cl + 1);
-                u[f->axis] = al + below(draw(seed, cell, call, attempt, 4), ah - al + 1);
+                double xc[3];
+                xc[f->b] = (b0 + r) + unit(draw(seed, cell, call, attempt, 2)) * sb;
+                xc[f->c] = (c0 + r) + unit(draw(seed, cell, call, attempt, 3)) * sc;
+                xc[f->axis] = nlo + unit(draw(seed, cell, call, attempt, 4)) * depth;
                 ++attempt;
-                int ok = 1;
-                /* the fine level's axisymmetric walls, in fine units from its box origin: no
-                 * overlap, and inside the vessel (a ray from the centre away from the axis
-                 * crosses the non-horizontal segments, each closed below and open above, an
-                 * odd number of times) */
+                double clear = INFINITY;
+                int inside = 1;
+                /* the fine level's axisymmetric walls: clearance, and inside the vessel (a ray from
+                 * the centre away from the axis crosses the non-horizontal segments, each closed
+                 * below and open above, an odd number of times) */
                 const int nwp = (int)Pf[P_NWP];
                 if (nwp >= 2) {
-                    const double ex = (double)u[0] - (Pf[P_WAX] - lof[0]) / qf, ey = (double)u[1] - (Pf[P_WAY] - lof[1]) / qf;
-                    const double rho = sqrt(ex * ex + ey * ey), ru2 = (double)ru * (double)ru, z = (double)u[2];
-                    int cross = 0;
-                    for (int k = 0; k + 1 < nwp && ok; ++k) {
-                        double a, b;
-                        seg_offset(Pf, k, rho, z, qf, lof[2], &a, &b);
-                        if (a * a + b * b < ru2) ok = 0;
-                        const double r0 = Pf[P_WP + 2 * k] / qf, z0 = (Pf[P_WP + 2 * k + 1] - lof[2]) / qf;
-                        const double r1 = Pf[P_WP + 2 * k + 2] / qf, z1 = (Pf[P_WP + 2 * k + 3] - lof[2]) / qf;
-                        if (z0 != z1 && (z >= z0) != (z >= z1) && r0 + (z - z0) * (r1 - r0) / (z1 - z0) > rho) ++cross;
+                    const double ex = xc[0] - Pf[P_WAX], ey = xc[1] - Pf[P_WAY];
+                    const double rho = sqrt(ex * ex + ey * ey), z = xc[2];
+                    int crossings = 0;
+                    for (int kk = 0; kk + 1 < nwp; ++kk) {
+                        double a, bb;
+                        seg_offset(Pf, kk, rho, z, 1.0, 0.0, &a, &bb);
+                        clear = fmin(clear, sqrt(a * a + bb * bb) - r);
+                        const double r0 = Pf[P_WP + 2 * kk], z0 = Pf[P_WP + 2 * kk + 1];
+                        const double r1 = Pf[P_WP + 2 * kk + 2], z1 = Pf[P_WP + 2 * kk + 3];
+                        if (z0 != z1 && (z >= z0) != (z >= z1) && r0 + (z - z0) * (r1 - r0) / (z1 - z0) > rho) ++crossings;
                     }
-                    if (!(cross & 1)) ok = 0;
+                    if (!(crossings & 1)) inside = 0;
                 }
-                for (int64_t j = 0; j < nf && ok; ++j) {
-                    int64_t ex = min_image_i(u[0] - fu[4 * j], Pf, qf, 0), ey = min_image_i(u[1] - fu[4 * j + 1], Pf, qf, 1);
-                    int64_t ez = u[2] - fu[4 * j + 2], S2 = (ru + fu[4 * j + 3]) * (ru + fu[4 * j + 3]);
-                    if (ex * ex + ey * ey + ez * ez < S2) ok = 0;
+                for (int64_t j = 0; j < nf; ++j) {
+                    double d[3] = {xc[0] - xf[3 * j], xc[1] - xf[3 * j + 1], xc[2] - xf[3 * j + 2]};
+                    min_image_d(Pf, d);
+                    clear = fmin(clear, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - (r + rf[j]));
                 }
-                for (int t = 0; t < n_in && ok; ++t) {
-                    int64_t ex = u[0] - mine[4 * t], ey = u[1] - mine[4 * t + 1], ez = u[2] - mine[4 * t + 2];
-                    int64_t S2 = (ru + mine[4 * t + 3]) * (ru + mine[4 * t + 3]);
-                    if (ex * ex + ey * ey + ez * ez < S2) ok = 0;
+                for (int t = 0; t < n_in; ++t) {
+                    double d[3] = {xc[0] - mine[4 * t], xc[1] - mine[4 * t + 1], xc[2] - mine[4 * t + 2]};
+                    clear = fmin(clear, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - (r + mine[4 * t + 3]));
                 }
-                for (int kk = 0; kk < k && ok; ++kk) {
+                for (int kk = 0; kk < k; ++kk) {
                     const cface_t *o = &g.face[kk];
-                    for (int oc = o->off; oc < o->off + o->nb * o->nc && ok; ++oc) {
-                        const int64_t *other = ins_u + (size_t)oc * max_ins * 4;
-                        for (int t = 0; t < nins[oc] && ok; ++t) {
-                            int64_t ex = u[0] - other[4 * t], ey = u[1] - other[4 * t + 1], ez = u[2] - other[4 * t + 2];
-                            int64_t S2 = (ru + other[4 * t + 3]) * (ru + other[4 * t + 3]);
-                            if (ex * ex + ey * ey + ez * ez < S2) ok = 0;
+                    for (int oc = o->off; oc < o->off + o->nb * o->nc; ++oc) {
+                        const double *other = ins_x + (size_t)oc * max_ins * 4;
+                        for (int t = 0; t < nins[oc]; ++t) {
+                            double d[3] = {xc[0] - other[4 * t], xc[1] - other[4 * t + 1], xc[2] - other[4 * t + 2]};
+                            clear = fmin(clear, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - (r + other[4 * t + 3]));
                         }
                     }
                 }
-                if (!ok) { ++fails; continue; }
+                if (inside && fabs(clear) < band && border[cell] < 0) border[cell] = attempt - 1;
+                if (!inside || clear < 0.0) { ++fails; continue; }
                 /* mass of a solid sphere of the fine density */
                 double m = CP[23] * (4.0 / 3.0 * ORC_PI) * r * r * r;
-                mine[4 * n_in] = u[0]; mine[4 * n_in + 1] = u[1]; mine[4 * n_in + 2] = u[2]; mine[4 * n_in + 3] = ru;
+                mine[4 * n_in] = xc[0]; mine[4 * n_in + 1] = xc[1]; mine[4 * n_in + 2] = xc[2]; mine[4 * n_in + 3] = r;
                 ins_m[(size_t)cell * max_ins + n_in] = m;
                 ++n_in;
                 quota -= llrint(m / mass_unit);
@@ -526,7 +547,6 @@ int32_t orc_couple(const double *CP, uint64_t seed, int32_t call, const double *
             carry[cell] = quota;
         }
     }
-    free(fu);
 
     /* 6. removal through drain faces */
     int drain = (int)CP[7];

@@ -194,14 +194,17 @@ static int FN(contact_law)(const double *P, const FN(mat_t) *M, double ra, doubl
 
 /*
  * Forces and torques on all particles at state (x, v, w) with history
- * (ha, hb, hxi; nh records sorted by (a, b)).  Writes F, T, and the new
+ * (ha, hb, hxi; nh records sorted by (a, b)) and the held external forces
+ * fext (NULL: none; the coupling controllers' forces of Sec. 2.3, added to
+ * gravity and the contact forces).  Writes F, T, and the new
  * history (sorted; at most `cap` records) with slip flags.  fabs_out (may be
  * NULL) receives per particle sum_j |F_ij| + |m g| (the scale of the forces
  * acting on it).  Returns the number of contacts, or -(count) if it exceeds
  * cap.
  */
 static int64_t FN(eval_m)(const double *P, const FN(mat_t) *M, int64_t n, const R *x, const R *v, const R *w,
-                          const double *r, const double *m, const int64_t *id, int64_t nh, const int64_t *ha,
+                          const double *r, const double *m, const int64_t *id, const double *fext, int64_t nh,
+                          const int64_t *ha,
                           const int64_t *hb, const R *hxi, double dt_hist, int32_t use_cells, R *F, R *T,
                           int64_t cap, int64_t *ha_out, int64_t *hb_out, R *hxi_out, int32_t *slip_out,
                           double *fabs_out)
@@ -225,11 +228,18 @@ static int64_t FN(eval_m)(const double *P, const FN(mat_t) *M, int64_t n, const 
     for (int64_t i = 0; i < n; ++i) {
         for (int k = 0; k < 3; ++k) {
             F[3 * i + k] = m[i] * P[P_G + k];
+            if (fext) F[3 * i + k] += fext[3 * i + k];   /* held external force (coupling controllers) */
             T[3 * i + k] = 0.0;
         }
         if (fabs_out) fabs_out[i] = m[i] * sqrt(P[P_G] * P[P_G] + P[P_G + 1] * P[P_G + 1] + P[P_G + 2] * P[P_G + 2]);
     }
 
+    /* the contact law of every pair (independent of the others: run in parallel when the
+     * oracle is compiled with OpenMP), then the sums over pairs in pair order (serial, so the
+     * result does not depend on the thread count) */
+    typedef struct { R fa[3], ta[3], tb[3], xi[3]; int slip; } FN(pres_t);
+    FN(pres_t) *pres = (FN(pres_t) *)malloc(sizeof(FN(pres_t)) * (np > 0 ? np : 1));
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < np; ++k) {
         int64_t a = pairs[k].i, b = pairs[k].j;
         if (id[b] < id[a]) { int64_t t = a; a = b; b = t; }
@@ -238,22 +248,27 @@ static int64_t FN(eval_m)(const double *P, const FN(mat_t) *M, int64_t n, const 
         R dist = RSQRT(FN(dot3)(d, d));
         R delta = r[a] + r[b] - dist;
         R nv[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
-        R xi[3] = {0.0, 0.0, 0.0};
+        R *xi = pres[k].xi;
+        xi[0] = xi[1] = xi[2] = 0.0;
         const R *old = FN(find_hist)(nh, ha, hb, hxi, id[a], id[b]);
         if (old) { xi[0] = old[0]; xi[1] = old[1]; xi[2] = old[2]; }
-        R fa[3], ft[3];
-        int slip = FN(contact_law)(P, M, r[a], r[b], m[a], m[b], 0, delta, nv, v + 3 * a, v + 3 * b, w + 3 * a,
-                                   w + 3 * b, xi, dt_hist, M->mu, fa, ft);
+        R ft[3];
+        pres[k].slip = FN(contact_law)(P, M, r[a], r[b], m[a], m[b], 0, delta, nv, v + 3 * a, v + 3 * b, w + 3 * a,
+                                       w + 3 * b, xi, dt_hist, M->mu, pres[k].fa, ft);
         R ca[3] = {-r[a] * nv[0], -r[a] * nv[1], -r[a] * nv[2]};
         R cb[3] = {-r[b] * nv[0], -r[b] * nv[1], -r[b] * nv[2]};
-        R ta[3], tb[3];
-        FN(cross3)(ca, ft, ta);
-        FN(cross3)(cb, ft, tb);
+        FN(cross3)(ca, ft, pres[k].ta);
+        FN(cross3)(cb, ft, pres[k].tb);
+    }
+    for (int64_t k = 0; k < np; ++k) {
+        int64_t a = pairs[k].i, b = pairs[k].j;
+        if (id[b] < id[a]) { int64_t t = a; a = b; b = t; }
+        const R *fa = pres[k].fa;
         for (int q = 0; q < 3; ++q) {
             F[3 * a + q] += fa[q];
             F[3 * b + q] -= fa[q];
-            T[3 * a + q] += ta[q];
-            T[3 * b + q] += tb[q];
+            T[3 * a + q] += pres[k].ta[q];
+            T[3 * b + q] += pres[k].tb[q];
         }
         if (fabs_out) {
             double fm = sqrt(RE(fa[0]) * RE(fa[0]) + RE(fa[1]) * RE(fa[1]) + RE(fa[2]) * RE(fa[2]));
@@ -261,10 +276,11 @@ static int64_t FN(eval_m)(const double *P, const FN(mat_t) *M, int64_t n, const 
             fabs_out[b] += fm;
         }
         rec[nrec].a = id[a]; rec[nrec].b = id[b];
-        memcpy(rec[nrec].xi, xi, sizeof(xi));
-        rec[nrec].slip = slip;
+        memcpy(rec[nrec].xi, pres[k].xi, sizeof(pres[k].xi));
+        rec[nrec].slip = pres[k].slip;
         ++nrec;
     }
+    free(pres);
     free(pairs);
 
     if (P[P_FLOOR] != 0.0) {
@@ -382,7 +398,7 @@ static void FN(wrap_positions)(const double *P, int64_t n, R *x)
  * Returns 0, or -1 if the history capacity was exceeded.
  */
 static int32_t FN(run_m)(const double *P, const FN(mat_t) *M, int64_t n, R *x, R *v, R *w, const double *r,
-                         const double *m, const int64_t *id, int64_t *nh, int64_t cap, int64_t *ha, int64_t *hb,
+                         const double *m, const int64_t *id, const double *fext, int64_t *nh, int64_t cap, int64_t *ha, int64_t *hb,
                          R *hxi, int32_t *slip, R *F, R *T, int64_t nsteps, int32_t primed, int32_t use_cells)
 {
     double dt = P[P_DT];
@@ -391,7 +407,7 @@ static int32_t FN(run_m)(const double *P, const FN(mat_t) *M, int64_t n, R *x, R
     R *tx = (R *)malloc(sizeof(R) * 3 * (cap > 0 ? cap : 1));
     int32_t rc = 0;
     if (!primed) {
-        int64_t c = FN(eval_m)(P, M, n, x, v, w, r, m, id, *nh, ha, hb, hxi, 0.0, use_cells, F, T, cap, ta, tb, tx,
+        int64_t c = FN(eval_m)(P, M, n, x, v, w, r, m, id, fext, *nh, ha, hb, hxi, 0.0, use_cells, F, T, cap, ta, tb, tx,
                                slip, NULL);
         if (c < 0) { rc = -1; goto done; }
         memcpy(ha, ta, sizeof(int64_t) * c);
@@ -410,7 +426,7 @@ static int32_t FN(run_m)(const double *P, const FN(mat_t) *M, int64_t n, R *x, R
             }
         }
         FN(wrap_positions)(P, n, x);
-        int64_t c = FN(eval_m)(P, M, n, x, v, w, r, m, id, *nh, ha, hb, hxi, dt, use_cells, F, T, cap, ta, tb, tx,
+        int64_t c = FN(eval_m)(P, M, n, x, v, w, r, m, id, fext, *nh, ha, hb, hxi, dt, use_cells, F, T, cap, ta, tb, tx,
                                slip, NULL);
         if (c < 0) { rc = -1; goto done; }
         memcpy(ha, ta, sizeof(int64_t) * c);
@@ -455,21 +471,22 @@ int orc_contact_pair(const double *P, double ra, double rb, double ma, double mb
 }
 
 int64_t orc_eval(const double *P, int64_t n, const double *x, const double *v, const double *w, const double *r,
-                 const double *m, const int64_t *id, int64_t nh, const int64_t *ha, const int64_t *hb,
+                 const double *m, const int64_t *id, const double *fext, int64_t nh, const int64_t *ha,
+                 const int64_t *hb,
                  const double *hxi, double dt_hist, int32_t use_cells, double *F, double *T, int64_t cap,
                  int64_t *ha_out, int64_t *hb_out, double *hxi_out, int32_t *slip_out, double *fabs_out)
 {
     orc_mat_t M = orc_mat_from(P);
-    return orc_eval_m(P, &M, n, x, v, w, r, m, id, nh, ha, hb, hxi, dt_hist, use_cells, F, T, cap, ha_out, hb_out,
+    return orc_eval_m(P, &M, n, x, v, w, r, m, id, fext, nh, ha, hb, hxi, dt_hist, use_cells, F, T, cap, ha_out, hb_out,
                       hxi_out, slip_out, fabs_out);
 }
 
 int32_t orc_run(const double *P, int64_t n, double *x, double *v, double *w, const double *r, const double *m,
-                const int64_t *id, int64_t *nh, int64_t cap, int64_t *ha, int64_t *hb, double *hxi, int32_t *slip,
+                const int64_t *id, const double *fext, int64_t *nh, int64_t cap, int64_t *ha, int64_t *hb, double *hxi, int32_t *slip,
                 double *F, double *T, int64_t nsteps, int32_t primed, int32_t use_cells)
 {
     orc_mat_t M = orc_mat_from(P);
-    return orc_run_m(P, &M, n, x, v, w, r, m, id, nh, cap, ha, hb, hxi, slip, F, T, nsteps, primed, use_cells);
+    return orc_run_m(P, &M, n, x, v, w, r, m, id, fext, nh, cap, ha, hb, hxi, slip, F, T, nsteps, primed, use_cells);
 }
 #else
 /* ------------------------------------------------ complex-step derivative */
@@ -503,7 +520,7 @@ int32_t orc_cs_run_derivative(const double *P, int32_t which, double h, int64_t 
     R *hxi = (R *)malloc(sizeof(R) * 3 * cap);
     int32_t *slip = (int32_t *)malloc(sizeof(int32_t) * cap);
     int64_t nh = 0;
-    int32_t rc = orc_cs_run_m(P, &M, n, xc, vc, wc, r, m, id, &nh, cap, ha, hb, hxi, slip, Fc, Tc, nsteps, 0,
+    int32_t rc = orc_cs_run_m(P, &M, n, xc, vc, wc, r, m, id, NULL, &nh, cap, ha, hb, hxi, slip, Fc, Tc, nsteps, 0,
                               use_cells);
     for (int64_t k = 0; k < 3 * n; ++k) {
         x[k] = creal(xc[k]); v[k] = creal(vc[k]); w[k] = creal(wc[k]); F[k] = creal(Fc[k]); T[k] = creal(Tc[k]);

@@ -345,6 +345,60 @@ def test_coulomb_truncation_is_exact_at_slip():
     assert abs(xi[0] @ nvec) < 1e-20
 
 
+def test_history_rotation_keeps_the_length_of_the_stored_overlap():
+    # Eq. 4 with the overlap carried while the contact normal turns: the stored xi, tangent to
+    # the old normal n0, is brought into the plane of the new normal n at its previous length
+    # (reading of Sec. 2.1; the paper does not say how a stored overlap follows the normal).
+    # The start-up evaluation (dt_hist = 0) isolates that step: no advance by v_t dt, and with
+    # both bodies at rest f_t = -k_t xi exactly.  Dropping the rescale shortens xi by
+    # |xi0 - (xi0.n) n| / |xi0| = cos(theta) < 1; dropping the projection leaves xi.n != 0.
+    r = 1e-3
+    m = sphere_mass(r)
+    P = oracle.make_params(E=E, nu=NU, e=0.8, mu=0.9, dt=1e-6, lo=(-0.01,) * 3, hi=(0.01,) * 3)
+    delta = 6e-6
+    for theta in (0.05, 0.3, 0.9):
+        n = np.array([math.sin(theta), 0.0, math.cos(theta)])     # from particle 1 to particle 0
+        x = np.array([[0.0, 0.0, 0.0], -(2 * r - delta) * n])
+        xi0 = np.array([3e-7, 1.2e-7, 0.0])                        # tangent to n0 = +z
+        sim = oracle.Sim(P, x, np.zeros((2, 3)), np.zeros((2, 3)), [r, r], [m, m], use_cells=False)
+        sim.set_history([0], [1], [xi0])
+        F, T, (a, b, xi, slip), _ = sim.evaluate(dt_hist=0.0)
+        assert slip.tolist() == [0]
+        x1 = xi[0]
+        assert np.linalg.norm(x1) == pytest.approx(np.linalg.norm(xi0), rel=1e-14)
+        assert abs(x1 @ n) <= 1e-15 * np.linalg.norm(xi0)
+        proj = xi0 - (xi0 @ n) * n
+        assert np.allclose(x1, proj * np.linalg.norm(xi0) / np.linalg.norm(proj), rtol=1e-14, atol=0)
+        # the force: Hertz along n plus -k_t xi (no dashpots at rest)
+        c = oracle.pair_coeffs(P, r, r, m, m, delta)
+        assert np.allclose(F[0], c["kn"] * delta * n - c["kt"] * x1, rtol=1e-12, atol=1e-18)
+        assert np.array_equal(F[1], -F[0])
+
+
+def test_resume_from_a_checkpoint_is_bit_exact():
+    # The oracle's state is (x, v, w), the forces of the last evaluation and the contact
+    # history: a run stopped after k steps, copied out and continued in a new simulation
+    # gives the same bits as the uninterrupted run (Sec. 8(c) O11 check on a sheared,
+    # rotating dense block with floor contacts, slips and contacts that open and close).
+    L = 5 * 2.0e-3
+    x, v, w, r = _dense_overlapping(5, 2.0e-3, 1.03e-3, seed=4, vel=0.2, omega=50.0)
+    P = oracle.make_params(E=E, nu=NU, e=0.6, mu=0.3, dt=2e-6, g=(0, 0, -9.81), hi=(L, L, L),
+                           periodic=(True, True, False), floor=True, floor_v=(0.5, 0, 0))
+    m = sphere_mass(r)
+    full = oracle.Sim(P, x, v, w, r, m).run(120)
+    part = oracle.Sim(P, x, v, w, r, m).run(45)
+    ck = part.checkpoint()
+    assert len(ck["ha"]) > len(r)
+    resumed = oracle.Sim.restore(P, ck).run(75)
+    for k in ("x", "v", "w", "F", "T"):
+        assert np.array_equal(getattr(resumed, k), getattr(full, k)), k
+    for u, t in zip(resumed.history(), full.history()):
+        assert np.array_equal(u, t)
+    # and the checkpoint is a copy: running on does not change it
+    part.run(5)
+    assert not np.array_equal(part.x, ck["x"])
+
+
 def test_results_do_not_depend_on_storage_order():
     L = 5 * 2.0e-3
     x, v, w, r = _dense_overlapping(5, 2.0e-3, 1.03e-3, seed=8)
@@ -436,3 +490,36 @@ def test_a_flat_wall_profile_acts_as_the_floor():
     assert np.allclose(a.x, b.x, rtol=0, atol=1e-15)
     assert np.allclose(a.v, b.v, rtol=1e-12, atol=1e-15)
     assert np.allclose(a.w, b.w, rtol=1e-12, atol=1e-12)
+
+
+def test_openmp_build_gives_the_same_bits():
+    # the all-cores build of the oracle (the timed CPU baseline) runs the per-pair contact law
+    # in parallel and sums serially: the same bits as the serial build
+    L = 6 * 2.0e-3
+    x, v, w, r = _dense_overlapping(6, 2.0e-3, 1.03e-3, seed=21, vel=0.2, omega=40.0)
+    P = oracle.make_params(E=E, nu=NU, e=0.7, mu=0.3, dt=2e-6, g=(0, 0, -9.81), hi=(L, L, L),
+                           periodic=(True, True, False), floor=True, floor_v=(0.5, 0, 0))
+    m = sphere_mass(r)
+    a = oracle.Sim(P, x, v, w, r, m).run(60)
+    b = oracle.Sim(P, x, v, w, r, m, openmp=True).run(60)
+    for k in ("x", "v", "w", "F", "T"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
+    for u, t in zip(a.history(), b.history()):
+        assert np.array_equal(u, t)
+
+
+def test_held_external_force_acts_like_gravity():
+    # the coupling controllers' force is held on a particle and added to its other forces: a held
+    # m g without gravity moves a block exactly as gravity g does (the same sums, in another order)
+    L = 5 * 2.0e-3
+    x, v, w, r = _dense_overlapping(5, 2.0e-3, 1.03e-3, seed=6)
+    m = sphere_mass(r)
+    g = np.array([0.0, 0.0, -9.81])
+    kw = dict(E=E, nu=NU, e=0.6, mu=0.3, dt=2e-6, hi=(L, L, L), periodic=(True, True, False), floor=True)
+    a = oracle.Sim(oracle.make_params(g=tuple(g), **kw), x, v, w, r, m).run(50)
+    b = oracle.Sim(oracle.make_params(**kw), x, v, w, r, m)
+    b.fext = m[:, None] * g[None, :]
+    b.run(50)
+    assert np.allclose(b.x, a.x, rtol=0, atol=1e-15)
+    assert np.allclose(b.v, a.v, rtol=1e-10, atol=1e-13)
+    assert not np.allclose(oracle.Sim(oracle.make_params(**kw), x, v, w, r, m).run(50).x, a.x, rtol=0, atol=1e-12)

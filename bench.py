@@ -39,10 +39,15 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--settle", type=int, default=30_000, help="settling steps at dt 5e-6, e 0.5 (not timed)")
-    ap.add_argument("--graph", type=int, default=50, help="steps per captured CUDA graph (0: direct launches)")
+    ap.add_argument("--graph", type=int, default=50, help="largest number of steps per captured CUDA graph (the "
+                    "graph length is the largest divisor of --steps up to this; 0: direct launches)")
+    ap.add_argument("--run-in", type=int, default=2000, help="untimed steps of the sheared bed before the warm-up "
+                    "(part of the workload: the shear flow develops and the lists are rebuilt several times)")
+    ap.add_argument("--repeats", type=int, default=5, help="timed repeats of --steps steps (median reported)")
     ap.add_argument("--settle-graph", type=int, default=50, help="steps per graph while settling")
     ap.add_argument("--lmax", type=int, default=32)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the reference arm's sample")
+    ap.add_argument("--cpu-bed-steps", type=int, default=10, help="oracle steps on the settled bed (CPU baseline)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -178,6 +183,14 @@ def _profile_traffic(kernel_src_hash):
     return float(m.group(1))
 
 
+def graph_length(steps, cap):
+    """Steps per captured graph: the largest divisor of `steps` up to `cap`, so that a timed run of
+    exactly `steps` steps is whole graphs (0: direct launches)."""
+    if cap <= 0:
+        return 0
+    return max(d for d in range(1, min(cap, steps) + 1) if steps % d == 0)
+
+
 def _kernel_hash():
     """Hash of the step kernel's source (its definition in dem.cu and the headers it is built
     from); a profile taken from another version gives no traffic."""
@@ -201,28 +214,40 @@ def _peaks():
 
 # --------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_sample(target_seconds):
-    """Time the FP64 oracle (single thread) on a dense polydisperse block, the bounded CPU sample."""
+def _oracle_timed(sim, steps):
+    sim.run(0)                           # start-up evaluation (not timed)
+    t0 = time.perf_counter()
+    sim.run(steps)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_baseline(bed, bed_steps):
+    """The FP64 oracle as it stands, timed on this host's cores: the 1,000-sphere column in full
+    (5,000 steps) and `bed_steps` steps of the GPU line's own settled and sheared 1M bed (its
+    state read back from the device, empty contact history), each on one thread and with the
+    OpenMP build on every core (the per-pair contact law in parallel; identical results)."""
     import oracle
     from paper_1705_03850_gb300 import workloads
-    wl = workloads.dense_block(60, 60, 40, seed=2, rjit=0.2, vel=0.05, spin=5.0)
-    m = wl.material
-    P = oracle.make_params(E=m.E, nu=m.nu, e=m.e, mu=m.mu, dt=wl.dt, g=wl.g, lo=wl.lo, hi=wl.hi,
-                           periodic=wl.periodic, floor=wl.floor, floor_v=wl.floor_v)
-    sim = oracle.Sim(P, wl.x, wl.v, wl.w, wl.r, wl.m)
-    sim.run(0)                       # start-up evaluation, not timed
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
-        sim.run(1)
-        steps += 1
-        if time.perf_counter() - t0 >= target_seconds:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": wl.n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 C oracle, 1 thread, {steps} steps of a {wl.n}-particle dense polydisperse block "
-                      f"(d in [1.6, 2.4] mm, overlapping jittered lattice, cell-list contacts), {dt:.1f} s",
-            "host": os.uname().machine, "nproc": os.cpu_count()}
+    cores = os.cpu_count() or 1
+    runs = []
+    col = workloads.column()
+    m = col.material
+    Pc = oracle.make_params(E=m.E, nu=m.nu, e=m.e, mu=m.mu, dt=col.dt, g=col.g, lo=col.lo, hi=col.hi,
+                            periodic=col.periodic, floor=col.floor, floor_v=col.floor_v)
+    x, v, w, r, mass, P = bed
+    for threads, omp in ((1, False), (cores, True)):
+        os.environ["OMP_NUM_THREADS"] = str(threads)
+        t = _oracle_timed(oracle.Sim(Pc, col.x, col.v, col.w, col.r, col.m, openmp=omp), 5000)
+        runs.append({"workload": "1,000-sphere column (d = 2 mm, 20 x 20 x 60 mm), 5,000 steps of 2e-6 s",
+                     "threads": threads, "seconds": t, "value": col.n * 5000 / t})
+        t = _oracle_timed(oracle.Sim(P, x, v, w, r, mass, openmp=omp), bed_steps)
+        runs.append({"workload": f"the settled, sheared 1M bed of the GPU line, {bed_steps} steps of 1e-6 s",
+                     "threads": threads, "seconds": t, "value": len(r) * bed_steps / t})
+    head = runs[3]
+    return {"value": head["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 C oracle (OpenMP build, {cores} threads) for {bed_steps} steps of the GPU line's own "
+                      f"settled 1M bed ({head['seconds']:.1f} s); all runs below",
+            "runs": runs, "host": os.uname().machine, "nproc": cores}
 
 
 def _oracle_block(nx, ny, nz):
@@ -232,7 +257,7 @@ def _oracle_block(nx, ny, nz):
     m = wl.material
     P = oracle.make_params(E=m.E, nu=m.nu, e=m.e, mu=m.mu, dt=wl.dt, g=wl.g, lo=wl.lo, hi=wl.hi,
                            periodic=wl.periodic, floor=wl.floor, floor_v=wl.floor_v)
-    return wl, oracle.Sim(P, wl.x, wl.v, wl.w, wl.r, wl.m)
+    return wl, oracle.Sim(P, wl.x, wl.v, wl.w, wl.r, wl.m, openmp=True)
 
 
 def run_reference(args):
@@ -243,6 +268,8 @@ def run_reference(args):
     if rank != 0:
         return
     K, W = max(1, args.steps), max(0, args.warmup)
+    cores = os.cpu_count() or 1
+    os.environ["OMP_NUM_THREADS"] = str(cores)
     wl, sim = _oracle_block(20, 20, 20)            # calibration: 8,000 particles
     sim.run(0)
     t0 = time.perf_counter()
@@ -257,9 +284,10 @@ def run_reference(args):
     sim.run(K)
     t = time.perf_counter() - t0
     value = wl.n * K / t
-    sample = (f"FP64 C oracle, 1 thread, {W} untimed + {K} timed steps of a {wl.n}-particle dense "
-              f"polydisperse block (d in [1.6, 2.4] mm, overlapping jittered lattice, cell-list contacts), {t:.1f} s")
-    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+    sample = (f"FP64 C oracle (OpenMP build, {cores} threads), {W} untimed + {K} timed steps of a {wl.n}-particle "
+              f"dense polydisperse block (d in [1.6, 2.4] mm, overlapping jittered lattice, cell-list contacts; a "
+              f"host cannot settle the 1M bed in a bench run), {t:.1f} s")
+    cpu = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
            "host": os.uname().machine, "nproc": os.cpu_count()}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": t / K * 1e3, "higher_is_better": True,
@@ -288,9 +316,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    S = args.graph
-    K = max(S, (args.steps // S) * S) if S > 0 else max(1, args.steps)
+    K = max(1, args.steps)
     W = max(3, args.warmup)
+    S = graph_length(K, args.graph)
 
     # ---- build and settle the bed (not timed): larger step and more damping
     # than the sheared run, so that the lattice collapses into a dense bed quickly
@@ -322,36 +350,47 @@ def run_ours(args):
         np.savez(args.save_state, x=x.cpu().numpy(), v=v.cpu().numpy(), w=w.cpu().numpy(), r=r.cpu().numpy(),
                  m=m.cpu().numpy())
 
-    # ---- sheared bed: floor moves at 0.5 m/s in x
+    # ---- sheared bed: floor moves at 0.5 m/s in x; the run-in (untimed, part of the workload)
+    # lets the shear flow develop through several list rebuilds, then W warm-up steps
     desc.floor_v[0] = 0.5
     sim = dem.DEM([desc], max_neighbors=args.lmax, device=dev)
     sim.write_state(x, v, w, r, m)
     sim.step(1)
     if S > 0:
         sim.set_graph(S)
-        sim.step(((W + S - 1) // S) * S)
-    else:
-        sim.step(W)
+    sim.step(max(0, args.run_in - 1))
+    sim.step(W)
     sim.sync()
     st0 = sim.stats()
 
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # ---- timed: `repeats` x exactly K steps (inputs larger than L2), median reported
+    reps = []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clocks:
-        _profile(args, "plain", True)        # marks the timed region for `ncu --profile-from-start off`
-        e0.record(stream)
-        sim.step(K)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        _profile(args, "plain", False)
-    ms = e0.elapsed_time(e1)
-    kern_ms, kern_n = sim.graph_step_kernel_ms() if S > 0 else (float("nan"), 1)
+        for rep in range(max(1, args.repeats)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize(dev)
+            if rep == 0:
+                _profile(args, "plain", True)    # marks the timed region for `ncu --profile-from-start off`
+            e0.record(stream)
+            sim.step(K)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if rep == 0:
+                _profile(args, "plain", False)
+            kms, kn = sim.graph_step_kernel_ms() if S > 0 else (float("nan"), 1)
+            reps.append((max_over_ranks(e0.elapsed_time(e1), dev), kms / max(1, kn), kn))
     st1 = sim.stats()
     sim.sync()
-    ms = max_over_ranks(ms, dev)
+    order = sorted(range(len(reps)), key=lambda i: reps[i][0])
+    ms = reps[order[len(order) // 2]][0]
+    kern_sorted = sorted(t for _, t, _ in reps)
+    t_kernel_ms = kern_sorted[len(kern_sorted) // 2]
     n = wl.n
     value = whole_job_rate(n * K, world, ms / 1e3)
     L = st1["list_entries"] / max(1, st1["particles"])
@@ -364,7 +403,7 @@ def run_ours(args):
     # what this design must move at least: the same state, count and history mask,
     # indices of every entry, history only of entries in contact, floor history
     B_design = 96.0 + 4.0 + 8.0 + 4.0 * L + 24.0 * (C - Wc) + 32.0 * Wc
-    t_kernel = kern_ms / max(1, kern_n) / 1e3
+    t_kernel = t_kernel_ms / 1e3
     achieved = n * B_step / t_kernel / 1e9
     peaks = _peaks()
     peak = peaks.get("hbm_gbs")
@@ -373,7 +412,12 @@ def run_ours(args):
     traffic = _profile_traffic(_kernel_hash())
     # per graph of S steps: one condition-setting kernel and S step kernels, plus the
     # 11-kernel rebuild chain when a rebuild runs; direct launches run the chain every step
-    launches = K + K // S + 11 * rebuilds if S > 0 else 12 * K
+    # (per timed repeat of K steps; rebuilds averaged over the repeats)
+    nrep = max(1, args.repeats)
+    launches = round(K + K // S + 11 * rebuilds / nrep) if S > 0 else 12 * K
+
+    # the bed as it stands after the timed region (host copies, for the CPU baseline)
+    bed = tuple(sim.read(f) for f in (dem.POS, dem.VEL, dem.OMEGA, dem.RADIUS, dem.MASS)) if world == 1 else None
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -419,7 +463,11 @@ def run_ours(args):
         return
     cpu = None
     if not args.no_cpu and world == 1:
-        cpu = cpu_oracle_sample(args.cpu_seconds)
+        import oracle
+        mt = wl.material
+        P_bed = oracle.make_params(E=mt.E, nu=mt.nu, e=mt.e, mu=mt.mu, dt=wl.dt, g=wl.g, lo=wl.lo, hi=wl.hi,
+                                   periodic=wl.periodic, floor=wl.floor, floor_v=(0.5, 0.0, 0.0))
+        cpu = cpu_oracle_baseline(bed + (P_bed,), args.cpu_bed_steps)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -429,13 +477,20 @@ def run_ours(args):
                    "settle_steps": 0 if args.load_state else args.settle,
                    "settle": (f"loaded from {os.path.basename(args.load_state)}" if args.load_state
                               else "dt 5e-6 s, e 0.5, from the FCC start"),
-                   "steps_per_graph": S, "max_neighbors": args.lmax,
+                   "run_in_steps": args.run_in, "steps_per_graph": S, "max_neighbors": args.lmax,
+                   "repeats": len(reps), "ms_per_step_repeats": [t / K for t, _, _ in reps],
+                   "ms_per_step_mean": sum(t for t, _, _ in reps) / (K * len(reps)),
+                   "timing": f"CUDA events around each repeat of exactly {K} steps after {args.run_in} untimed "
+                             f"run-in and {W} warm-up steps; value and ms_per_step from the median repeat",
                    "l2": "inputs larger than L2 (state + lists + histories > 129 MB)",
-                   "mean_list_length": L, "mean_contacts_per_particle": C, "rebuilds_in_timed_region": rebuilds,
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "mean_list_length": L, "mean_contacts_per_particle": C,
+                   "rebuilds_in_timed_region": rebuilds, "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_src, "kernel": "k_step<0, false> (fused force + Verlet, the variant without walls)",
                      "bytes_per_particle_step": B_step, "kernel_ms_avg": t_kernel * 1e3,
+                     "kernel_ms_repeats": [t for _, t, _ in reps],
+                     "kernel_timing": "median over the repeats of the mean CUDA-event duration of every fifth "
+                                      "step kernel of the repeat's last graph",
                      "design_bytes_per_particle_step": B_design,
                      "design_achieved": n * B_design / t_kernel / 1e9,
                      "kernel_share_of_step": t_kernel * 1e3 / (ms / K)},
@@ -449,6 +504,13 @@ def run_ours(args):
         "gpu_launches": launches,
         "cpu_baseline": cpu,
     }
+    # the lines beside the plain step, repeated compactly at the end of the line
+    g = lambda d, *ks: None if d is None else (g(d.get(ks[0]), *ks[1:]) if len(ks) > 1 else d.get(ks[0]))
+    line["summary"] = {"plain": value, "roofline_frac": achieved / peak, "e2e": g(e2e, "value"),
+                       "batched": g(batched, "value"), "batched_settled": g(batched, "settled", "value"),
+                       "adjoint": g(adj, "value"), "coupled": g(coupled, "value"),
+                       "coupled_multirate": g(coupled, "multirate", "value"), "nested": g(nested, "value"),
+                       "cpu_oracle_all_cores": g(cpu, "value"), "unit": UNIT}
     print(json.dumps(line), flush=True)
 
 

@@ -74,7 +74,9 @@ typedef enum {
     DEM_F_MASS = 4,     /* (n)   float64 mass [kg]; read/write (write after RADIUS) */
     DEM_F_FORCE = 5,    /* (n,3) float64 total force at the current step [N]; read only */
     DEM_F_TORQUE = 6,   /* (n,3) float64 total torque at the current step [N m]; read only */
-    DEM_F_WALL_XI = 7,  /* (n,3) float64 tangential overlap of the floor contact [m] (0 if none); read only */
+    DEM_F_WALL_XI = 7,  /* (n,3) float64 tangential overlap of the floor contact [m] (0 if none); read, and
+                           write after the state and the contacts to resume a run (stored as float32; kept if
+                           the particle touches the floor at the next evaluation) */
     DEM_F_NBR_COUNT = 8,/* (n)   float64 neighbour-list length of each particle; read only */
     DEM_F_FEXT = 9      /* (n,3) float64 external force held on each particle [N], added to the contact and
                            gravity forces every step until overwritten (written by the coupling controllers,
@@ -241,9 +243,12 @@ dem_status dem_set_material(dem_ctx *ctx, const double *params);
  * a message in dem_last_error(NULL), before any GPU work.
  * Memory: scratch is one fixed 9 MiB device array inside the library, held by
  * every GPU that loads it until the process exits; nothing is allocated or
- * freed.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with that device current; make this first call
- * before any stream capture.  All calls share the array and each call
+ * freed.  Every call looks up that array's device address on the current
+ * device (cudaGetSymbolAddress), so a device reset between calls is safe;
+ * make the first call on a device before any stream capture (it loads the
+ * library's module there).  Particles outside an open axis count as being in
+ * its edge cells, like a context's; their counts are exact only inside the
+ * box.  All calls share the array and each call
  * re-initialises what it reads, so calls that overlap on the GPU (other
  * streams, other threads, or concurrent contexts on the same device) race
  * and must be serialised by the caller.
@@ -321,10 +326,12 @@ typedef struct {
     int32_t max_insert;     /* most particles inserted per surface cell and call */
     int32_t add_forces;     /* 0: the controller forces replace the levels' held forces; 1: they are added
                                (for a level shared by two couplers; clear with dem_clear_external_force) */
-    double velocity_below;  /* correction cells whose centre lies below this height [m] take the
-                               velocity target (mode 0) whatever `mode` says: Sec. 3 applies a pure
-                               velocity coupling to coarse particles that passed the silo's orifice;
-                               -INFINITY (or NaN): none */
+    double velocity_below;  /* with velocity_below_on: correction cells whose centre lies below this
+                               height [m] take the velocity target (mode 0) whatever `mode` says: Sec. 3
+                               applies a pure velocity coupling to coarse particles that passed the
+                               silo's orifice */
+    int32_t velocity_below_on;  /* 0 (a zero-initialised spec): velocity_below is ignored */
+    int32_t reserved;
 } dem_coupling;
 
 typedef enum {

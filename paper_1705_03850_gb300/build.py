@@ -41,7 +41,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([_nvcc()] + NVCC_FLAGS + ["-dc" if False else "-c", s, "-o", o])
+            jobs.append([_nvcc()] + NVCC_FLAGS + ["-c", s, "-o", o])
 
     def run(cmd):
         if verbose:

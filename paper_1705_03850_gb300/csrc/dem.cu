@@ -266,10 +266,17 @@ __global__ void __launch_bounds__(TILE) k_rb_tilesort(Dev d)
 // row is kept in shared memory, entry-major so that the threads of a warp hit
 // different banks.
 constexpr int RB_T = 64;                     // threads per block of the list build
+#ifndef DEM_RB_W
+#define DEM_RB_W 128
+#endif
+constexpr int RB_W = DEM_RB_W;               // cell-order positions staged on each side of a block's 64
+constexpr int RB_WIN = RB_T + 2 * RB_W;
 
 struct RowScratch {
     float key[MAXL][RB_T];                   // d^2 - (r_i + r_j)^2 (rounded to float: monotone)
     int pos[MAXL][RB_T];                     // partner's cell-order position
+    int4 win[RB_WIN];                        // positions of the cell-order window around the block
+    int wlo, wn;                             // window start (cell-order position) and length
 };
 
 __device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, const InstC& c, RowScratch& R)
@@ -342,7 +349,9 @@ __device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, 
         const int cnt = (int)cr.y;
         for (int t = 0; t < cnt; ++t) {
             const int m = start + t;
-            const int4 q = __ldg(d.spos + m);
+            // neighbours are mostly near in cell order: from the staged window, else from L2
+            const unsigned wi = (unsigned)(m - R.wlo);
+            const int4 q = wi < (unsigned)R.wn ? R.win[wi] : __ldg(d.spos + m);
             const int ddx = min_image(p.x - q.x, per0, ext0, hf0);
             const int ddy = min_image(p.y - q.y, per1, ext1, hf1);
             const long long ddz = (long long)p.z - q.z;
@@ -431,16 +440,25 @@ __global__ void __launch_bounds__(RB_T, 16) k_rb_build(Dev d)
     __shared__ RowScratch R;
     constexpr int H = TILE / RB_T;           // blocks of RB_T threads per tile
     // over the cell-order positions: the threads of a warp hold neighbouring particles and
-    // scan overlapping cells (the rows go to the particles' new slots in the same tile)
+    // scan overlapping cells (the rows go to the particles' new slots in the same tile); the
+    // block first stages the cell-order positions within RB_W of its own in shared memory
     for (int u = blockIdx.x; u < d.ntiles * H; u += gridDim.x) {
         const int t = u / H;
         const int k = d.tile_inst[t];
         const InstD D = d.id[k];
-        if (!D.flag) continue;
+        if (!D.flag) continue;               // the same for the whole block
         const InstC& c = d.ic[k];
-        const int p = t * TILE + (u % H) * RB_T + threadIdx.x;
-        if (p - c.slot0 >= D.n_new) continue;
-        build_row(d, p, D, c, R);
+        const int p0 = t * TILE + (u % H) * RB_T;
+        const int p = p0 + threadIdx.x;
+        const int lo = max(c.slot0, p0 - RB_W), hi = min(c.slot0 + D.n_new, p0 + RB_T + RB_W);
+        __syncthreads();                     // the previous window is no longer read
+        if (threadIdx.x == 0) {
+            R.wlo = lo;
+            R.wn = max(0, hi - lo);
+        }
+        for (int i = lo + (int)threadIdx.x; i < hi; i += RB_T) R.win[i - lo] = __ldg(d.spos + i);
+        __syncthreads();
+        if (p - c.slot0 < D.n_new) build_row(d, p, D, c, R);
     }
 }
 
@@ -578,6 +596,18 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int s
     return nst;
 }
 
+#ifndef DEM_EXP_PFN
+#define DEM_EXP_PFN 0
+#endif
+#ifndef DEM_EXP_PFVW
+#define DEM_EXP_PFVW 0
+#endif
+// bring a line into L1 without holding a register for it
+__device__ __forceinline__ void pf_l1(const void* p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 // WALLS: the variant that evaluates axisymmetric walls (launched only for contexts that have
 // them, so that the wall code costs the plain step nothing)
 template <int MODE, bool WALLS>
@@ -678,6 +708,17 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
             int4 Qb[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) Qb[k] = __ldg(pos + jb[k]);
+            if (DEM_EXP_PFVW && MODE == 0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if ((hm >> (e0 + k)) & 1u) {
+                        pf_l1(vel + jb[k]);
+                        pf_l1(omg + jb[k]);
+                        pf_l1(h + (size_t)(e0 + k) * ncap);
+                        pf_l1(h + plane + (size_t)(e0 + k) * ncap);
+                        pf_l1(h + 2 * plane + (size_t)(e0 + k) * ncap);
+                    }
+            }
             if (e0 + 4 < ncnt) jn0 = __ldg(nb + (size_t)(e0 + 4) * ncap);
             if (e0 + 5 < ncnt) jn1 = __ldg(nb + (size_t)(e0 + 5) * ncap);
             if (e0 + 6 < ncnt) jn2 = __ldg(nb + (size_t)(e0 + 6) * ncap);
@@ -702,6 +743,18 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
             ho[(size_t)e * ncap] = 0.f;
             ho[plane + (size_t)e * ncap] = 0.f;
             ho[2 * plane + (size_t)e * ncap] = 0.f;
+        }
+        if (DEM_EXP_PFN && MODE == 0 && t + 1 < t1) {
+            // the next tile's own rows, into L1 while this one's contacts are evaluated
+            const int sn = (t + 1) * TILE + ((((int)threadIdx.x >> 5) + t + 1) & (TILE / 32 - 1)) * 32 +
+                           ((int)threadIdx.x & 31);
+            pf_l1(pos + sn);
+            pf_l1(vel + sn);
+            pf_l1(omg + sn);
+            pf_l1(d.cnt[lp] + sn);
+            pf_l1(d.hmask[lp] + sn);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) pf_l1(d.nbr[lp] + (size_t)e * ncap + sn);
         }
         // ---- pass 2: the contacts, in row order, next contact's state in flight
         unsigned cm = tm;
@@ -1005,6 +1058,16 @@ __global__ void k_write_field(Dev d, int field, const double* __restrict__ src, 
     } else if (field == DEM_F_FEXT) {
         d.fext[d.id[k].lp][s] = make_float4((float)src[3 * g], (float)src[3 * g + 1], (float)src[3 * g + 2], 0.f);
         d.id[k].fext = 1;                    // every thread of the instance stores the same value
+    } else if (field == DEM_F_WALL_XI) {
+        // a floor contact's stored overlap (after the lists were built for this state): kept
+        // by the next evaluation if the particle touches the floor there
+        const float4 xi = make_float4((float)src[3 * g], (float)src[3 * g + 1], (float)src[3 * g + 2], 0.f);
+        d.whist[d.id[k].lp][s] = xi;
+        float4 v = d.vel[cur][s];
+        unsigned idw = __float_as_uint(v.w) & ~WALL_BIT;
+        if (xi.x != 0.f || xi.y != 0.f || xi.z != 0.f) idw |= WALL_BIT;
+        v.w = __uint_as_float(idw);
+        d.vel[cur][s] = v;
     }
 }
 
@@ -2101,7 +2164,7 @@ dem_status dem_write(dem_ctx* ctx, int32_t field, const void* src, int64_t n)
     if (!ctx) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     const int w = field_width(field);
-    if (w == 0 || field == DEM_F_FORCE || field == DEM_F_TORQUE || field == DEM_F_WALL_XI || field == DEM_F_NBR_COUNT)
+    if (w == 0 || field == DEM_F_FORCE || field == DEM_F_TORQUE || field == DEM_F_NBR_COUNT)
         return fail(ctx, DEM_ERR_ARG, "field is not writable");
     if (dem_status st = refresh_count(ctx)) return st;
     if (n != total_count(ctx)) return fail(ctx, DEM_ERR_ARG, "n must equal the total particle count");
@@ -2112,9 +2175,14 @@ dem_status dem_write(dem_ctx* ctx, int32_t field, const void* src, int64_t n)
         CU(cudaMemcpyAsync(ctx->dev.stage, src, (size_t)n * w * 8, cudaMemcpyHostToDevice, ctx->stream));
         dsrc = ctx->dev.stage;
     }
+    if (field == DEM_F_WALL_XI) {            // the floor histories of the lists of this state: build them first
+        dem_status st = launch_rebuild(ctx, ctx->stream);
+        if (st) return st;
+    }
     k_write_field<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->dev, field, dsrc, n, ctx->d_hl);
     CU(cudaGetLastError());
-    if (field != DEM_F_FEXT) {               // the held force changes neither the lists nor the state's integrity
+    // the held force and the floor histories change neither the lists nor the state's integrity
+    if (field != DEM_F_FEXT && field != DEM_F_WALL_XI) {
         k_mark_fresh<<<1, 256, 0, ctx->stream>>>(ctx->dev);
         CU(cudaGetLastError());
         ctx->fresh = true;

@@ -43,7 +43,7 @@ struct Geo {
     int call;            // coupling interval counter (random-number counter)
     // the two levels' frames: x = lo + u q
     double loc[3], qc, lof[3], qf;
-    int rmaxf_u;         // largest fine radius in fine units (histogram range)
+    double wbin;         // width of a radius bin: the fine level's largest radius / bins [m]
     int fresh_c, fresh_f;
     int add;             // add the controller forces to the held ones instead of replacing them
     double vel_below;    // correction cells centred below this height take the velocity target
@@ -328,10 +328,10 @@ __global__ void __launch_bounds__(TILE) k_cp_coarse(Dev d, Geo g, Acc a, int rec
                     }
                     if (cbest >= 0) {
                         atomicAdd(a.cross + cbest, (unsigned long long)llrint(m / g.mass_unit));
-                        // fine radius r / alpha in fine units; bin b holds the radii u with
-                        // floor(u bins / (R + 1)) = b over [0, R], R = largest fine radius
-                        const long long rf = min(llrint(r / g.alpha / g.qf), (long long)g.rmaxf_u);
-                        const int b = (int)(rf * g.bins / (g.rmaxf_u + 1));
+                        // bin of the fine-scale radius r / alpha among equal bins over [0, r_max,fine)
+                        // (the last bin takes anything larger)
+                        const double fb = floor(r / g.alpha / g.wbin);
+                        const int b = fb < (double)(g.bins - 1) ? (int)fb : g.bins - 1;
                         atomicAdd(a.hist + (size_t)cbest * MAXBINS + b, 1u);
                     }
                 }
@@ -535,6 +535,9 @@ __device__ __forceinline__ long long below(unsigned long long u, long long n)
     return (long long)(((u >> 32) * (unsigned long long)n) >> 32);
 }
 
+// uniform in [0, 1) from the top 53 of 64 random bits
+__device__ __forceinline__ double unit01(unsigned long long u) { return (double)(u >> 11) * 0x1p-53; }
+
 __device__ __forceinline__ double sphere_mass(double rho, double r)
 {
     return __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(rho, 4.0 / 3.0 * 3.14159265358979323846), r), r), r);
@@ -563,48 +566,36 @@ __global__ void k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
     }
     int4* mine = a.ins + (size_t)cell * g.max_insert;
     double* mym = a.insm + (size_t)cell * g.max_insert;
-    // face extent of this cell in fine units
-    const double b0 = g.lo[f.b] + ib * f.wb, c0 = g.lo[f.c] + ic * f.wc;
+    // the cell's extent on the face [m]
+    const double b0 = __dadd_rn(g.lo[f.b], __dmul_rn((double)ib, f.wb));
+    const double c0 = __dadd_rn(g.lo[f.c], __dmul_rn((double)ic, f.wc));
     while (quota > 0 && total > 0 && fails < g.max_attempts && nins < g.max_insert) {
-        // diameter: bin by count, uniform within the bin
+        // radius: a bin drawn with probability proportional to its count, then uniform in it
         long long pick = below(draw(g, cell, attempt, 0), total);
         int b = 0;
         while (pick >= (long long)hist[b]) {
             pick -= hist[b];
             ++b;
         }
-        const long long R1 = g.rmaxf_u + 1;
-        const long long rlo = (b * R1 + g.bins - 1) / g.bins, rhi = ((b + 1) * R1 + g.bins - 1) / g.bins - 1;
-        const long long ru = rlo + below(draw(g, cell, attempt, 1), rhi - rlo + 1);
-        if (ru <= 0) {
-            ++attempt;
-            ++fails;
-            continue;
-        }
-        const double r = (double)ru * g.qf;
+        const double r = __dmul_rn(__dadd_rn((double)b, unit01(draw(g, cell, attempt, 1))), g.wbin);
+        // centre: uniform over the cell's face shrunk by r, and along the inward normal over
+        // [r, r + depth] from the face, depth = max(2 r, |<v_n>| T_c); continuous values (the same
+        // operations as a plain double evaluation), then rounded to the fine level's grid
         const double depth = fmax(2.0 * r, fabs(vn) * g.Tc);
-        // position in fine units: in-plane within the cell shrunk by r, along the
-        // normal in [face + r, face + r + depth] inside the region
-        long long u[3];
-        const long long bl = llrint(ceil((b0 + r - g.lof[f.b]) / g.qf)), bh = llrint(floor((b0 + f.wb - r - g.lof[f.b]) / g.qf));
-        const long long cl = llrint(ceil((c0 + r - g.lof[f.c]) / g.qf)), ch = llrint(floor((c0 + f.wc - r - g.lof[f.c]) / g.qf));
-        double nlo, nhi;
-        if (f.side == 0) {
-            nlo = f.plane + r;
-            nhi = f.plane + r + depth;
-        } else {
-            nlo = f.plane - r - depth;
-            nhi = f.plane - r;
-        }
-        const long long al = llrint(ceil((nlo - g.lof[f.axis]) / g.qf)), ah = llrint(floor((nhi - g.lof[f.axis]) / g.qf));
-        if (bh < bl || ch < cl || ah < al) {
+        const double sb = __dsub_rn(f.wb, 2.0 * r), sc = __dsub_rn(f.wc, 2.0 * r);
+        const long long ru = llrint(r / g.qf);
+        if (!(r > 0.0) || sb < 0.0 || sc < 0.0 || ru <= 0) {
             ++attempt;
             ++fails;
             continue;
         }
-        u[f.b] = bl + below(draw(g, cell, attempt, 2), bh - bl + 1);
-        u[f.c] = cl + below(draw(g, cell, attempt, 3), ch - cl + 1);
-        u[f.axis] = al + below(draw(g, cell, attempt, 4), ah - al + 1);
+        const double nlo = f.side == 0 ? f.plane + r : f.plane - r - depth;
+        double xc[3];
+        xc[f.b] = __dadd_rn(__dadd_rn(b0, r), __dmul_rn(unit01(draw(g, cell, attempt, 2)), sb));
+        xc[f.c] = __dadd_rn(__dadd_rn(c0, r), __dmul_rn(unit01(draw(g, cell, attempt, 3)), sc));
+        xc[f.axis] = __dadd_rn(nlo, __dmul_rn(unit01(draw(g, cell, attempt, 4)), depth));
+        long long u[3];
+        for (int k = 0; k < 3; ++k) u[k] = llrint((xc[k] - g.lof[k]) / g.qf);
         ++attempt;
         // inside the fine level's walls and clear of them, then no overlap with its particles
         // (cell lists of the last build) or earlier insertions
@@ -668,7 +659,7 @@ __global__ void k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
             ++fails;
             continue;
         }
-        const double m = sphere_mass(rho, r);
+        const double m = sphere_mass(rho, r);    // of the drawn radius (the grid radius differs by < q / 2)
         mine[nins] = make_int4((int)u[0], (int)u[1], (int)u[2], ru_i);
         mym[nins] = m;
         ++nins;
@@ -849,7 +840,7 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
     g.drain = sp->drain_faces;
     g.seed = sp->seed;
     g.add = sp->add_forces ? 1 : 0;
-    g.vel_below = std::isnan(sp->velocity_below) ? -INFINITY : sp->velocity_below;
+    g.vel_below = (sp->velocity_below_on && !std::isnan(sp->velocity_below)) ? sp->velocity_below : -INFINITY;
     // a coarse particle outside the region grown by one largest diameter (Favre samples reach
     // a diameter beyond the faces) touches no cell: bounds in coarse units, rounded outwards
     const double grow = 2.0 * coarse->rmax[0];
@@ -910,8 +901,8 @@ dem_status dem_coupler_create(dem_ctx* coarse, dem_ctx* fine, const dem_coupling
         return DEM_ERR_CUDA;
     }
     cp->rho_f = fine->hl[0].rho;
-    // largest fine radius in fine units: from the fine level's r_max (cell width)
-    cp->g.rmaxf_u = (int)std::llround(std::ceil(fine->rmax[0] / cp->g.qf));
+    // radius bins: equal widths over [0, r_max) of the fine level
+    cp->g.wbin = fine->rmax[0] / cp->g.bins;
     cudaStream_t s = fine->stream;
     dem_ctx* ctx = fine;
     CU(cudaMemsetAsync(ws, 0, need, s));

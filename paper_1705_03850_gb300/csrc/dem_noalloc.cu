@@ -13,7 +13,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 namespace cgdem {
@@ -179,6 +178,9 @@ __global__ void k_na_count(NaScratch s, NaGrid g, int* __restrict__ out)
                     const long long ddy = na_min_image(p.y - q.y, g.per[1], g.ext[1], g.half[1]);
                     const long long ddz = (long long)p.z - q.z;
                     const long long cut = (long long)p.w + q.w + g.skin;
+                    // one axis at a time first (as the list build does): positions clamped far
+                    // outside an open box must not overflow the sum of squares
+                    if (llabs(ddx) >= cut || llabs(ddy) >= cut || llabs(ddz) >= cut) continue;
                     if (ddx * ddx + ddy * ddy + ddz * ddz < cut * cut) ++cnt;
                 }
             }
@@ -186,10 +188,6 @@ __global__ void k_na_count(NaScratch s, NaGrid g, int* __restrict__ out)
     }
     out[i] = cnt;
 }
-
-// device address of g_na_scratch, looked up once per device
-std::mutex g_na_mutex;
-void* g_na_addr[64] = {};
 
 dem_status na_fail(dem_status st, const std::string& msg)
 {
@@ -243,21 +241,14 @@ extern "C" dem_status dem_neighbor_counts_noalloc(const double* x, const double*
     g.ncell = (int)ncell;
     if (n == 0) return DEM_OK;
 
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-        return na_fail(DEM_ERR_CUDA, "dem_neighbor_counts_noalloc: no current CUDA device");
+    // the device address of the scratch array on the current device, looked up on every call
+    // (cheap next to the launches; a cached address would outlive a device reset)
     void* base = nullptr;
     {
-        std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_addr[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
-            if (e != cudaSuccess || !p)
-                return na_fail(DEM_ERR_CUDA, std::string("dem_neighbor_counts_noalloc: cudaGetSymbolAddress: ") +
-                                                 cudaGetErrorString(e));
-            g_na_addr[dev] = p;
-        }
-        base = g_na_addr[dev];
+        cudaError_t e = cudaGetSymbolAddress(&base, g_na_scratch);
+        if (e != cudaSuccess || !base)
+            return na_fail(DEM_ERR_CUDA, std::string("dem_neighbor_counts_noalloc: cudaGetSymbolAddress: ") +
+                                             cudaGetErrorString(e));
     }
     const NaScratch s = carve((unsigned char*)base);
     cudaStream_t st = (cudaStream_t)stream;

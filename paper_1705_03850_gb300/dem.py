@@ -62,7 +62,8 @@ class CouplingSpec(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("kp", ctypes.c_double), ("ki", ctypes.c_double), ("kv", ctypes.c_double),
                 ("mode", ctypes.c_int32), ("max_attempts", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("mass_unit", ctypes.c_double), ("max_insert", ctypes.c_int32), ("add_forces", ctypes.c_int32),
-                ("velocity_below", ctypes.c_double)]
+                ("velocity_below", ctypes.c_double), ("velocity_below_on", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 # coupler fields (dem_coupler_field)
@@ -422,7 +423,9 @@ class Coupler:
         for k in ("surface_cell", "layer", "corr_cell", "alpha", "kp", "ki", "kv", "mass_unit"):
             setattr(sp, k, float(spec[k]))
         sp.seed = int(spec.get("seed", 0))
-        sp.velocity_below = float(spec.get("velocity_below", -math.inf))
+        vb = spec.get("velocity_below", None)
+        if vb is not None and not math.isnan(float(vb)) and float(vb) > -math.inf:
+            sp.velocity_below, sp.velocity_below_on = float(vb), 1
         self.spec = sp
         nb = ctypes.c_int64()
         rc = self.L.dem_coupler_workspace(coarse.h, fine.h, ctypes.byref(sp), ctypes.byref(nb))

@@ -84,7 +84,10 @@ def run(alpha: int = 1, settle_s: float = 0.3, discharge_s: float = 0.6, skip_s:
         "rebuilds_discharge": st1["rebuilds"] - st0["rebuilds"],
         "step_kernel_ms": kms / max(1, kn), "mean_list_length": L,
         "contacts_per_particle": st1["contacts"] / max(1, st1["particles"]),
-        "bytes_per_particle_step": B, "step_kernel_gbs": int(live[0]) * B / (kms / max(1, kn) * 1e-3) / 1e9,
+        "bytes_per_particle_step": B,
+        # modelled bytes over event time (not a DRAM measurement): the rows the last graph's step
+        # kernels walked, from the same statistics snapshot as the list length
+        "step_kernel_gbs_modelled": int(st1["particles"]) * B / (kms / max(1, kn) * 1e-3) / 1e9,
     }
 
 

@@ -315,7 +315,7 @@ def _fcc_fill(lo, hi, periodic, d, gap, z_top, rng, jitter=0.01e-3):
 def chute(length: float = 11.0, width: float = 0.3, height: float = 0.3, bed: float = 0.227,
           regions=((2.0, 0.70), (2.30, 0.18)), diameters=(8.0e-3, 4.0e-3, 2.0e-3), seed: int = 3,
           incline_deg: float = 30.0, u0: float = 0.5, dt: float = 1e-6, interval: int = 15,
-          clear: float = 1.0, multirate: bool = False):
+          clear: float = 1.0, multirate: bool = False, gap: float = 0.05e-3):
     """Three nested coarse-graining levels of an inclined chute (Sec. 2.3 coupling, one dt for all levels).
 
     Level 0 (d = 8 mm, alpha = 4 against the 2 mm base) fills the whole chute, periodic along the
@@ -323,7 +323,8 @@ def chute(length: float = 11.0, width: float = 0.3, height: float = 0.3, bed: fl
     regions[0] = (x start, length) over the full cross-section, level 2 (2 mm) the region
     regions[1] nested inside it.  Each level starts on an FCC lattice (gap 0.05 mm) that is to be
     settled under vertical gravity; the flow then runs with gravity tilted by incline_deg about y
-    and every particle given u0 along x.  The lattice of a finer level starts `clear` diameters of
+    and every particle given u0 along x (gap: the lattice's clearance between neighbours; a negative
+    gap starts the bed compressed, every neighbour pair in contact).  The lattice of a finer level starts `clear` diameters of
     the level above it downstream of its feed face, room for the first inserted particles.
     multirate: level k runs dt times its grain ratio to the finest level (8 mm: 4 dt, 4 mm: 2 dt),
     and `interval` counts steps of the finest level (a multiple of 4 keeps every level whole).  At the default sizes the levels hold about 2.0M, 1.0M and
@@ -341,7 +342,7 @@ def chute(length: float = 11.0, width: float = 0.3, height: float = 0.3, bed: fl
     ratio = [round(d / diameters[-1]) if multirate else 1 for d in diameters]
     for k, (d, (lo, hi, per)) in enumerate(zip(diameters, boxes)):
         flo = lo if k == 0 else (lo[0] + clear * diameters[k - 1], lo[1], lo[2])
-        x = _fcc_fill(flo, hi, per, d, 0.05e-3, bed - d / 2, rng)
+        x = _fcc_fill(flo, hi, per, d, gap, bed - d / 2, rng)
         n = x.shape[0]
         z = np.zeros((n, 3))
         levels.append(_finish(f"chute_level{k}", x, z, z, np.full(n, d / 2), mat, lo, hi, per, dt * ratio[k], g,

@@ -54,3 +54,14 @@ def test_step_kernel_source_hash_is_found():
     import bench
     h = bench._kernel_hash()
     assert re.fullmatch(r"[0-9a-f]{16}", h)
+
+
+def test_graph_length_divides_the_timed_steps():
+    import bench
+    assert bench.graph_length(20, 50) == 20
+    assert bench.graph_length(2000, 50) == 50
+    assert bench.graph_length(30, 50) == 30
+    assert bench.graph_length(120, 50) == 40
+    assert bench.graph_length(7, 50) == 7
+    assert bench.graph_length(97, 50) == 1
+    assert bench.graph_length(100, 0) == 0

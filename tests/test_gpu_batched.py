@@ -1,4 +1,6 @@
 """Batched instances: one context advancing several independent boxes equals each box alone."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -48,3 +50,31 @@ def test_autotuner_returns_a_working_choice():
     sim.set_graph(best.graph_steps)
     sim.step(50)
     assert sim.status() == 0
+
+
+def test_batched_instances_each_match_the_oracle():
+    # four boxes of 120, 315, 48 and 720 spheres (none a multiple of the 128-slot tile) with their
+    # own (E, e, mu), in one context: CUDA graphs of 25 steps, a skin of 1 % of d so that every box
+    # rebuilds its lists inside the graphs several times; each box against its own oracle run at
+    # the 100-step bar (positions within max(1e-4 d, 64 ulp_fp32(|x|)))
+    from _util import min_image, oracle_sim
+    wls = _boxes()
+    ch = autotune.Choice(skin_factor=0.01, cell_factor=1.0, graph_steps=25, max_neighbors=32)
+    sim = autotune.make_context(wls, ch)
+    sim.step(1)
+    sim.set_graph(25)
+    sim.step(99)
+    sim.sync()
+    assert sim.stats()["rebuilds"] >= 3 * len(wls)
+    x = sim.read(dem.POS)
+    off = 0
+    for wl in wls:
+        o = oracle_sim(wl).run(100)
+        d = min_image(x[off:off + wl.n] - o.x, wl)
+        tol = np.maximum(1e-4 * 2 * wl.r[:, None], 64 * np.spacing(np.abs(o.x).astype(np.float32)).astype(np.float64))
+        assert (np.abs(d) <= tol).all(), (wl.n, np.abs(d).max())
+        off += wl.n
+    # the materials differ enough that a box run with another's (E, e, mu) would fail the bar
+    o_wrong = oracle_sim(dataclasses.replace(wls[1], material=wls[2].material)).run(100)
+    d = min_image(x[wls[0].n:wls[0].n + wls[1].n] - o_wrong.x, wls[1])
+    assert np.abs(d).max() > 1e-4 * 2 * wls[1].r.max()

@@ -1,8 +1,14 @@
 """Coupling of a coarse and a fine level (Sec. 2.3) on the GPU against the FP64 oracle, same inputs.
 
-Integer bookkeeping (entered mass, histograms, carries, insertion sets) must be
-bit-exact; stresses, velocities and controller forces agree within float
-rounding of the contact forces (1e-5 relative to each cell's scale)."""
+Integer bookkeeping (entered mass, histograms, carries) must be bit-exact.  Insertion: the
+oracle draws radii and centres in continuous space and tests overlaps in metres; the GPU
+draws the same values and rounds them to its position grid (quantum q) before testing, so
+the two agree on every candidate whose clearance is outside (-4 q, 4 q) -- rounding moves
+a clearance by at most (sqrt(3) + 1) q.  Cells with such a borderline decision (and the
+cells of later faces, whose candidates test against them) are compared only up to it;
+elsewhere the inserted sets are equal, centres and radii within q / 2.  Stresses,
+velocities and controller forces agree within float rounding of the contact forces (1e-5
+relative to each cell's scale)."""
 import numpy as np
 import pytest
 
@@ -25,6 +31,23 @@ WALL = [(0.010, -0.01), (0.010, 0.07)]
 CONE = [(0.0, 0.0), (0.004, 0.0), (0.016, 0.024), (0.016, 0.06)]
 
 
+BAND_Q = 4.0      # borderline band of an insertion decision, in fine quanta
+
+
+def compared_cells(out, faces):
+    """Surface cells whose insertion sequence is compared in full: no borderline decision in the
+    cell, nor in any cell of an earlier face.  faces: list of (first cell, cell count)."""
+    ok = np.ones(len(out["nins"]), dtype=bool)
+    earlier = False
+    for off, n in faces:
+        cells = slice(off, off + n)
+        if earlier:
+            ok[cells] = False
+        ok[cells] &= out["border"][cells] < 0
+        earlier = earlier or bool((out["border"][cells] >= 0).any())
+    return ok
+
+
 def _setup(pre_force=None, walls=None, **extra):
     A, B, fine_wl, spec = workloads.coupling_case()
     spec = dict(spec, **extra)
@@ -43,37 +66,50 @@ def _setup(pre_force=None, walls=None, **extra):
         fine.write(dem.FEXT, pre_force(fine.n, 2e-5))
     cp.couple()
     qf = oracle.quantum(fine_wl.lo, fine_wl.hi)
-    orc = oracle.Coupler(spec, oracle_params(B, walls, WALL_AXIS), oracle_params(fine_wl, walls, WALL_AXIS), fine_wl.lo, qf,
-                         int(np.ceil(rmax_f / qf)), fine_wl.material.rho, idcap=A.n)
+    orc = oracle.Coupler(spec, oracle_params(B, walls, WALL_AXIS), oracle_params(fine_wl, walls, WALL_AXIS), rmax_f,
+                         fine_wl.material.rho, idcap=A.n, band=BAND_Q * qf)
     orc.record(A.x, np.arange(A.n))
     out = orc.call(_state(B), _state(fine_wl), 0.0, 0.0)
     return A, B, fine_wl, spec, coarse, fine, cp, out, qf
 
 
 @pytest.mark.parametrize("walls", [None, WALL, CONE])
-def test_coupling_bookkeeping_and_insertion_are_bit_exact(walls):
+def test_coupling_bookkeeping_and_insertion_match_the_oracle(walls):
     A, B, fine_wl, spec, coarse, fine, cp, out, qf = _setup(walls=walls)
     mu = spec["mass_unit"]
     assert out["cross"].sum() > 0 and out["nins"].sum() > 0      # material entered and was inserted
     assert np.array_equal(np.round(cp.read(dem.CPL_SURFACE_MASS) / mu).astype(np.int64), out["cross"].astype(np.int64))
     assert np.array_equal(cp.read(dem.CPL_SURFACE_HIST).astype(np.int64), out["hist"].astype(np.int64))
-    assert np.array_equal(np.round(cp.read(dem.CPL_SURFACE_CARRY) / mu).astype(np.int64), out["carry"])
     nins = cp.read(dem.CPL_SURFACE_INSERTED).astype(np.int64)
-    assert np.array_equal(nins, out["nins"].astype(np.int64))
+    carry = np.round(cp.read(dem.CPL_SURFACE_CARRY) / mu).astype(np.int64)
+    # only the top face feeds the column: one face of 2 x 2 cells
+    faces = [(0, len(nins))]
+    ok = compared_cells(out, faces)
+    assert ok.mean() >= 0.75, out["border"]
+    assert np.array_equal(nins[ok], out["nins"][ok].astype(np.int64))
+    assert np.array_equal(carry[ok], out["carry"][ok])
     # the inserted particles, in cell order, appended after the fine level's own
     live, ids = fine.counts()
     assert ids[0] == fine_wl.n + nins.sum()
     x = fine.read(dem.POS)[fine_wl.n:]
     r = fine.read(dem.RADIUS)[fine_wl.n:]
-    ref = np.concatenate([out["ins_u"][c, :out["nins"][c]] for c in range(len(nins))])
-    assert np.array_equal(x, np.asarray(fine_wl.lo) + ref[:, :3] * qf)
-    assert np.array_equal(r, ref[:, 3] * qf)
+    start = np.concatenate([[0], np.cumsum(nins)])
+    tol = 0.5 * qf * (1 + 1e-9)
+    for c in np.nonzero(ok)[0]:
+        ref = out["ins_x"][c, :out["nins"][c]]
+        gx, gr = x[start[c]:start[c + 1]], r[start[c]:start[c + 1]]
+        assert np.all(np.abs(gx - ref[:, :3]) <= tol), (c, np.abs(gx - ref[:, :3]).max() / qf)
+        assert np.all(np.abs(gr - ref[:, 3]) <= tol)
+    # the positions are not merely on a coarser grid: the inserted centres take the grid
+    # points nearest to the oracle's continuous ones (the radii, drawn continuously, differ from
+    # one another by more than q)
+    assert len(np.unique(np.round(r / qf))) > 0.9 * len(r)
     # no inserted particle overlaps another or a fine particle (brute force)
     allx = fine.read(dem.POS)
     allr = fine.read(dem.RADIUS)
     pairs = oracle.pairs(oracle_params(fine_wl), allx, allr, 0.0, method="brute")
     assert not np.any(pairs[:, 1] >= fine_wl.n)
-    # mass conservation: inserted + carry = entered (exact, integer units)
+    # mass conservation: inserted + carry = entered (exact, integer units; the GPU's carry equals it above)
     mass_in = np.array([sum(round(m / mu) for m in out["ins_m"][c, :out["nins"][c]]) for c in range(len(nins))])
     assert np.array_equal(mass_in + out["carry"], out["cross"].astype(np.int64))
     if walls is WALL:             # inserted spheres lie inside the wall, clear of it
@@ -105,8 +141,16 @@ def test_coupling_measurements_and_controllers_match_oracle(walls, extra):
     # controller forces held on the particles
     fc = coarse.read(dem.FEXT)
     assert np.abs(fc - out["fext_c"]).max() <= 1e-5 * np.abs(out["fext_c"]).max() + 1e-12
+    # fine controller force u pi r^2 w(s): u = (K_p + K_i T_c) e at the first call, and the
+    # error e = sigma_coarse - sigma_fine is a difference of two stresses each within 1e-5 of
+    # its cell's scale, so |du| <= 1e-5 (|sigma_c| + |sigma_f|) (K_p + K_i T_c): the bound
+    # below, plus float rounding of the product (the clip only lowers the sensitivity)
     ff = fine.read(dem.FEXT)[:fine_wl.n]
-    assert np.abs(ff - out["fext_f"]).max() <= 1e-4 * np.abs(out["fext_f"]).max() + 1e-12
+    Tc = spec["interval"] * spec["dt"]
+    sig = np.abs(out["lay"][:, :, 2])                  # (level, cell): sigma_zz of the top face's layer
+    du = 1e-5 * (sig[0] + sig[1]).max() * (spec["kp"] + spec["ki"] * Tc)
+    tol = du * np.pi * fine_wl.r[:, None] ** 2 + 1e-6 * np.abs(out["fext_f"]) + 1e-15
+    assert np.all(np.abs(ff - out["fext_f"]) <= tol), np.max(np.abs(ff - out["fext_f"]) / tol)
     assert np.abs(out["fext_f"]).max() > 0 and np.abs(out["fext_c"]).max() > 0
 
 
@@ -121,7 +165,11 @@ def test_added_controller_forces_sum_with_the_held_ones():
     assert np.abs(fc - out["fext_c"]).max() > 1e-2          # the held part is there
     ff = fine.read(dem.FEXT)[:fine_wl.n]
     ref_f = held(fine_wl.n, 2e-5) + out["fext_f"]         # (fine.n now counts the inserted particles)
-    assert np.abs(ff - ref_f).max() <= 1e-4 * np.abs(ref_f).max()
+    Tc = spec["interval"] * spec["dt"]
+    sig = np.abs(out["lay"][:, :, 2])
+    du = 1e-5 * (sig[0] + sig[1]).max() * (spec["kp"] + spec["ki"] * Tc)   # as in the test above
+    tol = du * np.pi * fine_wl.r[:, None] ** 2 + 1e-6 * np.abs(ref_f) + 1e-15
+    assert np.all(np.abs(ff - ref_f) <= tol)
     assert np.abs(ff - out["fext_f"]).max() > 2e-6
     # the inserted particles start with no held force; clearing zeroes every one
     assert np.abs(fine.read(dem.FEXT)[fine_wl.n:]).max() == 0.0

@@ -118,10 +118,19 @@ def test_rollout_positions(steps):
             assert np.array_equal(gxi[i, t], gxi[p, pos_of[(p, i)]]), (i, p)
             nsym += 1
     assert nsym > wl.n
-    _, _, hist, _ = o.evaluate(dt_hist=wl.dt)
-    g, r = gpu_pairs(partner), oracle_pairs(hist)
-    diff = g ^ r
-    assert len(diff) <= 2, diff
+    # contact sets: equal on every pair whose overlap (at the oracle's positions) is larger
+    # than the band the position differences allow (twice the largest difference plus the
+    # float32 resolution of the radii and coordinates); band pairs are counted, not failed
+    ha, hb, _, _ = o.history()
+    g, r = gpu_pairs(partner), oracle_pairs((ha, hb))
+    band = 2 * np.abs(d).max() + 8 * _ulp32(2 * wl.r.max()) + 8 * _ulp32(np.abs(o.x).max())
+    inband = 0
+    for i, j in g ^ r:
+        dd = min_image(o.x[i] - o.x[j], wl)
+        delta = o.r[i] + o.r[j] - np.linalg.norm(dd)
+        assert abs(delta) < band, (i, j, delta, band)
+        inband += 1
+    assert inband <= 0.01 * len(r)
 
 
 def test_graph_capture_matches_direct_launches_bitwise():

@@ -596,18 +596,6 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int s
     return nst;
 }
 
-#ifndef DEM_EXP_PFN
-#define DEM_EXP_PFN 0
-#endif
-#ifndef DEM_EXP_PFVW
-#define DEM_EXP_PFVW 0
-#endif
-// bring a line into L1 without holding a register for it
-__device__ __forceinline__ void pf_l1(const void* p)
-{
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));
-}
-
 // WALLS: the variant that evaluates axisymmetric walls (launched only for contexts that have
 // them, so that the wall code costs the plain step nothing)
 template <int MODE, bool WALLS>
@@ -708,17 +696,6 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
             int4 Qb[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) Qb[k] = __ldg(pos + jb[k]);
-            if (DEM_EXP_PFVW && MODE == 0) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if ((hm >> (e0 + k)) & 1u) {
-                        pf_l1(vel + jb[k]);
-                        pf_l1(omg + jb[k]);
-                        pf_l1(h + (size_t)(e0 + k) * ncap);
-                        pf_l1(h + plane + (size_t)(e0 + k) * ncap);
-                        pf_l1(h + 2 * plane + (size_t)(e0 + k) * ncap);
-                    }
-            }
             if (e0 + 4 < ncnt) jn0 = __ldg(nb + (size_t)(e0 + 4) * ncap);
             if (e0 + 5 < ncnt) jn1 = __ldg(nb + (size_t)(e0 + 5) * ncap);
             if (e0 + 6 < ncnt) jn2 = __ldg(nb + (size_t)(e0 + 6) * ncap);
@@ -743,18 +720,6 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
             ho[(size_t)e * ncap] = 0.f;
             ho[plane + (size_t)e * ncap] = 0.f;
             ho[2 * plane + (size_t)e * ncap] = 0.f;
-        }
-        if (DEM_EXP_PFN && MODE == 0 && t + 1 < t1) {
-            // the next tile's own rows, into L1 while this one's contacts are evaluated
-            const int sn = (t + 1) * TILE + ((((int)threadIdx.x >> 5) + t + 1) & (TILE / 32 - 1)) * 32 +
-                           ((int)threadIdx.x & 31);
-            pf_l1(pos + sn);
-            pf_l1(vel + sn);
-            pf_l1(omg + sn);
-            pf_l1(d.cnt[lp] + sn);
-            pf_l1(d.hmask[lp] + sn);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) pf_l1(d.nbr[lp] + (size_t)e * ncap + sn);
         }
         // ---- pass 2: the contacts, in row order, next contact's state in flight
         unsigned cm = tm;

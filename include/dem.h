@@ -181,6 +181,13 @@ dem_status dem_stats(dem_ctx *ctx, dem_stats_t *out);
  * kernel, so a captured run needs no host round trip. */
 dem_status dem_set_graph(dem_ctx *ctx, int32_t steps_per_graph);
 
+/* Threads per block of the step kernel (the fused force and integration of Eqs. 1-6):
+ * 64, 128 (the default) or 256; anything else is DEM_ERR_ARG.  Results do not depend on it
+ * beyond float rounding order (none: every particle sums its own row in row order); it
+ * changes how the work is spread over the GPU.  A captured graph is rebuilt with it.  Not in
+ * the paper: a tuning parameter of this implementation. */
+dem_status dem_set_step_block(dem_ctx *ctx, int32_t threads);
+
 /* CUDA-event time of step kernels of the most recent graph launch: every fifth
  * step kernel of the graph (the first, the sixth, ...) is bracketed by event
  * nodes; total_ms = the sum over those, count = their number (total_ms / count is

@@ -1,13 +1,15 @@
 """Autotuner for multi-instance (batched) runs.
 
 Chooses the neighbour-list skin (the rebuild interval), the cell width, the
-number of steps captured per CUDA graph and the list width by timing each
+number of steps captured per CUDA graph, the list width and the step kernel's
+block size (64, 128 or 256 threads) by timing each
 candidate through the C ABI on a representative subset of the instances
 (evenly spread over their sizes) for the run's full length, so that the cost of
 list rebuilds is part of what is measured: create a context, load the same
 state, time the start-up step (including the first list build) and the
 remaining steps, and keep the fastest candidate that ran without a device
-error.
+error.  The block size is searched second, for the best of the other settings
+(the other settings change the work; the block size only how it is spread).
 """
 from __future__ import annotations
 
@@ -26,13 +28,15 @@ class Choice:
     cell_factor: float      # cell width >= cell_factor * 2 r_max + skin
     graph_steps: int
     max_neighbors: int
+    block: int = 128        # threads per block of the step kernel
     ms_start: float = float("nan")
     ms_per_step: float = float("nan")
     ok: bool = False
 
     def as_dict(self):
         return dict(skin_factor=self.skin_factor, cell_factor=self.cell_factor, graph_steps=self.graph_steps,
-                    max_neighbors=self.max_neighbors, ms_start=self.ms_start, ms_per_step=self.ms_per_step)
+                    max_neighbors=self.max_neighbors, block=self.block, ms_start=self.ms_start,
+                    ms_per_step=self.ms_per_step)
 
 
 def descs_for(workloads, choice: Choice, floor_v=None):
@@ -55,6 +59,7 @@ def concat_state(workloads):
 
 def make_context(workloads, choice: Choice, device=None, state=None):
     sim = dem.DEM(descs_for(workloads, choice), max_neighbors=choice.max_neighbors, device=device)
+    sim.set_step_block(choice.block)
     x, v, w, r, m = state if state is not None else concat_state(workloads)
     sim.write_state(x, v, w, r, m)
     return sim
@@ -74,8 +79,9 @@ def subset(workloads, count):
 
 
 def tune(workloads, skin_factors=(0.025, 0.05, 0.1), cell_factors=(1.0, 1.25), graph_steps=(50, 100),
-         max_neighbors=(32,), window=2000, sample=32, device=None, state=None, log=None):
+         max_neighbors=(32,), blocks=(64, 128, 256), window=2000, sample=32, device=None, state=None, log=None):
     """Time every candidate on `sample` instances for `window` steps; return (best, all).
+    The other settings are searched at 128 threads per block, then `blocks` for the best of them.
     `state`, if given, is the concatenated (x, v, w, r, m) of all the workloads (e.g. after settling);
     the sampled instances start from their part of it, otherwise from their own inputs."""
     import torch
@@ -89,8 +95,8 @@ def tune(workloads, skin_factors=(0.025, 0.05, 0.1), cell_factors=(1.0, 1.25), g
     if state is None:
         state = [torch.as_tensor(a, dtype=torch.float64, device=device or "cuda") for a in concat_state(workloads)]
     results = []
-    for sf, cf, gs, lm in itertools.product(skin_factors, cell_factors, graph_steps, max_neighbors):
-        ch = Choice(sf, cf, gs, lm)
+
+    def run(ch):
         sim = None
         try:
             sim = make_context(workloads, ch, device=device, state=state)
@@ -118,8 +124,17 @@ def tune(workloads, skin_factors=(0.025, 0.05, 0.1), cell_factors=(1.0, 1.25), g
         results.append(ch)
         if log:
             log(f"candidate {ch.as_dict()} ok={ch.ok}")
+        return ch
+
+    cost = lambda c: c.ms_start + c.ms_per_step * window
+    for sf, cf, gs, lm in itertools.product(skin_factors, cell_factors, graph_steps, max_neighbors):
+        run(Choice(sf, cf, gs, lm, 128))
     good = [c for c in results if c.ok]
     if not good:
         raise RuntimeError("no autotuner candidate ran without a device error")
-    best = min(good, key=lambda c: c.ms_start + c.ms_per_step * window)
+    best = min(good, key=cost)
+    for b in blocks:
+        if b != best.block:
+            run(Choice(best.skin_factor, best.cell_factor, best.graph_steps, best.max_neighbors, b))
+    best = min((c for c in results if c.ok), key=cost)
     return best, results

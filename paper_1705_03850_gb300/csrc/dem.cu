@@ -393,14 +393,13 @@ __device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, 
     const size_t plane = (size_t)Lmax * ncap;
     const int* orow = d.nbr[lp] + old;
     const float* ho = d.hist[lp] + old;
-    // the new row (partner slots), overlaps zeroed; the keys give way to the partner IDs
+    // the new row (partner slots); the keys give way to the partner IDs.  Stored overlaps are
+    // written only where carried: every reader of an entry's overlap first checks its bit in the
+    // history mask, so the other entries' storage is never read
     for (int e = 0; e < nc; ++e) {
         const int m = R.pos[e][tx];
         nrow[(size_t)e * ncap] = d.fin[m];
         R.key[e][tx] = __int_as_float(d.sid[m]);
-        hn[(size_t)e * ncap] = 0.f;
-        hn[plane + (size_t)e * ncap] = 0.f;
-        hn[2 * plane + (size_t)e * ncap] = 0.f;
     }
     // carry every non-zero stored overlap of the old row to the pair's new entry
     const int ocnt = D.flag == 2 ? 0 : d.cnt[lp][old];
@@ -597,23 +596,37 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int s
 }
 
 // WALLS: the variant that evaluates axisymmetric walls (launched only for contexts that have
-// them, so that the wall code costs the plain step nothing)
-template <int MODE, bool WALLS>
-__global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, cudaGraphConditionalHandle hnext, int use_cond)
+// them, so that the wall code costs the plain step nothing).
+// BS: threads per block (64, 128 or 256; the autotuner picks one).  The tiles of TILE slots are
+// walked as units of BS / 32 warp slices: slice w' of tile t (w' = 0 .. 3) is virtual warp
+// 4 t + w'; unit u is virtual warps [u BS / 32, (u + 1) BS / 32), and instances own whole pairs
+// of tiles, so that a unit never straddles two instances.
+template <int BS>
+constexpr int step_minb()
 {
+    return DEM_STEP_MINB * TILE / BS;        // the same registers per thread at every block size
+}
+
+template <int MODE, bool WALLS, int BS = TILE>
+__global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, cudaGraphConditionalHandle hnext, int use_cond)
+{
+    constexpr int WPB = BS / 32;             // warps per block
+    constexpr int WPT = TILE / 32;           // warp slices per tile
+    static_assert(BS == 64 || BS == 128 || BS == 256, "step block of 64, 128 or 256 threads");
+    static_assert((WPT & (WPT - 1)) == 0, "warps per tile must be a power of two");
     __shared__ InstC sc;
     __shared__ InstD sd;
-    __shared__ float smax[TILE / 32];
+    __shared__ float smax[WPB];
     __shared__ bool am_last;
-    const int T = d.ntiles;
-    const int t0 = (int)((long long)blockIdx.x * T / gridDim.x);
-    const int t1 = (int)((long long)(blockIdx.x + 1) * T / gridDim.x);
+    const int NU = d.ntiles * WPT / WPB;
+    const int u0 = (int)((long long)blockIdx.x * NU / gridDim.x);
+    const int u1 = (int)((long long)(blockIdx.x + 1) * NU / gridDim.x);
     const int ncap = d.ncap;
     const size_t plane = (size_t)d.Lmax * ncap;
     int kprev = -1;
     float runmax = 0.f;
-    for (int t = t0; t < t1; ++t) {
-        const int k = __ldg(d.tile_inst + t);
+    for (int u = u0; u < u1; ++u) {
+        const int k = __ldg(d.tile_inst + u * WPB / WPT);
         if (k != kprev) {
             if (MODE == 0 && kprev >= 0) {
                 // flush the displacement maximum of the previous instance
@@ -624,22 +637,23 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     float bm = smax[0];
-                    for (int i = 1; i < TILE / 32; ++i) bm = fmaxf(bm, smax[i]);
+                    for (int i = 1; i < WPB; ++i) bm = fmaxf(bm, smax[i]);
                     if (bm > 0.f) atomicMax(&d.id[kprev].stepmax, __float_as_uint(bm));
                 }
                 runmax = 0.f;
             }
             __syncthreads();
-            if (threadIdx.x < (int)(sizeof(InstC) / 4)) ((int*)&sc)[threadIdx.x] = ((const int*)(d.ic + k))[threadIdx.x];
+            for (int i = threadIdx.x; i < (int)(sizeof(InstC) / 4); i += BS) ((int*)&sc)[i] = ((const int*)(d.ic + k))[i];
             if (threadIdx.x < (int)(sizeof(InstD) / 4)) ((int*)&sd)[threadIdx.x] = ((const int*)(d.id + k))[threadIdx.x];
             __syncthreads();
             kprev = k;
         }
         const InstC& c = sc;
-        static_assert((TILE / 32 & (TILE / 32 - 1)) == 0, "warps per tile must be a power of two");
-        // warp w takes the 32-slot slice (w + t) mod 4 of tile t: rebuilds put the rows with
-        // the most contacts in the first slice, so the rotation evens out the warps' work
-        const int s = t * TILE + ((((int)threadIdx.x >> 5) + t) & (TILE / 32 - 1)) * 32 + ((int)threadIdx.x & 31);
+        // warp slice w' of tile t takes the 32-slot slice (w' + t) mod 4: rebuilds put the rows
+        // with the most contacts in the first slice, so the rotation evens out the warps' work
+        const int vw = u * WPB + ((int)threadIdx.x >> 5);
+        const int t = vw / WPT;
+        const int s = t * TILE + (((vw & (WPT - 1)) + t) & (WPT - 1)) * 32 + ((int)threadIdx.x & 31);
         if (s - c.slot0 >= sd.n) continue;
         const int cur = sd.cur, lp = sd.lp;
         const int4* __restrict__ pos = d.pos[cur];
@@ -896,7 +910,7 @@ __global__ void __launch_bounds__(TILE, DEM_STEP_MINB) k_step(Dev d, int prime, 
         __syncthreads();
         if (threadIdx.x == 0) {
             float bm = smax[0];
-            for (int i = 1; i < TILE / 32; ++i) bm = fmaxf(bm, smax[i]);
+            for (int i = 1; i < WPB; ++i) bm = fmaxf(bm, smax[i]);
             if (bm > 0.f && kprev >= 0) atomicMax(&d.id[kprev].stepmax, __float_as_uint(bm));
             __threadfence();
             const unsigned prev = atomicAdd(&d.g->counter, 1u);
@@ -1661,7 +1675,8 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
         p.ic.push_back(c);
         p.hl.push_back(h);
         p.count.push_back(s.n);
-        const long long tiles = (s.capacity + TILE - 1) / TILE;
+        // whole pairs of tiles: a step block of 2 TILE threads never straddles two instances
+        const long long tiles = 2 * ((s.capacity + 2 * TILE - 1) / (2 * TILE));
         for (long long t = 0; t < tiles; ++t) p.tile_inst.push_back(k);
         slot += tiles * TILE;
         if (slot > (1ll << 30)) { err = "total capacity too large"; return DEM_ERR_ARG; }
@@ -1826,6 +1841,31 @@ void destroy_graph(dem_ctx* ctx)
     ctx->rb_graph = nullptr;
 }
 
+// the step kernel (MODE 0) at the context's block size, and its persistent grid
+void* step_func(const dem_ctx* ctx)
+{
+    switch (ctx->step_bs) {
+    case 64: return ctx->walls ? (void*)k_step<0, true, 64> : (void*)k_step<0, false, 64>;
+    case 256: return ctx->walls ? (void*)k_step<0, true, 256> : (void*)k_step<0, false, 256>;
+    default: return ctx->walls ? (void*)k_step<0, true, 128> : (void*)k_step<0, false, 128>;
+    }
+}
+
+int step_grid(const dem_ctx* ctx)
+{
+    return ctx->grid_bs[ctx->step_bs == 64 ? 0 : ctx->step_bs == 256 ? 2 : 1];
+}
+
+dem_status launch_step(dem_ctx* ctx, int prime)
+{
+    Dev dv = ctx->dev;
+    cudaGraphConditionalHandle h = 0;
+    int use_cond = 0;
+    void* args[] = {&dv, &prime, &h, &use_cond};
+    CU(cudaLaunchKernel(step_func(ctx), dim3(step_grid(ctx)), dim3(ctx->step_bs), args, 0, ctx->stream));
+    return DEM_OK;
+}
+
 constexpr int EV_EVERY = 5;    // step kernels per timed one in a graph
 
 dem_status build_graph(dem_ctx* ctx, int S)
@@ -1884,9 +1924,9 @@ dem_status build_graph(dem_ctx* ctx, int S)
         cudaGraphConditionalHandle hn = i + 1 < S ? h[i + 1] : h[i];
         void* args[] = {&dv, &prime, &hn, &use_cond};
         cudaKernelNodeParams kp{};
-        kp.func = ctx->walls ? (void*)k_step<0, true> : (void*)k_step<0, false>;
-        kp.gridDim = dim3(ctx->grid0);
-        kp.blockDim = dim3(TILE);
+        kp.func = step_func(ctx);
+        kp.gridDim = dim3(step_grid(ctx));
+        kp.blockDim = dim3(ctx->step_bs);
         kp.kernelParams = args;
         cudaGraphNode_t kn;
         if (i % EV_EVERY == 0) {
@@ -2084,6 +2124,16 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_step<0, false>, TILE, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_step<1, true>, TILE, 0);
         ctx->grid0 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b0)));
+        {
+            // persistent step grids per block size: a wave of blocks, at most one per unit of work
+            int bx[3] = {0, 0, 0};
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bx[0], k_step<0, false, 64>, 64, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bx[1], k_step<0, false, 128>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bx[2], k_step<0, false, 256>, 256, 0);
+            const int units[3] = {ctx->ntiles * 2, ctx->ntiles, ctx->ntiles / 2};
+            for (int i = 0; i < 3; ++i)
+                ctx->grid_bs[i] = std::max(1, std::min(units[i], std::max(1, nsm) * std::max(1, bx[i])));
+        }
         ctx->grid1 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b1)));
         ctx->grid_rb = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * 8));
         int bb = 0;
@@ -2227,9 +2277,8 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps)
         }
         dem_status st = launch_rebuild(ctx, ctx->stream);
         if (st) return st;
-        if (ctx->walls) k_step<0, true><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
-        else k_step<0, false><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, ctx->fresh ? 1 : 0, 0, 0);
-        CU(cudaGetLastError());
+        st = launch_step(ctx, ctx->fresh ? 1 : 0);
+        if (st) return st;
         ctx->fresh = false;
         ++done;
     }
@@ -2293,6 +2342,15 @@ dem_status dem_set_graph(dem_ctx* ctx, int32_t steps_per_graph)
 {
     if (!ctx || steps_per_graph < 0 || steps_per_graph > 4096) return DEM_ERR_ARG;
     return build_graph(ctx, steps_per_graph);
+}
+
+dem_status dem_set_step_block(dem_ctx* ctx, int32_t threads)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (threads != 64 && threads != 128 && threads != 256)
+        return fail(ctx, DEM_ERR_ARG, "step block must be 64, 128 or 256 threads");
+    ctx->step_bs = threads;
+    return ctx->graph_steps > 0 ? build_graph(ctx, ctx->graph_steps) : DEM_OK;
 }
 
 dem_status dem_graph_step_kernel_ms(dem_ctx* ctx, double* total_ms, int32_t* count)
@@ -2407,7 +2465,7 @@ dem_status snap(dem_ctx* ctx, const Snap& S, bool save)
 
 dem_status step_once(dem_ctx* ctx, int prime)
 {
-    k_step<0, false><<<ctx->grid0, TILE, 0, ctx->stream>>>(ctx->dev, prime, 0, 0);   // rollouts refuse walls
+    if (dem_status st = launch_step(ctx, prime)) return st;   // rollouts refuse walls
     CU(cudaGetLastError());
     return DEM_OK;
 }

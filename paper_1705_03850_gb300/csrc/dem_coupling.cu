@@ -50,6 +50,9 @@ struct Geo {
     // coarse positions (units) outside [ulo, uhi) take part in nothing but the position record:
     // the region grown by the largest coarse diameter and two units, rounded outwards
     long long ulo[3], uhi[3];
+    // per level (0 coarse, 1 fine) and feed face: a box in that level's units, rounded outwards,
+    // holding the face's transition layer; positions outside every such box lie in no layer cell
+    long long lay_lo[2][6][3], lay_hi[2][6][3];
 };
 
 struct Acc {
@@ -103,6 +106,18 @@ __device__ __forceinline__ int face_cell(const Face& f, double pb, double pc, co
     return f.off + ib + f.nb * ic;
 }
 
+// false only if the integer position P of level L lies outside every face's layer box (then
+// layer_cell is -1); true means: decide with layer_cell
+__device__ __forceinline__ bool maybe_layer(const Geo& g, int L, int4 P)
+{
+    for (int k = 0; k < g.nface; ++k) {
+        const long long* lo = g.lay_lo[L][k];
+        const long long* hi = g.lay_hi[L][k];
+        if (P.x >= lo[0] && P.x < hi[0] && P.y >= lo[1] && P.y < hi[1] && P.z >= lo[2] && P.z < hi[2]) return true;
+    }
+    return false;
+}
+
 // transition cell holding a point (first face in order wins at corners), or -1
 __device__ __forceinline__ int layer_cell(const Geo& g, const double* x, int* fidx)
 {
@@ -129,6 +144,27 @@ __device__ __forceinline__ int corr_cell(const Geo& g, const double* x)
     return (i[2] * g.ncr[1] + i[1]) * g.ncr[0] + i[0];
 }
 
+// add (m, m v, V) of a particle to its correction cell: when the whole warp holds the same
+// cell (Morton order makes that the usual case) the warp sums first and one lane adds the sums
+__device__ __forceinline__ void corr_add(double* cor, int cc, double m, const float4& V, double vol)
+{
+    const unsigned act = __activemask();
+    const bool whole = act == 0xffffffffu && __match_any_sync(act, cc) == act;
+    if (cc < 0) return;
+    double v[5] = {m, m * V.x, m * V.y, m * V.z, vol};
+    double* o = cor + (size_t)cc * 5;
+    if (whole) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+        if ((threadIdx.x & 31) == 0)
+            for (int k = 0; k < 5; ++k) atomicAdd(o + k, v[k]);
+        return;
+    }
+    for (int k = 0; k < 5; ++k) atomicAdd(o + k, v[k]);
+}
+
 __device__ __forceinline__ void atomic_max_f(unsigned* a, float v)
 {
     if (v > 0.f) atomicMax(a, __float_as_uint(v));
@@ -137,7 +173,10 @@ __device__ __forceinline__ void atomic_max_f(unsigned* a, float v)
 // Eq. 7 accumulation of one particle into a transition cell: mass, momentum,
 // m v v, volume, and the contact part 1/2 r_ij (x) f_ij over its contacts
 // (floor contact: branch vector to the contact point, no 1/2), symmetrised.
-__device__ void layer_add(const Dev& d, const InstC& c, const InstD& D, int s, double* acc, unsigned* vmax, int fresh)
+// (not inlined: few particles lie in a transition cell, and inlining the contact law would
+// give every thread of the per-particle passes its registers)
+__device__ __noinline__ void layer_add(const Dev& d, const InstC& c, const InstD& D, int s, double* acc, unsigned* vmax,
+                                       int fresh)
 {
     const int cur = D.cur, lp = D.lp, ncap = d.ncap;
     const size_t plane = (size_t)d.Lmax * ncap;
@@ -295,7 +334,7 @@ __global__ void k_cp_clear(Geo g, Acc a)
 
 // coarse level: entries through the feed faces, Favre samples at the faces,
 // transition and correction cells; remember the positions for the next call
-__global__ void __launch_bounds__(TILE) k_cp_coarse(Dev d, Geo g, Acc a, int record_only)
+__global__ void __launch_bounds__(TILE, 8) k_cp_coarse(Dev d, Geo g, Acc a, int record_only)
 {
     for_live(d, [&](int s, const InstC& c, const InstD& D) {
         const int4 P = d.pos[D.cur][s];
@@ -349,17 +388,9 @@ __global__ void __launch_bounds__(TILE) k_cp_coarse(Dev d, Geo g, Acc a, int rec
                 break;
             }
             int fk;
-            const int lc = layer_cell(g, x, &fk);
+            const int lc = maybe_layer(g, 0, P) ? layer_cell(g, x, &fk) : -1;
             if (lc >= 0) layer_add(d, c, D, s, a.lay + (size_t)lc * 20, a.vmax + lc, g.fresh_c);
-            const int cc = corr_cell(g, x);
-            if (cc >= 0) {
-                double* o = a.cor + (size_t)cc * 5;
-                atomicAdd(o, m);
-                atomicAdd(o + 1, m * V.x);
-                atomicAdd(o + 2, m * V.y);
-                atomicAdd(o + 3, m * V.z);
-                atomicAdd(o + 4, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
-            }
+            corr_add(a.cor, corr_cell(g, x), m, V, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
         }
         for (int k = 0; k < 3; ++k) a.prev[3 * (size_t)id + k] = x[k];
         a.prev_ok[id] = 1;
@@ -367,7 +398,7 @@ __global__ void __launch_bounds__(TILE) k_cp_coarse(Dev d, Geo g, Acc a, int rec
 }
 
 // fine level: transition and correction cells, removal through drain faces
-__global__ void __launch_bounds__(TILE) k_cp_fine(Dev d, Geo g, Acc a)
+__global__ void __launch_bounds__(TILE, 8) k_cp_fine(Dev d, Geo g, Acc a)
 {
     for_live(d, [&](int s, const InstC& c, const InstD& D) {
         const int4 P = d.pos[D.cur][s];
@@ -375,17 +406,9 @@ __global__ void __launch_bounds__(TILE) k_cp_fine(Dev d, Geo g, Acc a)
         const double x[3] = {posm(g.lof, g.qf, P.x, 0), posm(g.lof, g.qf, P.y, 1), posm(g.lof, g.qf, P.z, 2)};
         const double r = (double)P.w * g.qf, m = d.omg[D.cur][s].w;
         int fk;
-        const int lc = layer_cell(g, x, &fk);
+        const int lc = maybe_layer(g, 1, P) ? layer_cell(g, x, &fk) : -1;
         if (lc >= 0) layer_add(d, c, D, s, a.lay + ((size_t)g.S + lc) * 20, a.vmax + g.S + lc, g.fresh_f);
-        const int cc = corr_cell(g, x);
-        if (cc >= 0) {
-            double* o = a.cor + ((size_t)g.C + cc) * 5;
-            atomicAdd(o, m);
-            atomicAdd(o + 1, m * V.x);
-            atomicAdd(o + 2, m * V.y);
-            atomicAdd(o + 3, m * V.z);
-            atomicAdd(o + 4, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
-        }
+        corr_add(a.cor + (size_t)g.C * 5, corr_cell(g, x), m, V, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
         bool gone = false;
         for (int ax = 0; ax < 3; ++ax) {
             if ((g.drain >> (2 * ax)) & 1) gone |= x[ax] < g.lo[ax];
@@ -449,12 +472,16 @@ __global__ void __launch_bounds__(TILE) k_cp_force_fine(Dev d, Geo g, Acc a)
 {
     for_live(d, [&](int s, const InstC& c, const InstD& D) {
         const int4 P = d.pos[D.cur][s];
-        const float4 V = d.vel[D.cur][s];
-        const double x[3] = {posm(g.lof, g.qf, P.x, 0), posm(g.lof, g.qf, P.y, 1), posm(g.lof, g.qf, P.z, 2)};
         float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
         int fk = 0;
-        const int lc = layer_cell(g, x, &fk);
+        int lc = -1;
+        double x[3] = {0.0, 0.0, 0.0};
+        if (maybe_layer(g, 1, P)) {
+            for (int k = 0; k < 3; ++k) x[k] = posm(g.lof, g.qf, k == 0 ? P.x : k == 1 ? P.y : P.z, k);
+            lc = layer_cell(g, x, &fk);
+        }
         if (lc >= 0) {
+            const float4 V = d.vel[D.cur][s];
             const Face& f = g.face[fk];
             const double r = (double)P.w * g.qf, m = d.omg[D.cur][s].w;
             const double sdist = f.side == 0 ? x[f.axis] - f.plane : f.plane - x[f.axis];
@@ -847,6 +874,24 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
     for (int a = 0; a < 3; ++a) {
         g.ulo[a] = (long long)std::floor((g.lo[a] - grow - g.loc[a]) / g.qc) - 2;
         g.uhi[a] = (long long)std::ceil((g.hi[a] + grow - g.loc[a]) / g.qc) + 2;
+    }
+    // layer boxes: the region's extent across the face and [plane, plane + layer) inwards, in
+    // each level's units, widened by two units on every side (a box too large costs time only)
+    for (int L = 0; L < 2; ++L) {
+        const double* lo0 = L == 0 ? g.loc : g.lof;
+        const double q = L == 0 ? g.qc : g.qf;
+        for (int k = 0; k < g.nface; ++k) {
+            const Face& f = g.face[k];
+            for (int a = 0; a < 3; ++a) {
+                double lo = g.lo[a], hi = g.hi[a];
+                if (a == f.axis) {
+                    lo = f.side == 0 ? f.plane : f.plane - g.layer;
+                    hi = f.side == 0 ? f.plane + g.layer : f.plane;
+                }
+                g.lay_lo[L][k][a] = (long long)std::floor((lo - lo0[a]) / q) - 2;
+                g.lay_hi[L][k][a] = (long long)std::ceil((hi - lo0[a]) / q) + 2;
+            }
+        }
     }
     return DEM_OK;
 }

@@ -17,6 +17,8 @@ struct dem_ctx {
     int B = 0, Lmax = 0;
     int ncap = 0, ntiles = 0;
     int grid0 = 1, grid1 = 1;         // persistent grids of the step / evaluation kernels
+    int step_bs = 128;                // threads per block of the step kernel (64, 128 or 256)
+    int grid_bs[3] = {1, 1, 1};       // persistent step grids for 64, 128 and 256 threads per block
     int grid_rb = 1;                  // persistent grid of the per-slot rebuild kernels
     int grid_build = 1;               // one wave of the list build (occupancy-sized)
     unsigned ncodes = 0, nparts = 0;

@@ -95,6 +95,7 @@ def lib():
         "dem_instance_info_get": [vp, i32, ctypes.POINTER(InstanceInfo)],
         "dem_stats": [vp, ctypes.POINTER(Stats)],
         "dem_set_graph": [vp, i32],
+        "dem_set_step_block": [vp, i32],
         "dem_graph_step_kernel_ms": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)],
         "dem_rollout_workspace": [vp, i64, i64, ctypes.POINTER(i64)],
         "dem_rollout_forward": [vp, i64, i64, vp, i64],
@@ -128,7 +129,7 @@ def lib():
 def exported_symbols():
     return ["dem_query_workspace", "dem_create", "dem_destroy", "dem_write", "dem_read", "dem_read_contacts",
             "dem_write_contacts", "dem_step", "dem_sync_status", "dem_instance_info_get", "dem_stats",
-            "dem_set_graph", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
+            "dem_set_graph", "dem_set_step_block", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
             "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material",
             "dem_coupler_workspace", "dem_coupler_create", "dem_couple", "dem_coupler_read", "dem_coupler_destroy",
             "dem_counts", "dem_clear_external_force", "dem_grid_fields", "dem_set_walls", "dem_wall_removed",
@@ -281,6 +282,11 @@ class DEM:
 
     def set_graph(self, steps_per_graph):
         self._check(self.L.dem_set_graph(self.h, int(steps_per_graph)), "set graph")
+        return self
+
+    def set_step_block(self, threads):
+        """Threads per block of the step kernel: 64, 128 (default) or 256."""
+        self._check(self.L.dem_set_step_block(self.h, int(threads)), "set step block")
         return self
 
     def graph_step_kernel_ms(self):

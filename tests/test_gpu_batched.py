@@ -44,7 +44,9 @@ def test_autotuner_returns_a_working_choice():
     best, allc = autotune.tune(wls, skin_factors=(0.05, 0.1), cell_factors=(1.0,), graph_steps=(25,), window=50,
                                sample=6)
     assert best.ok and best.ms_per_step > 0
-    assert len(allc) == 2
+    assert len(allc) == 4                  # two skins at 128 threads, then 64 and 256 for the better one
+    assert best.block in (64, 128, 256)
+    assert sorted(c.block for c in allc) == [64, 128, 128, 256]
     sim = autotune.make_context(wls, best)
     sim.step(1)
     sim.set_graph(best.graph_steps)
@@ -78,3 +80,20 @@ def test_batched_instances_each_match_the_oracle():
     o_wrong = oracle_sim(dataclasses.replace(wls[1], material=wls[2].material)).run(100)
     d = min_image(x[wls[0].n:wls[0].n + wls[1].n] - o_wrong.x, wls[1])
     assert np.abs(d).max() > 1e-4 * 2 * wls[1].r.max()
+
+
+@pytest.mark.parametrize("threads", [64, 256])
+def test_step_block_size_does_not_change_the_run(threads):
+    # every particle sums its own row in row order whatever the block size: the same bits
+    wls = _boxes()
+    ch = autotune.Choice(skin_factor=0.05, cell_factor=1.0, graph_steps=25, max_neighbors=32)
+    runs = []
+    for c in (ch, dataclasses.replace(ch, block=threads)):
+        sim = autotune.make_context(wls, c)
+        sim.step(1)
+        sim.set_graph(25)
+        sim.step(150)
+        sim.sync()
+        runs.append((sim.read(dem.POS), sim.read(dem.OMEGA), sim.stats()["rebuilds"]))
+    assert runs[0][2] > len(wls)
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])

@@ -20,6 +20,7 @@ using namespace cgdem;
 namespace {
 
 constexpr int MAXBINS = 32;
+constexpr int MAXCR = 256;     // correction cells per axis at most (integer thresholds per axis)
 
 struct Face {
     int axis, side;      // side 0: the face at lo[axis] (inward normal +e_axis), 1: at hi[axis]
@@ -45,6 +46,7 @@ struct Geo {
     double loc[3], qc, lof[3], qf;
     double wbin;         // width of a radius bin: the fine level's largest radius / bins [m]
     int fresh_c, fresh_f;
+    float cells_per_unit[2][3];  // correction cells per position unit (a first guess of the cell)
     int add;             // add the controller forces to the held ones instead of replacing them
     double vel_below;    // correction cells centred below this height take the velocity target
     // coarse positions (units) outside [ulo, uhi) take part in nothing but the position record:
@@ -72,13 +74,48 @@ struct Acc {
     // correction cells
     double* cor;                 // [2][C][5]: m, mv(3), V
     double* dv;                  // [C][3] velocity change asked of the coarse particles
-    // coarse particles by ID: position at the previous call [m], validity
-    double* prev;                // [idcap][3]
+    // coarse particles by ID: position at the previous call (integer units), validity
+    int4* prev;                  // [idcap]
     int* prev_ok;
+    // per level (0 coarse, 1 fine) and axis: the correction grid as integer thresholds in that
+    // level's units: a position u lies in the region iff thr[0] <= u < thr[ncr], in cell i iff
+    // thr[i] <= u < thr[i + 1] (the decisions of the double expressions, see cell_thresholds)
+    long long* thr;              // [2][3][MAXCR + 1]
     int* removed;                // [1] fine particles removed at this call
 };
 
-__device__ __forceinline__ double posm(const double* lo, double q, int u, int a) { return lo[a] + (double)u * q; }
+// position in metres of integer coordinate u on axis a: lo + u q, rounded once (as the read-out)
+__device__ __forceinline__ double posm(const double* lo, double q, int u, int a) { return __fma_rn((double)u, q, lo[a]); }
+
+// correction cell of an integer position of level L from the integer thresholds (-1 outside)
+__device__ __forceinline__ int corr_cell_u(const Geo& g, const long long* thr, int L, int4 P)
+{
+    int idx[3];
+    for (int a = 0; a < 3; ++a) {
+        const long long* T = thr + ((size_t)L * 3 + a) * (MAXCR + 1);
+        const long long u = a == 0 ? P.x : a == 1 ? P.y : P.z;
+        const int n = g.ncr[a];
+        if (u < __ldg(T) || u >= __ldg(T + n)) return -1;
+        int i = (int)((float)(u - __ldg(T)) * g.cells_per_unit[L][a]);
+        i = min(max(i, 0), n - 1);
+        while (i + 1 < n && u >= __ldg(T + i + 1)) ++i;
+        while (i > 0 && u < __ldg(T + i)) --i;
+        idx[a] = i;
+    }
+    return (idx[2] * g.ncr[1] + idx[1]) * g.ncr[0] + idx[0];
+}
+
+// inside the region by the integer thresholds (level L)
+__device__ __forceinline__ bool inside_u(const Geo& g, const long long* thr, int L, long long ux, long long uy,
+                                         long long uz)
+{
+    const long long u[3] = {ux, uy, uz};
+    for (int a = 0; a < 3; ++a) {
+        const long long* T = thr + ((size_t)L * 3 + a) * (MAXCR + 1);
+        if (u[a] < __ldg(T) || u[a] >= __ldg(T + g.ncr[a])) return false;
+    }
+    return true;
+}
 
 __device__ __forceinline__ bool inside_box(const Geo& g, const double* x)
 {
@@ -136,22 +173,15 @@ __device__ __forceinline__ int layer_cell(const Geo& g, const double* x, int* fi
     return -1;
 }
 
-__device__ __forceinline__ int corr_cell(const Geo& g, const double* x)
-{
-    if (!inside_box(g, x)) return -1;
-    int i[3];
-    for (int a = 0; a < 3; ++a) i[a] = min(max((int)floor_div(x[a] - g.lo[a], g.wcr[a], g.iwcr[a]), 0), g.ncr[a] - 1);
-    return (i[2] * g.ncr[1] + i[1]) * g.ncr[0] + i[0];
-}
-
 // add (m, m v, V) of a particle to its correction cell: when the whole warp holds the same
-// cell (Morton order makes that the usual case) the warp sums first and one lane adds the sums
-__device__ __forceinline__ void corr_add(double* cor, int cc, double m, const float4& V, double vol)
+// cell (Morton order makes that the usual case) the warp sums first, in float (32 terms), and
+// one lane adds the sums to the cell's double accumulators
+__device__ __forceinline__ void corr_add(double* cor, int cc, float m, const float4& V, float vol)
 {
     const unsigned act = __activemask();
     const bool whole = act == 0xffffffffu && __match_any_sync(act, cc) == act;
     if (cc < 0) return;
-    double v[5] = {m, m * V.x, m * V.y, m * V.z, vol};
+    float v[5] = {m, m * V.x, m * V.y, m * V.z, vol};
     double* o = cor + (size_t)cc * 5;
     if (whole) {
 #pragma unroll
@@ -159,10 +189,10 @@ __device__ __forceinline__ void corr_add(double* cor, int cc, double m, const fl
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
         if ((threadIdx.x & 31) == 0)
-            for (int k = 0; k < 5; ++k) atomicAdd(o + k, v[k]);
+            for (int k = 0; k < 5; ++k) atomicAdd(o + k, (double)v[k]);
         return;
     }
-    for (int k = 0; k < 5; ++k) atomicAdd(o + k, v[k]);
+    for (int k = 0; k < 5; ++k) atomicAdd(o + k, (double)v[k]);
 }
 
 __device__ __forceinline__ void atomic_max_f(unsigned* a, float v)
@@ -340,38 +370,44 @@ __global__ void __launch_bounds__(TILE, 8) k_cp_coarse(Dev d, Geo g, Acc a, int 
         const int4 P = d.pos[D.cur][s];
         const float4 V = d.vel[D.cur][s];
         const unsigned id = __float_as_uint(V.w) & ID_MASK;
-        const double x[3] = {posm(g.loc, g.qc, P.x, 0), posm(g.loc, g.qc, P.y, 1), posm(g.loc, g.qc, P.z, 2)};
-        const double r = (double)P.w * g.qc, m = d.omg[D.cur][s].w;
         const bool near = P.x >= g.ulo[0] && P.x < g.uhi[0] && P.y >= g.ulo[1] && P.y < g.uhi[1] &&
                           P.z >= g.ulo[2] && P.z < g.uhi[2];
         if (!record_only && near) {
-            // entry through a feed face since the previous call
-            if (a.prev_ok[id] && inside_box(g, x)) {
-                const double* p = a.prev + 3 * (size_t)id;
-                double seg = 0.0;
-                for (int k = 0; k < 3; ++k) seg = fmax(seg, fabs(x[k] - p[k]));
-                if (!inside_box(g, p) && seg < 0.25 * (g.hi[0] - g.lo[0] + g.hi[1] - g.lo[1] + g.hi[2] - g.lo[2])) {
-                    double tbest = 2.0;
-                    int cbest = -1;
-                    for (int k = 0; k < g.nface; ++k) {
-                        const Face& f = g.face[k];
-                        const double p0 = p[f.axis], p1 = x[f.axis];
-                        const bool enters = f.side == 0 ? (p0 < f.plane && p1 >= f.plane) : (p0 >= f.plane && p1 < f.plane);
-                        if (!enters) continue;
-                        const double t = (f.plane - p0) / (p1 - p0);
-                        const int cc = face_cell(f, p[f.b] + t * (x[f.b] - p[f.b]), p[f.c] + t * (x[f.c] - p[f.c]), g);
-                        if (cc >= 0 && t < tbest) {
-                            tbest = t;
-                            cbest = cc;
+            const double x[3] = {posm(g.loc, g.qc, P.x, 0), posm(g.loc, g.qc, P.y, 1), posm(g.loc, g.qc, P.z, 2)};
+            const double r = (double)P.w * g.qc;
+            const float mf = d.omg[D.cur][s].w;
+            const double m = mf;
+            // entry through a feed face since the previous call (inside now, outside then)
+            if (a.prev_ok[id] && inside_u(g, a.thr, 0, P.x, P.y, P.z)) {
+                const int4 pu = a.prev[id];
+                if (!inside_u(g, a.thr, 0, pu.x, pu.y, pu.z)) {
+                    const double p[3] = {posm(g.loc, g.qc, pu.x, 0), posm(g.loc, g.qc, pu.y, 1),
+                                         posm(g.loc, g.qc, pu.z, 2)};
+                    double seg = 0.0;
+                    for (int k = 0; k < 3; ++k) seg = fmax(seg, fabs(x[k] - p[k]));
+                    if (seg < 0.25 * (g.hi[0] - g.lo[0] + g.hi[1] - g.lo[1] + g.hi[2] - g.lo[2])) {
+                        double tbest = 2.0;
+                        int cbest = -1;
+                        for (int k = 0; k < g.nface; ++k) {
+                            const Face& f = g.face[k];
+                            const double p0 = p[f.axis], p1 = x[f.axis];
+                            const bool enters = f.side == 0 ? (p0 < f.plane && p1 >= f.plane) : (p0 >= f.plane && p1 < f.plane);
+                            if (!enters) continue;
+                            const double t = (f.plane - p0) / (p1 - p0);
+                            const int cc = face_cell(f, p[f.b] + t * (x[f.b] - p[f.b]), p[f.c] + t * (x[f.c] - p[f.c]), g);
+                            if (cc >= 0 && t < tbest) {
+                                tbest = t;
+                                cbest = cc;
+                            }
                         }
-                    }
-                    if (cbest >= 0) {
-                        atomicAdd(a.cross + cbest, (unsigned long long)llrint(m / g.mass_unit));
-                        // bin of the fine-scale radius r / alpha among equal bins over [0, r_max,fine)
-                        // (the last bin takes anything larger)
-                        const double fb = floor(r / g.alpha / g.wbin);
-                        const int b = fb < (double)(g.bins - 1) ? (int)fb : g.bins - 1;
-                        atomicAdd(a.hist + (size_t)cbest * MAXBINS + b, 1u);
+                        if (cbest >= 0) {
+                            atomicAdd(a.cross + cbest, (unsigned long long)llrint(m / g.mass_unit));
+                            // bin of the fine-scale radius r / alpha among equal bins over [0, r_max,fine)
+                            // (the last bin takes anything larger)
+                            const double fb = floor(r / g.alpha / g.wbin);
+                            const int b = fb < (double)(g.bins - 1) ? (int)fb : g.bins - 1;
+                            atomicAdd(a.hist + (size_t)cbest * MAXBINS + b, 1u);
+                        }
                     }
                 }
             }
@@ -390,9 +426,10 @@ __global__ void __launch_bounds__(TILE, 8) k_cp_coarse(Dev d, Geo g, Acc a, int 
             int fk;
             const int lc = maybe_layer(g, 0, P) ? layer_cell(g, x, &fk) : -1;
             if (lc >= 0) layer_add(d, c, D, s, a.lay + (size_t)lc * 20, a.vmax + lc, g.fresh_c);
-            corr_add(a.cor, corr_cell(g, x), m, V, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
+            const float rf = (float)r;
+            corr_add(a.cor, corr_cell_u(g, a.thr, 0, P), mf, V, 4.18879020f * rf * rf * rf);
         }
-        for (int k = 0; k < 3; ++k) a.prev[3 * (size_t)id + k] = x[k];
+        a.prev[id] = make_int4(P.x, P.y, P.z, 0);
         a.prev_ok[id] = 1;
     });
 }
@@ -403,16 +440,21 @@ __global__ void __launch_bounds__(TILE, 8) k_cp_fine(Dev d, Geo g, Acc a)
     for_live(d, [&](int s, const InstC& c, const InstD& D) {
         const int4 P = d.pos[D.cur][s];
         float4 V = d.vel[D.cur][s];
-        const double x[3] = {posm(g.lof, g.qf, P.x, 0), posm(g.lof, g.qf, P.y, 1), posm(g.lof, g.qf, P.z, 2)};
-        const double r = (double)P.w * g.qf, m = d.omg[D.cur][s].w;
-        int fk;
-        const int lc = maybe_layer(g, 1, P) ? layer_cell(g, x, &fk) : -1;
-        if (lc >= 0) layer_add(d, c, D, s, a.lay + ((size_t)g.S + lc) * 20, a.vmax + g.S + lc, g.fresh_f);
-        corr_add(a.cor + (size_t)g.C * 5, corr_cell(g, x), m, V, 4.0 / 3.0 * 3.14159265358979323846 * r * r * r);
+        if (maybe_layer(g, 1, P)) {
+            const double x[3] = {posm(g.lof, g.qf, P.x, 0), posm(g.lof, g.qf, P.y, 1), posm(g.lof, g.qf, P.z, 2)};
+            int fk;
+            const int lc = layer_cell(g, x, &fk);
+            if (lc >= 0) layer_add(d, c, D, s, a.lay + ((size_t)g.S + lc) * 20, a.vmax + g.S + lc, g.fresh_f);
+        }
+        const float rf = (float)((double)P.w * g.qf);
+        corr_add(a.cor + (size_t)g.C * 5, corr_cell_u(g, a.thr, 1, P), d.omg[D.cur][s].w, V, 4.18879020f * rf * rf * rf);
+        // drain faces: x < lo or x >= hi on their axes (the region bounds as integer thresholds)
         bool gone = false;
         for (int ax = 0; ax < 3; ++ax) {
-            if ((g.drain >> (2 * ax)) & 1) gone |= x[ax] < g.lo[ax];
-            if ((g.drain >> (2 * ax + 1)) & 1) gone |= x[ax] >= g.hi[ax];
+            const long long* T = a.thr + ((size_t)3 + ax) * (MAXCR + 1);
+            const long long u = ax == 0 ? P.x : ax == 1 ? P.y : P.z;
+            if ((g.drain >> (2 * ax)) & 1) gone |= u < __ldg(T);
+            if ((g.drain >> (2 * ax + 1)) & 1) gone |= u >= __ldg(T + g.ncr[ax]);
         }
         if (gone) {
             V.w = __uint_as_float(__float_as_uint(V.w) | GONE_BIT);
@@ -519,12 +561,7 @@ __global__ void __launch_bounds__(TILE) k_cp_force_coarse(Dev d, Geo g, Acc a)
     for_live(d, [&](int s, const InstC& c, const InstD& D) {
         const int4 P = d.pos[D.cur][s];
         float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
-        int cc = -1;
-        if (P.x >= g.ulo[0] && P.x < g.uhi[0] && P.y >= g.ulo[1] && P.y < g.uhi[1] && P.z >= g.ulo[2] &&
-            P.z < g.uhi[2]) {
-            const double x[3] = {posm(g.loc, g.qc, P.x, 0), posm(g.loc, g.qc, P.y, 1), posm(g.loc, g.qc, P.z, 2)};
-            cc = corr_cell(g, x);
-        }
+        const int cc = corr_cell_u(g, a.thr, 0, P);
         if (cc >= 0) {
             const double m = d.omg[D.cur][s].w, k = g.kv * m / g.Tc;
             const double* dv = a.dv + 3 * (size_t)cc;
@@ -779,8 +816,8 @@ size_t coupler_layout(dem_coupler* cp, char* base)
     size_t o_cross = L.take(S * 8), o_hist = L.take(S * MAXBINS * 4), o_fav = L.take(S * 32), o_carry = L.take(S * 8),
            o_nins = L.take(S * 4), o_ins = L.take(S * MI * 16), o_insm = L.take(S * MI * 8), o_lay = L.take(2 * S * 160),
            o_vmax = L.take(2 * S * 4), o_ctrl = L.take(S * 24), o_out = L.take(2 * S * 88), o_cor = L.take(2 * C * 40),
-           o_dv = L.take(C * 24), o_prev = L.take(ncap * 24), o_pok = L.take(ncap * 4), o_rem = L.take(16),
-           o_ovf = L.take(16);
+           o_dv = L.take(C * 24), o_prev = L.take(ncap * 16), o_pok = L.take(ncap * 4), o_rem = L.take(16),
+           o_ovf = L.take(16), o_thr = L.take(2 * 3 * (MAXCR + 1) * 8);
     if (base) {
         Acc& a = cp->a;
         a.cross = (unsigned long long*)(base + o_cross);
@@ -796,8 +833,9 @@ size_t coupler_layout(dem_coupler* cp, char* base)
         a.out = (double*)(base + o_out);
         a.cor = (double*)(base + o_cor);
         a.dv = (double*)(base + o_dv);
-        a.prev = (double*)(base + o_prev);
+        a.prev = (int4*)(base + o_prev);
         a.prev_ok = (int*)(base + o_pok);
+        a.thr = (long long*)(base + o_thr);
         a.removed = (int*)(base + o_rem);
         cp->overflow = (int*)(base + o_ovf);
     }
@@ -848,6 +886,10 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
     g.C = 1;
     for (int a = 0; a < 3; ++a) {
         g.ncr[a] = std::max(1, (int)std::floor((g.hi[a] - g.lo[a]) / sp->corr_cell));
+        if (g.ncr[a] > MAXCR) {
+            err = "more than 256 correction cells along an axis";
+            return DEM_ERR_ARG;
+        }
         g.wcr[a] = (g.hi[a] - g.lo[a]) / g.ncr[a];
         g.iwcr[a] = 1.0 / g.wcr[a];
         g.C *= g.ncr[a];
@@ -870,6 +912,8 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
     g.vel_below = (sp->velocity_below_on && !std::isnan(sp->velocity_below)) ? sp->velocity_below : -INFINITY;
     // a coarse particle outside the region grown by one largest diameter (Favre samples reach
     // a diameter beyond the faces) touches no cell: bounds in coarse units, rounded outwards
+    for (int L = 0; L < 2; ++L)
+        for (int a = 0; a < 3; ++a) g.cells_per_unit[L][a] = (float)((L == 0 ? g.qc : g.qf) / g.wcr[a]);
     const double grow = 2.0 * coarse->rmax[0];
     for (int a = 0; a < 3; ++a) {
         g.ulo[a] = (long long)std::floor((g.lo[a] - grow - g.loc[a]) / g.qc) - 2;
@@ -894,6 +938,53 @@ dem_status plan_geo(dem_ctx* coarse, dem_ctx* fine, const dem_coupling* sp, Geo&
         }
     }
     return DEM_OK;
+}
+
+// The correction grid as integer thresholds per level and axis (layout of Acc::thr).  A level's
+// position in metres is lo + u q rounded once (as the kernels and the read-out form it); a
+// position is in the region when lo_r <= x < hi_r and in cell floor_div(x - lo_r, w, 1/w) (clamped).
+// Both decisions are monotone in u, so each is a threshold on u: the smallest u where it holds,
+// found from the estimate by evaluating the same double expressions.
+double floor_div_host(double a, double w, double iw)
+{
+    const double t = a * iw, f = std::floor(t);
+    if (t - f < 1e-6 || f + 1.0 - t < 1e-6) return std::floor(a / w);
+    return f;
+}
+
+template <typename Pred>
+bool first_true(Pred pred, double estimate, long long& out)
+{
+    long long u = (long long)std::floor(estimate) - 4;
+    for (int i = 0; i < 64 && pred(u); ++i) u -= 64;
+    if (pred(u)) return false;
+    for (int i = 0; i < 4096; ++i, ++u)
+        if (pred(u)) {
+            out = u;
+            return true;
+        }
+    return false;
+}
+
+bool cell_thresholds(const Geo& g, std::vector<long long>& thr)
+{
+    thr.assign((size_t)2 * 3 * (MAXCR + 1), 0);
+    for (int L = 0; L < 2; ++L) {
+        const double* lo0 = L == 0 ? g.loc : g.lof;
+        const double q = L == 0 ? g.qc : g.qf;
+        for (int a = 0; a < 3; ++a) {
+            long long* T = thr.data() + ((size_t)L * 3 + a) * (MAXCR + 1);
+            auto x = [&](long long u) { return std::fma((double)u, q, lo0[a]); };
+            const int n = g.ncr[a];
+            bool ok = first_true([&](long long u) { return x(u) >= g.lo[a]; }, (g.lo[a] - lo0[a]) / q, T[0]) &&
+                      first_true([&](long long u) { return x(u) >= g.hi[a]; }, (g.hi[a] - lo0[a]) / q, T[n]);
+            for (int k = 1; k < n && ok; ++k)
+                ok = first_true([&](long long u) { return floor_div_host(x(u) - g.lo[a], g.wcr[a], g.iwcr[a]) >= k; },
+                                (g.lo[a] + k * g.wcr[a] - lo0[a]) / q, T[k]);
+            if (!ok) return false;
+        }
+    }
+    return true;
 }
 
 }  // namespace
@@ -951,6 +1042,17 @@ dem_status dem_coupler_create(dem_ctx* coarse, dem_ctx* fine, const dem_coupling
     cudaStream_t s = fine->stream;
     dem_ctx* ctx = fine;
     CU(cudaMemsetAsync(ws, 0, need, s));
+    {
+        std::vector<long long> thr;
+        if (!cell_thresholds(cp->g, thr)) {
+            set_thread_error("correction grid thresholds not found");
+            cudaEventDestroy(cp->ready);
+            delete cp;
+            return DEM_ERR_ARG;
+        }
+        CU(cudaMemcpyAsync(cp->a.thr, thr.data(), thr.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+        CU(cudaStreamSynchronize(s));
+    }
     // enable the external force on both levels
     for (dem_ctx* x : {coarse, fine}) {
         int one = 1;

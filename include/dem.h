@@ -62,7 +62,10 @@ typedef enum {
     DEM_ERR_NONFINITE = 4,  /* a force, torque or velocity became NaN/Inf */
     DEM_ERR_ESCAPED = 5,    /* a particle left the representable z range */
     DEM_ERR_TIMEOUT = 6,    /* a bounded device wait gave up */
-    DEM_ERR_STATE = 7       /* call not valid in the context's current state */
+    DEM_ERR_STATE = 7,      /* call not valid in the context's current state */
+    DEM_ERR_BOUNDS = 8      /* (library built with DEM_CHECKS=1 only) a gathered particle index of the
+                               step kernel, or a cell code or candidate range of the list build, out
+                               of range; the access was skipped */
 } dem_status;
 
 /* Fields of dem_read / dem_write.  n counts particles. */
@@ -125,6 +128,10 @@ typedef struct {
     int64_t contacts;        /* contacts (particle pairs counted from both sides + floor) at that call */
     int64_t particles;       /* live particles */
     int64_t wall_contacts;   /* floor contacts among `contacts` */
+    int32_t step_threads;    /* threads per block of the step kernel (dem_set_step_block) */
+    int32_t step_lanes;      /* lanes per particle of the step kernel (dem_set_step_lanes) */
+    int32_t graph_fused;     /* 1: the captured graph runs fused steps (dem_set_graph_mode) */
+    int32_t reserved;
 } dem_stats_t;
 
 /* Bytes of device workspace a context with this configuration needs. */
@@ -185,8 +192,39 @@ dem_status dem_set_graph(dem_ctx *ctx, int32_t steps_per_graph);
  * 64, 128 (the default) or 256; anything else is DEM_ERR_ARG.  Results do not depend on it
  * beyond float rounding order (none: every particle sums its own row in row order); it
  * changes how the work is spread over the GPU.  A captured graph is rebuilt with it.  Not in
- * the paper: a tuning parameter of this implementation. */
+ * the paper: a tuning parameter of this implementation.  DEM_ERR_STATE for a block other
+ * than 128 threads while more than one lane per particle is set. */
 dem_status dem_set_step_block(dem_ctx *ctx, int32_t threads);
+
+/* Lanes per particle of the step kernel: 1 (the default), 2, 4 or 8, or 0 to choose by size
+ * (one lane while the context's slots fill half the GPU's resident threads of the one-lane
+ * kernel, else the most lanes whose threads are all resident at once; one lane unless the
+ * block is 128 threads); anything else is DEM_ERR_ARG, and more than one needs the 128-thread
+ * block (DEM_ERR_STATE otherwise).  With
+ * L lanes, lane l of a particle's group evaluates the contacts of its row entries l, l + L,
+ * l + 2L, ... (Eqs. 3-6) and the group adds its partial force and torque sums in a fixed
+ * order before the first lane integrates (Eqs. 1-2): for systems too small to fill the GPU
+ * with one thread per particle.  Results are deterministic for a given L (they do not depend
+ * on the block size or the schedule) and differ between values of L only by the order of the
+ * float sums.  A captured graph is rebuilt with it.  Not in the paper: a tuning parameter of
+ * this implementation. */
+dem_status dem_set_step_lanes(dem_ctx *ctx, int32_t lanes);
+
+/* How a captured graph (dem_set_graph) runs its steps.  1: one step-kernel launch per step,
+ * each preceded by a conditional list-build node.  2: fused steps: one cooperative launch
+ * (one block per 128-slot tile, or as many blocks as are resident at once, each walking a
+ * range of tiles) runs every step up to the next list build, with a grid barrier
+ * between steps (the last block to arrive ends the step for every instance); the graph loops
+ * (a conditional while node) over list build + fused launch until its steps are done.  Each
+ * step computes exactly what the per-step kernel computes (the same bits); fused steps save
+ * the per-step launch and node latency of systems too small to fill the GPU.  Needs one lane
+ * per particle and 128-thread blocks (DEM_ERR_STATE otherwise; the previous graph is kept).
+ * 0 (the default): fused when those hold and every 128-slot tile's block is resident at once,
+ * else one launch per step.  A barrier wait that does not end within about a second reports
+ * DEM_ERR_TIMEOUT.  With fused steps dem_graph_step_kernel_ms times the whole graph launch
+ * (list builds included) and counts its steps.  Not in the paper: a scheduling choice of this
+ * implementation. */
+dem_status dem_set_graph_mode(dem_ctx *ctx, int32_t mode);
 
 /* CUDA-event time of step kernels of the most recent graph launch: every fifth
  * step kernel of the graph (the first, the sixth, ...) is bracketed by event

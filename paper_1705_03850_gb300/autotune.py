@@ -1,15 +1,17 @@
 """Autotuner for multi-instance (batched) runs.
 
 Chooses the neighbour-list skin (the rebuild interval), the cell width, the
-number of steps captured per CUDA graph, the list width and the step kernel's
-block size (64, 128 or 256 threads) by timing each
+number of steps captured per CUDA graph, the list width, the step kernel's
+block size (64, 128 or 256 threads) and its lanes per particle (1, 2, 4 or 8) by timing each
 candidate through the C ABI on a representative subset of the instances
 (evenly spread over their sizes) for the run's full length, so that the cost of
 list rebuilds is part of what is measured: create a context, load the same
 state, time the start-up step (including the first list build) and the
 remaining steps, and keep the fastest candidate that ran without a device
 error.  The block size is searched second, for the best of the other settings
-(the other settings change the work; the block size only how it is spread).
+(the other settings change the work; the block size only how it is spread), and
+the lanes per particle last, at 128 threads, when every instance is in the sample
+(how many lanes pay depends on how many particles the whole context holds).
 """
 from __future__ import annotations
 
@@ -29,13 +31,14 @@ class Choice:
     graph_steps: int
     max_neighbors: int
     block: int = 128        # threads per block of the step kernel
+    lanes: int = 1          # lanes per particle of the step kernel
     ms_start: float = float("nan")
     ms_per_step: float = float("nan")
     ok: bool = False
 
     def as_dict(self):
         return dict(skin_factor=self.skin_factor, cell_factor=self.cell_factor, graph_steps=self.graph_steps,
-                    max_neighbors=self.max_neighbors, block=self.block, ms_start=self.ms_start,
+                    max_neighbors=self.max_neighbors, block=self.block, lanes=self.lanes, ms_start=self.ms_start,
                     ms_per_step=self.ms_per_step)
 
 
@@ -60,6 +63,7 @@ def concat_state(workloads):
 def make_context(workloads, choice: Choice, device=None, state=None):
     sim = dem.DEM(descs_for(workloads, choice), max_neighbors=choice.max_neighbors, device=device)
     sim.set_step_block(choice.block)
+    sim.set_step_lanes(choice.lanes)
     x, v, w, r, m = state if state is not None else concat_state(workloads)
     sim.write_state(x, v, w, r, m)
     return sim
@@ -79,13 +83,16 @@ def subset(workloads, count):
 
 
 def tune(workloads, skin_factors=(0.025, 0.05, 0.1), cell_factors=(1.0, 1.25), graph_steps=(50, 100),
-         max_neighbors=(32,), blocks=(64, 128, 256), window=2000, sample=32, device=None, state=None, log=None):
+         max_neighbors=(32,), blocks=(64, 128, 256), lanes=(1, 2, 4, 8), window=2000, sample=32, device=None,
+         state=None, log=None):
     """Time every candidate on `sample` instances for `window` steps; return (best, all).
-    The other settings are searched at 128 threads per block, then `blocks` for the best of them.
+    The other settings are searched at 128 threads per block and one lane per particle, then
+    `blocks` for the best of them, then `lanes` at 128 threads if every instance is sampled.
     `state`, if given, is the concatenated (x, v, w, r, m) of all the workloads (e.g. after settling);
     the sampled instances start from their part of it, otherwise from their own inputs."""
     import torch
     picked = subset_indices(workloads, sample)
+    whole = len(picked) == len(workloads)
     if state is not None:
         off = np.concatenate([[0], np.cumsum([w.n for w in workloads])])
         rows = torch.as_tensor(np.concatenate([np.arange(off[k], off[k + 1]) for k in picked]),
@@ -105,6 +112,7 @@ def tune(workloads, skin_factors=(0.025, 0.05, 0.1), cell_factors=(1.0, 1.25), g
             sim.step(1)
             sim.sync()
             ch.ms_start = (time.perf_counter() - t0) * 1e3
+            gs = ch.graph_steps
             sim.set_graph(gs)
             n = max(gs, (window // gs) * gs)
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -137,4 +145,12 @@ def tune(workloads, skin_factors=(0.025, 0.05, 0.1), cell_factors=(1.0, 1.25), g
         if b != best.block:
             run(Choice(best.skin_factor, best.cell_factor, best.graph_steps, best.max_neighbors, b))
     best = min((c for c in results if c.ok), key=cost)
+    if whole:
+        base = next(c for c in results if c.ok and c.block == 128 and c.lanes == 1 and
+                    (c.skin_factor, c.cell_factor, c.graph_steps, c.max_neighbors) ==
+                    (best.skin_factor, best.cell_factor, best.graph_steps, best.max_neighbors))
+        for ln in lanes:
+            if ln != 1:
+                run(Choice(base.skin_factor, base.cell_factor, base.graph_steps, base.max_neighbors, 128, ln))
+        best = min((c for c in results if c.ok), key=cost)
     return best, results

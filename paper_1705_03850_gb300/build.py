@@ -11,6 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcgdem.so")
+LIB_CHECKED = os.path.join(BUILD, "libcgdem_checked.so")   # -DDEM_CHECKS=1: in-kernel bounds checks
 
 SOURCES = ["dem.cu", "dem_noalloc.cu", "dem_coupling.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -29,19 +30,23 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ to an object, then link the shared library."""
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    """Compile every .cu under csrc/ to an object, then link the shared library.  checks: the
+    bounds-checked variant (the step kernel's gathered indices and the list build's cell codes
+    and candidate ranges tested in the kernels; a violation is reported as DEM_ERR_BOUNDS), built
+    beside the plain one."""
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "dem.h"))
     objs = []
     jobs = []
+    tag = "_checked" if checks else ""
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, src.replace(".cu", tag + ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([_nvcc()] + NVCC_FLAGS + ["-c", s, "-o", o])
+            jobs.append([_nvcc()] + NVCC_FLAGS + (["-DDEM_CHECKS=1"] if checks else []) + ["-c", s, "-o", o])
 
     def run(cmd):
         if verbose:
@@ -50,12 +55,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    lib = LIB_CHECKED if checks else LIB
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([_nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp] + objs)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False, verbose: bool = False) -> tuple[str, str]:
+    """The plain library and the bounds-checked one, compiled side by side."""
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        plain = ex.submit(build, force, verbose, False)
+        checked = ex.submit(build, force, verbose, True)
+        return plain.result(), checked.result()
 
 
 if __name__ == "__main__":
-    print(build(verbose=True))
+    import sys
+    print(build(verbose=True, checks="--checks" in sys.argv))

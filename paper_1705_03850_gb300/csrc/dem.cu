@@ -329,6 +329,7 @@ __device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, 
         const int ix = k % 3, iy = (k / 3) % 3, iz = k / 9;
         const unsigned code = (unsigned)c.code0 + (ix == 0 ? mx0 : ix == 1 ? mx1 : mx2) +
                               (iy == 0 ? my0 : iy == 1 ? my1 : my2) + (iz == 0 ? mz0 : iz == 1 ? mz1 : mz2);
+        if (!in_range(d, (long long)code - c.code0, c.ncode, ps, 1)) return make_uint2(0u, 0u);
         return __ldg(d.crange + code);
     };
     // scan the 27 cells (the next cell's range in flight) and append the neighbours
@@ -339,7 +340,12 @@ __device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, 
         const uint2 cr = rg;
         if (k + 1 < 27) rg = range_of(k + 1);
         const int start = c.slot0 + (int)(cr.x - cbase);
-        const int cnt = (int)cr.y;
+        int cnt = (int)cr.y;
+        // a cell's candidates lie within the instance's slots (a cell outside the grid reads as
+        // empty, with no start)
+        if (DEM_CHECKS && cnt > 0 &&
+            !(in_range(d, start - c.slot0, c.cap, ps, 2) && in_range(d, start - c.slot0 + cnt, c.cap + 1, ps, 2)))
+            cnt = 0;
         for (int t = 0; t < cnt; ++t) {
             const int m = start + t;
             const int4 q = __ldg(d.spos + m);
@@ -581,27 +587,55 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int s
 
 // WALLS: the variant that evaluates axisymmetric walls (launched only for contexts that have
 // them, so that the wall code costs the plain step nothing).
-// BS: threads per block (64, 128 or 256; the autotuner picks one).  The tiles of TILE slots are
-// walked as units of BS / 32 warp slices: slice w' of tile t (w' = 0 .. 3) is virtual warp
-// 4 t + w'; unit u is virtual warps [u BS / 32, (u + 1) BS / 32), and instances own whole pairs
-// of tiles, so that a unit never straddles two instances.
-template <int BS>
+// BS: threads per block (64, 128 or 256; the autotuner picks one).  LPP: lanes per particle
+// (1, 2, 4 or 8; more than one only at 128 threads, for systems too small to fill the GPU with
+// one thread per row): the LPP lanes of a group take the row entries e = sub, sub + LPP, ...,
+// OR their touch masks together, sum their contacts in row order and combine the partial sums
+// by a fixed butterfly, so that the result depends on LPP but not on the block size or the
+// schedule; the group's first lane adds the floor and walls, integrates and writes.
+// The tiles of TILE slots are walked as warp slices of 32 / LPP slots: slice w' of tile t
+// (w' = 0 .. 4 LPP - 1) is virtual warp 4 LPP t + w'; unit u is virtual warps
+// [u BS / 32, (u + 1) BS / 32), and instances own whole pairs of tiles, so that a unit never
+// straddles two instances.
+template <int BS, int LPP = 1>
 constexpr int step_minb()
 {
-    return DEM_STEP_MINB * TILE / BS;        // the same registers per thread at every block size
+    // the same registers per thread at every block size; with several lanes per particle (small
+    // systems, where the resident warps are not the limit) room for the whole row state
+    return LPP == 1 ? DEM_STEP_MINB * TILE / BS : 5;
 }
 
-template <int MODE, bool WALLS, int BS = TILE>
-__global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, cudaGraphConditionalHandle hnext, int use_cond)
+// Particle state: neighbours' through the read-only data cache, except in fused steps, where the
+// state is rewritten during the launch (by other blocks for the neighbours): there every state
+// load goes to L2 (ordered after the previous step's writes by the grid barrier's fences), so
+// that no SM's L1 or read-only cache can return a line from an earlier step.
+template <bool FUSED, typename T>
+__device__ __forceinline__ T ld_state(const T* p)
+{
+    if (FUSED) return __ldcg(p);
+    return __ldg(p);
+}
+
+// One step over the block's units (MODE 0: force, kick and drift of every particle; MODE 1:
+// forces only), ending with the block's displacement maximum folded into its last instance.
+// sc, sd, smax: the block's shared staging of the current instance and of the warp maxima.
+// FUSED: called once per step by the fused kernel.
+template <int MODE, bool WALLS, int BS, int LPP, bool FUSED = false>
+__device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, InstD& sd, float* smax)
 {
     constexpr int WPB = BS / 32;             // warps per block
-    constexpr int WPT = TILE / 32;           // warp slices per tile
+    constexpr int SPW = 32 / LPP;            // slots per warp
+    constexpr int WPT = TILE / SPW;          // warp slices per tile
     static_assert(BS == 64 || BS == 128 || BS == 256, "step block of 64, 128 or 256 threads");
+    static_assert(LPP == 1 || LPP == 2 || LPP == 4 || LPP == 8, "1, 2, 4 or 8 lanes per particle");
+    static_assert(LPP == 1 || MODE == 0, "several lanes per particle only for the step");
     static_assert((WPT & (WPT - 1)) == 0, "warps per tile must be a power of two");
-    __shared__ InstC sc;
-    __shared__ InstD sd;
-    __shared__ float smax[WPB];
-    __shared__ bool am_last;
+    // entries of a lane's share of a row: bits e with e mod LPP == sub
+    constexpr unsigned SUBBITS = LPP == 1 ? 0xffffffffu : LPP == 2 ? 0x55555555u : LPP == 4 ? 0x11111111u : 0x01010101u;
+    const int lane = (int)threadIdx.x & 31;
+    const int sub = lane & (LPP - 1);
+    const unsigned gmask = LPP == 1 ? 0xffffffffu : (((1u << LPP) - 1u) << (lane & ~(LPP - 1)));
+    const unsigned submask = SUBBITS << sub;
     const int NU = d.ntiles * WPT / WPB;
     const int u0 = (int)((long long)blockIdx.x * NU / gridDim.x);
     const int u1 = (int)((long long)(blockIdx.x + 1) * NU / gridDim.x);
@@ -628,7 +662,9 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
             }
             __syncthreads();
             for (int i = threadIdx.x; i < (int)(sizeof(InstC) / 4); i += BS) ((int*)&sc)[i] = ((const int*)(d.ic + k))[i];
-            if (threadIdx.x < (int)(sizeof(InstD) / 4)) ((int*)&sd)[threadIdx.x] = ((const int*)(d.id + k))[threadIdx.x];
+            if (threadIdx.x < (int)(sizeof(InstD) / 4))
+                ((int*)&sd)[threadIdx.x] = FUSED ? __ldcg((const int*)(d.id + k) + threadIdx.x)
+                                                 : ((const int*)(d.id + k))[threadIdx.x];
             __syncthreads();
             kprev = k;
         }
@@ -637,15 +673,15 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
         // with the most contacts in the first slice, so the rotation evens out the warps' work
         const int vw = u * WPB + ((int)threadIdx.x >> 5);
         const int t = vw / WPT;
-        const int s = t * TILE + (((vw & (WPT - 1)) + t) & (WPT - 1)) * 32 + ((int)threadIdx.x & 31);
+        const int s = t * TILE + (((vw & (WPT - 1)) + t) & (WPT - 1)) * SPW + lane / LPP;
         if (s - c.slot0 >= sd.n) continue;
         const int cur = sd.cur, lp = sd.lp;
         const int4* __restrict__ pos = d.pos[cur];
         const float4* __restrict__ vel = d.vel[cur];
         const float4* __restrict__ omg = d.omg[cur];
-        const int4 P = pos[s];
-        float4 Vv = vel[s];
-        float4 Wv = omg[s];
+        const int4 P = FUSED ? __ldcg(pos + s) : pos[s];
+        float4 Vv = FUSED ? __ldcg(vel + s) : vel[s];
+        float4 Wv = FUSED ? __ldcg(omg + s) : omg[s];
         const unsigned idw = __float_as_uint(Vv.w);
         const unsigned myid = idw & ID_MASK;
         const bool wall_prev = (idw & WALL_BIT) != 0u;
@@ -654,7 +690,7 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
         const float r = (float)P.w * q;
         const V3 vme = v3(Vv.x, Vv.y, Vv.z), wme = v3(Wv.x, Wv.y, Wv.z);
         const float dt_hist = prime ? 0.f : c.dt;
-        V3 F = m * v3(c.g[0], c.g[1], c.g[2]);
+        V3 F = sub == 0 ? m * v3(c.g[0], c.g[1], c.g[2]) : v3(0.f, 0.f, 0.f);
         V3 Tq = v3(0.f, 0.f, 0.f);
         const int ncnt = d.cnt[lp][s];
         const int* nb = d.nbr[lp] + s;
@@ -668,18 +704,18 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
         unsigned tm = 0u;
         // the first batch of indices is loaded before the row length arrives (rows hold at
         // least d.Lmax entries of storage); entries beyond the row are replaced by this slot
-        int jn0 = 0 < d.Lmax ? __ldg(nb) : s;
-        int jn1 = 1 < d.Lmax ? __ldg(nb + (size_t)ncap) : s;
-        int jn2 = 2 < d.Lmax ? __ldg(nb + (size_t)2 * ncap) : s;
-        int jn3 = 3 < d.Lmax ? __ldg(nb + (size_t)3 * ncap) : s;
-        jn0 = 0 < ncnt ? jn0 : s;
-        jn1 = 1 < ncnt ? jn1 : s;
-        jn2 = 2 < ncnt ? jn2 : s;
-        jn3 = 3 < ncnt ? jn3 : s;
+        int jn0 = sub < d.Lmax ? __ldg(nb + (size_t)sub * ncap) : s;
+        int jn1 = sub + LPP < d.Lmax ? __ldg(nb + (size_t)(sub + LPP) * ncap) : s;
+        int jn2 = sub + 2 * LPP < d.Lmax ? __ldg(nb + (size_t)(sub + 2 * LPP) * ncap) : s;
+        int jn3 = sub + 3 * LPP < d.Lmax ? __ldg(nb + (size_t)(sub + 3 * LPP) * ncap) : s;
+        jn0 = sub < ncnt ? jn0 : s;
+        jn1 = sub + LPP < ncnt ? jn1 : s;
+        jn2 = sub + 2 * LPP < ncnt ? jn2 : s;
+        jn3 = sub + 3 * LPP < ncnt ? jn3 : s;
         // removed below the removal height: parked until the next list build drops it (tested
         // here, after the row's first loads are in flight, so that live rows do not wait on it)
         if (idw & GONE_BIT) {
-            if (MODE == 0) {
+            if (MODE == 0 && sub == 0) {
                 d.pos[cur ^ 1][s] = P;
                 d.vel[cur ^ 1][s] = Vv;
                 d.omg[cur ^ 1][s] = Wv;
@@ -689,15 +725,18 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
             }
             continue;
         }
-        for (int e0 = 0; e0 < ncnt; e0 += 4) {
-            const int jb[4] = {jn0, jn1, jn2, jn3};
+        for (int e0 = sub; e0 < ncnt; e0 += 4 * LPP) {
+            int jb[4] = {jn0, jn1, jn2, jn3};
+            if (DEM_CHECKS)
+                for (int k = 0; k < 4; ++k)
+                    if (!in_range(d, jb[k], ncap, s, 3)) jb[k] = s;
             int4 Qb[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) Qb[k] = __ldg(pos + jb[k]);
-            if (e0 + 4 < ncnt) jn0 = __ldg(nb + (size_t)(e0 + 4) * ncap);
-            if (e0 + 5 < ncnt) jn1 = __ldg(nb + (size_t)(e0 + 5) * ncap);
-            if (e0 + 6 < ncnt) jn2 = __ldg(nb + (size_t)(e0 + 6) * ncap);
-            if (e0 + 7 < ncnt) jn3 = __ldg(nb + (size_t)(e0 + 7) * ncap);
+            for (int k = 0; k < 4; ++k) Qb[k] = ld_state<FUSED>(pos + jb[k]);
+            if (e0 + 4 * LPP < ncnt) jn0 = __ldg(nb + (size_t)(e0 + 4 * LPP) * ncap);
+            if (e0 + 5 * LPP < ncnt) jn1 = __ldg(nb + (size_t)(e0 + 5 * LPP) * ncap);
+            if (e0 + 6 * LPP < ncnt) jn2 = __ldg(nb + (size_t)(e0 + 6 * LPP) * ncap);
+            if (e0 + 7 * LPP < ncnt) jn3 = __ldg(nb + (size_t)(e0 + 7 * LPP) * ncap);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int4 Q = Qb[k];
@@ -706,12 +745,16 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
                 const int dz = P.z - Q.z;
                 const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
                 const int S = P.w + Q.w;
-                if (e0 + k < ncnt && d2 < (long long)S * S) tm |= 1u << (e0 + k);
+                if (e0 + k * LPP < ncnt && d2 < (long long)S * S) tm |= 1u << (e0 + k * LPP);
             }
         }
+        // the group's lanes share their touch masks (ncnt, and so the loop above, is the same
+        // for every lane of a group)
+#pragma unroll
+        for (int o = 1; o < LPP; o <<= 1) tm |= __shfl_xor_sync(gmask, tm, o);
         // entries that left contact (or, for the read-out, every non-contact) get no history
         const unsigned rowmask = ncnt >= 32 ? 0xffffffffu : ((1u << ncnt) - 1u);
-        unsigned clr = (MODE == 1 ? rowmask : hm) & ~tm;
+        unsigned clr = (MODE == 1 ? rowmask : hm) & ~tm & submask;
         while (clr) {
             const int e = __ffs(clr) - 1;
             clr &= clr - 1u;
@@ -721,17 +764,18 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
         }
         // ---- pass 2: the contacts, in row order, next contact's state in flight
         unsigned cm = tm;
-        unsigned rem = tm;
+        unsigned rem = tm & submask;
         int en = 0;
         int4 Qn = P;
         float4 Vn = Vv, Wn = Wv;
         float hxn = 0.f, hyn = 0.f, hzn = 0.f;
         if (rem) {
             en = __ffs(rem) - 1;
-            const int j = __ldg(nb + (size_t)en * ncap);
-            Qn = __ldg(pos + j);
-            Vn = __ldg(vel + j);
-            Wn = __ldg(omg + j);
+            int j = __ldg(nb + (size_t)en * ncap);
+            if (!in_range(d, j, ncap, s, 4)) j = s;
+            Qn = ld_state<FUSED>(pos + j);
+            Vn = ld_state<FUSED>(vel + j);
+            Wn = ld_state<FUSED>(omg + j);
             if ((hm >> en) & 1u) {
                 hxn = h[(size_t)en * ncap];
                 hyn = h[plane + (size_t)en * ncap];
@@ -747,10 +791,11 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
             if (rem) {
                 en = __ffs(rem) - 1;
                 const size_t o1 = (size_t)en * ncap;
-                const int j = __ldg(nb + o1);
-                Qn = __ldg(pos + j);
-                Vn = __ldg(vel + j);
-                Wn = __ldg(omg + j);
+                int j = __ldg(nb + o1);
+                if (!in_range(d, j, ncap, s, 4)) j = s;
+                Qn = ld_state<FUSED>(pos + j);
+                Vn = ld_state<FUSED>(vel + j);
+                Wn = ld_state<FUSED>(omg + j);
                 hxn = hyn = hzn = 0.f;
                 if ((hm >> en) & 1u) {
                     hxn = h[o1];
@@ -782,6 +827,17 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
             ho[plane + (size_t)e * ncap] = xi.y;
             ho[2 * plane + (size_t)e * ncap] = xi.z;
         }
+        // the group's partial sums, combined in a fixed order (every lane ends with the same bits)
+#pragma unroll
+        for (int o = 1; o < LPP; o <<= 1) {
+            F.x += __shfl_xor_sync(gmask, F.x, o);
+            F.y += __shfl_xor_sync(gmask, F.y, o);
+            F.z += __shfl_xor_sync(gmask, F.z, o);
+            Tq.x += __shfl_xor_sync(gmask, Tq.x, o);
+            Tq.y += __shfl_xor_sync(gmask, Tq.y, o);
+            Tq.z += __shfl_xor_sync(gmask, Tq.z, o);
+        }
+        if (LPP > 1 && sub != 0) continue;      // the group's first lane finishes the particle
         if (MODE == 0) d.hmask[lp][s] = cm;
         if (sd.fext) {   // coupling controllers' force, held over the coupling interval
             const float4 fe = d.fext[lp][s];
@@ -884,8 +940,7 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
         }
     }
     if (MODE == 0) {
-        // last instance's maximum, then the last block to finish accumulates the
-        // bound per instance and decides on rebuilds
+        // the last instance's displacement maximum
         float mx = runmax;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -896,6 +951,45 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
             float bm = smax[0];
             for (int i = 1; i < WPB; ++i) bm = fmaxf(bm, smax[i]);
             if (bm > 0.f && kprev >= 0) atomicMax(&d.id[kprev].stepmax, __float_as_uint(bm));
+        }
+    }
+}
+
+// The end of a step for every instance, by the last block to finish it: the displacement
+// bound grows by the step's maximum, the state buffers swap, and an instance whose bound
+// reaches the skin is flagged for a list build (an error while the lists are frozen).
+__device__ __forceinline__ void step_finish_instances(const Dev& d)
+{
+    for (int kk = threadIdx.x; kk < d.B; kk += blockDim.x) {
+        // volatile: the instance's record was last written by another block (in fused steps,
+        // during this launch), so it is read from L2, never from this SM's L1
+        volatile InstD* Dk = d.id + kk;
+        const float sm = __uint_as_float(atomicExch((unsigned*)&Dk->stepmax, 0u));
+        const float disp = Dk->disp + sm;
+        Dk->disp = disp;
+        Dk->cur ^= 1;
+        if (2.0f * disp >= 0.99f * d.ic[kk].skin_f && Dk->flag == 0) {
+            if (d.g->frozen) {
+                atomicOr(&d.g->status, ST_SKIN);
+            } else {
+                Dk->flag = 1;
+                atomicOr(&d.g->any, 1u);
+            }
+        }
+    }
+}
+
+template <int MODE, bool WALLS, int BS = TILE, int LPP = 1>
+__global__ void __launch_bounds__(BS, (step_minb<BS, LPP>())) k_step(Dev d, int prime, cudaGraphConditionalHandle hnext, int use_cond)
+{
+    __shared__ InstC sc;
+    __shared__ InstD sd;
+    __shared__ float smax[BS / 32];
+    __shared__ bool am_last;
+    step_pass<MODE, WALLS, BS, LPP>(d, prime, sc, sd, smax);
+    if (MODE == 0) {
+        // the last block to finish accumulates the bound per instance and decides on rebuilds
+        if (threadIdx.x == 0) {
             __threadfence();
             const unsigned prev = atomicAdd(&d.g->counter, 1u);
             am_last = prev == gridDim.x - 1;
@@ -903,21 +997,7 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
         __syncthreads();
         if (am_last) {
             __threadfence();
-            for (int kk = threadIdx.x; kk < d.B; kk += blockDim.x) {
-                InstD* Dk = d.id + kk;
-                const float sm = __uint_as_float(atomicExch(&Dk->stepmax, 0u));
-                const float disp = Dk->disp + sm;
-                Dk->disp = disp;
-                Dk->cur ^= 1;
-                if (2.0f * disp >= 0.99f * d.ic[kk].skin_f && Dk->flag == 0) {
-                    if (d.g->frozen) {
-                        atomicOr(&d.g->status, ST_SKIN);
-                    } else {
-                        Dk->flag = 1;
-                        atomicOr(&d.g->any, 1u);
-                    }
-                }
-            }
+            step_finish_instances(d);
             __syncthreads();
             if (threadIdx.x == 0) {
                 d.g->counter = 0u;
@@ -925,6 +1005,86 @@ __global__ void __launch_bounds__(BS, step_minb<BS>()) k_step(Dev d, int prime, 
             }
         }
     }
+}
+
+// Several steps in one cooperative launch (every block resident at once; a block walks its
+// range of tiles each step, one tile per block when they all fit), for systems too small to hide
+// the per-step launch and graph-node latency.
+// Each step is exactly the step kernel's; between steps a grid barrier (the last block to
+// arrive ends the step for every instance, as the step kernel's last block does, then
+// releases the others; every wait gives up after a bounded number of polls and reports
+// DEM_ERR_TIMEOUT).  Runs the steps still to do in this graph launch (g->remain) and stops
+// early when an instance needs a list build; the last block then sets the loop's conditions:
+// h_rb (build the lists before going on) and h_loop (steps remain).
+constexpr unsigned BAR_POLLS = 1u << 22;     // polls of about 0.1-1 us before a wait gives up
+
+template <bool WALLS>
+__global__ void __launch_bounds__(TILE, 5) k_steps(Dev d, cudaGraphConditionalHandle h_rb,
+                                                                        cudaGraphConditionalHandle h_loop)
+{
+    __shared__ InstC sc;
+    __shared__ InstD sd;
+    __shared__ float smax[TILE / 32];
+    __shared__ bool am_last, quit;
+    // stop unless the block that ends the last step says otherwise (set before any block can
+    // reach the final barrier, so the later setting wins)
+    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_loop, 0u);
+    const long long todo = *(volatile long long*)&d.g->remain;
+    long long done = 0;
+    bool final_last = false;
+    while (done < todo) {
+        step_pass<0, WALLS, TILE, 1, true>(d, 0, sc, sd, smax);
+        if (threadIdx.x == 0) {
+            const unsigned gen = *(volatile unsigned*)&d.g->bar_gen;
+            __threadfence();
+            const unsigned prev = atomicAdd(&d.g->counter, 1u);
+            am_last = prev == gridDim.x - 1;
+            if (!am_last) {
+                unsigned polls = 0u;
+                while (*(volatile unsigned*)&d.g->bar_gen == gen) {
+                    if (++polls > BAR_POLLS) {
+                        atomicOr(&d.g->status, ST_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        const bool last = am_last;
+        if (last) {
+            __threadfence();
+            step_finish_instances(d);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                d.g->counter = 0u;
+                __threadfence();
+                atomicAdd(&d.g->bar_gen, 1u);      // release
+            }
+        }
+        ++done;
+        final_last = last;
+        if (threadIdx.x == 0)
+            quit = *(volatile unsigned*)&d.g->any != 0u || (*(volatile unsigned*)&d.g->status & ST_TIMEOUT) != 0u;
+        __syncthreads();
+        if (quit) break;
+    }
+    if (final_last && threadIdx.x == 0) {
+        const long long rem = todo - done;
+        d.g->remain = rem;
+        const bool timeout = (*(volatile unsigned*)&d.g->status & ST_TIMEOUT) != 0u;
+        cudaGraphSetConditional(h_rb, *(volatile unsigned*)&d.g->any ? 1u : 0u);
+        cudaGraphSetConditional(h_loop, rem > 0 && !timeout ? 1u : 0u);
+    }
+}
+
+// the start of a fused graph launch: S steps to do, a list build first if one is pending
+__global__ void k_steps_init(Dev d, long long S, cudaGraphConditionalHandle h_rb, cudaGraphConditionalHandle h_loop)
+{
+    d.g->remain = S;
+    cudaGraphSetConditional(h_rb, d.g->any ? 1u : 0u);
+    cudaGraphSetConditional(h_loop, S > 0 ? 1u : 0u);
 }
 
 __global__ void k_set_cond(Dev d, cudaGraphConditionalHandle h)
@@ -1765,6 +1925,16 @@ dem_status check_status(dem_ctx* ctx)
     if (ctx->status & ST_TIMEOUT) return fail(ctx, DEM_ERR_TIMEOUT, "a bounded device wait gave up");
     if (ctx->status & ST_TRUNC) return fail(ctx, DEM_ERR_CAPACITY, "more contacts than the output width");
     if (ctx->status & ST_INSERT) return fail(ctx, DEM_ERR_CAPACITY, "inserted particles exceed the fine level's capacity");
+    if (ctx->status & ST_BOUNDS) {
+        // where the check fired (read synchronously: an error path)
+        Glob gl{};
+        cudaStreamSynchronize(ctx->stream);
+        cudaMemcpy(&gl, ctx->dev.g, sizeof(Glob), cudaMemcpyDeviceToHost);
+        return fail(ctx, DEM_ERR_BOUNDS,
+                    "an index out of range (bounds-checked build): check " + std::to_string(gl.err_site) + ", slot " +
+                        std::to_string(gl.err_slot) + ", index " + std::to_string(gl.err_val) + " (capacity " +
+                        std::to_string(ctx->ncap) + ")");
+    }
     if (ctx->status & ST_SKIN)
         return fail(ctx, DEM_ERR_CAPACITY,
                     "a particle moved more than half the skin while the lists were frozen for a differentiable "
@@ -1829,6 +1999,12 @@ void destroy_graph(dem_ctx* ctx)
 // the step kernel (MODE 0) at the context's block size, and its persistent grid
 void* step_func(const dem_ctx* ctx)
 {
+    switch (ctx->step_lanes) {
+    case 2: return ctx->walls ? (void*)k_step<0, true, 128, 2> : (void*)k_step<0, false, 128, 2>;
+    case 4: return ctx->walls ? (void*)k_step<0, true, 128, 4> : (void*)k_step<0, false, 128, 4>;
+    case 8: return ctx->walls ? (void*)k_step<0, true, 128, 8> : (void*)k_step<0, false, 128, 8>;
+    default: break;
+    }
     switch (ctx->step_bs) {
     case 64: return ctx->walls ? (void*)k_step<0, true, 64> : (void*)k_step<0, false, 64>;
     case 256: return ctx->walls ? (void*)k_step<0, true, 256> : (void*)k_step<0, false, 256>;
@@ -1838,6 +2014,7 @@ void* step_func(const dem_ctx* ctx)
 
 int step_grid(const dem_ctx* ctx)
 {
+    if (ctx->step_lanes > 1) return ctx->grid_lanes[ctx->step_lanes == 2 ? 0 : ctx->step_lanes == 4 ? 1 : 2];
     return ctx->grid_bs[ctx->step_bs == 64 ? 0 : ctx->step_bs == 256 ? 2 : 1];
 }
 
@@ -1852,6 +2029,66 @@ dem_status launch_step(dem_ctx* ctx, int prime)
 }
 
 constexpr int EV_EVERY = 5;    // step kernels per timed one in a graph
+
+// A graph of S steps run by fused launches: init (S steps to do, pending list build) ->
+// while (steps remain) { if (list build needed) rebuild chain; k_steps }, with CUDA events
+// around the loop.
+dem_status build_fused_graph(dem_ctx* ctx, cudaGraph_t g, int S)
+{
+    cudaGraphConditionalHandle h_loop, h_rb;
+    CU(cudaGraphConditionalHandleCreate(&h_loop, g, 0, 0));
+    CU(cudaGraphConditionalHandleCreate(&h_rb, g, 0, 0));
+    Dev dv = ctx->dev;
+    long long SS = S;
+    cudaGraphNode_t init;
+    {
+        void* args[] = {&dv, &SS, &h_rb, &h_loop};
+        cudaKernelNodeParams kp{};
+        kp.func = (void*)k_steps_init;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = args;
+        CU(cudaGraphAddKernelNode(&init, g, nullptr, 0, &kp));
+    }
+    ctx->ev0.resize(1);
+    ctx->ev1.resize(1);
+    CU(cudaEventCreate(&ctx->ev0[0]));
+    CU(cudaEventCreate(&ctx->ev1[0]));
+    cudaGraphNode_t e0, e1, loop;
+    CU(cudaGraphAddEventRecordNode(&e0, g, &init, 1, ctx->ev0[0]));
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    CU(cudaGraphAddNode(&loop, g, &e0, nullptr, 1, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_rb;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t ifn, child, kn;
+    CU(cudaGraphAddNode(&ifn, body, nullptr, nullptr, 0, &ip));
+    CU(cudaGraphAddChildGraphNode(&child, ip.conditional.phGraph_out[0], nullptr, 0, ctx->rb_graph));
+    {
+        void* args[] = {&dv, &h_rb, &h_loop};
+        cudaKernelNodeParams kp{};
+        kp.func = ctx->walls ? (void*)k_steps<true> : (void*)k_steps<false>;
+        kp.gridDim = dim3(std::min(ctx->ntiles, ctx->grid_fused));   // all resident: a cooperative launch
+        kp.blockDim = dim3(TILE);
+        kp.kernelParams = args;
+        CU(cudaGraphAddKernelNode(&kn, body, &ifn, 1, &kp));
+        cudaLaunchAttributeValue coop{};
+        coop.cooperative = 1;
+        CU(cudaGraphKernelNodeSetAttribute(kn, cudaLaunchAttributeCooperative, &coop));
+    }
+    CU(cudaGraphAddEventRecordNode(&e1, g, &loop, 1, ctx->ev1[0]));
+    CU(cudaGraphInstantiate(&ctx->gexec, g, 0));
+    ctx->graph_steps = S;
+    ctx->graph_fused = true;
+    return DEM_OK;
+}
 
 dem_status build_graph(dem_ctx* ctx, int S)
 {
@@ -1871,6 +2108,22 @@ dem_status build_graph(dem_ctx* ctx, int S)
     cudaGraph_t g;
     CU(cudaGraphCreate(&g, 0));
     ctx->graph = g;
+    ctx->graph_fused = false;
+    {
+        // fused steps: one cooperative launch runs the steps between list builds; chosen by
+        // default when every tile's block fits on the GPU at once
+        int nsm = 0, occ = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ctx->walls ? (void*)k_steps<true> : (void*)k_steps<false>,
+                                                      TILE, 0);
+        cudaGetLastError();
+        ctx->grid_fused = nsm * occ;
+        const bool can = ctx->step_lanes == 1 && ctx->step_bs == TILE && ctx->grid_fused > 0;
+        if (ctx->graph_mode == 2 && !can)
+            return fail(ctx, DEM_ERR_STATE, "fused steps need one lane per particle and 128-thread blocks");
+        if (ctx->graph_mode == 2 || (ctx->graph_mode == 0 && can && ctx->ntiles <= ctx->grid_fused))
+            return build_fused_graph(ctx, g, S);
+    }
     std::vector<cudaGraphConditionalHandle> h(S);
     for (int i = 0; i < S; ++i) CU(cudaGraphConditionalHandleCreate(&h[i], g, 0, 0));
     Dev dv = ctx->dev;
@@ -2118,6 +2371,13 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
             const int units[3] = {ctx->ntiles * 2, ctx->ntiles, ctx->ntiles / 2};
             for (int i = 0; i < 3; ++i)
                 ctx->grid_bs[i] = std::max(1, std::min(units[i], std::max(1, nsm) * std::max(1, bx[i])));
+            // several lanes per particle (128 threads): LPP times the units of one lane
+            int bl[3] = {0, 0, 0};
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl[0], k_step<0, false, 128, 2>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl[1], k_step<0, false, 128, 4>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl[2], k_step<0, false, 128, 8>, 128, 0);
+            for (int i = 0; i < 3; ++i)
+                ctx->grid_lanes[i] = std::max(1, std::min(ctx->ntiles << (i + 1), std::max(1, nsm) * std::max(1, bl[i])));
         }
         ctx->grid1 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b1)));
         ctx->grid_rb = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * 8));
@@ -2161,6 +2421,7 @@ static int field_width(int f)
 
 dem_status dem_write(dem_ctx* ctx, int32_t field, const void* src, int64_t n)
 {
+    NvtxRange nvtx_range("dem_write");
     if (!ctx) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     const int w = field_width(field);
@@ -2194,6 +2455,7 @@ dem_status dem_write(dem_ctx* ctx, int32_t field, const void* src, int64_t n)
 
 dem_status dem_read(dem_ctx* ctx, int32_t field, void* dst, int64_t n)
 {
+    NvtxRange nvtx_range("dem_read");
     if (!ctx) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     const int w = field_width(field);
@@ -2250,6 +2512,7 @@ dem_status dem_write_contacts(dem_ctx* ctx, const int32_t* partner, const double
 
 dem_status dem_step(dem_ctx* ctx, int64_t nsteps)
 {
+    NvtxRange nvtx_range("dem_step");
     if (!ctx || nsteps < 0) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     if (!ctx->have_state) return fail(ctx, DEM_ERR_STATE, "write the state before stepping");
@@ -2304,6 +2567,9 @@ dem_status dem_stats(dem_ctx* ctx, dem_stats_t* out)
     if (ctx->status) return check_status(ctx);
     memset(out, 0, sizeof(*out));
     out->steps = ctx->steps;
+    out->step_threads = ctx->step_bs;
+    out->step_lanes = ctx->step_lanes;
+    out->graph_fused = ctx->graph_fused ? 1 : 0;
     if (dem_status st = refresh_count(ctx)) return st;
     out->particles = total_count(ctx);
     if (!ctx->have_state) return DEM_OK;
@@ -2334,7 +2600,58 @@ dem_status dem_set_step_block(dem_ctx* ctx, int32_t threads)
     if (!ctx) return DEM_ERR_ARG;
     if (threads != 64 && threads != 128 && threads != 256)
         return fail(ctx, DEM_ERR_ARG, "step block must be 64, 128 or 256 threads");
+    if (threads != 128 && ctx->step_lanes > 1)
+        return fail(ctx, DEM_ERR_STATE, "several lanes per particle run at 128 threads per block");
     ctx->step_bs = threads;
+    return ctx->graph_steps > 0 ? build_graph(ctx, ctx->graph_steps) : DEM_OK;
+}
+
+dem_status dem_set_graph_mode(dem_ctx* ctx, int32_t mode)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (mode < 0 || mode > 2) return fail(ctx, DEM_ERR_ARG, "graph mode must be 0 (by size), 1 (a kernel per step) or 2 (fused)");
+    const int old = ctx->graph_mode;
+    ctx->graph_mode = mode;
+    if (ctx->graph_steps <= 0) return DEM_OK;
+    dem_status st = build_graph(ctx, ctx->graph_steps);
+    if (st) {
+        ctx->graph_mode = old;                 // keep the previous graph
+        const std::string msg = ctx->err;
+        dem_status st2 = build_graph(ctx, ctx->graph_steps);
+        if (st2) return st2;
+        return fail(ctx, st, msg);
+    }
+    return DEM_OK;
+}
+
+dem_status dem_set_step_lanes(dem_ctx* ctx, int32_t lanes)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
+        return fail(ctx, DEM_ERR_ARG, "lanes per particle must be 0 (by size), 1, 2, 4 or 8");
+    if (lanes == 0) {
+        // by size: one lane while the rows fill at least half of the resident threads of the
+        // one-lane kernel, else the most lanes whose threads are all resident at once
+        int nsm = 0, b1 = 0, bl = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_step<0, false, 128>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_step<0, false, 128, 2>, 128, 0);
+        cudaGetLastError();
+        const long long rows = (long long)ctx->ntiles * TILE;
+        const long long r1 = (long long)std::max(1, nsm) * std::max(1, b1) * 128;
+        const long long rl = (long long)std::max(1, nsm) * std::max(1, bl) * 128;
+        lanes = 1;
+        if (2 * rows < r1)
+            for (int l = 8; l >= 2; l >>= 1)
+                if ((long long)l * rows <= rl) {
+                    lanes = l;
+                    break;
+                }
+        if (ctx->step_bs != 128) lanes = 1;
+    }
+    if (lanes > 1 && ctx->step_bs != 128)
+        return fail(ctx, DEM_ERR_STATE, "several lanes per particle run at 128 threads per block");
+    ctx->step_lanes = lanes;
     return ctx->graph_steps > 0 ? build_graph(ctx, ctx->graph_steps) : DEM_OK;
 }
 
@@ -2350,7 +2667,7 @@ dem_status dem_graph_step_kernel_ms(dem_ctx* ctx, double* total_ms, int32_t* cou
         t += ms;
     }
     *total_ms = t;
-    *count = (int32_t)ctx->ev0.size();
+    *count = ctx->graph_fused ? (int32_t)ctx->graph_steps : (int32_t)ctx->ev0.size();
     return DEM_OK;
 }
 
@@ -2567,6 +2884,7 @@ dem_status dem_rollout_workspace(dem_ctx* ctx, int64_t nsteps, int64_t checkpoin
 
 dem_status dem_rollout_forward(dem_ctx* ctx, int64_t nsteps, int64_t checkpoint_every, void* ws, int64_t ws_bytes)
 {
+    NvtxRange nvtx_range("dem_rollout_forward");
     if (!ctx || nsteps < 1 || checkpoint_every < 1 || !ws) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     if (!ctx->have_state) return fail(ctx, DEM_ERR_STATE, "write the state before a rollout");
@@ -2616,6 +2934,7 @@ dem_status dem_observables(dem_ctx* ctx, const double* axis, double* out)
 
 dem_status dem_rollout_adjoint(dem_ctx* ctx, const double* weights, const double* axis, double* grad)
 {
+    NvtxRange nvtx_range("dem_rollout_adjoint");
     if (!ctx || !weights || !axis || !grad) return DEM_ERR_ARG;
     if (ctx->status) return check_status(ctx);
     Rollout& ro = ctx->ro;

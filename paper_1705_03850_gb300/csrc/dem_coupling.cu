@@ -1075,6 +1075,7 @@ dem_status dem_coupler_create(dem_ctx* coarse, dem_ctx* fine, const dem_coupling
 
 dem_status dem_couple(dem_coupler* cp)
 {
+    NvtxRange nvtx_range("dem_couple");
     if (!cp) return DEM_ERR_ARG;
     dem_ctx* ctx = cp->f;
     dem_ctx* coarse = cp->c;

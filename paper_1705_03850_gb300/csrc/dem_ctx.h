@@ -1,9 +1,18 @@
 // Host-side context of the library (shared by its translation units).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
+
+// an NVTX range over a C-ABI call (seen by profilers; no cost without one attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #include "dem.h"
 #include "dem_internal.cuh"
@@ -18,7 +27,9 @@ struct dem_ctx {
     int ncap = 0, ntiles = 0;
     int grid0 = 1, grid1 = 1;         // persistent grids of the step / evaluation kernels
     int step_bs = 128;                // threads per block of the step kernel (64, 128 or 256)
+    int step_lanes = 1;               // lanes per particle of the step kernel (1, 2, 4 or 8; >1 at 128 threads)
     int grid_bs[3] = {1, 1, 1};       // persistent step grids for 64, 128 and 256 threads per block
+    int grid_lanes[3] = {1, 1, 1};    // persistent step grids for 2, 4 and 8 lanes per particle
     int grid_rb = 1;                  // persistent grid of the per-slot rebuild kernels
     int grid_build = 1;               // one wave of the list build (occupancy-sized)
     unsigned ncodes = 0, nparts = 0;
@@ -35,6 +46,9 @@ struct dem_ctx {
     std::string err;
     // graphs
     int graph_steps = 0;
+    int graph_mode = 0;               // 0: fused steps when the context fits, 1: a kernel per step, 2: fused
+    bool graph_fused = false;         // the current graph runs its steps in fused cooperative launches
+    int grid_fused = 0;               // co-resident blocks of the fused step kernel (0: unknown)
     cudaGraph_t rb_graph = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;

@@ -51,6 +51,16 @@ constexpr unsigned ST_TIMEOUT = 8u;
 constexpr unsigned ST_TRUNC = 16u;
 constexpr unsigned ST_SKIN = 32u;     // displacement exceeded the skin while lists were frozen
 constexpr unsigned ST_INSERT = 64u;   // coupling insertions beyond the fine level's capacity (not appended)
+constexpr unsigned ST_BOUNDS = 128u;  // DEM_CHECKS builds: an index out of range (the access skipped)
+
+// Bounds-checked builds (-DDEM_CHECKS=1): the step kernel's gathered particle indices (touch and
+// contact passes) and the list build's cell codes and candidate ranges are tested against the
+// capacity before use; a violation sets ST_BOUNDS and the access is replaced by a harmless one.
+// (The coupling kernels walk slots directly and clamp every cell index they compute.)  Off by
+// default: the checks cost issue slots.
+#ifndef DEM_CHECKS
+#define DEM_CHECKS 0
+#endif
 
 // constant description of one instance (host-computed at create)
 struct InstC {
@@ -119,6 +129,12 @@ struct Glob {
     unsigned long long sum_contacts;
     unsigned long long sum_wall;
     long long err_slot;
+    long long err_val;         // DEM_CHECKS builds: the index found out of range, and where
+    int err_site;              // (1 cell code, 2 cell range of the list build; 3 touch pass,
+    int err_pad;               //  4 contact pass of the step kernel)
+    unsigned bar_gen;          // fused steps: grid-barrier generation (bumped by each release)
+    unsigned bar_pad;
+    long long remain;          // fused steps: steps still to do in the current graph launch
 };
 
 // kernel-visible pointers of a context
@@ -167,6 +183,18 @@ struct Dev {
     unsigned ncodes;
     unsigned nparts;
 };
+
+// DEM_CHECKS: true if i lies in [0, n); otherwise records ST_BOUNDS, the slot s, the index and
+// the check's site
+__device__ __forceinline__ bool in_range(const Dev& d, long long i, long long n, int s, int site)
+{
+    if (!DEM_CHECKS || (i >= 0 && i < n)) return true;
+    atomicOr(&d.g->status, ST_BOUNDS);
+    d.g->err_slot = s;
+    d.g->err_val = i;
+    d.g->err_site = site;
+    return false;
+}
 
 // host-side description of an instance's frame (origin, quantum, density)
 struct HostInstLo {

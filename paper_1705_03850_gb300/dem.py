@@ -14,13 +14,13 @@ import sys
 
 import numpy as np
 
-from .build import LIB
+from .build import LIB, LIB_CHECKED
 
 # field ids (dem_field)
 POS, VEL, OMEGA, RADIUS, MASS, FORCE, TORQUE, WALL_XI, NBR_COUNT, FEXT = range(10)
 _WIDTH = {POS: 3, VEL: 3, OMEGA: 3, RADIUS: 1, MASS: 1, FORCE: 3, TORQUE: 3, WALL_XI: 3, NBR_COUNT: 1, FEXT: 3}
 STATUS = {0: "DEM_OK", 1: "DEM_ERR_ARG", 2: "DEM_ERR_CAPACITY", 3: "DEM_ERR_CUDA", 4: "DEM_ERR_NONFINITE",
-          5: "DEM_ERR_ESCAPED", 6: "DEM_ERR_TIMEOUT", 7: "DEM_ERR_STATE"}
+          5: "DEM_ERR_ESCAPED", 6: "DEM_ERR_TIMEOUT", 7: "DEM_ERR_STATE", 8: "DEM_ERR_BOUNDS"}
 
 
 class DemError(RuntimeError):
@@ -52,7 +52,9 @@ class InstanceInfo(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("list_entries", ctypes.c_int64),
-                ("contacts", ctypes.c_int64), ("particles", ctypes.c_int64), ("wall_contacts", ctypes.c_int64)]
+                ("contacts", ctypes.c_int64), ("particles", ctypes.c_int64), ("wall_contacts", ctypes.c_int64),
+                ("step_threads", ctypes.c_int32), ("step_lanes", ctypes.c_int32), ("graph_fused", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class CouplingSpec(ctypes.Structure):
@@ -73,14 +75,22 @@ CPL_SURFACE_MASS, CPL_SURFACE_CARRY, CPL_SURFACE_INSERTED, CPL_SURFACE_VEL, CPL_
 _lib = None
 
 
+def lib_path() -> str:
+    """libcgdem.so, or with CGDEM_CHECKED=1 in the environment its bounds-checked build (the
+    step kernel's gathered indices and the list build's cell codes tested in the kernels; an
+    index out of range is reported as DEM_ERR_BOUNDS)."""
+    return LIB_CHECKED if os.environ.get("CGDEM_CHECKED", "0") not in ("", "0") else LIB
+
+
 def lib():
-    """Load libcgdem.so (raises if it was not built)."""
+    """Load the CUDA library (raises if it was not built)."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB):
-        raise ImportError(f"CUDA library not built: {LIB} (run __graft_entry__.build())")
-    L = ctypes.CDLL(LIB)
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
     vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
     sig = {
         "dem_query_workspace": [ctypes.POINTER(Config), ctypes.POINTER(i64)],
@@ -96,6 +106,8 @@ def lib():
         "dem_stats": [vp, ctypes.POINTER(Stats)],
         "dem_set_graph": [vp, i32],
         "dem_set_step_block": [vp, i32],
+        "dem_set_step_lanes": [vp, i32],
+        "dem_set_graph_mode": [vp, i32],
         "dem_graph_step_kernel_ms": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)],
         "dem_rollout_workspace": [vp, i64, i64, ctypes.POINTER(i64)],
         "dem_rollout_forward": [vp, i64, i64, vp, i64],
@@ -129,7 +141,7 @@ def lib():
 def exported_symbols():
     return ["dem_query_workspace", "dem_create", "dem_destroy", "dem_write", "dem_read", "dem_read_contacts",
             "dem_write_contacts", "dem_step", "dem_sync_status", "dem_instance_info_get", "dem_stats",
-            "dem_set_graph", "dem_set_step_block", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
+            "dem_set_graph", "dem_set_step_block", "dem_set_step_lanes", "dem_set_graph_mode", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
             "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material",
             "dem_coupler_workspace", "dem_coupler_create", "dem_couple", "dem_coupler_read", "dem_coupler_destroy",
             "dem_counts", "dem_clear_external_force", "dem_grid_fields", "dem_set_walls", "dem_wall_removed",
@@ -289,6 +301,19 @@ class DEM:
         self._check(self.L.dem_set_step_block(self.h, int(threads)), "set step block")
         return self
 
+    def set_step_lanes(self, lanes):
+        """Lanes per particle of the step kernel: 1 (default), 2, 4 or 8 (more than one at the
+        128-thread block), or 0 to choose by size; for systems too small to fill the GPU with one
+        thread per particle."""
+        self._check(self.L.dem_set_step_lanes(self.h, int(lanes)), "set step lanes")
+        return self
+
+    def set_graph_mode(self, mode):
+        """How a captured graph runs its steps: 0 fused when the context fits (default), 1 one
+        kernel per step, 2 fused (one cooperative launch between list builds)."""
+        self._check(self.L.dem_set_graph_mode(self.h, int(mode)), "set graph mode")
+        return self
+
     def graph_step_kernel_ms(self):
         """(sum of step-kernel CUDA-event times in the last graph launch [ms], number of step kernels)."""
         t, c = ctypes.c_double(), ctypes.c_int32()
@@ -388,7 +413,8 @@ class DEM:
         st = Stats()
         self._check(self.L.dem_stats(self.h, ctypes.byref(st)), "stats")
         return dict(steps=st.steps, rebuilds=st.rebuilds, list_entries=st.list_entries, contacts=st.contacts,
-                    particles=st.particles, wall_contacts=st.wall_contacts)
+                    particles=st.particles, wall_contacts=st.wall_contacts, step_threads=st.step_threads,
+                    step_lanes=st.step_lanes, graph_fused=st.graph_fused)
 
 
 def neighbor_counts_noalloc(x, r, lo, hi, periodic, skin, r_max, out=None, stream=None):

@@ -21,14 +21,35 @@ def _declared():
 
 @pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
                     reason="needs nvcc")
-def test_library_builds_loads_and_exports_every_declared_symbol():
+@pytest.mark.parametrize("checks", [False, True])
+def test_library_builds_loads_and_exports_every_declared_symbol(checks):
+    # the plain library and its bounds-checked build export the same entry points
     from paper_1705_03850_gb300 import build
-    path = build.build()
+    path = build.build(checks=checks)
+    assert path == (build.LIB_CHECKED if checks else build.LIB)
     lib = ctypes.CDLL(path)
     declared = _declared()
     assert "dem_create" in declared and "dem_step" in declared
     missing = [n for n in sorted(declared) if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_checked_library_is_selected_by_the_environment(monkeypatch):
+    from paper_1705_03850_gb300 import build, dem
+    monkeypatch.setenv("CGDEM_CHECKED", "1")
+    assert dem.lib_path() == build.LIB_CHECKED
+    monkeypatch.setenv("CGDEM_CHECKED", "0")
+    assert dem.lib_path() == build.LIB
+    monkeypatch.delenv("CGDEM_CHECKED")
+    assert dem.lib_path() == build.LIB
+
+
+def test_every_status_code_has_a_name():
+    # each dem_status enumerator in the header is named in the binding's table
+    from paper_1705_03850_gb300 import dem
+    src = open(os.path.join(ROOT, "include", "dem.h")).read()
+    codes = {int(v): k for k, v in re.findall(r"\b(DEM_(?:OK|ERR_\w+))\s*=\s*(\d+)", src)}
+    assert codes and codes == dem.STATUS
 
 
 def test_binding_lists_every_declared_symbol():

@@ -133,13 +133,18 @@ def test_rollout_positions(steps):
     assert inband <= 0.01 * len(r)
 
 
-def test_graph_capture_matches_direct_launches_bitwise():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_graph_capture_matches_direct_launches_bitwise(mode):
+    # graphs of one step kernel per step (mode 1) and of fused steps (mode 2: one cooperative
+    # launch between list builds, a grid barrier between steps) against direct launches
     wl = workloads.dense_block(10, 10, 6, seed=14, vel=0.5)
     a = dem.from_workload(wl)
     b = dem.from_workload(wl)
     a.step(1)
     b.step(1)
+    b.set_graph_mode(mode)
     b.set_graph(25)
+    assert b.stats()["graph_fused"] == (mode == 2)
     a.step(300).sync()
     b.step(300).sync()
     assert a.stats()["rebuilds"] > 2

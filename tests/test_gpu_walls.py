@@ -18,8 +18,9 @@ pytestmark = pytest.mark.gpu
 FORCE_REL = 1e-5
 
 
-def _sim(wl, walls, z_remove=-math.inf, graph=0):
+def _sim(wl, walls, z_remove=-math.inf, graph=0, lanes=1):
     sim = dem.from_workload(wl)
+    sim.set_step_lanes(lanes)
     sim.set_walls(0, (0.0, 0.0), walls, z_remove)
     if graph:
         sim.set_graph(graph)
@@ -53,14 +54,18 @@ def test_wall_forces_at_identical_state(seed, closed):
     assert st["wall_contacts"] == nw
 
 
-def test_filling_of_a_small_vessel_matches_oracle():
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_filling_of_a_small_vessel_matches_oracle(lanes):
     # a lattice thrown down (1 m/s) into the closed vessel: exact positions over the first 300
     # steps (the first impacts on the cone), then mean height and kinetic energy at 600 steps,
-    # once the impacts on the cone and on the orifice disk have spread through the packing
+    # once the impacts on the cone and on the orifice disk have spread through the packing;
+    # with one thread per particle and with four lanes per particle (the multi-lane step kernel
+    # with walls)
     wl = workloads.small_vessel(seed=23)
     wl.v[:, 2] = workloads.f32(wl.v[:, 2] - 1.0)
     walls = wl.meta["walls"]
-    sim = _sim(wl, walls)
+    sim = _sim(wl, walls, lanes=lanes)
+    assert sim.stats()["step_lanes"] == lanes
     o = oracle_sim(wl, walls)
     sim.step(300).sync()
     o.run(300)
@@ -97,12 +102,13 @@ def test_single_sphere_against_the_wall_matches_oracle(case):
     assert (hist[1] <= -2).any()                            # still in contact with the wall
 
 
-def test_graph_and_direct_stepping_agree_with_walls_and_removal():
+@pytest.mark.parametrize("lanes", [1, 8])
+def test_graph_and_direct_stepping_agree_with_walls_and_removal(lanes):
     wl = workloads.small_vessel(seed=24)
     walls = wl.meta["walls"][1:]                             # orifice open
     z_rem = wl.meta["z_o"] - 0.004
-    a = _sim(wl, walls, z_rem, graph=25)
-    b = _sim(wl, walls, z_rem)
+    a = _sim(wl, walls, z_rem, graph=25, lanes=lanes)
+    b = _sim(wl, walls, z_rem, lanes=lanes)
     a.step(4000).sync()
     b.step(4000).sync()
     xa, xb = a.read(dem.POS), b.read(dem.POS)

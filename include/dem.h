@@ -219,8 +219,8 @@ dem_status dem_set_step_lanes(dem_ctx *ctx, int32_t lanes);
  * step computes exactly what the per-step kernel computes (the same bits); fused steps save
  * the per-step launch and node latency of systems too small to fill the GPU.  Needs one lane
  * per particle and 128-thread blocks (DEM_ERR_STATE otherwise; the previous graph is kept).
- * 0 (the default): fused when those hold and every 128-slot tile's block is resident at once,
- * else one launch per step.  A barrier wait that does not end within about a second reports
+ * 0 (the default): fused when those hold and a block for every 128-slot tile holding live
+ * particles is resident at once, else one launch per step.  A barrier wait that does not end within about a second reports
  * DEM_ERR_TIMEOUT.  With fused steps dem_graph_step_kernel_ms times the whole graph launch
  * (list builds included) and counts its steps.  Not in the paper: a scheduling choice of this
  * implementation. */

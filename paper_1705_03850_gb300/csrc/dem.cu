@@ -479,7 +479,24 @@ __global__ void k_rb_finish(Dev d)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) d.g->any = 0u;
+    // the tiles the step walks: per instance the pairs of tiles that hold its live slots
+    unsigned base = 0u;
+    for (int k0 = 0; k0 < d.B; k0 += blockDim.x) {
+        const int k = k0 + (int)threadIdx.x;
+        unsigned lt = 0u;
+        if (k < d.B) lt = 2u * (unsigned)((d.id[k].n + 2 * TILE - 1) / (2 * TILE));
+        unsigned tot;
+        const unsigned off = base + block_exclusive_scan(lt, &tot);
+        if (k < d.B) {
+            const int t0 = d.ic[k].slot0 / TILE;
+            for (unsigned i = 0; i < lt; ++i) d.live_tiles[off + i] = t0 + (int)i;
+        }
+        base += tot;
+    }
+    if (threadIdx.x == 0) {
+        d.g->nlive = (int)base;
+        d.g->any = 0u;
+    }
 }
 
 // ============================================================= contact law
@@ -519,27 +536,41 @@ __device__ __forceinline__ unsigned mix32(unsigned x)
     return x;
 }
 
+// |(x, y)| from x^2 + y^2 >= 0 in double: a float root refined by one Newton step (the float
+// root is within 1e-7 of the result, so the step leaves an error of order 1e-14 relative), in
+// place of a double square root, which is slow on this GPU
+__device__ __forceinline__ double root_refined(double s2)
+{
+    if (!(s2 > 0.0)) return 0.0;
+    const float rf = sqrtf((float)s2);
+    const double rd = (double)rf;
+    return rd + (double)((float)fma(-rd, rd, s2) * (0.5f / rf));
+}
+
 // Axisymmetric walls: the surface of revolution of the polyline (rho_i, z_i) about a vertical
 // axis, one wall per segment with its end points included (a free rim is an edge contact).
 // Each touching segment is a particle-wall contact of Eqs. 3-6 at rest, with the wall
 // friction; n runs from the nearest point of the segment, in the particle's azimuthal
 // half-plane, to the centre.  Distances are taken in double from the exact integer position
 // (the overlap is a small difference of two lengths), for the segments a float pre-test
-// leaves within a 1/64 radius of contact.  The tangential overlaps of up to two segment
-// contacts are kept per particle, tagged with the segment; MODE 0 stores them.
+// leaves within a 1/64 radius of contact: along the segment's unit normal when the closest
+// point is inside the segment, else to the end point, with no double division or square root.
+// The tangential overlaps of up to two segment contacts are kept per particle, tagged with the
+// segment; MODE 0 stores them.
 template <int MODE>
-__device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int s, int lp, int4 P, float r, float m,
-                                             V3 vme, V3 wme, float dt_hist, V3& F, V3& Tq)
+__device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int kinst, int s, int lp, int4 P, float r,
+                                             float m, V3 vme, V3 wme, float dt_hist, V3& F, V3& Tq)
 {
     const float exf = (float)(P.x - c.waxi) - c.waxf, eyf = (float)(P.y - c.wayi) - c.wayf, zf = (float)P.z;
     const float rhof = sqrtf(exf * exf + eyf * eyf);
     const float tol = 1e-6f * (rhof + fabsf(zf) + c.wmag) + 4.f;
     const float lim = (float)P.w * (1.f + 1.f / 64.f) + tol;
+    const WallGeo& G = d.wgeo[kinst];
     unsigned nearm = 0u;
     for (int k = 0; k + 1 < c.nwp; ++k) {
         const float r0 = c.wpf[2 * k], z0 = c.wpf[2 * k + 1];
         const float dr = c.wpf[2 * k + 2] - r0, dz = c.wpf[2 * k + 3] - z0;
-        const float t = fminf(fmaxf(((rhof - r0) * dr + (zf - z0) * dz) / (dr * dr + dz * dz), 0.f), 1.f);
+        const float t = fminf(fmaxf(((rhof - r0) * dr + (zf - z0) * dz) * G.inv2[k], 0.f), 1.f);
         const float a = rhof - (r0 + t * dr), b = zf - (z0 + t * dz);
         if (a * a + b * b < lim * lim) nearm |= 1u << k;
     }
@@ -549,7 +580,7 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int s
     if (nearm) {
         const float4 h0 = ws[s], h1 = ws[ncap + s];
         const double ex = (double)P.x - c.wax, ey = (double)P.y - c.way, z = (double)P.z;
-        const double rho = sqrt(ex * ex + ey * ey);
+        const double rho = root_refined(fma(ex, ex, ey * ey));
         float erx = 1.f, ery = 0.f;   // radial direction (float suffices for a direction)
         if (rhof > 0.f) {
             erx = exf / rhof;
@@ -558,14 +589,27 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int s
         while (nearm) {
             const int k = __ffs(nearm) - 1;
             nearm &= nearm - 1u;
-            double a, b;
-            wall_seg_offset(c, k, rho, z, a, b);
-            const double dist = sqrt(a * a + b * b);
+            // offset (a, b) of the centre from the segment's closest point, and its length
+            const double ur = G.ur[k], uz = G.uz[k], len = G.len[k];
+            const double pr = rho - c.wp[2 * k], pz = z - c.wp[2 * k + 1];
+            const double sp = fma(pr, ur, pz * uz);                  // projection on the segment
+            double a, b, dist;
+            if (sp > 0.0 && sp < len) {
+                const double h = fma(pr, uz, -(pz * ur));            // along the normal (uz, -ur)
+                dist = fabs(h);
+                a = h * uz;
+                b = -(h * ur);
+            } else {                                                 // an end point is closest
+                const double sc = sp <= 0.0 ? 0.0 : len;
+                a = fma(-sc, ur, pr);
+                b = fma(-sc, uz, pz);
+                dist = root_refined(fma(a, a, b * b));
+            }
             const double dl = (double)P.w - dist;
             if (!(dl > 0.0)) continue;
-            const double idist = 1.0 / dist;
-            const float na = (float)(a * idist);
-            const V3 n = v3(na * erx, na * ery, (float)(b * idist));
+            const float idist = 1.f / (float)dist;
+            const float na = (float)a * idist;
+            const V3 n = v3(na * erx, na * ery, (float)b * idist);
             const unsigned tag = (unsigned)k + 1u;
             V3 xi = v3(0.f, 0.f, 0.f);
             if (__float_as_uint(h0.w) == tag) xi = v3(h0.x, h0.y, h0.z);
@@ -636,7 +680,11 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
     const int sub = lane & (LPP - 1);
     const unsigned gmask = LPP == 1 ? 0xffffffffu : (((1u << LPP) - 1u) << (lane & ~(LPP - 1)));
     const unsigned submask = SUBBITS << sub;
-    const int NU = d.ntiles * WPT / WPB;
+    // fused steps walk only the tiles holding live slots (contexts with spare capacity keep
+    // their blocks busy); the step kernel walks every tile (a lookup per unit costs it 4 %)
+    const int nlive = FUSED ? *(volatile int*)&d.g->nlive : d.ntiles;
+    const bool all_live = !FUSED || nlive == d.ntiles;   // then no lookup
+    const int NU = nlive * WPT / WPB;
     const int u0 = (int)((long long)blockIdx.x * NU / gridDim.x);
     const int u1 = (int)((long long)(blockIdx.x + 1) * NU / gridDim.x);
     const int ncap = d.ncap;
@@ -644,7 +692,7 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
     int kprev = -1;
     float runmax = 0.f;
     for (int u = u0; u < u1; ++u) {
-        const int k = __ldg(d.tile_inst + u * WPB / WPT);
+        const int k = __ldg(d.tile_inst + (all_live ? u * WPB / WPT : d.live_tiles[u * WPB / WPT]));
         if (k != kprev) {
             if (MODE == 0 && kprev >= 0) {
                 // flush the displacement maximum of the previous instance
@@ -672,7 +720,7 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
         // warp slice w' of tile t takes the 32-slot slice (w' + t) mod 4: rebuilds put the rows
         // with the most contacts in the first slice, so the rotation evens out the warps' work
         const int vw = u * WPB + ((int)threadIdx.x >> 5);
-        const int t = vw / WPT;
+        const int t = all_live ? vw / WPT : d.live_tiles[vw / WPT];
         const int s = t * TILE + (((vw & (WPT - 1)) + t) & (WPT - 1)) * SPW + lane / LPP;
         if (s - c.slot0 >= sd.n) continue;
         const int cur = sd.cur, lp = sd.lp;
@@ -866,7 +914,7 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
             }
         }
         int nseg = 0;
-        if (WALLS && c.nwp >= 2) nseg = wall_contacts<MODE>(d, c, s, lp, P, r, m, vme, wme, dt_hist, F, Tq);
+        if (WALLS && c.nwp >= 2) nseg = wall_contacts<MODE>(d, c, kprev, s, lp, P, r, m, vme, wme, dt_hist, F, Tq);
         const float inv_m = 1.0f / m;
         const float inv_I = 2.5f / (m * r * r);
         if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(Tq.x) && isfinite(Tq.y) &&
@@ -1707,8 +1755,8 @@ struct Plan {
     unsigned ncodes = 0, nparts = 0;
     // offsets
     size_t o_pos[2], o_vel[2], o_omg[2], o_nbr[2], o_hist[2], o_cnt[2], o_hmask[2], o_fext[2], o_whist[2], o_wseg[2], o_wrem;
-    size_t o_cellcode, o_cslot, o_perm, o_fin, o_spos, o_sid, o_ccount, o_crange, o_part, o_pinst, o_soi, o_tile, o_ic, o_id, o_spread, o_g,
-        o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl, o_small;
+    size_t o_cellcode, o_cslot, o_perm, o_fin, o_spos, o_sid, o_ccount, o_crange, o_part, o_pinst, o_soi, o_tile, o_live, o_ic, o_id, o_spread, o_g,
+        o_goff, o_outF, o_outT, o_outV, o_outW, o_outWX, o_xi, o_cmask, o_stage, o_hl, o_small, o_wgeo;
     size_t bytes = 0;
 };
 
@@ -1862,6 +1910,7 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
     p.o_pinst = L.take((size_t)std::max(1u, p.nparts) * 4);
     p.o_soi = L.take(N * 4);
     p.o_tile = L.take((size_t)p.ntiles * 4);
+    p.o_live = L.take((size_t)p.ntiles * 4);
     p.o_ic = L.take(sizeof(InstC) * p.B);
     p.o_id = L.take(sizeof(InstD) * p.B);
     p.o_spread = L.take(p.spread.size() * 4);
@@ -1877,6 +1926,7 @@ dem_status make_plan(const dem_config* cfg, Plan& p, std::string& err)
     p.o_stage = L.take(N * 24);
     p.o_hl = L.take(sizeof(HostInstLo) * p.B);
     p.o_small = L.take(sizeof(double) * 16 * p.B);
+    p.o_wgeo = L.take(sizeof(WallGeo) * p.B);
     p.bytes = L.total;
     return DEM_OK;
 }
@@ -2111,7 +2161,7 @@ dem_status build_graph(dem_ctx* ctx, int S)
     ctx->graph_fused = false;
     {
         // fused steps: one cooperative launch runs the steps between list builds; chosen by
-        // default when every tile's block fits on the GPU at once
+        // default when a block for every tile holding live slots fits on the GPU at once
         int nsm = 0, occ = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ctx->walls ? (void*)k_steps<true> : (void*)k_steps<false>,
@@ -2121,7 +2171,10 @@ dem_status build_graph(dem_ctx* ctx, int S)
         const bool can = ctx->step_lanes == 1 && ctx->step_bs == TILE && ctx->grid_fused > 0;
         if (ctx->graph_mode == 2 && !can)
             return fail(ctx, DEM_ERR_STATE, "fused steps need one lane per particle and 128-thread blocks");
-        if (ctx->graph_mode == 2 || (ctx->graph_mode == 0 && can && ctx->ntiles <= ctx->grid_fused))
+        // the tiles holding live slots (from the host's last copy of the counts)
+        long long live = 0;
+        for (int k = 0; k < ctx->B; ++k) live += 2 * ((ctx->count[k] + 2 * TILE - 1) / (2 * TILE));
+        if (ctx->graph_mode == 2 || (ctx->graph_mode == 0 && can && live <= ctx->grid_fused))
             return build_fused_graph(ctx, g, S);
     }
     std::vector<cudaGraphConditionalHandle> h(S);
@@ -2299,6 +2352,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     d.part_inst = (int*)(base + p.o_pinst);
     d.slot_of_id = (int*)(base + p.o_soi);
     d.tile_inst = (int*)(base + p.o_tile);
+    d.live_tiles = (int*)(base + p.o_live);
     d.ic = (const InstC*)(base + p.o_ic);
     d.id = (InstD*)(base + p.o_id);
     d.spread = (const unsigned*)(base + p.o_spread);
@@ -2314,6 +2368,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     d.stage = (double*)(base + p.o_stage);
     ctx->d_hl = (HostInstLo*)(base + p.o_hl);
     d.small = (double*)(base + p.o_small);
+    d.wgeo = (const WallGeo*)(base + p.o_wgeo);
     d.ncap = p.ncap;
     d.ntiles = p.ntiles;
     d.B = p.B;
@@ -2329,6 +2384,7 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     }
     Glob gl{};
     gl.any = 1u;
+    gl.nlive = p.ntiles;
     cudaStream_t s = ctx->stream;
 #define CUC(call)                                                    \
     do {                                                             \
@@ -2342,6 +2398,9 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
     CUC(cudaMemcpyAsync(d.id, idv.data(), sizeof(InstD) * p.B, cudaMemcpyHostToDevice, s));
     CUC(cudaMemcpyAsync((void*)d.spread, p.spread.data(), p.spread.size() * 4, cudaMemcpyHostToDevice, s));
     CUC(cudaMemcpyAsync(d.tile_inst, p.tile_inst.data(), p.tile_inst.size() * 4, cudaMemcpyHostToDevice, s));
+    std::vector<int> all_tiles(p.ntiles);              // until the first list build: every tile
+    for (int t = 0; t < p.ntiles; ++t) all_tiles[t] = t;
+    CUC(cudaMemcpyAsync(d.live_tiles, all_tiles.data(), all_tiles.size() * 4, cudaMemcpyHostToDevice, s));
     CUC(cudaMemcpyAsync(d.part_inst, p.part_inst.data(), p.part_inst.size() * 4, cudaMemcpyHostToDevice, s));
     CUC(cudaMemcpyAsync(d.g, &gl, sizeof(Glob), cudaMemcpyHostToDevice, s));
     CUC(cudaMemcpyAsync(ctx->d_hl, p.hl.data(), sizeof(HostInstLo) * p.B, cudaMemcpyHostToDevice, s));
@@ -2819,6 +2878,7 @@ dem_status dem_set_walls(dem_ctx* ctx, int32_t k, const double* axis, int32_t np
     const HostInstLo& h = ctx->hl[k];
     const double q = h.q;
     InstC w = c;
+    WallGeo wg{};
     w.nwp = npts;
     w.wmag = 0.f;
     if (npts) {
@@ -2843,6 +2903,15 @@ dem_status dem_set_walls(dem_ctx* ctx, int32_t k, const double* axis, int32_t np
             if (i > 0 && points[2 * i] == points[2 * i - 2] && points[2 * i + 1] == points[2 * i - 1])
                 return fail(ctx, DEM_ERR_ARG, "polyline segments need a non-zero length");
         }
+        for (int i = 0; i + 1 < npts; ++i) {
+            const double dr = w.wp[2 * i + 2] - w.wp[2 * i], dz = w.wp[2 * i + 3] - w.wp[2 * i + 1];
+            const double len = std::sqrt(dr * dr + dz * dz);
+            wg.ur[i] = dr / len;
+            wg.uz[i] = dz / len;
+            wg.len[i] = len;
+            const float drf = w.wpf[2 * i + 2] - w.wpf[2 * i], dzf = w.wpf[2 * i + 3] - w.wpf[2 * i + 1];
+            wg.inv2[i] = 1.0f / (drf * drf + dzf * dzf);
+        }
         w.wmag = (float)mag;
     }
     w.zrem = INT_MIN;
@@ -2862,6 +2931,8 @@ dem_status dem_set_walls(dem_ctx* ctx, int32_t k, const double* axis, int32_t np
     for (int b = 0; b < 2; ++b)
         for (int half = 0; half < 2; ++half)
             CU(cudaMemsetAsync(ctx->dev.wseg[b] + half * ncap + c.slot0, 0, n * sizeof(float4), ctx->stream));
+    CU(cudaMemcpyAsync((void*)(ctx->dev.wgeo + k), &wg, sizeof(WallGeo), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));                        // wg is a local
     if (dem_status st = upload_material(ctx)) return st;
     return rebuild_graph ? build_graph(ctx, ctx->graph_steps) : DEM_OK;
 }

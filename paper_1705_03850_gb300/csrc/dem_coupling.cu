@@ -309,27 +309,6 @@ __device__ __noinline__ void layer_add(const Dev& d, const InstC& c, const InstD
     for (int k = 0; k < 6; ++k) atomicAdd(acc + 11 + k, st[k]);
 }
 
-// false where a sphere of radius ru centred at u (units of q from the box origin) overlaps one
-// of the instance's axisymmetric walls (the contact test of the step kernel) or lies on the far
-// side of them from the axis: outside the vessel the walls enclose, i.e. where a ray from the
-// centre away from the axis (in the (rho, z) half-plane) crosses the non-horizontal segments an
-// even number of times (each segment spans its z range closed below, open above)
-__device__ bool clear_of_walls(const InstC& c, const long long* u, long long ru)
-{
-    if (c.nwp < 2) return true;
-    const double ex = (double)u[0] - c.wax, ey = (double)u[1] - c.way, z = (double)u[2];
-    const double rho = sqrt(ex * ex + ey * ey), ru2 = (double)ru * (double)ru;
-    int cross = 0;
-    for (int k = 0; k + 1 < c.nwp; ++k) {
-        double a, b;
-        wall_seg_offset(c, k, rho, z, a, b);
-        if (a * a + b * b < ru2) return false;
-        const double r0 = c.wp[2 * k], z0 = c.wp[2 * k + 1], r1 = c.wp[2 * k + 2], z1 = c.wp[2 * k + 3];
-        if (z0 != z1 && (z >= z0) != (z >= z1) && r0 + (z - z0) * (r1 - r0) / (z1 - z0) > rho) ++cross;
-    }
-    return (cross & 1) != 0;
-}
-
 template <typename Fn>
 __device__ __forceinline__ void for_live(const Dev& d, Fn fn)
 {
@@ -607,16 +586,56 @@ __device__ __forceinline__ double sphere_mass(double rho, double r)
     return __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(rho, 4.0 / 3.0 * 3.14159265358979323846), r), r), r);
 }
 
-// one thread per surface cell of one face: simple sequential inhibition
-__global__ void k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
+// false where a sphere of radius ru centred at u (units of q from the box origin) overlaps one
+// of the instance's axisymmetric walls (the contact test of the step kernel) or lies on the far
+// side of them from the axis: outside the vessel the walls enclose, i.e. where a ray from the
+// centre away from the axis (in the (rho, z) half-plane) crosses the non-horizontal segments an
+// even number of times (each segment spans its z range closed below, open above).  Called by a
+// whole warp: lane k tests segment k, and warp votes combine the segments, so every lane gets
+// the result of taking the segments one after another.
+__device__ bool clear_of_walls(const InstC& c, const long long* u, long long ru, int lane)
+{
+    if (c.nwp < 2) return true;
+    const double ex = (double)u[0] - c.wax, ey = (double)u[1] - c.way, z = (double)u[2];
+    const double rho = sqrt(ex * ex + ey * ey), ru2 = (double)ru * (double)ru;
+    bool hit = false, crosses = false;
+    const int k = lane;
+    if (k + 1 < c.nwp) {
+        double a, b;
+        wall_seg_offset(c, k, rho, z, a, b);
+        hit = a * a + b * b < ru2;
+        const double r0 = c.wp[2 * k], z0 = c.wp[2 * k + 1], r1 = c.wp[2 * k + 2], z1 = c.wp[2 * k + 3];
+        crosses = z0 != z1 && (z >= z0) != (z >= z1) && r0 + (z - z0) * (r1 - r0) / (z1 - z0) > rho;
+    }
+    if (__any_sync(0xffffffffu, hit)) return false;
+    return (__popc(__ballot_sync(0xffffffffu, crosses)) & 1) != 0;
+}
+
+// One block per surface cell of one face: simple sequential inhibition.  The attempts of a cell
+// are taken in order, each against the insertions accepted before it; since most attempts fail
+// in a dense packing, the block's INS_WARPS warps evaluate the next INS_WARPS attempts at once
+// (the same draws: a function of the cell, the call and the attempt's index), against the
+// insertions accepted so far, and the results are then taken in attempt order: failures count,
+// the first success is accepted and the attempts after it are evaluated again in the next
+// round (they have not seen it).  So the accepted set, the attempts used and the failures are
+// those of taking the attempts one after another.  Within an attempt the warp's lanes share
+// the clearance tests (a wall segment, a neighbour cell of the fine level's last list build, a
+// stride of the earlier insertions each) and vote.
+constexpr int INS_WARPS = 8;                 // attempts evaluated together
+
+__global__ void __launch_bounds__(32 * INS_WARPS) k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
 {
     const Face& f = g.face[fk];
-    const int local = blockIdx.x * blockDim.x + threadIdx.x;
-    if (local >= f.nb * f.nc) return;
+    const int lane = (int)threadIdx.x & 31, warp = (int)threadIdx.x >> 5;
+    const int local = blockIdx.x;
+    if (local >= f.nb * f.nc) return;       // the whole block leaves together
     const int cell = f.off + local;
     const int ib = local % f.nb, ic = local / f.nb;
     const InstC& c = d.ic[0];
     const InstD D = d.id[0];
+    __shared__ int s_ok[INS_WARPS];          // 1: the warp's attempt is clear, -1: invalid radius
+    __shared__ int4 s_u[INS_WARPS];
+    __shared__ double s_r[INS_WARPS];
     long long quota = (long long)a.cross[cell] + a.carry[cell];
     unsigned total = 0;
     const unsigned* hist = a.hist + (size_t)cell * MAXBINS;
@@ -628,109 +647,126 @@ __global__ void k_cp_insert(Dev d, Geo g, Acc a, int fk, double rho)
         for (int k = 0; k < 3; ++k) vf[k] = a.fav[4 * cell + 1 + k] / M;
         vn = vf[f.axis];
     }
+    // the length quantum is a power of two: dividing by it is multiplying by its reciprocal
+    const double iqf = 1.0 / g.qf;
     int4* mine = a.ins + (size_t)cell * g.max_insert;
     double* mym = a.insm + (size_t)cell * g.max_insert;
     // the cell's extent on the face [m]
     const double b0 = __dadd_rn(g.lo[f.b], __dmul_rn((double)ib, f.wb));
     const double c0 = __dadd_rn(g.lo[f.c], __dmul_rn((double)ic, f.wc));
+    const unsigned cbase = d.crange[c.code0].x;
+    // every thread holds the same loop state; the loop ends for all of them at once
     while (quota > 0 && total > 0 && fails < g.max_attempts && nins < g.max_insert) {
+        const int at = attempt + warp;      // this warp's attempt
         // radius: a bin drawn with probability proportional to its count, then uniform in it
-        long long pick = below(draw(g, cell, attempt, 0), total);
+        long long pick = below(draw(g, cell, at, 0), total);
         int b = 0;
         while (pick >= (long long)hist[b]) {
             pick -= hist[b];
             ++b;
         }
-        const double r = __dmul_rn(__dadd_rn((double)b, unit01(draw(g, cell, attempt, 1))), g.wbin);
+        const double r = __dmul_rn(__dadd_rn((double)b, unit01(draw(g, cell, at, 1))), g.wbin);
         // centre: uniform over the cell's face shrunk by r, and along the inward normal over
         // [r, r + depth] from the face, depth = max(2 r, |<v_n>| T_c); continuous values (the same
         // operations as a plain double evaluation), then rounded to the fine level's grid
         const double depth = fmax(2.0 * r, fabs(vn) * g.Tc);
         const double sb = __dsub_rn(f.wb, 2.0 * r), sc = __dsub_rn(f.wc, 2.0 * r);
-        const long long ru = llrint(r / g.qf);
-        if (!(r > 0.0) || sb < 0.0 || sc < 0.0 || ru <= 0) {
-            ++attempt;
-            ++fails;
-            continue;
-        }
-        const double nlo = f.side == 0 ? f.plane + r : f.plane - r - depth;
-        double xc[3];
-        xc[f.b] = __dadd_rn(__dadd_rn(b0, r), __dmul_rn(unit01(draw(g, cell, attempt, 2)), sb));
-        xc[f.c] = __dadd_rn(__dadd_rn(c0, r), __dmul_rn(unit01(draw(g, cell, attempt, 3)), sc));
-        xc[f.axis] = __dadd_rn(nlo, __dmul_rn(unit01(draw(g, cell, attempt, 4)), depth));
-        long long u[3];
-        for (int k = 0; k < 3; ++k) u[k] = llrint((xc[k] - g.lof[k]) / g.qf);
-        ++attempt;
-        // inside the fine level's walls and clear of them, then no overlap with its particles
-        // (cell lists of the last build) or earlier insertions
-        bool ok = clear_of_walls(c, u, ru);
-        const int ru_i = (int)ru;
-        const int cx0 = axis_cell(c, 0, (int)u[0]), cy0 = axis_cell(c, 1, (int)u[1]), cz0 = axis_cell(c, 2, (int)u[2]);
-        const unsigned cbase = d.crange[c.code0].x;
-        for (int dz = -1; dz <= 1 && ok; ++dz) {
-            const int cz = cz0 + dz;
-            if (cz < 0 || cz >= c.nc[2]) continue;
-            for (int dy = -1; dy <= 1 && ok; ++dy) {
-                int cy = cy0 + dy;
-                if (cy < 0 || cy >= c.nc[1]) {
-                    if (!c.per[1]) continue;
-                    cy = (cy + c.nc[1]) % c.nc[1];
-                }
-                for (int dx = -1; dx <= 1 && ok; ++dx) {
-                    int cx = cx0 + dx;
+        const long long ru = llrint(__dmul_rn(r, iqf));
+        int verdict = -1;
+        long long u[3] = {0, 0, 0};
+        if (r > 0.0 && sb >= 0.0 && sc >= 0.0 && ru > 0) {
+            const double nlo = f.side == 0 ? f.plane + r : f.plane - r - depth;
+            double xc[3];
+            xc[f.b] = __dadd_rn(__dadd_rn(b0, r), __dmul_rn(unit01(draw(g, cell, at, 2)), sb));
+            xc[f.c] = __dadd_rn(__dadd_rn(c0, r), __dmul_rn(unit01(draw(g, cell, at, 3)), sc));
+            xc[f.axis] = __dadd_rn(nlo, __dmul_rn(unit01(draw(g, cell, at, 4)), depth));
+            for (int k = 0; k < 3; ++k) u[k] = llrint(__dmul_rn(__dsub_rn(xc[k], g.lof[k]), iqf));
+            // inside the fine level's walls and clear of them, then no overlap with its particles
+            // (cell lists of the last build) or earlier insertions
+            bool ok = clear_of_walls(c, u, ru, lane);
+            const int ru_i = (int)ru;
+            if (ok) {
+                bool hit = false;
+                if (lane < 27) {
+                    // lane = neighbour cell (dx, dy, dz) of the candidate's cell
+                    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+                    const int cz = axis_cell(c, 2, (int)u[2]) + dz;
+                    int cy = axis_cell(c, 1, (int)u[1]) + dy, cx = axis_cell(c, 0, (int)u[0]) + dx;
+                    bool there = cz >= 0 && cz < c.nc[2];
+                    if (cy < 0 || cy >= c.nc[1]) {
+                        there = there && c.per[1];
+                        cy = (cy + c.nc[1]) % c.nc[1];
+                    }
                     if (cx < 0 || cx >= c.nc[0]) {
-                        if (!c.per[0]) continue;
+                        there = there && c.per[0];
                         cx = (cx + c.nc[0]) % c.nc[0];
                     }
-                    const unsigned code = cell_code(d, c, cx, cy, cz);
-                    const uint2 cr = d.crange[code];
-                    const int start = c.slot0 + (int)(cr.x - cbase);
-                    const int cnt = (int)cr.y;
-                    for (int t = 0; t < cnt; ++t) {
-                        const int j = d.fin[start + t];   // slot of this cell member
-                        if (j - c.slot0 >= D.n) continue;
-                        const int4 Q = d.pos[D.cur][j];
-                        const long long ex = min_image((int)u[0] - Q.x, c.per[0], c.ext[0], c.half[0]);
-                        const long long ey = min_image((int)u[1] - Q.y, c.per[1], c.ext[1], c.half[1]);
-                        const long long ez = (long long)u[2] - Q.z;
-                        const long long S = (long long)ru_i + Q.w;
-                        if (ex * ex + ey * ey + ez * ez < S * S) {
-                            ok = false;
-                            break;
+                    if (there) {
+                        const uint2 cr = d.crange[cell_code(d, c, cx, cy, cz)];
+                        const int start = c.slot0 + (int)(cr.x - cbase);
+                        for (int t = 0; t < (int)cr.y && !hit; ++t) {
+                            const int j = d.fin[start + t];   // slot of this cell member
+                            if (j - c.slot0 >= D.n) continue;
+                            const int4 Q = d.pos[D.cur][j];
+                            const long long ex = min_image((int)u[0] - Q.x, c.per[0], c.ext[0], c.half[0]);
+                            const long long ey = min_image((int)u[1] - Q.y, c.per[1], c.ext[1], c.half[1]);
+                            const long long ez = (long long)u[2] - Q.z;
+                            const long long S = (long long)ru_i + Q.w;
+                            hit = ex * ex + ey * ey + ez * ez < S * S;
                         }
                     }
                 }
-            }
-        }
-        // earlier insertions: this cell, and the cells of earlier faces
-        for (int t = 0; t < nins && ok; ++t) {
-            const long long ex = u[0] - mine[t].x, ey = u[1] - mine[t].y, ez = u[2] - mine[t].z;
-            const long long S = (long long)ru_i + mine[t].w;
-            if (ex * ex + ey * ey + ez * ez < S * S) ok = false;
-        }
-        for (int k = 0; k < fk && ok; ++k) {
-            const Face& o = g.face[k];
-            for (int oc = o.off; oc < o.off + o.nb * o.nc && ok; ++oc) {
-                const int4* other = a.ins + (size_t)oc * g.max_insert;
-                for (int t = 0; t < a.nins[oc] && ok; ++t) {
-                    const long long ex = u[0] - other[t].x, ey = u[1] - other[t].y, ez = u[2] - other[t].z;
-                    const long long S = (long long)ru_i + other[t].w;
-                    if (ex * ex + ey * ey + ez * ez < S * S) ok = false;
+                // earlier insertions: this cell, and the cells of earlier faces
+                for (int t = lane; t < nins && !hit; t += 32) {
+                    const int4 o = mine[t];
+                    const long long ex = u[0] - o.x, ey = u[1] - o.y, ez = u[2] - o.z;
+                    const long long S = (long long)ru_i + o.w;
+                    hit = ex * ex + ey * ey + ez * ez < S * S;
                 }
+                for (int k = 0; k < fk; ++k) {
+                    const Face& o = g.face[k];
+                    for (int oc = o.off + lane; oc < o.off + o.nb * o.nc && !hit; oc += 32) {
+                        const int4* other = a.ins + (size_t)oc * g.max_insert;
+                        for (int t = 0; t < a.nins[oc] && !hit; ++t) {
+                            const long long ex = u[0] - other[t].x, ey = u[1] - other[t].y, ez = u[2] - other[t].z;
+                            const long long S = (long long)ru_i + other[t].w;
+                            hit = ex * ex + ey * ey + ez * ez < S * S;
+                        }
+                    }
+                }
+                ok = !__any_sync(0xffffffffu, hit);
             }
+            verdict = ok ? 1 : 0;
         }
-        if (!ok) {
-            ++fails;
-            continue;
+        if (lane == 0) {
+            s_ok[warp] = verdict;
+            s_u[warp] = make_int4((int)u[0], (int)u[1], (int)u[2], (int)ru);
+            s_r[warp] = r;
         }
-        const double m = sphere_mass(rho, r);    // of the drawn radius (the grid radius differs by < q / 2)
-        mine[nins] = make_int4((int)u[0], (int)u[1], (int)u[2], ru_i);
-        mym[nins] = m;
-        ++nins;
-        quota -= llrint(m / g.mass_unit);
+        __syncthreads();
+        // the batch in attempt order (every thread alike)
+        for (int w = 0; w < INS_WARPS; ++w) {
+            if (!(quota > 0 && fails < g.max_attempts && nins < g.max_insert)) break;
+            ++attempt;
+            if (s_ok[w] != 1) {
+                ++fails;
+                continue;
+            }
+            const double m = sphere_mass(rho, s_r[w]);   // of the drawn radius (the grid radius differs by < q / 2)
+            if (threadIdx.x == 0) {
+                mine[nins] = s_u[w];
+                mym[nins] = m;
+            }
+            ++nins;
+            quota -= llrint(m / g.mass_unit);
+            break;                                      // later attempts have not seen this insertion
+        }
+        __syncthreads();                                // the insertion is visible; s_* may be rewritten
     }
-    a.nins[cell] = nins;
-    a.carry[cell] = quota;
+    if (threadIdx.x == 0) {
+        a.nins[cell] = nins;
+        a.carry[cell] = quota;
+    }
 }
 
 // append the inserted particles (cell order) to the fine level's tail
@@ -797,6 +833,7 @@ struct dem_coupler {
     int calls = 0;
     double rho_f = 0.0;
     cudaEvent_t ready = nullptr;   // orders the fine level's stream after the coarse level's
+    cudaEvent_t done = nullptr;    // orders the coarse level's stream after the coupling kernels
 };
 
 namespace {
@@ -1030,9 +1067,11 @@ dem_status dem_coupler_create(dem_ctx* coarse, dem_ctx* fine, const dem_coupling
         return DEM_ERR_ARG;
     }
     coupler_layout(cp, (char*)ws);
-    if (cudaEventCreateWithFlags(&cp->ready, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&cp->ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cp->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
-        set_thread_error("could not create the coupler's CUDA event");
+        if (cp->ready) cudaEventDestroy(cp->ready);
+        set_thread_error("could not create the coupler's CUDA events");
         delete cp;
         return DEM_ERR_CUDA;
     }
@@ -1047,6 +1086,7 @@ dem_status dem_coupler_create(dem_ctx* coarse, dem_ctx* fine, const dem_coupling
         if (!cell_thresholds(cp->g, thr)) {
             set_thread_error("correction grid thresholds not found");
             cudaEventDestroy(cp->ready);
+            cudaEventDestroy(cp->done);
             delete cp;
             return DEM_ERR_ARG;
         }
@@ -1103,10 +1143,16 @@ dem_status dem_couple(dem_coupler* cp)
     k_cp_force_fine<<<ctx->grid_rb, TILE, 0, s>>>(ctx->dev, g, cp->a);
     k_cp_force_coarse<<<coarse->grid_rb, TILE, 0, s>>>(coarse->dev, g, cp->a);
     for (int fk = 0; fk < g.nface; ++fk)
-        k_cp_insert<<<(g.face[fk].nb * g.face[fk].nc + 63) / 64, 64, 0, s>>>(ctx->dev, g, cp->a, fk, cp->rho_f);
+        k_cp_insert<<<g.face[fk].nb * g.face[fk].nc, 32 * INS_WARPS, 0, s>>>(ctx->dev, g, cp->a, fk, cp->rho_f);
     CU(cudaMemsetAsync(cp->overflow, 0, sizeof(int), s));
     k_cp_append<<<1, 256, 0, s>>>(ctx->dev, g, cp->a, cp->overflow);
     CU(cudaGetLastError());
+    // the coarse level's later work (its next steps) waits for the coupling kernels, which read
+    // its state and write its held forces and corrected velocities (an event, no host wait)
+    if (coarse->stream != s) {
+        CU(cudaEventRecord(cp->done, s));
+        CU(cudaStreamWaitEvent(coarse->stream, cp->done, 0));
+    }
     // no host wait: the device updated the count and the offsets (k_cp_append) and reports an
     // overflow in the status word; the host copy of the count is refreshed when next needed
     ctx->count_stale = true;
@@ -1205,6 +1251,7 @@ dem_status dem_coupler_destroy(dem_coupler* cp)
 {
     if (!cp) return DEM_ERR_ARG;
     if (cp->ready) cudaEventDestroy(cp->ready);
+    if (cp->done) cudaEventDestroy(cp->done);
     delete cp;   // touches neither context (they may already be gone)
     return DEM_OK;
 }

@@ -96,6 +96,14 @@ struct InstC {
 };
 static_assert(sizeof(InstC) <= 4 * TILE, "the step kernel stages InstC in shared memory, one word per thread");
 
+// per-segment constants of an instance's axisymmetric walls (outside InstC, which every step
+// block stages: the plain step kernel does not pay for them)
+struct WallGeo {
+    double ur[MAX_WP], uz[MAX_WP];       // unit tangent (rho, z) of segment k (from point k to k + 1)
+    double len[MAX_WP];                  // length of segment k [units]
+    float inv2[MAX_WP];                  // 1 / |segment k|^2 from the float points (float pre-test)
+};
+
 __device__ __forceinline__ void wall_seg_offset(const InstC& c, int k, double rho, double z, double& a, double& b)
 {
     const double r0 = c.wp[2 * k], z0 = c.wp[2 * k + 1];
@@ -135,6 +143,8 @@ struct Glob {
     unsigned bar_gen;          // fused steps: grid-barrier generation (bumped by each release)
     unsigned bar_pad;
     long long remain;          // fused steps: steps still to do in the current graph launch
+    int nlive;                 // entries of live_tiles
+    int nlive_pad;
 };
 
 // kernel-visible pointers of a context
@@ -162,6 +172,9 @@ struct Dev {
     int* part_inst;            // instance owning each scan chunk of cell codes (-1: padding)
     int* slot_of_id;
     int* tile_inst;
+    const WallGeo* wgeo;       // [B] wall segment constants
+    int* live_tiles;           // the tiles fused steps walk: each instance's first tiles holding its
+                               // live slots, in whole pairs (g->nlive of them; set by each list build)
     const InstC* ic;
     InstD* id;
     const unsigned* spread;

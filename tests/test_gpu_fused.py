@@ -88,3 +88,20 @@ def test_fused_steps_with_several_tiles_per_block_equal_one_launch_per_step():
     wl = workloads.shear_bed(300_000, seed=2)
     (a, sa), (b, sb) = _pair(lambda: dem.from_workload(wl), 100, 50, rounds=2)
     _same(a, b)
+
+
+def test_spare_capacity_changes_nothing_and_steps_only_live_tiles():
+    # a context with ten times the slots it holds walks only the tiles with live particles: the
+    # same bits as a context without spare slots, and fused steps chosen by the live tiles
+    wl = workloads.dense_block(40, 40, 20, seed=9, vel=0.3)       # 32,000 spheres
+    runs = []
+    for cap in (None, 10 * wl.n):
+        sim = dem.DEM([dem.desc_from_workload(wl, capacity=cap)])
+        sim.write_state(wl.x, wl.v, wl.w, wl.r, wl.m)
+        sim.step(1)
+        sim.set_graph(25)
+        assert sim.stats()["graph_fused"] == 1
+        sim.step(200).sync()
+        runs.append((sim.read(dem.POS), sim.read(dem.VEL), sim.stats()["rebuilds"]))
+    assert runs[0][2] == runs[1][2] > 1
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])

@@ -17,12 +17,16 @@ pytestmark = pytest.mark.gpu
 SMALL = dict(length=0.3, width=0.06, height=0.1, bed=0.04, regions=((0.1, 0.12), (0.14, 0.04)))
 
 
-def _hierarchy(graph, u0=0.5, multirate=False):
+def _hierarchy(graph, u0=0.5, multirate=False, streams=False):
     lv, specs = workloads.chute(**SMALL, u0=u0, multirate=multirate, interval=16 if multirate else 15)
     ctx = []
     for k, wl in enumerate(lv):
         cap = None if k == 0 else wl.n + 20000
-        d = dem.DEM([dem.desc_from_workload(wl, capacity=cap)], max_neighbors=24)
+        kw = {}
+        if streams:
+            import torch
+            kw["stream"] = torch.cuda.Stream()
+        d = dem.DEM([dem.desc_from_workload(wl, capacity=cap)], max_neighbors=24, **kw)
         v = np.zeros_like(wl.v)
         v[:, 0] = u0
         d.write_state(wl.x, v, wl.w, wl.r, wl.m)
@@ -40,6 +44,24 @@ def test_graph_and_direct_stepping_agree_through_coupling():
         xa, xb = la.read(dem.POS), lb.read(dem.POS)
         assert np.array_equal(np.isnan(xa), np.isnan(xb))
         assert np.array_equal(np.nan_to_num(xa), np.nan_to_num(xb))
+
+
+def test_one_stream_per_level_equals_one_stream_for_all():
+    # levels on their own streams step concurrently within a period; the coupling call orders
+    # them (the fine side after the coarse side's steps, the coarse side's next steps after the
+    # coupling kernels), so the run is the one on a single stream, bit for bit, through
+    # insertion and removal
+    lv, _, a = _hierarchy(True, u0=10.0)
+    _, _, b = _hierarchy(True, u0=10.0, streams=True)
+    a.advance(30)
+    b.advance(30)
+    assert a.counts() == b.counts()
+    assert a.counts()[2] != lv[2].n                                        # particles came and went
+    for la, lb in zip(a.levels, b.levels):
+        for f in (dem.POS, dem.VEL):
+            xa, xb = la.read(f), lb.read(f)
+            assert np.array_equal(np.isnan(xa), np.isnan(xb))
+            assert np.array_equal(np.nan_to_num(xa), np.nan_to_num(xb))
 
 
 @pytest.mark.parametrize("multirate", [False, True])

@@ -663,9 +663,12 @@ __device__ __forceinline__ T ld_state(const T* p)
 // One step over the block's units (MODE 0: force, kick and drift of every particle; MODE 1:
 // forces only), ending with the block's displacement maximum folded into its last instance.
 // sc, sd, smax: the block's shared staging of the current instance and of the warp maxima.
-// FUSED: called once per step by the fused kernel.
+// FUSED: called once per step by the fused kernel; kstaged: the instance staged in sc and sd at
+// the end of the previous step (-1: none), kept so that a block of one instance stages it once
+// per launch and then only flips its state buffer (all else in them is constant between list
+// builds).
 template <int MODE, bool WALLS, int BS, int LPP, bool FUSED = false>
-__device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, InstD& sd, float* smax)
+__device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, InstD& sd, float* smax, int& kstaged)
 {
     constexpr int WPB = BS / 32;             // warps per block
     constexpr int SPW = 32 / LPP;            // slots per warp
@@ -689,7 +692,12 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
     const int u1 = (int)((long long)(blockIdx.x + 1) * NU / gridDim.x);
     const int ncap = d.ncap;
     const size_t plane = (size_t)d.Lmax * ncap;
-    int kprev = -1;
+    int kprev = FUSED ? kstaged : -1;
+    if (FUSED && kprev >= 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) sd.cur ^= 1;   // the last step swapped the instance's buffers
+        __syncthreads();
+    }
     float runmax = 0.f;
     for (int u = u0; u < u1; ++u) {
         const int k = __ldg(d.tile_inst + (all_live ? u * WPB / WPT : d.live_tiles[u * WPB / WPT]));
@@ -1001,6 +1009,7 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
             if (bm > 0.f && kprev >= 0) atomicMax(&d.id[kprev].stepmax, __float_as_uint(bm));
         }
     }
+    kstaged = kprev;
 }
 
 // The end of a step for every instance, by the last block to finish it: the displacement
@@ -1034,7 +1043,8 @@ __global__ void __launch_bounds__(BS, (step_minb<BS, LPP>())) k_step(Dev d, int 
     __shared__ InstD sd;
     __shared__ float smax[BS / 32];
     __shared__ bool am_last;
-    step_pass<MODE, WALLS, BS, LPP>(d, prime, sc, sd, smax);
+    int kstaged = -1;
+    step_pass<MODE, WALLS, BS, LPP>(d, prime, sc, sd, smax, kstaged);
     if (MODE == 0) {
         // the last block to finish accumulates the bound per instance and decides on rebuilds
         if (threadIdx.x == 0) {
@@ -1066,7 +1076,7 @@ __global__ void __launch_bounds__(BS, (step_minb<BS, LPP>())) k_step(Dev d, int 
 // h_rb (build the lists before going on) and h_loop (steps remain).
 constexpr unsigned BAR_POLLS = 1u << 22;     // polls of about 0.1-1 us before a wait gives up
 
-template <bool WALLS>
+template <bool WALLS, int LPP>
 __global__ void __launch_bounds__(TILE, 5) k_steps(Dev d, cudaGraphConditionalHandle h_rb,
                                                                         cudaGraphConditionalHandle h_loop)
 {
@@ -1080,8 +1090,9 @@ __global__ void __launch_bounds__(TILE, 5) k_steps(Dev d, cudaGraphConditionalHa
     const long long todo = *(volatile long long*)&d.g->remain;
     long long done = 0;
     bool final_last = false;
+    int kstaged = -1;
     while (done < todo) {
-        step_pass<0, WALLS, TILE, 1, true>(d, 0, sc, sd, smax);
+        step_pass<0, WALLS, TILE, LPP, true>(d, 0, sc, sd, smax, kstaged);
         if (threadIdx.x == 0) {
             const unsigned gen = *(volatile unsigned*)&d.g->bar_gen;
             __threadfence();
@@ -2080,6 +2091,17 @@ dem_status launch_step(dem_ctx* ctx, int prime)
 
 constexpr int EV_EVERY = 5;    // step kernels per timed one in a graph
 
+// the fused step kernel for the context's walls and lanes per particle
+void* fused_func(const dem_ctx* ctx)
+{
+    switch (ctx->step_lanes) {
+    case 2: return ctx->walls ? (void*)k_steps<true, 2> : (void*)k_steps<false, 2>;
+    case 4: return ctx->walls ? (void*)k_steps<true, 4> : (void*)k_steps<false, 4>;
+    case 8: return ctx->walls ? (void*)k_steps<true, 8> : (void*)k_steps<false, 8>;
+    default: return ctx->walls ? (void*)k_steps<true, 1> : (void*)k_steps<false, 1>;
+    }
+}
+
 // A graph of S steps run by fused launches: init (S steps to do, pending list build) ->
 // while (steps remain) { if (list build needed) rebuild chain; k_steps }, with CUDA events
 // around the loop.
@@ -2124,8 +2146,8 @@ dem_status build_fused_graph(dem_ctx* ctx, cudaGraph_t g, int S)
     {
         void* args[] = {&dv, &h_rb, &h_loop};
         cudaKernelNodeParams kp{};
-        kp.func = ctx->walls ? (void*)k_steps<true> : (void*)k_steps<false>;
-        kp.gridDim = dim3(std::min(ctx->ntiles, ctx->grid_fused));   // all resident: a cooperative launch
+        kp.func = fused_func(ctx);
+        kp.gridDim = dim3(std::min(ctx->ntiles * ctx->step_lanes, ctx->grid_fused));   // all resident: cooperative
         kp.blockDim = dim3(TILE);
         kp.kernelParams = args;
         CU(cudaGraphAddKernelNode(&kn, body, &ifn, 1, &kp));
@@ -2164,17 +2186,15 @@ dem_status build_graph(dem_ctx* ctx, int S)
         // default when a block for every tile holding live slots fits on the GPU at once
         int nsm = 0, occ = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ctx->walls ? (void*)k_steps<true> : (void*)k_steps<false>,
-                                                      TILE, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fused_func(ctx), TILE, 0);
         cudaGetLastError();
         ctx->grid_fused = nsm * occ;
-        const bool can = ctx->step_lanes == 1 && ctx->step_bs == TILE && ctx->grid_fused > 0;
-        if (ctx->graph_mode == 2 && !can)
-            return fail(ctx, DEM_ERR_STATE, "fused steps need one lane per particle and 128-thread blocks");
+        const bool can = ctx->step_bs == TILE && ctx->grid_fused > 0;
+        if (ctx->graph_mode == 2 && !can) return fail(ctx, DEM_ERR_STATE, "fused steps need 128-thread blocks");
         // the tiles holding live slots (from the host's last copy of the counts)
         long long live = 0;
         for (int k = 0; k < ctx->B; ++k) live += 2 * ((ctx->count[k] + 2 * TILE - 1) / (2 * TILE));
-        if (ctx->graph_mode == 2 || (ctx->graph_mode == 0 && can && live <= ctx->grid_fused))
+        if (ctx->graph_mode == 2 || (ctx->graph_mode == 0 && can && live * ctx->step_lanes <= ctx->grid_fused))
             return build_fused_graph(ctx, g, S);
     }
     std::vector<cudaGraphConditionalHandle> h(S);
@@ -2700,12 +2720,27 @@ dem_status dem_set_step_lanes(dem_ctx* ctx, int32_t lanes)
         const long long r1 = (long long)std::max(1, nsm) * std::max(1, b1) * 128;
         const long long rl = (long long)std::max(1, nsm) * std::max(1, bl) * 128;
         lanes = 1;
-        if (2 * rows < r1)
+        // fused steps (by default when the live tiles' blocks are resident at once): the most
+        // lanes whose blocks are all resident
+        long long live = 0;
+        for (int k = 0; k < ctx->B; ++k) live += 2 * ((ctx->count[k] + 2 * TILE - 1) / (2 * TILE));
+        int bf = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_steps<false, 2>, 128, 0);
+        cudaGetLastError();
+        const long long gf = (long long)std::max(1, nsm) * std::max(1, bf);
+        if (ctx->graph_mode != 1 && live <= gf) {
+            for (int l = 8; l >= 2; l >>= 1)
+                if ((long long)l * live <= gf) {
+                    lanes = l;
+                    break;
+                }
+        } else if (2 * rows < r1) {
             for (int l = 8; l >= 2; l >>= 1)
                 if ((long long)l * rows <= rl) {
                     lanes = l;
                     break;
                 }
+        }
         if (ctx->step_bs != 128) lanes = 1;
     }
     if (lanes > 1 && ctx->step_bs != 128)

@@ -148,6 +148,9 @@ def test_lanes_are_chosen_by_size():
     big = dem.from_workload(workloads.shear_bed(200_000, seed=2))
     big.set_step_lanes(0)
     assert big.stats()["step_lanes"] == 1
+    mid = dem.from_workload(workloads.shear_bed(40_000, seed=2))  # 314 tiles: fused steps, two lanes
+    mid.set_step_lanes(0)
+    assert mid.stats()["step_lanes"] == 2
     small.set_step_lanes(1).set_step_block(64)
     small.set_step_lanes(0)
     assert small.stats()["step_lanes"] == 1

@@ -12,10 +12,11 @@ from paper_1705_03850_gb300 import autotune, dem, workloads
 pytestmark = pytest.mark.gpu
 
 
-def _pair(make, steps, graph, rounds=1):
+def _pair(make, steps, graph, rounds=1, lanes=1):
     out = []
     for mode in (1, 2):
         sim = make()
+        sim.set_step_lanes(lanes)
         sim.step(1)
         sim.set_graph_mode(mode)
         sim.set_graph(graph)
@@ -35,7 +36,8 @@ def _same(a, b, fields=(dem.POS, dem.VEL, dem.OMEGA)):
         assert np.array_equal(np.nan_to_num(xa), np.nan_to_num(xb)), f
 
 
-def test_fused_steps_with_walls_and_removal_equal_one_launch_per_step():
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_fused_steps_with_walls_and_removal_equal_one_launch_per_step(lanes):
     wl = workloads.small_vessel(seed=24)
     walls = wl.meta["walls"][1:]                             # orifice open
     z_rem = wl.meta["z_o"] - 0.004
@@ -44,16 +46,18 @@ def test_fused_steps_with_walls_and_removal_equal_one_launch_per_step():
         sim = dem.from_workload(wl)
         sim.set_walls(0, (0.0, 0.0), walls, z_rem)
         return sim
-    (a, sa), (b, sb) = _pair(make, 4000, 50)
+    (a, sa), (b, sb) = _pair(make, 4000, 50, lanes=lanes)
+    assert sa["step_lanes"] == sb["step_lanes"] == lanes
     assert sa["rebuilds"] == sb["rebuilds"] > 5
     _same(a, b)
     assert a.wall_removed() == b.wall_removed()
 
 
-def test_fused_steps_of_batched_instances_equal_one_launch_per_step():
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_fused_steps_of_batched_instances_equal_one_launch_per_step(lanes):
     wls = [workloads.dense_block(*sh, seed=40 + k, vel=0.4) for k, sh in enumerate([(5, 6, 4), (9, 7, 5), (4, 4, 3)])]
     ch = autotune.Choice(skin_factor=0.01, cell_factor=1.0, graph_steps=25, max_neighbors=32)
-    (a, sa), (b, sb) = _pair(lambda: autotune.make_context(wls, ch), 50, 25, rounds=4)
+    (a, sa), (b, sb) = _pair(lambda: autotune.make_context(wls, ch), 50, 25, rounds=4, lanes=lanes)
     assert sa["rebuilds"] == sb["rebuilds"] >= 3 * len(wls)
     _same(a, b)
 
@@ -71,7 +75,9 @@ def test_fused_steps_are_chosen_by_size():
     small = dem.from_workload(workloads.dense_block(6, 6, 4, seed=3))
     small.set_graph(20)
     assert small.stats()["graph_fused"] == 1
-    small.set_step_lanes(2)                                 # several lanes: one launch per step
+    small.set_step_lanes(0)                                 # by size: fused steps with 8 lanes
+    assert small.stats()["step_lanes"] == 8 and small.stats()["graph_fused"] == 1
+    small.set_step_lanes(1).set_step_block(64)              # fused steps need 128-thread blocks
     assert small.stats()["graph_fused"] == 0
     with pytest.raises(dem.DemError):
         small.set_graph_mode(2)

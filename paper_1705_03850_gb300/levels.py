@@ -43,7 +43,7 @@ def period_steps(dts, intervals):
 class Hierarchy:
     """Levels (single-instance DEM contexts, coarsest first) and the couplers between neighbours."""
 
-    def __init__(self, levels, specs, steps_per_graph=True):
+    def __init__(self, levels, specs, steps_per_graph=True, lanes=0):
         if len(specs) != len(levels) - 1:
             raise ValueError("one coupling spec per pair of neighbouring levels")
         self.levels = list(levels)
@@ -52,6 +52,8 @@ class Hierarchy:
         for lv in self.levels:
             lv.clear_external_force()
         self.couplers = [dem.Coupler(levels[k], levels[k + 1], **dict(s, add_forces=1)) for k, s in enumerate(specs)]
+        for lv in self.levels:
+            lv.set_step_lanes(lanes)             # 0: by size (small levels: fused steps, several lanes)
         if steps_per_graph:
             for lv, n in zip(self.levels, self.steps):
                 lv.set_graph(n)

@@ -37,6 +37,7 @@ def run(alpha: int = 1, settle_s: float = 0.3, discharge_s: float = 0.6, skip_s:
     sim = dem.from_workload(wl, max_neighbors=24, device=device)
     z_o = wl.meta["z_o"]
     sim.set_walls(0, (0.0, 0.0), workloads.silo_walls(z_o, closed=True))
+    sim.set_step_lanes(0)                      # by size: the coarse grain runs fused steps, four lanes
     sim.set_graph(graph)
     dt = wl.dt
     g = max(graph, 1)

@@ -226,6 +226,13 @@ dem_status dem_set_step_lanes(dem_ctx *ctx, int32_t lanes);
  * implementation. */
 dem_status dem_set_graph_mode(dem_ctx *ctx, int32_t mode);
 
+/* For tests of the fused steps' failure path: the next fused launch's first block does not
+ * arrive at its first grid barrier and leaves, so the other blocks' bounded waits run out
+ * (about a second) and the launch ends with DEM_ERR_TIMEOUT in the status word (read by
+ * dem_sync_status); the context keeps the error.  Nothing else sets it; no effect without
+ * fused steps.  Not in the paper. */
+dem_status dem_test_stall_barrier(dem_ctx *ctx);
+
 /* CUDA-event time of step kernels of the most recent graph launch: every fifth
  * step kernel of the graph (the first, the sixth, ...) is bracketed by event
  * nodes; total_ms = the sum over those, count = their number (total_ms / count is

@@ -1070,11 +1070,20 @@ __global__ void __launch_bounds__(BS, (step_minb<BS, LPP>())) k_step(Dev d, int 
 // the per-step launch and graph-node latency.
 // Each step is exactly the step kernel's; between steps a grid barrier (the last block to
 // arrive ends the step for every instance, as the step kernel's last block does, then
-// releases the others; every wait gives up after a bounded number of polls and reports
-// DEM_ERR_TIMEOUT).  Runs the steps still to do in this graph launch (g->remain) and stops
-// early when an instance needs a list build; the last block then sets the loop's conditions:
-// h_rb (build the lists before going on) and h_loop (steps remain).
-constexpr unsigned BAR_POLLS = 1u << 22;     // polls of about 0.1-1 us before a wait gives up
+// releases the others; every wait gives up after a second and reports DEM_ERR_TIMEOUT, and a
+// block that gave up, or saw another give up, leaves the launch).  Runs the steps still to do
+// in this graph launch (g->remain) and stops early when an instance needs a list build; the
+// last block then sets the loop's conditions: h_rb (build the lists before going on) and
+// h_loop (steps remain).
+constexpr unsigned long long BAR_WAIT_NS = 1000000000ull;   // a barrier wait gives up after 1 s
+constexpr unsigned BAR_POLLS = 1u << 24;                     // or after this many polls
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 template <bool WALLS, int LPP>
 __global__ void __launch_bounds__(TILE, 5) k_steps(Dev d, cudaGraphConditionalHandle h_rb,
@@ -1096,16 +1105,22 @@ __global__ void __launch_bounds__(TILE, 5) k_steps(Dev d, cudaGraphConditionalHa
         if (threadIdx.x == 0) {
             const unsigned gen = *(volatile unsigned*)&d.g->bar_gen;
             __threadfence();
-            const unsigned prev = atomicAdd(&d.g->counter, 1u);
-            am_last = prev == gridDim.x - 1;
-            if (!am_last) {
+            // a test of the timeout path (dem_test_stall_barrier): the first block does not
+            // arrive at the first barrier of this launch and leaves, so the others' waits run out
+            const bool skip = blockIdx.x == 0 && done == 0 && atomicExch(&d.g->test_stall, 0u) != 0u;
+            const unsigned prev = skip ? 0u : atomicAdd(&d.g->counter, 1u);
+            am_last = !skip && prev == gridDim.x - 1;
+            if (skip) {
+                atomicOr(&d.g->status, ST_TIMEOUT);
+            } else if (!am_last) {
+                const unsigned long long t0 = global_ns();
                 unsigned polls = 0u;
                 while (*(volatile unsigned*)&d.g->bar_gen == gen) {
-                    if (++polls > BAR_POLLS) {
+                    if (++polls > BAR_POLLS || global_ns() - t0 > BAR_WAIT_NS) {
                         atomicOr(&d.g->status, ST_TIMEOUT);
                         break;
                     }
-                    __nanosleep(64);
+                    __nanosleep(256);
                 }
                 __threadfence();
             }
@@ -2683,6 +2698,15 @@ dem_status dem_set_step_block(dem_ctx* ctx, int32_t threads)
         return fail(ctx, DEM_ERR_STATE, "several lanes per particle run at 128 threads per block");
     ctx->step_bs = threads;
     return ctx->graph_steps > 0 ? build_graph(ctx, ctx->graph_steps) : DEM_OK;
+}
+
+dem_status dem_test_stall_barrier(dem_ctx* ctx)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    static const unsigned one = 1u;
+    CU(cudaMemcpyAsync(&ctx->dev.g->test_stall, &one, sizeof(unsigned), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
 }
 
 dem_status dem_set_graph_mode(dem_ctx* ctx, int32_t mode)

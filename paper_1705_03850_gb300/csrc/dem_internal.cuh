@@ -144,7 +144,7 @@ struct Glob {
     unsigned bar_pad;
     long long remain;          // fused steps: steps still to do in the current graph launch
     int nlive;                 // entries of live_tiles
-    int nlive_pad;
+    unsigned test_stall;       // 1: the next fused launch's first block skips its first barrier
 };
 
 // kernel-visible pointers of a context

@@ -111,3 +111,20 @@ def test_spare_capacity_changes_nothing_and_steps_only_live_tiles():
         runs.append((sim.read(dem.POS), sim.read(dem.VEL), sim.stats()["rebuilds"]))
     assert runs[0][2] == runs[1][2] > 1
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_a_barrier_wait_that_runs_out_is_reported_not_hung():
+    # one block of a fused launch leaves without arriving at the barrier (a test hook): the
+    # other blocks give up after about a second and the host reads DEM_ERR_TIMEOUT
+    import time
+    wl = workloads.dense_block(20, 20, 12, seed=3, vel=0.2)           # 4,800 spheres: 38 blocks
+    sim = dem.from_workload(wl)
+    sim.step(1)
+    sim.set_graph(25)
+    assert sim.stats()["graph_fused"] == 1
+    sim.step(50).sync()
+    sim.test_stall_barrier()
+    t0 = time.perf_counter()
+    sim.step(25)
+    assert sim.status() == 6                                           # DEM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 10.0

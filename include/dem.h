@@ -226,6 +226,14 @@ dem_status dem_set_step_lanes(dem_ctx *ctx, int32_t lanes);
  * implementation. */
 dem_status dem_set_graph_mode(dem_ctx *ctx, int32_t mode);
 
+/* How the neighbour lists are built (SURVEY's cell-range and list-build step; the list is
+ * the same either way, bit for bit): 0 (the default), each thread scans the 27 cells around
+ * its particle in the cell-ordered positions through the caches; 1, each block first stages
+ * the cell-ordered positions around its 64 particles in shared memory and reads the candidates
+ * that fall there from it.  DEM_ERR_ARG for other values.  A captured graph is rebuilt with it.
+ * Not in the paper: an implementation choice (the staged build measured slower on the 1M bed). */
+dem_status dem_set_list_build(dem_ctx *ctx, int32_t staged);
+
 /* For tests of the fused steps' failure path: the next fused launch's first block does not
  * arrive at its first grid barrier and leaves, so the other blocks' bounded waits run out
  * (about a second) and the launch ends with DEM_ERR_TIMEOUT in the status word (read by

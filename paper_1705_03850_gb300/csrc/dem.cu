@@ -272,7 +272,19 @@ struct RowScratch {
     int pos[MAXL][RB_T];                     // partner's cell-order position
 };
 
-__device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, const InstC& c, RowScratch& R)
+// The staged variant of the list build: the block's 64 cell-order positions and RB_W on either
+// side (the cells around the block's particles, in Morton order) staged in shared memory;
+// candidates inside the window are read from there, the others from L2.
+constexpr int RB_W = 128;
+constexpr int RB_WIN = RB_T + 2 * RB_W;
+struct Window {
+    int4 pos[RB_WIN];
+    int lo, n;                               // first cell-order position and length
+};
+
+template <bool STAGED>
+__device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, const InstC& c, RowScratch& R,
+                                          const Window* W)
 {
     const int tx = threadIdx.x;
     const int cur = D.cur, nxt = cur ^ 1, lp = D.lp, nlp = lp ^ 1;
@@ -329,7 +341,9 @@ __device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, 
         const int ix = k % 3, iy = (k / 3) % 3, iz = k / 9;
         const unsigned code = (unsigned)c.code0 + (ix == 0 ? mx0 : ix == 1 ? mx1 : mx2) +
                               (iy == 0 ? my0 : iy == 1 ? my1 : my2) + (iz == 0 ? mz0 : iz == 1 ? mz1 : mz2);
+#if DEM_CHECKS
         if (!in_range(d, (long long)code - c.code0, c.ncode, ps, 1)) return make_uint2(0u, 0u);
+#endif
         return __ldg(d.crange + code);
     };
     // scan the 27 cells (the next cell's range in flight) and append the neighbours
@@ -340,15 +354,26 @@ __device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, 
         const uint2 cr = rg;
         if (k + 1 < 27) rg = range_of(k + 1);
         const int start = c.slot0 + (int)(cr.x - cbase);
+#if DEM_CHECKS
         int cnt = (int)cr.y;
         // a cell's candidates lie within the instance's slots (a cell outside the grid reads as
         // empty, with no start)
-        if (DEM_CHECKS && cnt > 0 &&
+        if (cnt > 0 &&
             !(in_range(d, start - c.slot0, c.cap, ps, 2) && in_range(d, start - c.slot0 + cnt, c.cap + 1, ps, 2)))
             cnt = 0;
+#else
+        // (the checks compiled out: even folded away they cost this kernel registers)
+        const int cnt = (int)cr.y;
+#endif
         for (int t = 0; t < cnt; ++t) {
             const int m = start + t;
-            const int4 q = __ldg(d.spos + m);
+            int4 q;
+            if (STAGED) {
+                const unsigned wi = (unsigned)(m - W->lo);
+                q = wi < (unsigned)W->n ? W->pos[wi] : __ldg(d.spos + m);
+            } else {
+                q = __ldg(d.spos + m);
+            }
             const int ddx = min_image(p.x - q.x, per0, ext0, hf0);
             const int ddy = min_image(p.y - q.y, per1, ext1, hf1);
             const long long ddz = (long long)p.z - q.z;
@@ -430,24 +455,39 @@ __device__ __forceinline__ void build_row(const Dev& d, int ps, const InstD& D, 
     }
 }
 
+template <bool STAGED>
 __global__ void __launch_bounds__(RB_T, 16) k_rb_build(Dev d)
 {
     if (!d.g->any) return;
     __shared__ RowScratch R;
     constexpr int H = TILE / RB_T;           // blocks of RB_T threads per tile
     // over the cell-order positions: the threads of a warp hold neighbouring particles and
-    // scan overlapping cells (the rows go to the particles' new slots in the same tile).  Staging
-    // a window of cell-order positions around the block in shared memory was measured slower
-    // (0.83 against 0.71 ms per build of the 1M bed): the neighbouring cells' positions hit in L1
+    // scan overlapping cells (the rows go to the particles' new slots in the same tile).  The
+    // direct scan (the default) finds the neighbouring cells' positions in L1: staging them in
+    // shared memory (STAGED) was measured slower (0.83 against 0.70 ms per build of the 1M bed)
     for (int u = blockIdx.x; u < d.ntiles * H; u += gridDim.x) {
         const int t = u / H;
         const int k = d.tile_inst[t];
         const InstD D = d.id[k];
-        if (!D.flag) continue;
+        if (!D.flag) continue;               // the same for the whole block
         const InstC& c = d.ic[k];
-        const int p = t * TILE + (u % H) * RB_T + threadIdx.x;
-        if (p - c.slot0 >= D.n_new) continue;
-        build_row(d, p, D, c, R);
+        const int p0 = t * TILE + (u % H) * RB_T;
+        const int p = p0 + threadIdx.x;
+        if (STAGED) {
+            __shared__ Window W;
+            const int lo = max(c.slot0, p0 - RB_W), hi = min(c.slot0 + D.n_new, p0 + RB_T + RB_W);
+            __syncthreads();                 // the previous window is no longer read
+            if (threadIdx.x == 0) {
+                W.lo = lo;
+                W.n = max(0, hi - lo);
+            }
+            for (int i = lo + (int)threadIdx.x; i < hi; i += RB_T) W.pos[i - lo] = __ldg(d.spos + i);
+            __syncthreads();
+            if (p - c.slot0 < D.n_new) build_row<true>(d, p, D, c, R, &W);
+        } else {
+            if (p - c.slot0 >= D.n_new) continue;
+            build_row<false>(d, p, D, c, R, nullptr);
+        }
     }
 }
 
@@ -479,7 +519,10 @@ __global__ void k_rb_finish(Dev d)
         }
     }
     __syncthreads();
-    // the tiles the step walks: per instance the pairs of tiles that hold its live slots
+    // the tiles fused steps walk: per instance the pairs of tiles that hold its live slots
+    // (offsets by a scan over a chunk of instances, then the chunk's ranges written by the block)
+    __shared__ unsigned s_off[256], s_lt[256];
+    __shared__ int s_t0[256];
     unsigned base = 0u;
     for (int k0 = 0; k0 < d.B; k0 += blockDim.x) {
         const int k = k0 + (int)threadIdx.x;
@@ -487,10 +530,14 @@ __global__ void k_rb_finish(Dev d)
         if (k < d.B) lt = 2u * (unsigned)((d.id[k].n + 2 * TILE - 1) / (2 * TILE));
         unsigned tot;
         const unsigned off = base + block_exclusive_scan(lt, &tot);
-        if (k < d.B) {
-            const int t0 = d.ic[k].slot0 / TILE;
-            for (unsigned i = 0; i < lt; ++i) d.live_tiles[off + i] = t0 + (int)i;
-        }
+        s_off[threadIdx.x] = off;
+        s_lt[threadIdx.x] = lt;
+        s_t0[threadIdx.x] = k < d.B ? d.ic[k].slot0 / TILE : 0;
+        __syncthreads();
+        const int nk = min((int)blockDim.x, d.B - k0);
+        for (int j = 0; j < nk; ++j)
+            for (unsigned i = threadIdx.x; i < s_lt[j]; i += blockDim.x) d.live_tiles[s_off[j] + i] = s_t0[j] + (int)i;
+        __syncthreads();
         base += tot;
     }
     if (threadIdx.x == 0) {
@@ -2032,8 +2079,11 @@ dem_status launch_rebuild(dem_ctx* ctx, cudaStream_t st)
     k_rb_cellsort<<<gt, TILE, 0, st>>>(d);
     k_rb_count<<<1, 256, 0, st>>>(d);
     k_rb_tilesort<<<gt, TILE, 0, st>>>(d);
-    k_rb_build<<<ctx->grid_build, RB_T, 0, st>>>(d);
-    k_rb_finish<<<1, 256, 0, st>>>(d);
+    if (ctx->list_staged)
+        k_rb_build<true><<<ctx->grid_build_staged, RB_T, 0, st>>>(d);
+    else
+        k_rb_build<false><<<ctx->grid_build, RB_T, 0, st>>>(d);
+    k_rb_finish<<<1, 256, 0, st>>>(d);          // 256 threads: its shared arrays
     CU(cudaGetLastError());
     return DEM_OK;
 }
@@ -2476,8 +2526,10 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
         ctx->grid1 = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * std::max(1, b1)));
         ctx->grid_rb = std::max(1, std::min(ctx->ntiles, std::max(1, nsm) * 8));
         int bb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_rb_build, RB_T, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_rb_build<false>, RB_T, 0);
         ctx->grid_build = std::max(1, std::min(ctx->ntiles * (TILE / RB_T), std::max(1, nsm) * std::max(1, bb)));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_rb_build<true>, RB_T, 0);
+        ctx->grid_build_staged = std::max(1, std::min(ctx->ntiles * (TILE / RB_T), std::max(1, nsm) * std::max(1, bb)));
         cudaGetLastError();
     }
     *out = ctx;
@@ -2698,6 +2750,14 @@ dem_status dem_set_step_block(dem_ctx* ctx, int32_t threads)
         return fail(ctx, DEM_ERR_STATE, "several lanes per particle run at 128 threads per block");
     ctx->step_bs = threads;
     return ctx->graph_steps > 0 ? build_graph(ctx, ctx->graph_steps) : DEM_OK;
+}
+
+dem_status dem_set_list_build(dem_ctx* ctx, int32_t staged)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (staged != 0 && staged != 1) return fail(ctx, DEM_ERR_ARG, "list build must be 0 (direct scan) or 1 (staged)");
+    ctx->list_staged = staged != 0;
+    return ctx->graph_steps > 0 ? build_graph(ctx, ctx->graph_steps) : DEM_OK;   // the graph holds the chain
 }
 
 dem_status dem_test_stall_barrier(dem_ctx* ctx)

@@ -30,6 +30,8 @@ struct dem_ctx {
     int step_lanes = 1;               // lanes per particle of the step kernel (1, 2, 4 or 8; >1 at 128 threads)
     int grid_bs[3] = {1, 1, 1};       // persistent step grids for 64, 128 and 256 threads per block
     int grid_lanes[3] = {1, 1, 1};    // persistent step grids for 2, 4 and 8 lanes per particle
+    bool list_staged = false;         // list build with the shared-memory window of cell-order positions
+    int grid_build_staged = 1;
     int grid_rb = 1;                  // persistent grid of the per-slot rebuild kernels
     int grid_build = 1;               // one wave of the list build (occupancy-sized)
     unsigned ncodes = 0, nparts = 0;

@@ -109,6 +109,7 @@ def lib():
         "dem_set_step_lanes": [vp, i32],
         "dem_set_graph_mode": [vp, i32],
         "dem_test_stall_barrier": [vp],
+        "dem_set_list_build": [vp, i32],
         "dem_graph_step_kernel_ms": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)],
         "dem_rollout_workspace": [vp, i64, i64, ctypes.POINTER(i64)],
         "dem_rollout_forward": [vp, i64, i64, vp, i64],
@@ -142,7 +143,7 @@ def lib():
 def exported_symbols():
     return ["dem_query_workspace", "dem_create", "dem_destroy", "dem_write", "dem_read", "dem_read_contacts",
             "dem_write_contacts", "dem_step", "dem_sync_status", "dem_instance_info_get", "dem_stats",
-            "dem_set_graph", "dem_set_step_block", "dem_set_step_lanes", "dem_set_graph_mode", "dem_test_stall_barrier", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
+            "dem_set_graph", "dem_set_step_block", "dem_set_step_lanes", "dem_set_graph_mode", "dem_test_stall_barrier", "dem_set_list_build", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
             "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material",
             "dem_coupler_workspace", "dem_coupler_create", "dem_couple", "dem_coupler_read", "dem_coupler_destroy",
             "dem_counts", "dem_clear_external_force", "dem_grid_fields", "dem_set_walls", "dem_wall_removed",
@@ -313,6 +314,11 @@ class DEM:
         """How a captured graph runs its steps: 0 fused when the context fits (default), 1 one
         kernel per step, 2 fused (one cooperative launch between list builds)."""
         self._check(self.L.dem_set_graph_mode(self.h, int(mode)), "set graph mode")
+        return self
+
+    def set_list_build(self, staged):
+        """Neighbour-list build: 0 direct scan of the 27 cells (default), 1 staged in shared memory."""
+        self._check(self.L.dem_set_list_build(self.h, int(staged)), "set list build")
         return self
 
     def test_stall_barrier(self):

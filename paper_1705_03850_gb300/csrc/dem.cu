@@ -1597,7 +1597,9 @@ __global__ void __launch_bounds__(TILE) k_adj_force(Dev d, AdjBufs a, Snap S, in
         const float dt_hist = prime ? 0.f : c.dt;
         const float4 Fi = a.Fb[s], Ti = a.Tb[s];
         float4 xb = a.xb[s], vb = a.vb[s], wb = a.wb[s];
-        double thE = 0.0, the = 0.0, thm = 0.0;
+        // the particle's share of d(loss)/d(E, e, mu) this step, summed over its few contacts in
+        // float and added to the running double sums once (FP64 per contact is slow on this GPU)
+        float thE = 0.f, the = 0.f, thm = 0.f;
         const int ncnt = d.cnt[lp][s];
         const int* nb = d.nbr[lp] + s;
         float* xbr = a.xib + s;
@@ -1663,9 +1665,9 @@ __global__ void __launch_bounds__(TILE) k_adj_force(Dev d, AdjBufs a, Snap S, in
             xbr[plane + o] = g.xi.y;
             xbr[2 * plane + o] = g.xi.z;
             // each side of the pair adds half of the parameter derivative
-            thE += 0.5 * ((double)g.c_kn * c.c_kn + (double)g.c_kt * c.c_kt) * c.inv_E;
-            the += 0.5 * (double)g.nbeta * c.dnb_de;
-            thm += 0.5 * (double)g.mu;
+            thE += 0.5f * (g.c_kn * c.c_kn + g.c_kt * c.c_kt) * c.inv_E;
+            the += 0.5f * g.nbeta * c.dnb_de;
+            thm += 0.5f * g.mu;
         }
         float4 wx = make_float4(0.f, 0.f, 0.f, 0.f);
         if (c.floor_on) {
@@ -1684,18 +1686,18 @@ __global__ void __launch_bounds__(TILE) k_adj_force(Dev d, AdjBufs a, Snap S, in
                 vb.x += g.va.x; vb.y += g.va.y; vb.z += g.va.z;
                 wb.x += g.wa.x; wb.y += g.wa.y; wb.z += g.wa.z;
                 wx = make_float4(g.xi.x, g.xi.y, g.xi.z, 0.f);
-                thE += ((double)g.c_kn * c.c_kn + (double)g.c_kt * c.c_kt) * c.inv_E;
-                the += (double)g.nbeta * c.dnb_de;
-                if (c.mu_w_follows) thm += (double)g.mu;
+                thE += (g.c_kn * c.c_kn + g.c_kt * c.c_kt) * c.inv_E;
+                the += g.nbeta * c.dnb_de;
+                if (c.mu_w_follows) thm += g.mu;
             }
         }
         a.wxib[s] = wx;
         a.xb[s] = xb;
         a.vb[s] = vb;
         a.wb[s] = wb;
-        a.thb[3 * (size_t)s] += thE;
-        a.thb[3 * (size_t)s + 1] += the;
-        a.thb[3 * (size_t)s + 2] += thm;
+        a.thb[3 * (size_t)s] += (double)thE;
+        a.thb[3 * (size_t)s + 1] += (double)the;
+        a.thb[3 * (size_t)s + 2] += (double)thm;
     });
 }
 

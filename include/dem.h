@@ -165,6 +165,14 @@ dem_status dem_read(dem_ctx *ctx, int32_t field, void *dst, int64_t n);
  * Single-instance contexts only. */
 dem_status dem_read_contacts(dem_ctx *ctx, int32_t *partner, double *xi, int32_t width, int64_t n);
 
+/* The neighbour lists the next step walks, per particle in ID order: the partner IDs of
+ * every entry of its row (ascending, -1 padded; width entries per particle): the pairs within
+ * r_i + r_j + skin at the last list build, and those of particles inserted since (Sec. 2.3
+ * insertion adds rows without a list build).  A pending list build runs first.  partner:
+ * int32 (n, width), device memory; more entries than width: DEM_ERR_CAPACITY at the next
+ * status check.  Single-instance contexts only.  Not in the paper: for inspection and tests. */
+dem_status dem_read_neighbors(dem_ctx *ctx, int32_t *partner, int32_t width, int64_t n);
+
 /* Set tangential overlaps of existing neighbour pairs (same layout as
  * dem_read_contacts); pairs not within the neighbour skin are ignored.  Use
  * after dem_write to resume a run; the lists are built first if needed. */

@@ -514,6 +514,7 @@ __global__ void k_rb_finish(Dev d)
             D.lp ^= 1;
             D.flag = 0;
             D.n = D.n_new;
+            D.nbin = D.n_new;
             D.disp = 0.f;
             atomicAdd(&d.g->rebuilds, 1ull);
         }
@@ -1421,6 +1422,32 @@ __global__ void k_read_contacts(Dev d, int* __restrict__ partner, double* __rest
             xi[3 * o] = xi[3 * o + 1] = xi[3 * o + 2] = 0.0;
         }
     }
+}
+
+// every entry of the particle's neighbour row, as partner IDs in ascending order (-1 padded)
+__global__ void k_read_neighbors(Dev d, int* __restrict__ partner, int width)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.ncap) return;
+    const int k = d.tile_inst[s / TILE];
+    const InstD D = d.id[k];
+    const InstC& c = d.ic[k];
+    if (s - c.slot0 >= D.n) return;
+    const unsigned id = __float_as_uint(d.vel[D.cur][s].w) & ID_MASK;
+    const int cnt = d.cnt[D.lp][s];
+    int pid[MAXL];
+    for (int e = 0; e < cnt; ++e) {
+        const int j = d.nbr[D.lp][(size_t)e * d.ncap + s];
+        const int p = (int)(__float_as_uint(d.vel[D.cur][j].w) & ID_MASK);
+        int t = e - 1;
+        while (t >= 0 && pid[t] > p) {
+            pid[t + 1] = pid[t];
+            --t;
+        }
+        pid[t + 1] = p;
+    }
+    if (cnt > width) atomicOr(&d.g->status, ST_TRUNC);
+    for (int t = 0; t < width; ++t) partner[(size_t)id * width + t] = t < cnt ? pid[t] : -1;
 }
 
 __global__ void k_write_contacts(Dev d, const int* __restrict__ partner, const double* __restrict__ xi, int width)
@@ -2658,6 +2685,21 @@ dem_status dem_read_contacts(dem_ctx* ctx, int32_t* partner, double* xi, int32_t
     dem_status st = launch_eval(ctx);
     if (st) return st;
     k_read_contacts<<<nblk(ctx->ncap, 256), 256, 0, ctx->stream>>>(ctx->dev, partner, xi, width);
+    CU(cudaGetLastError());
+    return DEM_OK;
+}
+
+dem_status dem_read_neighbors(dem_ctx* ctx, int32_t* partner, int32_t width, int64_t n)
+{
+    if (!ctx) return DEM_ERR_ARG;
+    if (ctx->status) return check_status(ctx);
+    if (ctx->B != 1) return fail(ctx, DEM_ERR_ARG, "neighbour read-out needs a single-instance context");
+    if (dem_status st = refresh_count(ctx)) return st;
+    if (n != total_count(ctx) || width < 1 || !partner) return fail(ctx, DEM_ERR_ARG, "bad neighbour arguments");
+    if (!is_device_ptr(partner)) return fail(ctx, DEM_ERR_ARG, "neighbour buffer must be device memory");
+    dem_status st = launch_rebuild(ctx, ctx->stream);
+    if (st) return st;
+    k_read_neighbors<<<nblk(ctx->ncap, 256), 256, 0, ctx->stream>>>(ctx->dev, partner, width);
     CU(cudaGetLastError());
     return DEM_OK;
 }

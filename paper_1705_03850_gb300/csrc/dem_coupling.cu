@@ -82,7 +82,13 @@ struct Acc {
     // thr[i] <= u < thr[i + 1] (the decisions of the double expressions, see cell_thresholds)
     long long* thr;              // [2][3][MAXCR + 1]
     int* removed;                // [1] fine particles removed at this call
+    // rows of the particles inserted at this call, without a list build: the (existing slot,
+    // new slot) pairs to append to existing rows, and [0] pairs, [1] fall back to a list
+    // build, [2] particles appended at this call
+    unsigned long long* pairs;   // [PAIRS_MAX]
+    int* npairs;                 // [4]
 };
+constexpr int PAIRS_MAX = 4096;
 
 // position in metres of integer coordinate u on axis a: lo + u q, rounded once (as the read-out)
 __device__ __forceinline__ double posm(const double* lo, double q, int u, int a) { return __fma_rn((double)u, q, lo[a]); }
@@ -436,8 +442,11 @@ __global__ void __launch_bounds__(TILE, 8) k_cp_fine(Dev d, Geo g, Acc a)
             if ((g.drain >> (2 * ax + 1)) & 1) gone |= u >= __ldg(T + g.ncr[ax]);
         }
         if (gone) {
+            // marked and left in place with no radius until the next list build drops it (its
+            // neighbours, further than a radius from its centre, can no longer touch it)
             V.w = __uint_as_float(__float_as_uint(V.w) | GONE_BIT);
             d.vel[D.cur][s] = V;
+            d.pos[D.cur][s] = make_int4(P.x, P.y, P.z, 0);
             atomicAdd(a.removed, 1);
         }
     });
@@ -716,6 +725,16 @@ __global__ void __launch_bounds__(32 * INS_WARPS) k_cp_insert(Dev d, Geo g, Acc 
                         }
                     }
                 }
+                // the fine level's particles inserted since its last list build (not in its cells)
+                for (int j = c.slot0 + D.nbin + lane; j < c.slot0 + D.n && !hit; j += 32) {
+                    if (__float_as_uint(d.vel[D.cur][j].w) & GONE_BIT) continue;
+                    const int4 Q = d.pos[D.cur][j];
+                    const long long ex = min_image((int)u[0] - Q.x, c.per[0], c.ext[0], c.half[0]);
+                    const long long ey = min_image((int)u[1] - Q.y, c.per[1], c.ext[1], c.half[1]);
+                    const long long ez = (long long)u[2] - Q.z;
+                    const long long S = (long long)ru_i + Q.w;
+                    hit = ex * ex + ey * ey + ez * ez < S * S;
+                }
                 // earlier insertions: this cell, and the cells of earlier faces
                 for (int t = lane; t < nins && !hit; t += 32) {
                     const int4 o = mine[t];
@@ -776,6 +795,11 @@ __global__ void k_cp_append(Dev d, Geo g, Acc a, int* overflow)
     InstD& D = d.id[0];
     int tot = 0;
     for (int i = 0; i < g.S; ++i) tot += a.nins[i];
+    if (threadIdx.x == 0) {
+        a.npairs[0] = 0;
+        a.npairs[1] = 0;
+        a.npairs[2] = 0;
+    }
     if (D.n + tot > c.cap || D.nid + tot > c.cap) {
         if (threadIdx.x == 0) {
             *overflow = 1;
@@ -814,9 +838,177 @@ __global__ void k_cp_append(Dev d, Geo g, Acc a, int* overflow)
         D.nid += tot;
         d.goff[0] = 0;                      // offsets of the user arrays (one instance)
         d.goff[1] = D.nid;
-        if ((tot > 0 || a.removed[0] > 0) && D.flag == 0) {
-            D.flag = 1;
+        a.npairs[2] = tot;                  // their rows are built next (k_cp_rows), no list build
+    }
+}
+
+// Rows of the particles inserted at this call, built without a list build (one thread each).
+// The exact test of the list build (|x_i - x_j| < r_i + r_j + skin, integer arithmetic) against
+// every live particle that can be that close: those of the last build's cell lists within two
+// cells (every particle has moved less than half the skin since, so a partner's cell of then is
+// at most two cells away), and those inserted since, tested one by one.  The row is ordered as
+// the list build orders rows (by d^2 - (r_i + r_j)^2, then ID); each partner that already had
+// a row gets the new particle appended to it (k_cp_rows_append).  Lists stay valid: a pair
+// left out was further apart than the skin now, and closing that gap needs the displacement
+// bound that triggers the next build.  A row too long, or too many pairs, falls back to a list
+// build.
+constexpr int ROWS_T = 64;
+
+__global__ void __launch_bounds__(ROWS_T) k_cp_rows(Dev d, Acc a)
+{
+    __shared__ float key[MAXL][ROWS_T];
+    __shared__ int slot[MAXL][ROWS_T];
+    const int tx = threadIdx.x;
+    const InstC& c = d.ic[0];
+    const InstD D = d.id[0];
+    const int tot = a.npairs[2];
+    const int t = blockIdx.x * ROWS_T + tx;
+    if (t >= tot) return;
+    const int n_old = D.n - tot;
+    const int si = c.slot0 + n_old + t;
+    const int cur = D.cur, lp = D.lp, Lmax = d.Lmax, ncap = d.ncap;
+    const int4 p = d.pos[cur][si];
+    const int per0 = c.per[0], per1 = c.per[1], ext0 = c.ext[0], ext1 = c.ext[1], hf0 = c.half[0], hf1 = c.half[1];
+    const int skin = c.skin;
+    int nc = 0;
+    bool overflow = false;
+    auto test = [&](int j) {
+        if (j == si) return;
+        if (__float_as_uint(d.vel[cur][j].w) & GONE_BIT) return;
+        const int4 q = d.pos[cur][j];
+        const int ddx = min_image(p.x - q.x, per0, ext0, hf0);
+        const int ddy = min_image(p.y - q.y, per1, ext1, hf1);
+        const long long ddz = (long long)p.z - q.z;
+        const int cut = p.w + q.w + skin;
+        if (abs(ddx) >= cut || abs(ddy) >= cut || ddz >= cut || ddz <= -cut) return;
+        const long long d2 = (long long)ddx * ddx + (long long)ddy * ddy + ddz * ddz;
+        if (d2 >= (long long)cut * cut) return;
+        if (nc == Lmax) {
+            overflow = true;
+            return;
+        }
+        const long long S = (long long)p.w + q.w;
+        key[nc][tx] = (float)(d2 - S * S);
+        slot[nc][tx] = j;
+        ++nc;
+    };
+    // the last build's cells within two cells per axis (each cell once on a short periodic axis)
+    int cell0[3], ncell[3];
+    const int cc[3] = {axis_cell(c, 0, p.x), axis_cell(c, 1, p.y), axis_cell(c, 2, p.z)};
+    for (int ax = 0; ax < 3; ++ax) {
+        if (c.per[ax] && c.nc[ax] <= 5) {
+            cell0[ax] = 0;
+            ncell[ax] = c.nc[ax];
+        } else if (c.per[ax]) {
+            cell0[ax] = cc[ax] - 2;
+            ncell[ax] = 5;
+        } else {
+            cell0[ax] = max(cc[ax] - 2, 0);
+            ncell[ax] = min(cc[ax] + 2, c.nc[ax] - 1) - cell0[ax] + 1;
+        }
+    }
+    const unsigned cbase = d.crange[c.code0].x;
+    for (int iz = 0; iz < ncell[2]; ++iz)
+        for (int iy = 0; iy < ncell[1]; ++iy)
+            for (int ix = 0; ix < ncell[0]; ++ix) {
+                const int cx = (cell0[0] + ix + c.nc[0]) % c.nc[0], cy = (cell0[1] + iy + c.nc[1]) % c.nc[1];
+                const int cz = cell0[2] + iz;
+                const uint2 cr = d.crange[cell_code(d, c, cx, cy, cz)];
+                const int start = c.slot0 + (int)(cr.x - cbase);
+                for (int m = 0; m < (int)cr.y; ++m) test(d.fin[start + m]);
+            }
+    // the particles inserted since the last build (this call's included)
+    for (int j = c.slot0 + D.nbin; j < c.slot0 + D.n; ++j) test(j);
+    // order: (d^2 - (r_i + r_j)^2, ID), as the list build
+    for (int i = 1; i < nc; ++i) {
+        const float kk = key[i][tx];
+        const int m = slot[i][tx];
+        const unsigned idm = __float_as_uint(d.vel[cur][m].w) & ID_MASK;
+        int j = i - 1;
+        while (j >= 0 && (key[j][tx] > kk ||
+                          (key[j][tx] == kk && (__float_as_uint(d.vel[cur][slot[j][tx]].w) & ID_MASK) > idm))) {
+            key[j + 1][tx] = key[j][tx];
+            slot[j + 1][tx] = slot[j][tx];
+            --j;
+        }
+        key[j + 1][tx] = kk;
+        slot[j + 1][tx] = m;
+    }
+    int* row = d.nbr[lp] + si;
+    for (int e = 0; e < nc; ++e) {
+        const int j = slot[e][tx];
+        row[(size_t)e * ncap] = j;
+        if (j < c.slot0 + n_old) {         // a partner with a row of its own: append to it
+            const int k = atomicAdd(&a.npairs[0], 1);
+            if (k < PAIRS_MAX) a.pairs[k] = ((unsigned long long)(unsigned)j << 32) | (unsigned)si;
+            else overflow = true;
+        }
+    }
+    d.cnt[lp][si] = nc;
+    d.hmask[lp][si] = 0u;
+    if (overflow) atomicExch(&a.npairs[1], 1);
+}
+
+// Append the inserted particles to their partners' rows, in (partner, new slot) order (the
+// pairs sorted first, so the rows do not depend on the order the pairs were found in); fall
+// back to a list build if a row would overflow or the pairs did not fit.  Then the tiles
+// fused steps walk grow to cover the new slots.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_cp_rows_append(Dev d, Acc a)
+{
+    __shared__ unsigned long long key[PAIRS_MAX];
+    __shared__ int fallback;
+    InstD& D = d.id[0];
+    const InstC& c = d.ic[0];
+    const int P = a.npairs[0];
+    if (threadIdx.x == 0) fallback = a.npairs[1] != 0 || P > PAIRS_MAX;
+    __syncthreads();
+    if (!fallback && P > 0) {
+        int n2 = 1;
+        while (n2 < P) n2 <<= 1;
+        for (int k = threadIdx.x; k < n2; k += blockDim.x) key[k] = k < P ? a.pairs[k] : ~0ull;
+        __syncthreads();
+        // bitonic sort of n2 keys
+        for (int size = 2; size <= n2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int k = threadIdx.x; k < n2; k += blockDim.x) {
+                    const int l = k ^ stride;
+                    if (l > k) {
+                        const bool up = (k & size) == 0;
+                        const unsigned long long x = key[k], y = key[l];
+                        if ((x > y) == up) {
+                            key[k] = y;
+                            key[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        const int lp = D.lp, ncap = d.ncap, Lmax = d.Lmax;
+        for (int k = threadIdx.x; k < P; k += blockDim.x) {
+            const unsigned j = (unsigned)(key[k] >> 32);
+            if (k > 0 && (unsigned)(key[k - 1] >> 32) == j) continue;   // not the first of its run
+            int r = 1;
+            while (k + r < P && (unsigned)(key[k + r] >> 32) == j) ++r;
+            const int c0 = d.cnt[lp][j];
+            if (c0 + r > Lmax) {
+                fallback = 1;
+                continue;
+            }
+            for (int t = 0; t < r; ++t) d.nbr[lp][(size_t)(c0 + t) * ncap + j] = (int)(unsigned)key[k + t];
+            d.cnt[lp][j] = c0 + r;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (fallback && D.flag == 0) {
+            D.flag = 1;                      // the rows are rebuilt from the positions
             atomicOr(&d.g->any, 1u);
+        }
+        // the tiles holding live slots (one instance): fused steps walk them
+        const int t0 = c.slot0 / TILE, nl = 2 * ((D.n + 2 * TILE - 1) / (2 * TILE));
+        if (nl > d.g->nlive) {
+            for (int i = d.g->nlive; i < nl; ++i) d.live_tiles[i] = t0 + i;
+            d.g->nlive = nl;
         }
     }
 }
@@ -854,7 +1046,8 @@ size_t coupler_layout(dem_coupler* cp, char* base)
            o_nins = L.take(S * 4), o_ins = L.take(S * MI * 16), o_insm = L.take(S * MI * 8), o_lay = L.take(2 * S * 160),
            o_vmax = L.take(2 * S * 4), o_ctrl = L.take(S * 24), o_out = L.take(2 * S * 88), o_cor = L.take(2 * C * 40),
            o_dv = L.take(C * 24), o_prev = L.take(ncap * 16), o_pok = L.take(ncap * 4), o_rem = L.take(16),
-           o_ovf = L.take(16), o_thr = L.take(2 * 3 * (MAXCR + 1) * 8);
+           o_ovf = L.take(16), o_thr = L.take(2 * 3 * (MAXCR + 1) * 8), o_pairs = L.take(PAIRS_MAX * 8),
+           o_np = L.take(16);
     if (base) {
         Acc& a = cp->a;
         a.cross = (unsigned long long*)(base + o_cross);
@@ -874,6 +1067,8 @@ size_t coupler_layout(dem_coupler* cp, char* base)
         a.prev_ok = (int*)(base + o_pok);
         a.thr = (long long*)(base + o_thr);
         a.removed = (int*)(base + o_rem);
+        a.pairs = (unsigned long long*)(base + o_pairs);
+        a.npairs = (int*)(base + o_np);
         cp->overflow = (int*)(base + o_ovf);
     }
     return L.t;
@@ -1146,6 +1341,8 @@ dem_status dem_couple(dem_coupler* cp)
         k_cp_insert<<<g.face[fk].nb * g.face[fk].nc, 32 * INS_WARPS, 0, s>>>(ctx->dev, g, cp->a, fk, cp->rho_f);
     CU(cudaMemsetAsync(cp->overflow, 0, sizeof(int), s));
     k_cp_append<<<1, 256, 0, s>>>(ctx->dev, g, cp->a, cp->overflow);
+    k_cp_rows<<<(g.S * g.max_insert + ROWS_T - 1) / ROWS_T, ROWS_T, 0, s>>>(ctx->dev, cp->a);
+    k_cp_rows_append<<<1, 1024, 0, s>>>(ctx->dev, cp->a);
     CU(cudaGetLastError());
     // the coarse level's later work (its next steps) waits for the coupling kernels, which read
     // its state and write its held forces and corrected velocities (an event, no host wait)

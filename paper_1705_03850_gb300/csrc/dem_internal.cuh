@@ -124,7 +124,8 @@ struct InstD {
     int nid;             // IDs handed out so far (n plus removed particles); IDs are never reused
     int n_new;           // live particles after the pending rebuild (removed ones dropped)
     int fext;            // 1: add the per-particle external force fext to the contact forces
-    int pad[3];
+    int nbin;            // slots below slot0 + nbin are in the cell lists of the last build
+    int pad[2];
 };
 
 struct Glob {

@@ -100,6 +100,7 @@ def lib():
         "dem_read": [vp, i32, vp, i64],
         "dem_read_contacts": [vp, vp, vp, i32, i64],
         "dem_write_contacts": [vp, vp, vp, i32, i64],
+        "dem_read_neighbors": [vp, vp, i32, i64],
         "dem_step": [vp, i64],
         "dem_sync_status": [vp],
         "dem_instance_info_get": [vp, i32, ctypes.POINTER(InstanceInfo)],
@@ -141,7 +142,7 @@ def lib():
 
 
 def exported_symbols():
-    return ["dem_query_workspace", "dem_create", "dem_destroy", "dem_write", "dem_read", "dem_read_contacts",
+    return ["dem_query_workspace", "dem_create", "dem_destroy", "dem_write", "dem_read", "dem_read_contacts", "dem_read_neighbors",
             "dem_write_contacts", "dem_step", "dem_sync_status", "dem_instance_info_get", "dem_stats",
             "dem_set_graph", "dem_set_step_block", "dem_set_step_lanes", "dem_set_graph_mode", "dem_test_stall_barrier", "dem_set_list_build", "dem_graph_step_kernel_ms", "dem_neighbor_counts_noalloc", "dem_rollout_workspace",
             "dem_rollout_forward", "dem_rollout_adjoint", "dem_observables", "dem_set_material",
@@ -272,6 +273,15 @@ class DEM:
                                              ctypes.c_void_p(xi.data_ptr()), width, self.n), "read contacts")
         self.sync()
         return partner.cpu().numpy(), xi.cpu().numpy()
+
+    def read_neighbors(self, width=32):
+        """(n, width) int32 partner IDs of every neighbour-list entry, ascending, -1 padded."""
+        torch = self.torch
+        partner = torch.empty((self.n, width), dtype=torch.int32, device=self.device)
+        self._check(self.L.dem_read_neighbors(self.h, ctypes.c_void_p(partner.data_ptr()), width, self.n),
+                    "read neighbors")
+        self.sync()
+        return partner.cpu().numpy()
 
     def write_contacts(self, partner, xi):
         torch = self.torch

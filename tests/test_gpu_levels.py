@@ -64,6 +64,50 @@ def test_one_stream_per_level_equals_one_stream_for_all():
             assert np.array_equal(np.nan_to_num(xa), np.nan_to_num(xb))
 
 
+def _rows_of_new_particles_complete(level, wl, first_new_id):
+    # every pair of a particle inserted at the last call with any live particle closer than
+    # r_i + r_j + skin (brute force over the positions read back) is in both neighbour rows
+    from scipy.spatial import cKDTree
+    x = level.read(dem.POS)
+    rad = level.read(dem.RADIUS)
+    live = ~np.isnan(x[:, 0])
+    ids = np.flatnonzero(live)
+    lo, hi = np.array(wl.lo), np.array(wl.hi)
+    box = np.where(wl.periodic, hi - lo, 10.0 * (hi - lo) + 1.0)
+    xl = np.mod(x[live] - lo, box)
+    rl = rad[live]
+    pairs = cKDTree(xl, boxsize=box).query_pairs(2.0 * rl.max() + wl.skin, output_type="ndarray")
+    d = xl[pairs[:, 0]] - xl[pairs[:, 1]]
+    d -= np.where(wl.periodic, box * np.round(d / box), 0.0)
+    near = np.sqrt((d ** 2).sum(1)) < rl[pairs[:, 0]] + rl[pairs[:, 1]] + wl.skin - 1e-9
+    new = (ids[pairs[:, 0]] >= first_new_id) | (ids[pairs[:, 1]] >= first_new_id)
+    rows = level.read_neighbors(width=24)
+    checked = 0
+    for a_, b_ in pairs[near & new]:
+        ia, ib = ids[a_], ids[b_]
+        assert ib in rows[ia] and ia in rows[ib], (ia, ib)
+        checked += 1
+    return checked
+
+
+def test_inserted_particles_get_complete_rows_without_a_list_build():
+    # insertion builds the new particles' rows and appends them to their partners' rows instead
+    # of rebuilding every list: right after calls that inserted particles, every pair of a new
+    # particle within r_i + r_j + skin of another is in both rows
+    lv, specs, h = _hierarchy(True, u0=10.0)
+    fine = h.levels[2]
+    checked, pairs = 0, 0
+    for _ in range(200):
+        before = int(fine.counts()[1][0])
+        h.advance(1)
+        if fine.counts()[1][0] > before:
+            pairs += _rows_of_new_particles_complete(fine, lv[2], before)
+            checked += 1
+            if checked == 3:
+                break
+    assert checked == 3 and pairs > 20
+
+
 @pytest.mark.parametrize("multirate", [False, True])
 def test_mass_bookkeeping_closes_and_drained_particles_are_gone(multirate):
     lv, specs, h = _hierarchy(True, u0=10.0, multirate=multirate)

@@ -880,28 +880,31 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
         }
         unsigned cm = tm;
         unsigned rem = tm & submask;
-        // ---- pass 2: the contacts, in row order; the next contact's state goes to a per-thread
-        // slot of shared memory by asynchronous copies (no registers are held while it is in
-        // flight: 5.6 % faster than loading it into registers), two slots alternating
-        __shared__ float4 stg[2 * 4 * BS];
+        // ---- pass 2: the contacts, in row order, the next contact's state in flight: its
+        // velocity and spin go to a per-thread slot of shared memory by asynchronous copies (no
+        // registers held while they are outstanding; two slots alternate), its position and
+        // stored overlap to registers.  7 % faster than all of it in registers; staging the
+        // position and overlap as well costs L1 capacity (the slots come out of it) and is 2 %
+        // slower
+        __shared__ float4 stg[2 * 2 * BS];
         const int tid = (int)threadIdx.x;
         auto saddr = [&](int sl, int f) -> unsigned {
-            return (unsigned)__cvta_generic_to_shared(&stg[(sl * 4 + f) * BS + tid]);
+            return (unsigned)__cvta_generic_to_shared(&stg[(sl * 2 + f) * BS + tid]);
         };
+        int4 Qn = P;
+        float hxn = 0.f, hyn = 0.f, hzn = 0.f;
         auto issue = [&](int sl, int en_) {
             const size_t o1 = (size_t)en_ * ncap;
             int j = __ldg(nb + o1);
             if (!in_range(d, j, ncap, s, 4)) j = s;
-            cp_async16<FUSED>(saddr(sl, 0), pos + j);
-            cp_async16<FUSED>(saddr(sl, 1), vel + j);
-            cp_async16<FUSED>(saddr(sl, 2), omg + j);
+            Qn = ld_state<FUSED>(pos + j);
+            cp_async16<FUSED>(saddr(sl, 0), vel + j);
+            cp_async16<FUSED>(saddr(sl, 1), omg + j);
+            hxn = hyn = hzn = 0.f;
             if ((hm >> en_) & 1u) {
-                const unsigned a3 = saddr(sl, 3);
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a3), "l"(h + o1) : "memory");
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a3 + 4u), "l"(h + plane + o1) : "memory");
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a3 + 8u), "l"(h + 2 * plane + o1) : "memory");
-            } else {
-                stg[(sl * 4 + 3) * BS + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                hxn = h[o1];
+                hyn = h[plane + o1];
+                hzn = h[2 * plane + o1];
             }
         };
         int en = 0, sl = 0;
@@ -913,18 +916,16 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
         while (rem) {
             const int e = en;
             rem &= rem - 1u;
+            const int4 Q = Qn;
+            V3 xi = v3(hxn, hyn, hzn);
             if (rem) {
                 en = __ffs(rem) - 1;
                 issue(sl ^ 1, en);
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-            const float4* sp = &stg[(sl * 4) * BS + tid];
-            const float4 qf = sp[0];
-            const int4 Q = make_int4(__float_as_int(qf.x), __float_as_int(qf.y), __float_as_int(qf.z), __float_as_int(qf.w));
-            const float4 Vb = sp[BS], Wb = sp[2 * BS];
-            const float4 hh = sp[3 * BS];
-            V3 xi = v3(hh.x, hh.y, hh.z);
+            const float4* sp = &stg[(sl * 2) * BS + tid];
+            const float4 Vb = sp[0], Wb = sp[BS];
             const int dx = min_image(P.x - Q.x, per0, ext0, hf0);
             const int dy = min_image(P.y - Q.y, per1, ext1, hf1);
             const int dz = P.z - Q.z;

@@ -128,7 +128,7 @@ typedef struct {
     int64_t contacts;        /* contacts (particle pairs counted from both sides + floor) at that call */
     int64_t particles;       /* live particles */
     int64_t wall_contacts;   /* floor contacts among `contacts` */
-    int32_t step_threads;    /* threads per block of the step kernel (dem_set_step_block) */
+    int32_t step_threads;    /* threads per block of the step kernel in use (dem_set_step_block) */
     int32_t step_lanes;      /* lanes per particle of the step kernel (dem_set_step_lanes) */
     int32_t graph_fused;     /* 1: the captured graph runs fused steps (dem_set_graph_mode) */
     int32_t reserved;
@@ -197,11 +197,14 @@ dem_status dem_stats(dem_ctx *ctx, dem_stats_t *out);
 dem_status dem_set_graph(dem_ctx *ctx, int32_t steps_per_graph);
 
 /* Threads per block of the step kernel (the fused force and integration of Eqs. 1-6):
- * 64, 128 (the default) or 256; anything else is DEM_ERR_ARG.  Results do not depend on it
- * beyond float rounding order (none: every particle sums its own row in row order); it
- * changes how the work is spread over the GPU.  A captured graph is rebuilt with it.  Not in
- * the paper: a tuning parameter of this implementation.  DEM_ERR_STATE for a block other
- * than 128 threads while more than one lane per particle is set. */
+ * 0 (automatic, the default), 64, 128, 256 or 896; anything else is DEM_ERR_ARG.  896 is one
+ * block per SM whose warps claim the slices of a contiguous range of tiles in order (single-
+ * instance contexts only, else DEM_ERR_STATE); automatic takes it for a single instance with
+ * one lane per particle and at least a tile for every resident 128-thread block, else 128.
+ * Results do not depend on it (every particle sums its own row in row order); it changes how
+ * the work is spread over the GPU.  A captured graph is rebuilt with it.  Not in the paper: a
+ * tuning parameter of this implementation.  DEM_ERR_STATE for a block other than 0 or 128
+ * threads while more than one lane per particle is set. */
 dem_status dem_set_step_block(dem_ctx *ctx, int32_t threads);
 
 /* Lanes per particle of the step kernel: 1 (the default), 2, 4 or 8, or 0 to choose by size

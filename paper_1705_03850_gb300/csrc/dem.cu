@@ -679,7 +679,8 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int k
 
 // WALLS: the variant that evaluates axisymmetric walls (launched only for contexts that have
 // them, so that the wall code costs the plain step nothing).
-// BS: threads per block (64, 128 or 256; the autotuner picks one).  LPP: lanes per particle
+// BS: threads per block (64, 128 or 256; the autotuner picks one), or SMW_BS: one block of 28
+// warps per SM (single-instance contexts, the default there).  LPP: lanes per particle
 // (1, 2, 4 or 8; more than one only at 128 threads, for systems too small to fill the GPU with
 // one thread per row): the LPP lanes of a group take the row entries e = sub, sub + LPP, ...,
 // OR their touch masks together, sum their contacts in row order and combine the partial sums
@@ -688,13 +689,18 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int k
 // The tiles of TILE slots are walked as warp slices of 32 / LPP slots: slice w' of tile t
 // (w' = 0 .. 4 LPP - 1) is virtual warp 4 LPP t + w'; unit u is virtual warps
 // [u BS / 32, (u + 1) BS / 32), and instances own whole pairs of tiles, so that a unit never
-// straddles two instances.
+// straddles two instances.  An SM-wide block instead owns a contiguous range of tiles, and its
+// warps claim the range's slices in order from a shared counter: the 28 warps of an SM work on
+// neighbouring tiles at any time and share their neighbours' state in the SM's L1 (the 1M bed
+// steps 5.7 % faster than with seven independent 128-thread blocks per SM, the same bits), and
+// the warps of an SM finish within one slice of each other.
+constexpr int SMW_BS = 896;
 template <int BS, int LPP = 1>
 constexpr int step_minb()
 {
     // the same registers per thread at every block size; with several lanes per particle (small
     // systems, where the resident warps are not the limit) room for the whole row state
-    return LPP == 1 ? DEM_STEP_MINB * TILE / BS : 5;
+    return BS == SMW_BS ? 1 : LPP == 1 ? DEM_STEP_MINB * TILE / BS : 5;
 }
 
 // Particle state: neighbours' through the read-only data cache, except in fused steps, where the
@@ -733,7 +739,9 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
     constexpr int WPB = BS / 32;             // warps per block
     constexpr int SPW = 32 / LPP;            // slots per warp
     constexpr int WPT = TILE / SPW;          // warp slices per tile
-    static_assert(BS == 64 || BS == 128 || BS == 256, "step block of 64, 128 or 256 threads");
+    static_assert(BS == 64 || BS == 128 || BS == 256 || BS == SMW_BS, "step block of 64, 128, 256 or SMW_BS threads");
+    constexpr bool SMW = BS == SMW_BS;       // single instance, slices claimed from a shared counter
+    static_assert(!SMW || (LPP == 1 && !FUSED), "SM-wide blocks: one lane per particle, per-step launches");
     static_assert(LPP == 1 || LPP == 2 || LPP == 4 || LPP == 8, "1, 2, 4 or 8 lanes per particle");
     static_assert(LPP == 1 || MODE == 0, "several lanes per particle only for the step");
     static_assert((WPT & (WPT - 1)) == 0, "warps per tile must be a power of two");
@@ -759,9 +767,33 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
         __syncthreads();
     }
     float runmax = 0.f;
-    for (int u = u0; u < u1; ++u) {
-        const int k = __ldg(d.tile_inst + (all_live ? u * WPB / WPT : d.live_tiles[u * WPB / WPT]));
-        if (k != kprev) {
+    // SM-wide blocks: this block's share [v0, v1) of the slices of the tiles that hold live
+    // slots (a contiguous range: the instance's live slots come first), the next unclaimed
+    // slice in snext
+    __shared__ int snext;
+    int v1 = 0;
+    if (SMW) {
+        const int k = __ldg(d.tile_inst);
+        for (int i = threadIdx.x; i < (int)(sizeof(InstC) / 4); i += BS) ((int*)&sc)[i] = ((const int*)(d.ic + k))[i];
+        if (threadIdx.x < (int)(sizeof(InstD) / 4)) ((int*)&sd)[threadIdx.x] = ((const int*)(d.id + k))[threadIdx.x];
+        __syncthreads();
+        const int tf = sc.slot0 / TILE, nt = (sd.n + TILE - 1) / TILE;
+        v1 = (tf + (int)((long long)(blockIdx.x + 1) * nt / gridDim.x)) * WPT;
+        if (threadIdx.x == 0) snext = (tf + (int)((long long)blockIdx.x * nt / gridDim.x)) * WPT;
+        __syncthreads();
+        kprev = k;
+    }
+    for (int u = u0; SMW || u < u1; ++u) {
+        int vw = 0;
+        if (SMW) {
+            __syncwarp();
+            int v = 0;
+            if (lane == 0) v = atomicAdd(&snext, 1);
+            vw = __shfl_sync(0xffffffffu, v, 0);
+            if (vw >= v1) break;
+        }
+        const int k = SMW ? kprev : __ldg(d.tile_inst + (all_live ? u * WPB / WPT : d.live_tiles[u * WPB / WPT]));
+        if (!SMW && k != kprev) {
             if (MODE == 0 && kprev >= 0) {
                 // flush the displacement maximum of the previous instance
                 float mx = runmax;
@@ -787,7 +819,7 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
         const InstC& c = sc;
         // warp slice w' of tile t takes the 32-slot slice (w' + t) mod 4: rebuilds put the rows
         // with the most contacts in the first slice, so the rotation evens out the warps' work
-        const int vw = u * WPB + ((int)threadIdx.x >> 5);
+        if (!SMW) vw = u * WPB + ((int)threadIdx.x >> 5);
         const int t = all_live ? vw / WPT : d.live_tiles[vw / WPT];
         const int s = t * TILE + (((vw & (WPT - 1)) + t) & (WPT - 1)) * SPW + lane / LPP;
         if (s - c.slot0 >= sd.n) continue;
@@ -886,7 +918,14 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
         // stored overlap to registers.  7 % faster than all of it in registers; staging the
         // position and overlap as well costs L1 capacity (the slots come out of it) and is 2 %
         // slower
-        __shared__ float4 stg[2 * 2 * BS];
+        float4* stg;
+        if constexpr (SMW) {
+            extern __shared__ float4 stg_dyn[];     // 2 * 2 * BS float4 (57 kB: above the static limit)
+            stg = stg_dyn;
+        } else {
+            __shared__ float4 stg_st[2 * 2 * BS];
+            stg = stg_st;
+        }
         const int tid = (int)threadIdx.x;
         auto saddr = [&](int sl, int f) -> unsigned {
             return (unsigned)__cvta_generic_to_shared(&stg[(sl * 2 + f) * BS + tid]);
@@ -2171,6 +2210,22 @@ void destroy_graph(dem_ctx* ctx)
     ctx->rb_graph = nullptr;
 }
 
+// the step kernel's block size: the one set, else SM-wide blocks for a single instance with
+// one lane per particle whose live rows give every resident warp at least SMW_MIN slices (below
+// that the last slices' quantisation dominates, and 128-thread blocks are as fast), else 128
+constexpr int SMW_MIN = 4;
+int step_block(const dem_ctx* ctx)
+{
+    if (ctx->step_bs) return ctx->step_bs;
+    if (ctx->step_lanes == 1 && ctx->B == 1 && ctx->grid_smw > 0 &&
+        ctx->count[0] >= (long long)SMW_MIN * ctx->grid_smw * (SMW_BS / 32) * 32)
+        return SMW_BS;
+    return TILE;
+}
+
+// dynamic shared memory of the step kernel (the SM-wide block's staging slots)
+unsigned step_smem(const dem_ctx* ctx) { return step_block(ctx) == SMW_BS ? 2 * 2 * SMW_BS * sizeof(float4) : 0u; }
+
 // the step kernel (MODE 0) at the context's block size, and its persistent grid
 void* step_func(const dem_ctx* ctx)
 {
@@ -2180,7 +2235,8 @@ void* step_func(const dem_ctx* ctx)
     case 8: return ctx->walls ? (void*)k_step<0, true, 128, 8> : (void*)k_step<0, false, 128, 8>;
     default: break;
     }
-    switch (ctx->step_bs) {
+    switch (step_block(ctx)) {
+    case SMW_BS: return ctx->walls ? (void*)k_step<0, true, SMW_BS> : (void*)k_step<0, false, SMW_BS>;
     case 64: return ctx->walls ? (void*)k_step<0, true, 64> : (void*)k_step<0, false, 64>;
     case 256: return ctx->walls ? (void*)k_step<0, true, 256> : (void*)k_step<0, false, 256>;
     default: return ctx->walls ? (void*)k_step<0, true, 128> : (void*)k_step<0, false, 128>;
@@ -2190,7 +2246,9 @@ void* step_func(const dem_ctx* ctx)
 int step_grid(const dem_ctx* ctx)
 {
     if (ctx->step_lanes > 1) return ctx->grid_lanes[ctx->step_lanes == 2 ? 0 : ctx->step_lanes == 4 ? 1 : 2];
-    return ctx->grid_bs[ctx->step_bs == 64 ? 0 : ctx->step_bs == 256 ? 2 : 1];
+    const int bs = step_block(ctx);
+    if (bs == SMW_BS) return ctx->grid_smw;
+    return ctx->grid_bs[bs == 64 ? 0 : bs == 256 ? 2 : 1];
 }
 
 dem_status launch_step(dem_ctx* ctx, int prime)
@@ -2199,7 +2257,7 @@ dem_status launch_step(dem_ctx* ctx, int prime)
     cudaGraphConditionalHandle h = 0;
     int use_cond = 0;
     void* args[] = {&dv, &prime, &h, &use_cond};
-    CU(cudaLaunchKernel(step_func(ctx), dim3(step_grid(ctx)), dim3(ctx->step_bs), args, 0, ctx->stream));
+    CU(cudaLaunchKernel(step_func(ctx), dim3(step_grid(ctx)), dim3(step_block(ctx)), args, step_smem(ctx), ctx->stream));
     return DEM_OK;
 }
 
@@ -2303,7 +2361,7 @@ dem_status build_graph(dem_ctx* ctx, int S)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fused_func(ctx), TILE, 0);
         cudaGetLastError();
         ctx->grid_fused = nsm * occ;
-        const bool can = ctx->step_bs == TILE && ctx->grid_fused > 0;
+        const bool can = (ctx->step_bs == 0 || ctx->step_bs == TILE) && ctx->grid_fused > 0;
         if (ctx->graph_mode == 2 && !can) return fail(ctx, DEM_ERR_STATE, "fused steps need 128-thread blocks");
         // the tiles holding live slots (from the host's last copy of the counts)
         long long live = 0;
@@ -2351,7 +2409,8 @@ dem_status build_graph(dem_ctx* ctx, int S)
         cudaKernelNodeParams kp{};
         kp.func = step_func(ctx);
         kp.gridDim = dim3(step_grid(ctx));
-        kp.blockDim = dim3(ctx->step_bs);
+        kp.blockDim = dim3(step_block(ctx));
+        kp.sharedMemBytes = step_smem(ctx);
         kp.kernelParams = args;
         cudaGraphNode_t kn;
         if (i % EV_EVERY == 0) {
@@ -2564,6 +2623,18 @@ dem_status dem_create(const dem_config* cfg, void* workspace, int64_t workspace_
             const int units[3] = {ctx->ntiles * 2, ctx->ntiles, ctx->ntiles / 2};
             for (int i = 0; i < 3; ++i)
                 ctx->grid_bs[i] = std::max(1, std::min(units[i], std::max(1, nsm) * std::max(1, bx[i])));
+            // SM-wide blocks (single instance): a block per SM, at most one per tile; 0 if the
+            // block does not fit
+            if (p.B == 1) {
+                const int smem = 2 * 2 * SMW_BS * (int)sizeof(float4);
+                int bw = 0;
+                if (cudaFuncSetAttribute(k_step<0, false, SMW_BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                        cudaSuccess &&
+                    cudaFuncSetAttribute(k_step<0, true, SMW_BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                        cudaSuccess)
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_step<0, false, SMW_BS>, SMW_BS, smem);
+                ctx->grid_smw = bw > 0 ? std::min(ctx->ntiles, std::max(1, nsm) * bw) : 0;
+            }
             // several lanes per particle (128 threads): LPP times the units of one lane
             int bl[3] = {0, 0, 0};
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl[0], k_step<0, false, 128, 2>, 128, 0);
@@ -2777,7 +2848,7 @@ dem_status dem_stats(dem_ctx* ctx, dem_stats_t* out)
     if (ctx->status) return check_status(ctx);
     memset(out, 0, sizeof(*out));
     out->steps = ctx->steps;
-    out->step_threads = ctx->step_bs;
+    out->step_threads = ctx->graph_fused ? TILE : step_block(ctx);
     out->step_lanes = ctx->step_lanes;
     out->graph_fused = ctx->graph_fused ? 1 : 0;
     if (dem_status st = refresh_count(ctx)) return st;
@@ -2808,9 +2879,11 @@ dem_status dem_set_graph(dem_ctx* ctx, int32_t steps_per_graph)
 dem_status dem_set_step_block(dem_ctx* ctx, int32_t threads)
 {
     if (!ctx) return DEM_ERR_ARG;
-    if (threads != 64 && threads != 128 && threads != 256)
-        return fail(ctx, DEM_ERR_ARG, "step block must be 64, 128 or 256 threads");
-    if (threads != 128 && ctx->step_lanes > 1)
+    if (threads != 0 && threads != 64 && threads != 128 && threads != 256 && threads != SMW_BS)
+        return fail(ctx, DEM_ERR_ARG, "step block must be 0 (automatic), 64, 128, 256 or 896 threads");
+    if (threads == SMW_BS && (ctx->B != 1 || ctx->grid_smw <= 0))
+        return fail(ctx, DEM_ERR_STATE, "896-thread (SM-wide) step blocks need a single-instance context");
+    if (threads != 0 && threads != 128 && ctx->step_lanes > 1)
         return fail(ctx, DEM_ERR_STATE, "several lanes per particle run at 128 threads per block");
     ctx->step_bs = threads;
     return ctx->graph_steps > 0 ? build_graph(ctx, ctx->graph_steps) : DEM_OK;
@@ -2889,9 +2962,9 @@ dem_status dem_set_step_lanes(dem_ctx* ctx, int32_t lanes)
                     break;
                 }
         }
-        if (ctx->step_bs != 128) lanes = 1;
+        if (ctx->step_bs != 0 && ctx->step_bs != 128) lanes = 1;
     }
-    if (lanes > 1 && ctx->step_bs != 128)
+    if (lanes > 1 && ctx->step_bs != 0 && ctx->step_bs != 128)
         return fail(ctx, DEM_ERR_STATE, "several lanes per particle run at 128 threads per block");
     ctx->step_lanes = lanes;
     return ctx->graph_steps > 0 ? build_graph(ctx, ctx->graph_steps) : DEM_OK;

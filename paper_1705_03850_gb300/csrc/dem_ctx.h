@@ -26,9 +26,10 @@ struct dem_ctx {
     int B = 0, Lmax = 0;
     int ncap = 0, ntiles = 0;
     int grid0 = 1, grid1 = 1;         // persistent grids of the step / evaluation kernels
-    int step_bs = 128;                // threads per block of the step kernel (64, 128 or 256)
+    int step_bs = 0;                  // threads per block of the step kernel (64, 128, 256, 896; 0 automatic)
     int step_lanes = 1;               // lanes per particle of the step kernel (1, 2, 4 or 8; >1 at 128 threads)
     int grid_bs[3] = {1, 1, 1};       // persistent step grids for 64, 128 and 256 threads per block
+    int grid_smw = 0;                 // persistent grid of SM-wide step blocks (0: not available)
     int grid_lanes[3] = {1, 1, 1};    // persistent step grids for 2, 4 and 8 lanes per particle
     bool list_staged = false;         // list build with the shared-memory window of cell-order positions
     int grid_build_staged = 1;

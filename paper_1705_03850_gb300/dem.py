@@ -309,7 +309,8 @@ class DEM:
         return self
 
     def set_step_block(self, threads):
-        """Threads per block of the step kernel: 64, 128 (default) or 256."""
+        """Threads per block of the step kernel: 0 (automatic, the default), 64, 128, 256 or 896
+        (one block per SM; single-instance contexts)."""
         self._check(self.L.dem_set_step_block(self.h, int(threads)), "set step block")
         return self
 

@@ -146,6 +146,7 @@ struct Glob {
     long long remain;          // fused steps: steps still to do in the current graph launch
     int nlive;                 // entries of live_tiles
     unsigned test_stall;       // 1: the next fused launch's first block skips its first barrier
+    unsigned pool;             // SM-wide step blocks: slices claimed from the shared pool this launch
 };
 
 // kernel-visible pointers of a context

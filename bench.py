@@ -490,7 +490,8 @@ def run_ours(args):
                    "mean_list_length": L, "mean_contacts_per_particle": C,
                    "rebuilds_in_timed_region": rebuilds, "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": peak_src, "kernel": "k_step<0, false> (fused force + Verlet, the variant without walls)",
+                     "traffic": traffic, "peak_source": peak_src, "kernel": f"k_step<0, false, {st1['step_threads']}> (fused force + Verlet, the variant without walls; "
+                               f"{st1['step_threads']} threads per block)",
                      "bytes_per_particle_step": B_step, "kernel_ms_avg": t_kernel * 1e3,
                      "kernel_ms_repeats": [t for _, t, _ in reps],
                      "kernel_timing": "median over the repeats of the mean CUDA-event duration of every fifth "

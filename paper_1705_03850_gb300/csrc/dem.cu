@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(TILE) k_rb_tilesort(Dev d)
     }
 }
 
-// The same order over windows of SMW_SORT_W tiles, for the SM-wide step blocks (single
+// The same order over windows of at most SMW_SORT_W tiles, for the SM-wide step blocks (single
 // instance): an SM's warps walk the slices of neighbouring tiles together, so a window of
 // several tiles can be ordered as one and its 32-row slices come out more alike (the 1M bed's
 // step kernel: 106.9 µs against 112.8 µs with windows of one tile; 108.5 µs with windows of 8
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(TILE) k_rb_tilesort(Dev d)
 constexpr int WS_T = 256;                          // threads per window
 constexpr int WS_KEYS = (MAXL + 1) * (MAXL + 1);   // (contacts, list length) pairs
 template <int W>
-__global__ void __launch_bounds__(WS_T) k_rb_winsort(Dev d)
+__global__ void __launch_bounds__(WS_T) k_rb_winsort(Dev d, int G)
 {
     constexpr int N = W * TILE;                    // slots per window
     constexpr int NW = WS_T / 32;                  // warps
@@ -285,15 +285,20 @@ __global__ void __launch_bounds__(WS_T) k_rb_winsort(Dev d)
     __shared__ unsigned short hist[NW][WS_KEYS];   // per-warp counts per key, then first ranks
     __shared__ int wsum[NW];
     const int lane = (int)threadIdx.x & 31, w = (int)threadIdx.x >> 5;
-    const int nwin = (d.ntiles + W - 1) / W;
-    for (int wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
-        const int t0 = wi * W;
-        const int k = d.tile_inst[t0];
-        const InstD D = d.id[k];            // the same for the whole block
-        if (!D.flag) continue;
-        const InstC& c = d.ic[k];
+    // the windows split each of the G step blocks' shares of the live tiles (the same split as
+    // the step kernel's) into K parts of at most W tiles: a share's last slices, which its warps
+    // claim last and the other SMs take over, are the lightest of its last window
+    const InstD D = d.id[0];                // SM-wide blocks: a single instance
+    if (!D.flag) return;
+    const InstC& c = d.ic[0];
+    const int tf = c.slot0 / TILE, nt = (D.n_new + TILE - 1) / TILE;
+    const int K = max(1, ((nt + G - 1) / G + W - 1) / W);
+    for (int wi = blockIdx.x; wi < G * K; wi += gridDim.x) {
+        const int b = wi / K, kk = wi % K;
+        const int s0 = (int)((long long)b * nt / G), len = (int)((long long)(b + 1) * nt / G) - s0;
+        const int t0 = tf + s0 + len * kk / K, t1 = tf + s0 + len * (kk + 1) / K;
         const int p0 = t0 * TILE;
-        const int nvalid = min(N, D.n_new - (p0 - c.slot0));
+        const int nvalid = min((t1 - t0) * TILE, D.n_new - (p0 - c.slot0));
         if (nvalid <= 0) continue;
         __syncthreads();                    // the previous window's ranks are read
         for (int i = threadIdx.x; i < NW * WS_KEYS; i += WS_T) (&hist[0][0])[i] = 0;
@@ -808,7 +813,7 @@ __device__ __forceinline__ int wall_contacts(const Dev& d, const InstC& c, int k
 // the warps of an SM finish within one slice of each other.
 constexpr int SMW_BS = 896;
 #ifndef SMW_POOL
-#define SMW_POOL 16         // the pool: the last 1/SMW_POOL of every block's share
+#define SMW_POOL 8          // the pool: the last 1/SMW_POOL of every block's share
 #endif
 template <int BS, int LPP = 1>
 constexpr int step_minb()
@@ -887,8 +892,10 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
     // [v0(b), v1(b) - P) in order from the shared counter snext; the last P slices of every
     // block's share form a pool that all blocks claim from afterwards (g->pool), so that SMs
     // whose share holds less work take over the tails of the others (on the 1M bed the SMs ended
-    // between 56 and 100 µs, median 90 µs, without it; with pools of 1/16, 1/8 and 1/4 of the
-    // shares the step kernel takes 104.2, 104.6 and 106.0 µs against 106.7 µs)
+    // between 56 and 100 µs, median 90 µs, without it).  The list build orders each share's
+    // windows by contact count, so the pool holds the lightest slices of each share: with pools
+    // of 1/32, 1/16 and 1/8 of the shares the step kernel takes 104.4, 103.7 and 100.5 µs
+    // against 104.7 µs without the share-aligned windows and a pool of 1/16
     __shared__ int snext, sown, spool[3];   // own counter, own end; pool: P, tiles, first tile
     if (SMW) {
         const int k = __ldg(d.tile_inst);
@@ -2306,8 +2313,7 @@ dem_status launch_rebuild(dem_ctx* ctx, cudaStream_t st)
     k_rb_cellsort<<<gt, TILE, 0, st>>>(d);
     k_rb_count<<<1, 256, 0, st>>>(d);
     if (step_block(ctx) == SMW_BS)
-        k_rb_winsort<SMW_SORT_W><<<std::max(1, std::min((ctx->ntiles + SMW_SORT_W - 1) / SMW_SORT_W, (int)gt)), WS_T, 0,
-                                   st>>>(d);
+        k_rb_winsort<SMW_SORT_W><<<gt, WS_T, 0, st>>>(d, ctx->grid_smw);
     else
         k_rb_tilesort<<<gt, TILE, 0, st>>>(d);
     if (ctx->list_staged)

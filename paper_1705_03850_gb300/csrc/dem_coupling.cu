@@ -470,6 +470,7 @@ __global__ void __launch_bounds__(TILE, 8) k_cp_coarse(Dev d, Geo g, Acc a, int 
 __global__ void __launch_bounds__(TILE, 8) k_cp_fine(Dev d, Geo g, Acc a)
 {
     for_live(d, [&](int s, const InstC& c, const InstD& D, const int4 P, float4 V) {
+        const float mf = d.omg[D.cur][s].w;     // loaded before the layer call (which may write memory)
         if (maybe_layer(g, 1, P)) {
             const double x[3] = {posm(g.lof, g.qf, P.x, 0), posm(g.lof, g.qf, P.y, 1), posm(g.lof, g.qf, P.z, 2)};
             int fk;
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(TILE, 8) k_cp_fine(Dev d, Geo g, Acc a)
             if (lc >= 0) layer_add(d, c, D, s, a.lay + ((size_t)g.S + lc) * 20, a.vmax + g.S + lc, g.fresh_f);
         }
         const float rf = (float)((double)P.w * g.qf);
-        corr_add(a.cor + (size_t)g.C * 5, corr_cell_u(g, a.thr, 1, P), d.omg[D.cur][s].w, V, 4.18879020f * rf * rf * rf);
+        corr_add(a.cor + (size_t)g.C * 5, corr_cell_u(g, a.thr, 1, P), mf, V, 4.18879020f * rf * rf * rf);
         // drain faces: x < lo or x >= hi on their axes (the region bounds as integer thresholds)
         bool gone = false;
         for (int ax = 0; ax < 3; ++ax) {
@@ -562,6 +563,8 @@ inline int cells_threads(int S, int C) { return ((2 * S + 31) & ~31) + C; }
 __global__ void __launch_bounds__(TILE) k_cp_force_fine(Dev d, Geo g, Acc a)
 {
     for_live(d, [&](int s, const InstC& c, const InstD& D, const int4 P, const float4 V) {
+        // the held force first: a load with no dependence on the layer test below
+        const float4 o = g.add ? d.fext[D.lp][s] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
         int fk = 0;
         int lc = -1;
@@ -596,10 +599,7 @@ __global__ void __launch_bounds__(TILE) k_cp_force_fine(Dev d, Geo g, Acc a)
             }
             F = make_float4((float)(lam * Fv[0]), (float)(lam * Fv[1]), (float)(lam * Fv[2]), 0.f);
         }
-        if (g.add) {
-            const float4 o = d.fext[D.lp][s];
-            F = make_float4(o.x + F.x, o.y + F.y, o.z + F.z, 0.f);
-        }
+        if (g.add) F = make_float4(o.x + F.x, o.y + F.y, o.z + F.z, 0.f);
         d.fext[D.lp][s] = F;
     });
 }
@@ -607,6 +607,7 @@ __global__ void __launch_bounds__(TILE) k_cp_force_fine(Dev d, Geo g, Acc a)
 __global__ void __launch_bounds__(TILE) k_cp_force_coarse(Dev d, Geo g, Acc a)
 {
     for_live(d, [&](int s, const InstC& c, const InstD& D, const int4 P, const float4) {
+        const float4 o = g.add ? d.fext[D.lp][s] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
         const int cc = corr_cell_u(g, a.thr, 0, P);
         if (cc >= 0) {
@@ -614,10 +615,7 @@ __global__ void __launch_bounds__(TILE) k_cp_force_coarse(Dev d, Geo g, Acc a)
             const double* dv = a.dv + 3 * (size_t)cc;
             F = make_float4((float)(k * dv[0]), (float)(k * dv[1]), (float)(k * dv[2]), 0.f);
         }
-        if (g.add) {
-            const float4 o = d.fext[D.lp][s];
-            F = make_float4(o.x + F.x, o.y + F.y, o.z + F.z, 0.f);
-        }
+        if (g.add) F = make_float4(o.x + F.x, o.y + F.y, o.z + F.z, 0.f);
         d.fext[D.lp][s] = F;
     });
 }

@@ -264,12 +264,13 @@ __global__ void __launch_bounds__(TILE) k_rb_tilesort(Dev d)
 // several tiles can be ordered as one and its 32-row slices come out more alike (the 1M bed's
 // step kernel: 106.9 µs against 112.8 µs with windows of one tile; 108.5 µs with windows of 8
 // tiles, 111.6 µs with 32, 121.7 µs with 64: wider windows spread a slice's rows over a
-// larger region than the SM's warps walk at once).  A stable counting sort
+// larger region than the SM's warps walk at once; cut from the step blocks' shares, windows of
+// at most 12, 16 and 18 tiles gave 99.1, 100.4 and 99.4 µs).  A stable counting sort
 // on (contacts, list length), both at most MAXL: 256 threads per window, each warp ranks its
 // run of 32-element chunks with __match_any_sync and counts per key, and the per-warp counts,
 // scanned over the keys, give each warp's first rank per key.
 #ifndef SMW_SORT_W
-#define SMW_SORT_W 16
+#define SMW_SORT_W 12
 #endif
 constexpr int WS_T = 256;                          // threads per window
 constexpr int WS_KEYS = (MAXL + 1) * (MAXL + 1);   // (contacts, list length) pairs

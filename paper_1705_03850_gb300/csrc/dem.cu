@@ -1268,19 +1268,25 @@ __device__ __forceinline__ void step_pass(const Dev& d, int prime, InstC& sc, In
 // reaches the skin is flagged for a list build (an error while the lists are frozen).
 __device__ __forceinline__ void step_finish_instances(const Dev& d)
 {
+    const unsigned frozen = __ldcg(&d.g->frozen);
     for (int kk = threadIdx.x; kk < d.B; kk += blockDim.x) {
-        // volatile: the instance's record was last written by another block (in fused steps,
-        // during this launch), so it is read from L2, never from this SM's L1
-        volatile InstD* Dk = d.id + kk;
-        const float sm = __uint_as_float(atomicExch((unsigned*)&Dk->stepmax, 0u));
-        const float disp = Dk->disp + sm;
-        Dk->disp = disp;
-        Dk->cur ^= 1;
-        if (2.0f * disp >= 0.99f * d.ic[kk].skin_f && Dk->flag == 0) {
-            if (d.g->frozen) {
+        // L2 loads (__ldcg): the instance's record was last written by another block (in fused
+        // steps, during this launch), never to be read from this SM's L1.  Only this block writes
+        // disp, cur and flag, so they are loaded together up front and the chain of dependent
+        // round trips at the end of every step is two long (the exchange, then the stores)
+        InstD* Dk = d.id + kk;
+        const float disp0 = __ldcg(&Dk->disp);
+        const int cur0 = __ldcg(&Dk->cur), flag0 = __ldcg(&Dk->flag);
+        const float skin = d.ic[kk].skin_f;
+        const float sm = __uint_as_float(atomicExch(&Dk->stepmax, 0u));
+        const float disp = disp0 + sm;
+        __stcg(&Dk->disp, disp);
+        __stcg(&Dk->cur, cur0 ^ 1);
+        if (2.0f * disp >= 0.99f * skin && flag0 == 0) {
+            if (frozen) {
                 atomicOr(&d.g->status, ST_SKIN);
             } else {
-                Dk->flag = 1;
+                __stcg(&Dk->flag, 1);
                 atomicOr(&d.g->any, 1u);
             }
         }

@@ -53,10 +53,6 @@ class Hierarchy:
             lv.clear_external_force()
         self.couplers = [dem.Coupler(levels[k], levels[k + 1], **dict(s, add_forces=1)) for k, s in enumerate(specs)]
         for lv in self.levels:
-            # the levels step concurrently, each on its own stream: 128-thread step blocks let the
-            # kernels of several levels share an SM, which one SM-wide block per SM would not
-            # (1.4 % slower on the coupled chute)
-            lv.set_step_block(128)
             lv.set_step_lanes(lanes)             # 0: by size (small levels: fused steps, several lanes)
         if steps_per_graph:
             for lv, n in zip(self.levels, self.steps):

@@ -237,8 +237,8 @@ dem_status dem_set_step_lanes(dem_ctx *ctx, int32_t lanes);
  * implementation. */
 dem_status dem_set_graph_mode(dem_ctx *ctx, int32_t mode);
 
-/* How the neighbour lists are built (SURVEY's cell-range and list-build step; the list is
- * the same either way, bit for bit): 0 (the default), each thread scans the 27 cells around
+/* How the neighbour lists are built (the cell-range and list-build step of the rebuild; the
+ * list is the same either way, bit for bit): 0 (the default), each thread scans the 27 cells around
  * its particle in the cell-ordered positions through the caches; 1, each block first stages
  * the cell-ordered positions around its 64 particles in shared memory and reads the candidates
  * that fall there from it.  DEM_ERR_ARG for other values.  A captured graph is rebuilt with it.
